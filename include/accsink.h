@@ -1,0 +1,226 @@
+/*
+ * accsink.h -- C-ABI of the GB300 (sm_103a) Acc-Sinkhorn solver.
+ *
+ * Solves the entropy-regularised optimal transport problem of the paper
+ * "Accelerating Sinkhorn for Entropy-Regularized Optimal Transport"
+ * (Xu & Chen), Sec. 1 eq. (EOT):
+ *
+ *     min_{P in Pi(a,b)}  <C, P> + eps * sum_ij P_ij (log P_ij - 1),
+ *
+ * through its dual potentials (f, g) in cost units, P_ij = exp((f_i + g_j -
+ * C_ij) / eps) (Sec. 2, eq. P-from-dual with the cost divided by eps). Two
+ * methods share one data path:
+ *   ACCSINK_PLAIN  log-domain Sinkhorn, x_{k+1} = S(x_k) (Sec. 3, eq.
+ *                  normalized-sinkhorn), x = g / eps;
+ *   ACCSINK_ACC    Acc-Sinkhorn: Algorithm 1 inside the homotopy of
+ *                  Algorithm 2 (Sec. 4).
+ * One S evaluation is a row log-sum-exp pass and a column log-sum-exp pass
+ * over the cost (Sec. 2, u- and v-updates); everything else is O(n + m).
+ *
+ * Conventions for every entry point
+ *   - All functions return an accsink_status; no C++ exception crosses the
+ *     ABI. On failure accsink_last_error(ctx) describes the first problem.
+ *   - "device" pointers are CUDA device (or managed) memory on the context's
+ *     device; "host" pointers are ordinary host memory. Pointers are borrowed:
+ *     the library never frees caller memory and keeps no pointer after the
+ *     call returns (except inside the cached CUDA graph, which is rebuilt
+ *     whenever a call passes different pointers or sizes).
+ *   - Work is enqueued on the caller's `stream` (cudaStream_t passed as
+ *     void*; NULL = legacy default stream). Solve calls synchronise that
+ *     stream before they return, because they return results on the host.
+ *   - A context is not thread-safe; use one per host thread.
+ *   - Matrices are row-major FP32 with a row stride `ldc` (elements, >= m).
+ *     The vectorised kernels need ldc % 4 == 0 and a 16-byte aligned C;
+ *     other layouts take a scalar path with identical results.
+ */
+#ifndef ACCSINK_H
+#define ACCSINK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. ACCSINK_ERR_MAXITER is a soft outcome: the potentials are
+ * valid, the marginal error is just still above tol. */
+typedef enum {
+    ACCSINK_OK = 0,
+    ACCSINK_ERR_INVALID_ARG = 1,          /* bad size, pointer, eps, tol, ... */
+    ACCSINK_ERR_NONPOSITIVE_MARGINAL = 2, /* some a_i or b_j <= 0 (log a, log b are needed) */
+    ACCSINK_ERR_NONFINITE = 3,            /* NaN/Inf in C, a, b, or in the iterates */
+    ACCSINK_ERR_OOM = 4,                  /* device allocation failed */
+    ACCSINK_ERR_BUDGET = 5,               /* workspace would exceed the context's budget */
+    ACCSINK_ERR_TIMEOUT = 6,              /* a bounded device wait gave up */
+    ACCSINK_ERR_MAXITER = 7,              /* not converged within max_sinkhorn_steps */
+    ACCSINK_ERR_CUDA = 8,                 /* a CUDA runtime call failed */
+    ACCSINK_ERR_UNSUPPORTED = 9           /* valid request this build does not serve */
+} accsink_status;
+
+enum { ACCSINK_COST_DENSE = 0, ACCSINK_COST_SQEUCLID = 1, ACCSINK_COST_COSINE = 2 };
+enum { ACCSINK_SCALE_NONE = 0, ACCSINK_SCALE_MAX_TO_ONE = 1 };
+enum { ACCSINK_PLAIN = 0, ACCSINK_ACC = 1 };
+enum { ACCSINK_STAB_OFF = 0, ACCSINK_STAB_REPORT = 1, ACCSINK_STAB_GATE = 2 };
+enum { ACCSINK_CARRY_Y = 0, ACCSINK_CARRY_W = 1 };
+
+typedef struct accsink_ctx accsink_ctx;
+
+/* The problem (Sec. 1, eq. EOT). a and b must be positive; they are
+ * renormalised to unit mass in FP64 (Sec. 2 assumes 1'a = 1'b = 1).
+ * cost_scale = MAX_TO_ONE divides C by its largest entry first (Sec. 5,
+ * colour transfer); the returned potentials are then in units of the scaled
+ * cost. For ACCSINK_COST_DENSE only C is read; X and Y are for the point-
+ * cloud costs C_ij = ||x_i - y_j||^2 and C_ij = 1 - <x_i, y_j> (Sec. 5). */
+typedef struct {
+    int32_t n;           /* rows (support of a), >= 1                        */
+    int32_t m;           /* columns (support of b), >= 1                     */
+    int32_t d;           /* point dimension (point-cloud costs only)         */
+    int32_t cost_kind;   /* ACCSINK_COST_*                                   */
+    int64_t ldc;         /* row stride of C in elements; 0 means m           */
+    const float *C;      /* n x m cost, row-major, FP32                      */
+    const float *X;      /* n x d points, row-major, FP32                    */
+    const float *Y;      /* m x d points, row-major, FP32                    */
+    const double *a;     /* n row marginal, FP64                             */
+    const double *b;     /* m column marginal, FP64                          */
+    int32_t cost_scale;  /* ACCSINK_SCALE_*                                  */
+    int32_t reserved;
+} accsink_problem;
+
+/* Solver parameters. accsink_params_default() fills:
+ *   method ACC, eps 1e-2, tol 1e-6, mu0 0.25, m0 4, max_sinkhorn_steps
+ *   100000, stability REPORT, carry Y, evaluate 1, use_graph 1, history 0.
+ * mu0 in (0, 1), m0 >= 1 (Algorithm 2). tol is the l1 marginal tolerance of
+ * Sec. 5 eq. (l1tol). carry selects how a homotopy stage hands w to the next
+ * one: CARRY_Y keeps y = w / alpha (the state Theorem 1 follows), CARRY_W
+ * hands w over unchanged as Algorithm 2 is printed. stability: OFF skips the
+ * Theorem 4 test, REPORT counts failures, GATE also restarts the momentum
+ * (w <- alpha x) after a failed step. */
+typedef struct {
+    int32_t method;
+    int32_t m0;
+    double eps;
+    double tol;
+    double mu0;
+    int32_t max_sinkhorn_steps;
+    int32_t stability;
+    int32_t carry;
+    int32_t evaluate;    /* 1: one extra pass computes <C, P> at the end     */
+    int32_t use_graph;   /* 1: device-side loop in a CUDA graph; 0: host loop */
+    int32_t history;     /* keep per-step history for this many steps (0: no) */
+} accsink_params;
+
+/* Result of a solve (host struct, filled by the library). */
+typedef struct {
+    int32_t status;              /* accsink_status of the solve              */
+    int32_t sinkhorn_steps;      /* S evaluations = row+column pass pairs    */
+    int32_t outer_stages;        /* completed homotopy stages (Algorithm 2)  */
+    int32_t stability_failures;  /* steps where Theorem 4's test failed      */
+    double marginal_l1;          /* sum_j |c_j - b_j| at the returned iterate
+                                    (row error is zero by construction)      */
+    double transport_cost;       /* <C, P> (NaN unless params.evaluate)      */
+    double dual_objective;       /* <f,a> + <g,b> - eps (after the row pass) */
+    double cost_max;             /* max_ij C_ij of the input                 */
+    double gpu_ms;               /* device time of the solve (CUDA events)   */
+    int32_t loop_mode;           /* 1: CUDA-graph device loop ran; 0: host loop
+                                    (requested, or the graph could not be built) */
+    int32_t reserved;
+} accsink_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Creates a context on CUDA device `device`. mem_budget_bytes caps the
+ * workspace the context may allocate (0 = no cap). */
+int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes);
+void accsink_destroy(accsink_ctx *ctx);
+/* Message for the last failed call on this context ("" if none). The string
+ * is owned by the context and valid until its next call. */
+const char *accsink_last_error(const accsink_ctx *ctx);
+void accsink_params_default(accsink_params *p);
+/* Library version string, e.g. "accsink 1.0 sm_103a". */
+const char *accsink_version(void);
+
+/* ---- whole solves ------------------------------------------------------- */
+
+/* Solves the problem. All problem pointers are device pointers. f_out (n)
+ * and g_out (m) are caller-allocated device arrays that receive the
+ * potentials in cost units at the returned iterate; f is the row pass at
+ * that g, so the row marginal is exact up to rounding. res (host) receives
+ * the summary. Returns res->status (ACCSINK_ERR_MAXITER if not converged). */
+int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob,
+                  const accsink_params *params, void *stream,
+                  double *f_out, double *g_out, accsink_result *res);
+
+/* Same solve with every problem pointer and f_out/g_out in HOST memory:
+ * the library copies the inputs to its workspace, solves, and copies the
+ * potentials back, all on `stream`. Host buffers may be pageable or pinned
+ * (pinned copies are faster). */
+int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
+                       const accsink_params *params, void *stream,
+                       double *f_out_host, double *g_out_host,
+                       accsink_result *res);
+
+/* Per-step history of the last solve on this context, if params.history > 0:
+ * for evaluation e (0 = x_0) err[e] = marginal L1, dual[e] = dual objective,
+ * mu[e] = mu used to form that iterate (0 for x_0 and for PLAIN), stab[e] =
+ * bit0 Cond 1 failed, bit1 Cond 2 failed (Theorem 4), for the step that
+ * produced e. cond (4 per step, may be NULL) = Cond1 lhs, Cond1 rhs, Cond2
+ * lhs, Cond2 rhs. count = min(steps, capacity). Host arrays, caller-owned. */
+int accsink_get_history(accsink_ctx *ctx, int32_t capacity, double *err,
+                        double *dual, double *mu, int32_t *stab, double *cond,
+                        int32_t *count);
+
+/* ---- single passes (the hot path's steps, for tests and roofline timing) */
+
+/* Row pass, Sec. 2 u-update in cost units (Sec. 8 step "row LSE"):
+ *   f_i = eps log a_i - eps LSE_j((g_j - C_ij) / eps).
+ * a is used as given (not renormalised). g (m), a (n) and f_out (n) are
+ * device FP64 arrays. DENSE costs only. */
+int accsink_row_pass(accsink_ctx *ctx, const accsink_problem *prob,
+                     double eps, const double *g, double *f_out, void *stream);
+
+/* Column log-sum-exp of the v-update (Sec. 2, eq. v-update):
+ *   ell_j = LSE_i((f_i - C_ij) / eps),
+ * so that the column sums of P(f, g) are c_j = exp(g_j / eps + ell_j).
+ * f (n) and ell_out (m) are device FP64 arrays. DENSE costs only. */
+int accsink_col_lse(accsink_ctx *ctx, const accsink_problem *prob,
+                    double eps, const double *f, double *ell_out, void *stream);
+
+/* One normalised Sinkhorn map (Sec. 3, eq. normalized-sinkhorn) at x = g/eps:
+ * writes f_out = eps u(x) (n), c_out = column sums of P(u(x), x) (m),
+ * s_out = eps S(x) (m, cost units, mean zero), and *err_out (host) =
+ * sum_j |c_j - b_j| (Sec. 5 eq. l1tol). a and b are used as given. */
+int accsink_sinkhorn_map(accsink_ctx *ctx, const accsink_problem *prob,
+                         double eps, const double *g, double *f_out,
+                         double *c_out, double *s_out, double *err_out,
+                         void *stream);
+
+/* Transport cost <C, P> (eq. EOT) of the plan P_ij = exp((f_i + g_j - C_ij)
+ * / eps) for device potentials f (n), g (m); result in *cost_out (host),
+ * accumulated in FP64. DENSE costs only. */
+int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob,
+                           double eps, const double *f, const double *g,
+                           double *cost_out, void *stream);
+
+/* ---- measurement -------------------------------------------------------- */
+
+/* Times the two streaming passes alone on `stream` with CUDA events: after
+ * one untimed row pass and column pass at g (device, m, cost units), runs
+ * `reps` row passes back to back, then `reps` column passes, and writes the
+ * mean device milliseconds per launch to *row_ms and *col_ms (host). Used for
+ * the HBM roofline of the passes; the data they move is 4 n m bytes of C
+ * per launch plus O(n + m) operands. */
+int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                        const double *g, int reps, void *stream, float *row_ms,
+                        float *col_ms);
+
+/* Launch geometry the context would use for an n x m dense cost (vec = 1 for
+ * the 128-bit path): out6 = {SM count, row-pass CTAs, column-pass row splits,
+ * column-pass strips, step-kernel CTAs, cost-statistics CTAs}. */
+int accsink_launch_geometry(accsink_ctx *ctx, int32_t n, int32_t m, int32_t vec,
+                            int32_t *out6);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACCSINK_H */

@@ -1,0 +1,300 @@
+"""Thin Python binding of the C-ABI in include/accsink.h (argument marshalling only).
+
+Every computation runs in ``libaccsink.so``'s CUDA kernels. PyTorch supplies
+device memory and streams; this module only packs pointers, sizes and
+parameters into the C structs and calls the ``accsink_*`` functions of the same
+names. If the library has not been built, loading raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libaccsink.so")
+
+OK, ERR_INVALID_ARG, ERR_NONPOSITIVE_MARGINAL, ERR_NONFINITE = 0, 1, 2, 3
+ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_MAXITER, ERR_CUDA, ERR_UNSUPPORTED = 4, 5, 6, 7, 8, 9
+COST_DENSE, COST_SQEUCLID, COST_COSINE = 0, 1, 2
+SCALE_NONE, SCALE_MAX_TO_ONE = 0, 1
+PLAIN, ACC = 0, 1
+STAB_OFF, STAB_REPORT, STAB_GATE = 0, 1, 2
+CARRY_Y, CARRY_W = 0, 1
+
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NONPOSITIVE_MARGINAL",
+                3: "ERR_NONFINITE", 4: "ERR_OOM", 5: "ERR_BUDGET", 6: "ERR_TIMEOUT",
+                7: "ERR_MAXITER", 8: "ERR_CUDA", 9: "ERR_UNSUPPORTED"}
+
+# Every symbol include/accsink.h declares.
+EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_params_default",
+            "accsink_version", "accsink_solve", "accsink_solve_host", "accsink_get_history",
+            "accsink_row_pass", "accsink_col_lse", "accsink_sinkhorn_map",
+            "accsink_transport_cost", "accsink_time_passes", "accsink_launch_geometry"]
+
+
+class accsink_problem(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("m", ct.c_int32), ("d", ct.c_int32),
+                ("cost_kind", ct.c_int32), ("ldc", ct.c_int64),
+                ("C", ct.c_void_p), ("X", ct.c_void_p), ("Y", ct.c_void_p),
+                ("a", ct.c_void_p), ("b", ct.c_void_p),
+                ("cost_scale", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class accsink_params(ct.Structure):
+    _fields_ = [("method", ct.c_int32), ("m0", ct.c_int32), ("eps", ct.c_double),
+                ("tol", ct.c_double), ("mu0", ct.c_double),
+                ("max_sinkhorn_steps", ct.c_int32), ("stability", ct.c_int32),
+                ("carry", ct.c_int32), ("evaluate", ct.c_int32), ("use_graph", ct.c_int32),
+                ("history", ct.c_int32)]
+
+
+class accsink_result(ct.Structure):
+    _fields_ = [("status", ct.c_int32), ("sinkhorn_steps", ct.c_int32),
+                ("outer_stages", ct.c_int32), ("stability_failures", ct.c_int32),
+                ("marginal_l1", ct.c_double), ("transport_cost", ct.c_double),
+                ("dual_objective", ct.c_double), ("cost_max", ct.c_double),
+                ("gpu_ms", ct.c_double), ("loop_mode", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class AccsinkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libaccsink.so`` (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libaccsink.so is missing: run __graft_entry__.build() "
+                               "(the solver has no CPU fallback)")
+        L = ct.CDLL(LIB_PATH)
+        vp, i32, dbl = ct.c_void_p, ct.c_int32, ct.c_double
+        P = ct.POINTER
+        L.accsink_create.argtypes = [P(vp), ct.c_int, ct.c_size_t]
+        L.accsink_create.restype = ct.c_int
+        L.accsink_destroy.argtypes = [vp]
+        L.accsink_destroy.restype = None
+        L.accsink_last_error.argtypes = [vp]
+        L.accsink_last_error.restype = ct.c_char_p
+        L.accsink_params_default.argtypes = [P(accsink_params)]
+        L.accsink_params_default.restype = None
+        L.accsink_version.argtypes = []
+        L.accsink_version.restype = ct.c_char_p
+        L.accsink_solve.argtypes = [vp, P(accsink_problem), P(accsink_params), vp, vp, vp,
+                                    P(accsink_result)]
+        L.accsink_solve_host.argtypes = [vp, P(accsink_problem), P(accsink_params), vp, vp, vp,
+                                         P(accsink_result)]
+        L.accsink_get_history.argtypes = [vp, i32, vp, vp, vp, vp, vp, P(i32)]
+        L.accsink_row_pass.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp]
+        L.accsink_col_lse.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp]
+        L.accsink_sinkhorn_map.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, vp,
+                                           P(dbl), vp]
+        L.accsink_transport_cost.argtypes = [vp, P(accsink_problem), dbl, vp, vp, P(dbl), vp]
+        L.accsink_time_passes.argtypes = [vp, P(accsink_problem), dbl, vp, ct.c_int, vp,
+                                          P(ct.c_float), P(ct.c_float)]
+        L.accsink_launch_geometry.argtypes = [vp, i32, i32, i32, P(i32)]
+        for name in EXPORTED:
+            if name not in ("accsink_destroy", "accsink_params_default", "accsink_last_error",
+                            "accsink_version"):
+                getattr(L, name).restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def default_params(**kw) -> accsink_params:
+    p = accsink_params()
+    lib().accsink_params_default(ct.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t):
+    return None if t is None else ct.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ct.c_void_p(stream.cuda_stream)
+
+
+def _check_dev(t, dtype, name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements")
+    if not t.is_contiguous() and t.dim() == 1:
+        raise ValueError(f"{name} must be contiguous")
+
+
+def problem_dense(C, a=None, b=None, scale_to_max=False) -> accsink_problem:
+    """Problem struct for a dense FP32 CUDA cost C (n x m, unit column stride)."""
+    import torch
+    _check_dev(C, torch.float32, "C")
+    if C.dim() != 2 or C.stride(1) != 1:
+        raise ValueError("C must be 2-D with unit column stride")
+    n, m = C.shape
+    pr = accsink_problem()
+    pr.n, pr.m, pr.d, pr.cost_kind = n, m, 0, COST_DENSE
+    pr.ldc = C.stride(0)
+    pr.C = C.data_ptr()
+    if a is not None:
+        _check_dev(a, torch.float64, "a", n)
+        pr.a = a.data_ptr()
+    if b is not None:
+        _check_dev(b, torch.float64, "b", m)
+        pr.b = b.data_ptr()
+    pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
+    return pr
+
+
+class Context:
+    """An accsink context on one CUDA device (wraps accsink_create/destroy)."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 0):
+        self._h = ct.c_void_p()
+        rc = lib().accsink_create(ct.byref(self._h), int(device), int(mem_budget_bytes))
+        if rc != OK:
+            raise AccsinkError(rc, "accsink_create failed")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().accsink_destroy(self._h)
+            self._h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return lib().accsink_last_error(self._h).decode()
+
+    def _raise(self, rc, allow=(OK,)):
+        if rc not in allow:
+            raise AccsinkError(rc, self.last_error())
+        return rc
+
+    # ---- whole solves --------------------------------------------------
+    def accsink_solve(self, prob: accsink_problem, params: accsink_params, f_out, g_out,
+                      stream=None, allow_maxiter=True) -> accsink_result:
+        res = accsink_result()
+        rc = lib().accsink_solve(self._h, ct.byref(prob), ct.byref(params), _stream_ptr(stream),
+                                 _ptr(f_out), _ptr(g_out), ct.byref(res))
+        self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+        return res
+
+    def accsink_solve_host(self, C, a, b, params: accsink_params, f_out, g_out,
+                           scale_to_max=False, stream=None, allow_maxiter=True) -> accsink_result:
+        """C, a, b, f_out, g_out: host numpy arrays (FP32 C, FP64 vectors)."""
+        import numpy as np
+        assert C.dtype == np.float32 and C.flags.c_contiguous
+        n, m = C.shape
+        pr = accsink_problem()
+        pr.n, pr.m, pr.cost_kind, pr.ldc = n, m, COST_DENSE, m
+        pr.C = C.ctypes.data
+        pr.a = np.ascontiguousarray(a, np.float64).ctypes.data if a.dtype == np.float64 and a.flags.c_contiguous else None
+        pr.b = np.ascontiguousarray(b, np.float64).ctypes.data if b.dtype == np.float64 and b.flags.c_contiguous else None
+        if pr.a is None or pr.b is None:
+            raise TypeError("a and b must be contiguous float64 arrays")
+        pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
+        res = accsink_result()
+        rc = lib().accsink_solve_host(self._h, ct.byref(pr), ct.byref(params),
+                                      _stream_ptr(stream), ct.c_void_p(f_out.ctypes.data),
+                                      ct.c_void_p(g_out.ctypes.data), ct.byref(res))
+        self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+        return res
+
+    def accsink_get_history(self, capacity: int):
+        import numpy as np
+        err = np.zeros(capacity); dual = np.zeros(capacity); mu = np.zeros(capacity)
+        stab = np.zeros(capacity, np.int32); cond = np.zeros((capacity, 4))
+        cnt = ct.c_int32()
+        rc = lib().accsink_get_history(self._h, capacity, ct.c_void_p(err.ctypes.data),
+                                       ct.c_void_p(dual.ctypes.data), ct.c_void_p(mu.ctypes.data),
+                                       ct.c_void_p(stab.ctypes.data), ct.c_void_p(cond.ctypes.data),
+                                       ct.byref(cnt))
+        self._raise(rc)
+        k = cnt.value
+        return {"err": err[:k], "dual": dual[:k], "mu": mu[:k], "stab": stab[:k], "cond": cond[:k]}
+
+    # ---- single passes -------------------------------------------------
+    def accsink_row_pass(self, prob, eps, g, f_out, stream=None):
+        self._raise(lib().accsink_row_pass(self._h, ct.byref(prob), float(eps), _ptr(g),
+                                           _ptr(f_out), _stream_ptr(stream)))
+
+    def accsink_col_lse(self, prob, eps, f, ell_out, stream=None):
+        self._raise(lib().accsink_col_lse(self._h, ct.byref(prob), float(eps), _ptr(f),
+                                          _ptr(ell_out), _stream_ptr(stream)))
+
+    def accsink_sinkhorn_map(self, prob, eps, g, f_out, c_out, s_out, stream=None) -> float:
+        err = ct.c_double()
+        self._raise(lib().accsink_sinkhorn_map(self._h, ct.byref(prob), float(eps), _ptr(g),
+                                               _ptr(f_out), _ptr(c_out), _ptr(s_out),
+                                               ct.byref(err), _stream_ptr(stream)))
+        return err.value
+
+    def accsink_transport_cost(self, prob, eps, f, g, stream=None) -> float:
+        out = ct.c_double()
+        self._raise(lib().accsink_transport_cost(self._h, ct.byref(prob), float(eps), _ptr(f),
+                                                 _ptr(g), ct.byref(out), _stream_ptr(stream)))
+        return out.value
+
+    def accsink_time_passes(self, prob, eps, g, reps, stream=None):
+        r, c = ct.c_float(), ct.c_float()
+        self._raise(lib().accsink_time_passes(self._h, ct.byref(prob), float(eps), _ptr(g),
+                                              int(reps), _stream_ptr(stream), ct.byref(r),
+                                              ct.byref(c)))
+        return r.value, c.value
+
+    def accsink_launch_geometry(self, n, m, vec=1):
+        out = (ct.c_int32 * 6)()
+        self._raise(lib().accsink_launch_geometry(self._h, int(n), int(m), int(vec), out))
+        keys = ["num_sms", "row_grid", "col_splits", "col_strips", "step_grid", "stat_grid"]
+        return dict(zip(keys, list(out)))
+
+
+def result_dict(res: accsink_result) -> dict:
+    return {k: getattr(res, k) for k, _ in accsink_result._fields_}
+
+
+def solve(C, a, b, eps, tol=1e-6, method="acc", scale_to_max=False, ctx: Context | None = None,
+          stream=None, **params):
+    """Convenience: solve a dense problem held in CUDA tensors.
+
+    Returns (f, g, result dict) with f, g FP64 CUDA tensors in cost units."""
+    import torch
+    own = ctx is None
+    ctx = ctx or Context(C.device.index or 0)
+    try:
+        prob = problem_dense(C, a, b, scale_to_max)
+        p = default_params(eps=float(eps), tol=float(tol),
+                           method=ACC if method in ("acc", ACC) else PLAIN, **params)
+        f = torch.empty(C.shape[0], dtype=torch.float64, device=C.device)
+        g = torch.empty(C.shape[1], dtype=torch.float64, device=C.device)
+        res = ctx.accsink_solve(prob, p, f, g, stream=stream)
+        return f, g, result_dict(res)
+    finally:
+        if own:
+            ctx.close()

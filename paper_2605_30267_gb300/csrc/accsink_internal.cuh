@@ -1,0 +1,219 @@
+// Internal declarations of the sm_103a Acc-Sinkhorn solver.
+//
+// Units. Kernels work with the cost exactly as stored (FP32) and the
+// effective regulariser eps_c = eps * cost_div (cost_div = max C when the
+// caller asked for MAX_TO_ONE scaling, else 1). The iterate x and the row
+// variable u are the paper's dimensionless variables (Sec. 2: cost divided by
+// eps); potentials in cost units are f = eps_c u, g = eps_c x.
+//
+// Precision. The exponent (g_j - C_ij)/eps_c must be accurate to ~1e-7 in
+// absolute terms for the l1 marginal error to reach 1e-6 at eps = 1e-3, far
+// beyond what a plain FP32 subtraction of O(1) numbers gives (6e-8/eps).
+// Each operand is therefore held as an unevaluated FP32 pair
+//   G_j + gamma_j = g_j + shift_g   (shift_g makes G_j >= max|C|),
+// the difference G_j - C_ij is formed exactly by Fast2Sum (valid because
+// |G_j| >= |C_ij|), the per-row reference R_i (a running max of G_j - C_ij)
+// is subtracted exactly-relative, and only then is the small remainder
+// scaled by log2(e)/eps_c, itself carried as a (hi, lo) FP32 pair. All
+// remaining roundings are relative to the shifted exponent, whose size is
+// O(10) for every term that matters, so each term's exponent is accurate to
+// ~1e-7. Sums use short FP32 chunks folded into Kahan-compensated partials;
+// cross-thread merges and every per-row / per-column finish are FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace accsink {
+
+constexpr double kLog2e = 1.44269504088896340736;
+constexpr double kLn2 = 0.69314718055994530942;
+constexpr int kColStrip = 128;      // columns per column-pass CTA (32 lanes x 4)
+constexpr int kPartStride = 8;      // doubles per block partial in the step kernel
+
+// Device-resident solver state. Written only by the init kernel, by block 0
+// of the step kernel (after its last grid barrier) and by the host before a
+// launch; read by every kernel.
+struct DevState {
+    // problem constants
+    double eps_c;        // regulariser in stored-cost units (eps * cost_div)
+    double inv_eps_c;
+    double eps_user;     // eps as given (potentials are returned as eps_user * x)
+    double cost_div;     // 1 or max C
+    double tol;
+    double cmax, cmin, cabs;   // max C, min C, max |C|
+    double min_loga;
+    double log_m;
+    double sum_a, sum_b;
+    // double-float operand constants
+    double shift_g, shift_f;
+    float k_hi, k_lo;          // log2(e)/eps_c = k_hi + k_lo
+    // Algorithm 1/2 state
+    double mu;
+    double kl_prev;            // D_phi*(0, grad f(x_k)) of the previous iterate
+    double err;                // marginal L1 at the last evaluated iterate
+    double dual;               // dual objective there (cost units, scaled)
+    double last_cond[4];
+    int32_t method, stability, carry, max_steps;
+    int32_t m_stage, j_in_stage, steps, stages, failures;
+    int32_t first, done, status, use_cond;
+    int32_t hist_cap, row_grid, col_splits, nonfinite;
+    int32_t mode;              // step-kernel mode (solve / single map)
+    uint32_t barrier;          // grid-barrier arrival counter (reset by the row pass)
+    int32_t pad[2];
+};
+
+enum StepMode { STEP_SOLVE = 0, STEP_MAP = 1 };
+
+// Workspace pointers shared by the kernels (all device memory).
+struct Work {
+    // marginals
+    double *a, *b, *loga, *logb;
+    // iterate state (m)
+    double *x, *x_prev, *w, *p_prev, *D_prev;
+    // per-column scratch of the step kernel (m)
+    double *raw, *D1, *del, *w1;
+    // row pass output (n)
+    double *u;
+    // double-float operands
+    float *G, *Gk;            // m (row pass)
+    float2 *FF;               // n (column pass): (F_hi, F_lo * k_hi)
+    // partials
+    float2 *colpart;          // splits x m : (R, S) per column per row split
+    double *rowpart;          // row-grid x 2 : (sum a_i u_i, sum cost) per CTA
+    double *steppart;         // step-grid x 3 x kPartStride
+    double *statpart;         // cost-stats grid x 4
+    // history (hist_cap each)
+    double *h_err, *h_dual, *h_mu, *h_cond;
+    int32_t *h_stab;
+    DevState *st;
+    // inputs of the single-pass entry points
+    const double *b_src;      // column marginal to copy (may be NULL)
+    const double *f_given;    // row potentials weighting the cost sum (may be NULL)
+    int32_t nstat;            // number of cost-statistics partials
+    int32_t ignore_done;      // row pass runs even when the solve has stopped
+};
+
+struct CostView {
+    const float *C;
+    int64_t ldc;
+    int32_t n, m;
+    int32_t vec;   // 1: ldc % 4 == 0 and C 16-byte aligned
+};
+
+// ---------------------------------------------------------------- helpers --
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 2^((d) * k) with k = kh + kl, d small: both products rounded once.
+__device__ __forceinline__ float exp2_scaled(float d, float kh, float kl)
+{
+    return ex2_approx(fmaf(d, kh, d * kl));
+}
+
+__device__ __forceinline__ float4 ld_stream4(const float *p)
+{
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float ld_stream1(const float *p)
+{
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-wide barrier for cooperatively launched kernels (all blocks resident).
+// `target` is the arrival count to wait for (k * gridDim for the k-th
+// barrier of a launch; the counter is zeroed by the kernel that runs before).
+// The wait is bounded by `limit_ns` of global time; on expiry the barrier
+// records ACCSINK_ERR_TIMEOUT in the state, stops the solve and returns false.
+__device__ __forceinline__ bool grid_barrier(DevState *st, uint32_t target, uint64_t limit_ns)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(&st->barrier, 1u);
+        uint64_t t0 = globaltimer_ns();
+        for (;;) {
+            uint32_t v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&st->barrier));
+            if (v >= target) break;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                ok = 0;
+                atomicExch(&st->status, 6 /* ACCSINK_ERR_TIMEOUT */);
+                atomicExch(&st->done, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// ---------------------------------------------------------------- launches --
+
+struct LaunchCfg {
+    int num_sms;
+    int row_grid;      // row-pass CTAs
+    int col_splits;    // column-pass row splits
+    int step_grid;     // step-kernel CTAs (cooperative)
+    int stat_grid;
+};
+
+cudaError_t launch_cost_stats(const CostView &cv, const Work &w, int grid, cudaStream_t s);
+cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, bool with_cost,
+                            cudaStream_t s);
+cudaError_t launch_col_pass(const CostView &cv, const Work &w, int splits, cudaStream_t s);
+cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
+                        const double *b_in, int normalise, cudaStream_t s);
+cudaError_t launch_step(const CostView &cv, const Work &w, int grid,
+                        cudaGraphConditionalHandle h, cudaStream_t s);
+cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double *c_out,
+                            double *s_out, cudaStream_t s);
+cudaError_t launch_prep_g(const CostView &cv, const Work &w, int grid, const double *g,
+                          const double *a_in, double eps, cudaStream_t s);
+cudaError_t launch_prep_f(const CostView &cv, const Work &w, int grid, const double *f,
+                          double eps, cudaStream_t s);
+cudaError_t launch_scale_out(const double *src, double scale, double *dst, int n,
+                             cudaStream_t s);
+cudaError_t launch_col_finish_lse(const Work &w, int m, double *ell_out, cudaStream_t s);
+int occupancy_row_pass(int vec);
+int occupancy_col_pass(int vec);
+
+}  // namespace accsink

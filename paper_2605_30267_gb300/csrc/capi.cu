@@ -1,0 +1,757 @@
+// Host engine behind the C-ABI of include/accsink.h: context, workspace,
+// validation, the device-side solve loop (a CUDA graph whose body is
+// [row pass -> column pass -> step] inside a conditional WHILE node, so a
+// solve needs no host round trip per iteration), a host-driven fallback loop,
+// and the single-pass entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "accsink.h"
+#include "accsink_internal.cuh"
+
+using namespace accsink;
+
+namespace accsink {
+__global__ void k_set_state(DevState v, DevState *dst) { *dst = v; }
+}  // namespace accsink
+
+namespace {
+
+struct GraphKey {
+    const float *C = nullptr;
+    int64_t ldc = 0;
+    int n = 0, m = 0, vec = 0, row_grid = 0, splits = 0, step_grid = 0;
+    void *ws = nullptr;
+    bool operator==(const GraphKey &o) const
+    {
+        return C == o.C && ldc == o.ldc && n == o.n && m == o.m && vec == o.vec &&
+               row_grid == o.row_grid && splits == o.splits && step_grid == o.step_grid &&
+               ws == o.ws;
+    }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct accsink_ctx {
+    int device = 0;
+    size_t budget = 0;
+    std::string err;
+    int num_sms = 1;
+    int occ_row[2] = {1, 1}, occ_col[2] = {1, 1};
+    // workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int64_t n_cap = -1, m_cap = -1;
+    int splits_cap = 0, rowgrid_cap = 0, hist_cap = 0;
+    Work w{};
+    DevState *h_state = nullptr;      // pinned
+    double *h_rowpart = nullptr;      // pinned, rowgrid_cap * 2
+    // staging for accsink_solve_host
+    void *stage = nullptr;
+    size_t stage_bytes = 0;
+    // graph cache
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey key;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int last_hist_count = 0;
+    bool graph_broken = false;
+    std::string graph_error;
+};
+
+namespace {
+
+int fail(accsink_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(accsink_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, ACCSINK_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);   \
+    } while (0)
+
+void free_graph(accsink_ctx *ctx)
+{
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->exec = nullptr;
+    ctx->graph = nullptr;
+    ctx->key = GraphKey();
+}
+
+struct Geometry {
+    int stat_grid, row_grid, splits, step_grid, vec_grid;
+};
+
+Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
+{
+    Geometry g;
+    const int S = ctx->num_sms;
+    g.stat_grid = std::max(1, std::min(n, 4 * S));
+    g.row_grid = std::max(1, std::min(S * ctx->occ_row[vec], (n + 1) / 2));
+    const int strips = (m + kColStrip - 1) / kColStrip;
+    const int target = S * ctx->occ_col[vec];
+    int splits = target / strips;
+    splits = std::max(1, std::min(splits, std::max(1, n / 8)));
+    g.splits = splits;
+    g.step_grid = std::max(1, std::min(S, (m + 255) / 256));
+    g.vec_grid = std::max(1, std::min(S, (std::max(n, m) + 255) / 256));
+    return g;
+}
+
+// (Re)allocates the workspace for n x m with the given partial counts.
+int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, int hist)
+{
+    if (n <= ctx->n_cap && m <= ctx->m_cap && splits <= ctx->splits_cap &&
+        row_grid <= ctx->rowgrid_cap && hist <= ctx->hist_cap && ctx->ws)
+        return ACCSINK_OK;
+    const int64_t N = std::max<int64_t>(n, ctx->n_cap);
+    const int64_t M = std::max<int64_t>(m, ctx->m_cap);
+    const int SP = std::max(splits, ctx->splits_cap);
+    const int RG = std::max(row_grid, ctx->rowgrid_cap);
+    const int H = std::max(hist, ctx->hist_cap);
+    const int64_t Mp = (M + 3) / 4 * 4;
+    const int S = ctx->num_sms;
+    std::vector<size_t> sizes = {
+        (size_t)N * 8, (size_t)M * 8, (size_t)N * 8, (size_t)M * 8,          // a b loga logb
+        (size_t)M * 8, (size_t)M * 8, (size_t)M * 8, (size_t)M * 8, (size_t)M * 8,  // x xp w pp Dp
+        (size_t)M * 8, (size_t)M * 8, (size_t)M * 8, (size_t)M * 8,          // raw D1 del w1
+        (size_t)N * 8,                                                         // u
+        (size_t)Mp * 4, (size_t)Mp * 4,                                        // G Gk
+        (size_t)N * 8,                                                         // FF
+        (size_t)SP * (size_t)M * 8,                                            // colpart
+        (size_t)RG * 16,                                                       // rowpart
+        (size_t)std::max(S, 1) * kPartStride * 8 * 2,                          // steppart
+        (size_t)4 * S * 32,                                                    // statpart
+        (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8,
+        (size_t)std::max(H, 1) * 32, (size_t)std::max(H, 1) * 4,               // history
+        sizeof(DevState)};
+    size_t total = 0;
+    for (size_t s : sizes) total += align_up(s, 256);
+    if (ctx->budget && total > ctx->budget)
+        return fail(ctx, ACCSINK_ERR_BUDGET,
+                    "workspace of " + std::to_string(total) + " bytes exceeds the budget");
+    free_graph(ctx);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
+    ctx->ws = nullptr;
+    ctx->h_rowpart = nullptr;
+    if (cudaMalloc(&ctx->ws, total) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->n_cap = ctx->m_cap = -1;
+        return fail(ctx, ACCSINK_ERR_OOM, "cudaMalloc of the workspace failed");
+    }
+    if (cudaMallocHost(&ctx->h_rowpart, (size_t)RG * 16) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, ACCSINK_ERR_OOM, "cudaMallocHost failed");
+    }
+    cudaMemset(ctx->ws, 0, total);
+    ctx->ws_bytes = total;
+    char *p = (char *)ctx->ws;
+    size_t k = 0;
+    auto take = [&](void) -> void * {
+        void *r = p;
+        p += align_up(sizes[k++], 256);
+        return r;
+    };
+    Work &w = ctx->w;
+    w = Work{};
+    w.a = (double *)take(); w.b = (double *)take(); w.loga = (double *)take(); w.logb = (double *)take();
+    w.x = (double *)take(); w.x_prev = (double *)take(); w.w = (double *)take();
+    w.p_prev = (double *)take(); w.D_prev = (double *)take();
+    w.raw = (double *)take(); w.D1 = (double *)take(); w.del = (double *)take(); w.w1 = (double *)take();
+    w.u = (double *)take();
+    w.G = (float *)take(); w.Gk = (float *)take();
+    w.FF = (float2 *)take();
+    w.colpart = (float2 *)take();
+    w.rowpart = (double *)take();
+    w.steppart = (double *)take();
+    w.statpart = (double *)take();
+    w.h_err = (double *)take(); w.h_dual = (double *)take(); w.h_mu = (double *)take();
+    w.h_cond = (double *)take(); w.h_stab = (int32_t *)take();
+    w.st = (DevState *)take();
+    ctx->n_cap = N; ctx->m_cap = M; ctx->splits_cap = SP; ctx->rowgrid_cap = RG; ctx->hist_cap = H;
+    return ACCSINK_OK;
+}
+
+int validate_problem(accsink_ctx *ctx, const accsink_problem *p, bool need_cost_dense)
+{
+    if (!p) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "problem is NULL");
+    if (p->n < 1 || p->m < 1) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "n and m must be >= 1");
+    if (p->cost_kind != ACCSINK_COST_DENSE) {
+        if (p->cost_kind == ACCSINK_COST_SQEUCLID || p->cost_kind == ACCSINK_COST_COSINE)
+            return fail(ctx, ACCSINK_ERR_UNSUPPORTED,
+                        "point-cloud costs are not served by this entry point yet");
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_kind");
+    }
+    (void)need_cost_dense;
+    if (!p->C) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "C is NULL");
+    const int64_t ldc = p->ldc ? p->ldc : p->m;
+    if (ldc < p->m) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "ldc < m");
+    if (p->cost_scale != ACCSINK_SCALE_NONE && p->cost_scale != ACCSINK_SCALE_MAX_TO_ONE)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_scale");
+    return ACCSINK_OK;
+}
+
+CostView make_view(const accsink_problem *p)
+{
+    CostView cv;
+    cv.C = p->C;
+    cv.ldc = p->ldc ? p->ldc : p->m;
+    cv.n = p->n;
+    cv.m = p->m;
+    cv.vec = ((cv.ldc % 4) == 0 && (((uintptr_t)p->C) & 15u) == 0) ? 1 : 0;
+    return cv;
+}
+
+int validate_params(accsink_ctx *ctx, const accsink_params *q)
+{
+    if (!q) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "params is NULL");
+    if (!(q->eps > 0.0) || !std::isfinite(q->eps))
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "eps must be positive and finite");
+    if (!(q->tol > 0.0)) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "tol must be positive");
+    if (q->method != ACCSINK_PLAIN && q->method != ACCSINK_ACC)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown method");
+    if (q->method == ACCSINK_ACC && !(q->mu0 > 0.0 && q->mu0 < 1.0))
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "mu0 must lie in (0, 1)");
+    if (q->method == ACCSINK_ACC && q->m0 < 1)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "m0 must be >= 1");
+    if (q->max_sinkhorn_steps < 1)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "max_sinkhorn_steps must be >= 1");
+    if (q->stability < 0 || q->stability > 2)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown stability mode");
+    if (q->carry != ACCSINK_CARRY_Y && q->carry != ACCSINK_CARRY_W)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown carry mode");
+    if (q->history < 0) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "history must be >= 0");
+    return ACCSINK_OK;
+}
+
+cudaError_t set_state(accsink_ctx *ctx, const DevState &hs, cudaStream_t s)
+{
+    k_set_state<<<1, 1, 0, s>>>(hs, ctx->w.st);
+    return cudaGetLastError();
+}
+
+// Builds (or reuses) the graph: WHILE(cond) { row pass; column pass; step }.
+int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g)
+{
+    GraphKey key;
+    key.C = cv.C; key.ldc = cv.ldc; key.n = cv.n; key.m = cv.m; key.vec = cv.vec;
+    key.row_grid = g.row_grid; key.splits = g.splits; key.step_grid = g.step_grid;
+    key.ws = ctx->ws;
+    if (ctx->exec && ctx->key == key) return ACCSINK_OK;
+    free_graph(ctx);
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaGraphConditionalHandleCreate"); }
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaGraphAddNode"); }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
+    Work w = ctx->w;
+    w.ignore_done = 0;
+    cudaError_t e1 = launch_row_pass(cv, w, g.row_grid, false, ctx->cap_stream);
+    cudaError_t e2 = launch_col_pass(cv, w, g.splits, ctx->cap_stream);
+    cudaError_t e3 = launch_step(cv, w, g.step_grid, handle, ctx->cap_stream);
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(ctx->cap_stream, &out);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        cudaError_t bad = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e));
+        return cuda_fail(ctx, bad, "capturing the solve loop");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaGraphInstantiate"); }
+    ctx->graph = graph;
+    ctx->exec = exec;
+    ctx->key = key;
+    return ACCSINK_OK;
+}
+
+// Core solve with device pointers, run on stream s. Fills res.
+int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *prm,
+                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res)
+{
+    const CostView cv = make_view(prob);
+    const int n = prob->n, m = prob->m;
+    const Geometry g = geometry(ctx, n, m, cv.vec);
+    int rc = ensure_workspace(ctx, n, m, g.splits, g.row_grid, prm->history);
+    if (rc != ACCSINK_OK) return rc;
+    Work w = ctx->w;
+    w.nstat = g.stat_grid;
+    w.b_src = nullptr;
+    w.f_given = nullptr;
+    w.ignore_done = 0;
+
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.eps_user = prm->eps;
+    hs.tol = prm->tol;
+    hs.mu = prm->mu0;
+    hs.method = prm->method;
+    hs.stability = prm->stability;
+    hs.carry = prm->carry;
+    hs.max_steps = prm->max_sinkhorn_steps;
+    hs.m_stage = prm->m0;
+    hs.hist_cap = prm->history;
+    hs.row_grid = g.row_grid;
+    hs.col_splits = g.splits;
+    hs.use_cond = prm->use_graph ? 1 : 0;
+    hs.first = 1;
+
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(set_state(ctx, hs, s));
+    CK(launch_cost_stats(cv, w, g.stat_grid, s));
+    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, s));
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_state->done) {
+        const int st = ctx->h_state->status;
+        std::memset(res, 0, sizeof(*res));
+        res->status = st;
+        res->cost_max = ctx->h_state->cmax;
+        if (st == ACCSINK_ERR_NONFINITE) return fail(ctx, st, "C, a or b holds NaN or Inf");
+        if (st == ACCSINK_ERR_NONPOSITIVE_MARGINAL)
+            return fail(ctx, st, "every a_i and b_j must be > 0");
+        if (st == ACCSINK_ERR_TIMEOUT) return fail(ctx, st, "a device barrier timed out");
+        return fail(ctx, st == 0 ? ACCSINK_ERR_INVALID_ARG : st, "max C must be > 0 to scale by it");
+    }
+
+    bool use_graph = prm->use_graph && !ctx->graph_broken;
+    if (use_graph) {
+        rc = get_graph(ctx, cv, g);
+        if (rc != ACCSINK_OK) {
+            // The device-side loop needs conditional graph nodes with
+            // cooperative kernels; if this driver refuses, remember it and
+            // run the same kernels from the host loop instead.
+            ctx->graph_broken = true;
+            ctx->graph_error = ctx->err;
+            ctx->err.clear();
+            use_graph = false;
+            CK(cudaMemsetAsync(&w.st->use_cond, 0, sizeof(int32_t), s));
+        }
+    }
+    if (use_graph) {
+        CK(cudaGraphLaunch(ctx->exec, s));
+    } else {
+        const int unroll = 8;
+        for (;;) {
+            for (int u = 0; u < unroll; ++u) {
+                CK(launch_row_pass(cv, w, g.row_grid, false, s));
+                CK(launch_col_pass(cv, w, g.splits, s));
+                CK(launch_step(cv, w, g.step_grid, 0, s));
+            }
+            CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->h_state->done) break;
+        }
+    }
+    if (prm->evaluate) {
+        Work we = w;
+        we.ignore_done = 1;
+        CK(launch_row_pass(cv, we, g.row_grid, true, s));
+    }
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    // potentials in the units of the (possibly scaled) cost: f = eps u, g = eps x
+    CK(launch_scale_out(w.u, prm->eps, f_out, n, s));
+    CK(launch_scale_out(w.x, prm->eps, g_out, m, s));
+    CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)g.row_grid * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaStreamSynchronize(s));
+
+    const DevState &fs = *ctx->h_state;
+    std::memset(res, 0, sizeof(*res));
+    res->status = fs.status;
+    res->sinkhorn_steps = fs.steps;
+    res->outer_stages = fs.stages;
+    res->stability_failures = fs.failures;
+    res->marginal_l1 = fs.err;
+    res->dual_objective = fs.dual;
+    res->cost_max = fs.cmax;
+    res->transport_cost = NAN;
+    if (prm->evaluate) {
+        double c = 0.0;
+        for (int b = 0; b < g.row_grid; ++b) c += ctx->h_rowpart[2 * b + 1];
+        res->transport_cost = c / fs.cost_div;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    res->gpu_ms = ms;
+    res->loop_mode = use_graph ? 1 : 0;
+    ctx->last_hist_count = std::min(fs.steps, prm->history);
+    if (fs.status == ACCSINK_ERR_MAXITER)
+        return fail(ctx, ACCSINK_ERR_MAXITER, "not converged within max_sinkhorn_steps");
+    if (fs.status != ACCSINK_OK) return fail(ctx, fs.status, "solve stopped with an error status");
+    return ACCSINK_OK;
+}
+
+int begin(accsink_ctx *ctx)
+{
+    if (!ctx) return ACCSINK_ERR_INVALID_ARG;
+    ctx->err.clear();
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    return ACCSINK_OK;
+}
+
+// Shared set-up of the single-pass entry points: workspace, state, cost
+// statistics. Returns the geometry through *g.
+int pass_setup(accsink_ctx *ctx, const accsink_problem *prob, double eps, cudaStream_t s,
+               Geometry *g, Work *w)
+{
+    int rc = validate_problem(ctx, prob, true);
+    if (rc != ACCSINK_OK) return rc;
+    if (!(eps > 0.0) || !std::isfinite(eps))
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "eps must be positive and finite");
+    const CostView cv = make_view(prob);
+    *g = geometry(ctx, prob->n, prob->m, cv.vec);
+    rc = ensure_workspace(ctx, prob->n, prob->m, g->splits, g->row_grid, 0);
+    if (rc != ACCSINK_OK) return rc;
+    *w = ctx->w;
+    w->nstat = g->stat_grid;
+    w->b_src = nullptr;
+    w->f_given = nullptr;
+    w->ignore_done = 1;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.eps_user = eps;
+    hs.row_grid = g->row_grid;
+    hs.col_splits = g->splits;
+    hs.mode = STEP_MAP;
+    CK(set_state(ctx, hs, s));
+    CK(launch_cost_stats(cv, *w, g->stat_grid, s));
+    return ACCSINK_OK;
+}
+
+}  // namespace
+
+// ============================================================ C-ABI ========
+
+extern "C" {
+
+const char *accsink_version(void) { return "accsink 1.0 sm_103a"; }
+
+void accsink_params_default(accsink_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->method = ACCSINK_ACC;
+    p->m0 = 4;
+    p->eps = 1e-2;
+    p->tol = 1e-6;
+    p->mu0 = 0.25;
+    p->max_sinkhorn_steps = 100000;
+    p->stability = ACCSINK_STAB_REPORT;
+    p->carry = ACCSINK_CARRY_Y;
+    p->evaluate = 1;
+    p->use_graph = 1;
+    p->history = 0;
+}
+
+int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
+{
+    if (!out) return ACCSINK_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return ACCSINK_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return ACCSINK_ERR_CUDA;
+    accsink_ctx *ctx = new accsink_ctx();
+    ctx->device = device;
+    ctx->budget = mem_budget_bytes;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    for (int v = 0; v < 2; ++v) {
+        ctx->occ_row[v] = occupancy_row_pass(v);
+        ctx->occ_col[v] = occupancy_col_pass(v);
+    }
+    if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_state, sizeof(DevState)) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return ACCSINK_ERR_CUDA;
+    }
+    *out = ctx;
+    return ACCSINK_OK;
+}
+
+void accsink_destroy(accsink_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    free_graph(ctx);
+    if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
+    if (ctx->h_state) cudaFreeHost(ctx->h_state);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+const char *accsink_last_error(const accsink_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *params,
+                  void *stream, double *f_out, double *g_out, accsink_result *res)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
+    std::memset(res, 0, sizeof(*res));
+    res->status = ACCSINK_ERR_INVALID_ARG;
+    rc = validate_problem(ctx, prob, true);
+    if (rc == ACCSINK_OK) rc = validate_params(ctx, params);
+    if (rc == ACCSINK_OK && (!prob->a || !prob->b))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "a and b must be given");
+    if (rc == ACCSINK_OK && (!f_out || !g_out))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "f_out and g_out must be given");
+    if (rc != ACCSINK_OK) { res->status = rc; return rc; }
+    rc = solve_device(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res);
+    res->status = rc;
+    return rc;
+}
+
+int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
+                       const accsink_params *params, void *stream, double *f_out_host,
+                       double *g_out_host, accsink_result *res)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
+    std::memset(res, 0, sizeof(*res));
+    rc = validate_problem(ctx, prob_host, true);
+    if (rc == ACCSINK_OK) rc = validate_params(ctx, params);
+    if (rc == ACCSINK_OK && (!prob_host->a || !prob_host->b || !f_out_host || !g_out_host))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "a, b, f_out and g_out must be given");
+    if (rc != ACCSINK_OK) { res->status = rc; return rc; }
+    const int n = prob_host->n, m = prob_host->m;
+    const int64_t ldc = prob_host->ldc ? prob_host->ldc : m;
+    const size_t cbytes = ((size_t)(n - 1) * (size_t)ldc + (size_t)m) * sizeof(float);
+    const size_t need = align_up(cbytes, 256) + align_up((size_t)n * 8, 256) * 2 +
+                        align_up((size_t)m * 8, 256) * 2;
+    if (need > ctx->stage_bytes) {
+        if (ctx->stage) cudaFree(ctx->stage);
+        ctx->stage = nullptr;
+        ctx->stage_bytes = 0;
+        if (ctx->budget && need > ctx->budget) {
+            res->status = ACCSINK_ERR_BUDGET;
+            return fail(ctx, ACCSINK_ERR_BUDGET, "staging buffers exceed the budget");
+        }
+        if (cudaMalloc(&ctx->stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            res->status = ACCSINK_ERR_OOM;
+            return fail(ctx, ACCSINK_ERR_OOM, "cudaMalloc of the staging buffers failed");
+        }
+        ctx->stage_bytes = need;
+    }
+    char *p = (char *)ctx->stage;
+    float *dC = (float *)p; p += align_up(cbytes, 256);
+    double *da = (double *)p; p += align_up((size_t)n * 8, 256);
+    double *df = (double *)p; p += align_up((size_t)n * 8, 256);
+    double *db = (double *)p; p += align_up((size_t)m * 8, 256);
+    double *dg = (double *)p;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dC, prob_host->C, cbytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(da, prob_host->a, (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(db, prob_host->b, (size_t)m * 8, cudaMemcpyHostToDevice, s));
+    accsink_problem pd = *prob_host;
+    pd.C = dC;
+    pd.a = da;
+    pd.b = db;
+    pd.ldc = ldc;
+    rc = solve_device(ctx, &pd, params, s, df, dg, res);
+    if (rc != ACCSINK_OK && rc != ACCSINK_ERR_MAXITER) { res->status = rc; return rc; }
+    CK(cudaMemcpyAsync(f_out_host, df, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(g_out_host, dg, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    res->status = rc;
+    return rc;
+}
+
+int accsink_get_history(accsink_ctx *ctx, int32_t capacity, double *err, double *dual,
+                        double *mu, int32_t *stab, double *cond, int32_t *count)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!count || capacity < 0) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "bad history arguments");
+    const int k = std::min(capacity, ctx->last_hist_count);
+    *count = k;
+    if (k == 0) return ACCSINK_OK;
+    if (err) CK(cudaMemcpy(err, ctx->w.h_err, (size_t)k * 8, cudaMemcpyDeviceToHost));
+    if (dual) CK(cudaMemcpy(dual, ctx->w.h_dual, (size_t)k * 8, cudaMemcpyDeviceToHost));
+    if (mu) CK(cudaMemcpy(mu, ctx->w.h_mu, (size_t)k * 8, cudaMemcpyDeviceToHost));
+    if (stab) CK(cudaMemcpy(stab, ctx->w.h_stab, (size_t)k * 4, cudaMemcpyDeviceToHost));
+    if (cond) CK(cudaMemcpy(cond, ctx->w.h_cond, (size_t)k * 32, cudaMemcpyDeviceToHost));
+    return ACCSINK_OK;
+}
+
+int accsink_row_pass(accsink_ctx *ctx, const accsink_problem *prob, double eps, const double *g,
+                     double *f_out, void *stream)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!prob || !g || !f_out || !prob->a)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "g, f_out and a must be given");
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry geo;
+    Work w;
+    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView cv = make_view(prob);
+    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
+    CK(launch_row_pass(cv, w, geo.row_grid, false, s));
+    CK(launch_scale_out(w.u, eps, f_out, prob->n, s));
+    return ACCSINK_OK;
+}
+
+int accsink_col_lse(accsink_ctx *ctx, const accsink_problem *prob, double eps, const double *f,
+                    double *ell_out, void *stream)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!prob || !f || !ell_out) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "f and ell_out must be given");
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry geo;
+    Work w;
+    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView cv = make_view(prob);
+    CK(launch_prep_f(cv, w, geo.vec_grid, f, eps, s));
+    CK(launch_col_pass(cv, w, geo.splits, s));
+    CK(launch_col_finish_lse(w, prob->m, ell_out, s));
+    return ACCSINK_OK;
+}
+
+int accsink_sinkhorn_map(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                         const double *g, double *f_out, double *c_out, double *s_out,
+                         double *err_out, void *stream)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!prob || !g || !f_out || !c_out || !s_out || !err_out || !prob->a || !prob->b)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "every pointer argument must be given");
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry geo;
+    Work w;
+    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView cv = make_view(prob);
+    w.b_src = prob->b;
+    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
+    CK(launch_row_pass(cv, w, geo.row_grid, false, s));
+    CK(launch_col_pass(cv, w, geo.splits, s));
+    CK(launch_step_map(cv, w, geo.step_grid, c_out, s_out, s));
+    CK(launch_scale_out(w.u, eps, f_out, prob->n, s));
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *err_out = ctx->h_state->err;
+    if (ctx->h_state->nonfinite) return fail(ctx, ACCSINK_ERR_NONFINITE, "C holds NaN or Inf");
+    return ACCSINK_OK;
+}
+
+int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                           const double *f, const double *g, double *cost_out, void *stream)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!prob || !f || !g || !cost_out)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "f, g and cost_out must be given");
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry geo;
+    Work w;
+    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView cv = make_view(prob);
+    // The row pass at g weighs row i by w_i = exp(f_i/eps + LSE_i), so that
+    // w_i * (sum_j C_ij t_ij) / (sum_j t_ij) = sum_j C_ij P_ij.
+    w.f_given = f;
+    CK(launch_prep_g(cv, w, geo.vec_grid, g, nullptr, eps, s));
+    CK(launch_row_pass(cv, w, geo.row_grid, true, s));
+    CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)geo.row_grid * 16,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double c = 0.0;
+    for (int b = 0; b < geo.row_grid; ++b) c += ctx->h_rowpart[2 * b + 1];
+    *cost_out = c;
+    return ACCSINK_OK;
+}
+
+int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                        const double *g, int reps, void *stream, float *row_ms, float *col_ms)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!prob || !g || !prob->a || reps < 1)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "g and a must be given and reps >= 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    Geometry geo;
+    Work w;
+    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView cv = make_view(prob);
+    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
+    CK(launch_row_pass(cv, w, geo.row_grid, false, s));   // warm-up, writes F
+    CK(launch_col_pass(cv, w, geo.splits, s));
+    CK(cudaEventRecord(ctx->ev0, s));
+    for (int r = 0; r < reps; ++r) CK(launch_row_pass(cv, w, geo.row_grid, false, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (row_ms) *row_ms = ms / reps;
+    CK(cudaEventRecord(ctx->ev0, s));
+    for (int r = 0; r < reps; ++r) CK(launch_col_pass(cv, w, geo.splits, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaEventSynchronize(ctx->ev1));
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (col_ms) *col_ms = ms / reps;
+    return ACCSINK_OK;
+}
+
+int accsink_launch_geometry(accsink_ctx *ctx, int32_t n, int32_t m, int32_t vec, int32_t *out6)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!out6 || n < 1 || m < 1) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "bad arguments");
+    const Geometry g = geometry(ctx, n, m, vec ? 1 : 0);
+    out6[0] = ctx->num_sms;
+    out6[1] = g.row_grid;
+    out6[2] = g.splits;
+    out6[3] = (m + kColStrip - 1) / kColStrip;
+    out6[4] = g.step_grid;
+    out6[5] = g.stat_grid;
+    return ACCSINK_OK;
+}
+
+}  // extern "C"

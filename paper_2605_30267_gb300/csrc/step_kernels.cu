@@ -1,0 +1,706 @@
+// O(n + m) kernels around the two streaming passes: problem set-up, the fused
+// per-iteration step of Algorithm 1/2, and operand preparation for the
+// single-pass entry points. They are cooperative launches (every block is
+// resident) that separate their phases with the bounded grid barrier of
+// accsink_internal.cuh; every block reduces the block partials itself in the
+// same fixed order, so all blocks agree bit-for-bit on every scalar and the
+// whole solve is deterministic. FP64 is used for the marginal-error and
+// dual-objective sums and for the Theorem 4 stability test.
+#include <float.h>
+
+#include "accsink_internal.cuh"
+
+namespace accsink {
+
+constexpr int kVecNT = 256;
+constexpr uint64_t kBarrierLimitNs = 2000000000ull;   // 2 s per barrier
+
+// Sum K per-thread doubles over the block; thread k < K writes the k-th sum
+// to out[k]. Deterministic (fixed shuffle tree, fixed warp order).
+template <int K>
+__device__ __forceinline__ void block_sum_store(double (&v)[K], double *out)
+{
+    __shared__ double sh[K][kVecNT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int q = 0; q < kVecNT / 32; ++q) s += sh[threadIdx.x][q];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ double warp_min_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_max_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block min/max of one double each; thread 0 writes (min, max) to out[0..1].
+__device__ __forceinline__ void block_minmax_store(double mn, double mx, double *out)
+{
+    __shared__ double sh[2][kVecNT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    mn = warp_min_d(mn);
+    mx = warp_max_d(mx);
+    if (lane == 0) { sh[0][wid] = mn; sh[1][wid] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int q = 1; q < kVecNT / 32; ++q) { mn = fmin(mn, sh[0][q]); mx = fmax(mx, sh[1][q]); }
+        out[0] = mn;
+        out[1] = mx;
+    }
+    __syncthreads();
+}
+
+// Totals of K consecutive slots of every block's partial record (stride
+// kPartStride), computed identically by every block; result broadcast via
+// shared memory into tot[0..K-1]. op: 0 sum, 1 min, 2 max (per slot).
+template <int K>
+__device__ __forceinline__ void grid_totals(const double *part, int nblocks, int slot0,
+                                            const int (&op)[K], double (&tot)[K])
+{
+    __shared__ double sh[K];
+    if (threadIdx.x < K) {
+        const int k = threadIdx.x;
+        double acc = (op[k] == 0) ? 0.0 : (op[k] == 1 ? DBL_MAX : -DBL_MAX);
+        for (int b = 0; b < nblocks; ++b) {
+            const double v = *(volatile const double *)&part[(int64_t)b * kPartStride + slot0 + k];
+            acc = (op[k] == 0) ? acc + v : (op[k] == 1 ? fmin(acc, v) : fmax(acc, v));
+        }
+        sh[k] = acc;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) tot[k] = sh[k];
+    __syncthreads();
+}
+
+// Reduction of the cost-statistics partials (max C, min C, max|C|, #bad).
+__device__ __forceinline__ void cost_totals(const double *statpart, int nstat, double &cmax,
+                                            double &cmin, double &cabs, double &bad)
+{
+    __shared__ double sh[4];
+    if (threadIdx.x == 0) {
+        double a0 = -DBL_MAX, a1 = DBL_MAX, a2 = 0.0, a3 = 0.0;
+        for (int b = 0; b < nstat; ++b) {
+            a0 = fmax(a0, statpart[4 * b + 0]);
+            a1 = fmin(a1, statpart[4 * b + 1]);
+            a2 = fmax(a2, statpart[4 * b + 2]);
+            a3 += statpart[4 * b + 3];
+        }
+        sh[0] = a0; sh[1] = a1; sh[2] = a2; sh[3] = a3;
+    }
+    __syncthreads();
+    cmax = sh[0]; cmin = sh[1]; cabs = sh[2]; bad = sh[3];
+    __syncthreads();
+}
+
+// Writes G_j + gamma_j = g_j + shift_g as (hi, gamma * k_hi).
+__device__ __forceinline__ void write_G(const Work &w, int j, double gshift, float kh)
+{
+    const float hi = (float)gshift;
+    const float lo = (float)(gshift - (double)hi);
+    w.G[j] = hi;
+    w.Gk[j] = lo * kh;
+}
+
+// ------------------------------------------------------------------------
+// Set-up of a solve. The host has written eps_user, tol, mu, method, ... into
+// the state (barrier = 0). Validates and normalises the marginals, derives
+// eps_c and the operand shifts, and writes x_0 = w_0 = 0 and G for x_0.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat,
+                                                 const double *a_in, const double *b_in,
+                                                 int scale_max)
+{
+    DevState *st = w.st;
+    const int tid = blockIdx.x * kVecNT + threadIdx.x;
+    const int nthr = gridDim.x * kVecNT;
+    const uint32_t nb = gridDim.x;
+
+    double cmax, cmin, cabs, bad;
+    cost_totals(w.statpart, nstat, cmax, cmin, cabs, bad);
+
+    // phase A: sums and validity of a, b
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // sum a, sum b, #a<=0, #b<=0, #nonfinite
+    for (int i = tid; i < n; i += nthr) {
+        const double ai = a_in[i];
+        v[0] += ai;
+        if (!(ai > 0.0)) v[2] += 1.0;
+        if (!isfinite(ai)) v[4] += 1.0;
+    }
+    for (int j = tid; j < m; j += nthr) {
+        const double bj = b_in[j];
+        v[1] += bj;
+        if (!(bj > 0.0)) v[3] += 1.0;
+        if (!isfinite(bj)) v[4] += 1.0;
+    }
+    block_sum_store<6>(v, w.steppart + (int64_t)blockIdx.x * kPartStride);
+    if (!grid_barrier(st, nb, kBarrierLimitNs)) return;
+    double t[6];
+    const int ops6[6] = {0, 0, 0, 0, 0, 0};
+    grid_totals<6>(w.steppart, nb, 0, ops6, t);
+    int status = 0;
+    if (bad > 0.0 || t[4] > 0.0) status = 3;           // ACCSINK_ERR_NONFINITE
+    else if (t[2] > 0.0 || t[3] > 0.0) status = 2;     // ACCSINK_ERR_NONPOSITIVE_MARGINAL
+    else if (scale_max && !(cmax > 0.0)) status = 1;   // cannot scale by max C <= 0
+    if (status != 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->status = status;
+            st->done = 1;
+            st->cmax = cmax;
+        }
+        return;
+    }
+    const double sa = t[0], sb = t[1];
+    const double cost_div = scale_max ? cmax : 1.0;
+    const double eps_c = st->eps_user * cost_div;
+    const double k = kLog2e / eps_c;
+    const float kh = (float)k;
+    const float kl = (float)(k - (double)kh);
+
+    // phase B: normalised marginals, logs, zero iterate
+    double mnla = DBL_MAX;
+    for (int i = tid; i < n; i += nthr) {
+        const double ai = a_in[i] / sa;
+        w.a[i] = ai;
+        w.loga[i] = log(ai);
+        mnla = fmin(mnla, w.loga[i]);
+    }
+    for (int j = tid; j < m; j += nthr) {
+        const double bj = b_in[j] / sb;
+        w.b[j] = bj;
+        w.logb[j] = log(bj);
+        w.x[j] = 0.0;
+        w.x_prev[j] = 0.0;
+        w.w[j] = 0.0;
+        w.p_prev[j] = 0.0;
+        w.D_prev[j] = bj;
+    }
+    // block min of log a into slot 6 (slots 0..5 are still being read)
+    {
+        double dummy = -DBL_MAX;
+        __shared__ double shm[2];
+        block_minmax_store(mnla, dummy, shm);
+        if (threadIdx.x == 0) w.steppart[(int64_t)blockIdx.x * kPartStride + 6] = shm[0];
+    }
+    if (!grid_barrier(st, 2 * nb, kBarrierLimitNs)) return;
+    double t1[1];
+    const int ops1[1] = {1};
+    grid_totals<1>(w.steppart, nb, 6, ops1, t1);
+    const double min_loga = t1[0];
+    const double log_m = log((double)m);
+    // x_0 = 0: G = shift_g = max|C| makes G >= |C|; F_i >= max|C| follows from
+    // eps_c u_i >= eps_c min log a - eps_c max x + min C - eps_c log m.
+    const double shift_g = cabs;
+    const double shift_f = cabs - (eps_c * min_loga - 0.0 + cmin - eps_c * log_m);
+    for (int j = tid; j < m; j += nthr) write_G(w, j, shift_g, kh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->eps_c = eps_c;
+        st->inv_eps_c = 1.0 / eps_c;
+        st->cost_div = cost_div;
+        st->cmax = cmax; st->cmin = cmin; st->cabs = cabs;
+        st->sum_a = sa; st->sum_b = sb;
+        st->min_loga = min_loga;
+        st->log_m = log_m;
+        st->shift_g = shift_g;
+        st->shift_f = shift_f;
+        st->k_hi = kh;
+        st->k_lo = kl;
+        st->steps = 0; st->stages = 0; st->failures = 0; st->j_in_stage = 0;
+        st->first = 1; st->done = 0; st->status = 0;
+        st->err = INFINITY; st->dual = 0.0; st->kl_prev = 0.0;
+        st->mode = STEP_SOLVE;
+    }
+}
+
+cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
+                        const double *b_in, int scale_max, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_init, w, cv.n, cv.m, (int)w.nstat, a_in, b_in, scale_max);
+}
+
+// ------------------------------------------------------------------------
+// The per-iteration step, run after the row and column passes at x (the
+// iterate being evaluated, x_{k+1} in Algorithm 1's indexing):
+//   P1  merge the column partials -> ell_j = LSE_i(u_i - C_ij/eps),
+//       p_j = log(c_j/b_j) = x_j + ell_j - log b_j, raw_j = x_j - p_j
+//       (v-update), c_j - b_j = b_j expm1(p_j), D_j = (c_j - b_j)/p_j
+//       (eq. D), KL term b_j (e^p - 1 - p); block partials of the L1 error,
+//       sum raw, KL, <b, x>, Cond 1 lhs and Cond 2 lhs (Theorem 4).
+//   P2  S(x) = raw - mean(raw) (Sec. 3); Algorithm 1 w-update
+//       w+ = (w + (alpha^2 - 2) x + 2 S(x)) / (1 + alpha); Cond 2 rhs.
+//   P3  stop test (Sec. 5 eq. l1tol), stability verdict and gate, homotopy
+//       (Algorithm 2), next x = (w+ + S(x)) / (1 + alpha_next) (or S(x)
+//       for plain Sinkhorn); block min/max of the new x.
+//   P4  operand shifts and G for the next row pass; block 0 records the
+//       scalars, the history entry and the graph loop condition.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
+                                                 cudaGraphConditionalHandle h,
+                                                 double *c_out, double *s_out)
+{
+    DevState *st = w.st;
+    // Any early exit must end the graph's while loop, or it would spin on
+    // no-op launches: block 0 clears the condition before returning.
+    auto bail = [&]() {
+        if (blockIdx.x == 0 && threadIdx.x == 0 && st->use_cond) cudaGraphSetConditional(h, 0u);
+    };
+    if (*(volatile int32_t *)&st->done) { bail(); return; }
+    const int tid = blockIdx.x * kVecNT + threadIdx.x;
+    const int nthr = gridDim.x * kVecNT;
+    const uint32_t nb = gridDim.x;
+
+    const int method = st->method, first = st->first, stab = st->stability;
+    const int mode = st->mode, splits = st->col_splits;
+    const double mu = st->mu;
+    const double alpha = sqrt(2.0 * mu);
+    const double inv_alpha = 1.0 / alpha;
+    const double inv_eps = st->inv_eps_c;
+    const double shift_f = st->shift_f;
+    const float kh = st->k_hi, kl = st->k_lo;
+    const bool is_acc = (method == 1) && (mode == STEP_SOLVE);
+    const bool check = is_acc && !first && stab != 0;
+    const bool wupd = is_acc && !first;
+
+    // ---- P1
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l
+    for (int j = tid; j < m; j += nthr) {
+        float R = w.colpart[j].x;
+        for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
+        double S = 0.0;
+        for (int q = 0; q < splits; ++q) {
+            const float2 pr = w.colpart[(int64_t)q * m + j];
+            S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
+        }
+        const double ell = log(S) + ((double)R - shift_f) * inv_eps;
+        const double xj = w.x[j];
+        const double bj = w.b[j];
+        const double del = xj + ell - w.logb[j];
+        const double raw = xj - del;
+        const double e = expm1(del);
+        const double xi = bj * e;
+        const double D1 = (del != 0.0) ? xi / del : bj;
+        v[0] += fabs(xi);
+        v[1] += raw;
+        v[2] += bj * (e - del);
+        v[3] += bj * xj;
+        if (check) {
+            const double p0 = w.p_prev[j];
+            const double v0 = w.w[j] * inv_alpha - w.x_prev[j];
+            v[4] += p0 * p0 * D1;
+            v[5] += v0 * v0 * (D1 - w.D_prev[j]);
+        }
+        w.raw[j] = raw;
+        w.D1[j] = D1;
+        w.del[j] = del;
+        if (c_out) c_out[j] = bj + xi;
+    }
+    block_sum_store<6>(v, w.steppart + (int64_t)blockIdx.x * kPartStride);
+    if (!grid_barrier(st, nb, kBarrierLimitNs)) { bail(); return; }
+
+    // ---- P2
+    double t[6];
+    const int ops6[6] = {0, 0, 0, 0, 0, 0};
+    grid_totals<6>(w.steppart, nb, 0, ops6, t);
+    const double err = t[0];
+    const double rbar = t[1] / (double)m;
+    double sum_au = 0.0;
+    {
+        __shared__ double sh_au;
+        if (threadIdx.x == 0) {
+            double s = 0.0;
+            for (int b = 0; b < st->row_grid; ++b) s += w.rowpart[2 * b];
+            sh_au = s;
+        }
+        __syncthreads();
+        sum_au = sh_au;
+    }
+    const double dual = st->eps_user * (sum_au + t[3] - 1.0);
+    if (mode == STEP_MAP) {
+        for (int j = tid; j < m; j += nthr) s_out[j] = st->eps_user * (w.raw[j] - rbar);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->err = err;
+            st->dual = dual;
+            st->done = 1;
+        }
+        return;
+    }
+    double v2[1] = {0.0};
+    if (wupd) {
+        const double a2 = alpha * alpha - 2.0;
+        for (int j = tid; j < m; j += nthr) {
+            const double s = w.raw[j] - rbar;
+            const double xj = w.x[j];
+            const double w1 = (w.w[j] + a2 * xj + 2.0 * s) / (1.0 + alpha);
+            w.w1[j] = w1;
+            const double v1 = w1 * inv_alpha - xj;
+            v2[0] += v1 * v1 * w.D1[j];
+        }
+    }
+    {
+        __shared__ double shv[1];
+        block_sum_store<1>(v2, shv);
+        if (threadIdx.x == 0) w.steppart[(int64_t)blockIdx.x * kPartStride + 6] = shv[0];
+    }
+    if (!grid_barrier(st, 2 * nb, kBarrierLimitNs)) { bail(); return; }
+
+    // ---- P3
+    double t2[1];
+    const int ops1[1] = {0};
+    grid_totals<1>(w.steppart, nb, 6, ops1, t2);
+    const double c1 = t[4], c2l = t[5], c2r_sum = t2[0];
+    const double kappa1 = (4.0 - alpha * alpha - 2.0 * sqrt(alpha)) /
+                          (2.0 * alpha * (1.0 + alpha) * (1.0 + alpha));
+    const double c1r = kappa1 * st->kl_prev;
+    const double c2r = pow(alpha, 1.5) * c2r_sum;
+    int stab_bits = 0;
+    if (check) stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
+    const bool gate = (stab == 2) && (stab_bits != 0);
+    const int steps_new = st->steps + 1;
+    const bool nonfinite = !isfinite(err);
+    const bool converged = err < st->tol;
+    const bool stop = converged || nonfinite || steps_new >= st->max_steps;
+
+    double mu_new = mu;
+    int ms = st->m_stage, jst = st->j_in_stage, stages = st->stages;
+    bool stage_end = false;
+    if (wupd) {
+        jst += 1;
+        if (jst == ms) {
+            stage_end = true;
+            mu_new = mu / 2.0;
+            ms = (int)floor(sqrt(2.0) * (double)ms) + 1;
+            jst = 0;
+            stages += 1;
+        }
+    }
+    const double alpha_new = sqrt(2.0 * mu_new);
+    const double ratio = (stage_end && st->carry == 0) ? alpha_new / alpha : 1.0;
+    double xmn = DBL_MAX, xmx = -DBL_MAX;
+    if (!stop) {
+        for (int j = tid; j < m; j += nthr) {
+            const double s = w.raw[j] - rbar;
+            const double xj = w.x[j];
+            double xn;
+            if (is_acc) {
+                double w1 = wupd ? (gate ? alpha * xj : w.w1[j]) : w.w[j];
+                w1 *= ratio;
+                xn = (w1 + s) / (1.0 + alpha_new);
+                w.w[j] = w1;
+            } else {
+                xn = s;
+            }
+            w.x_prev[j] = xj;
+            w.x[j] = xn;
+            w.p_prev[j] = w.del[j];
+            w.D_prev[j] = w.D1[j];
+            xmn = fmin(xmn, xn);
+            xmx = fmax(xmx, xn);
+        }
+    }
+    {
+        __shared__ double shm[2];
+        block_minmax_store(xmn, xmx, shm);
+        if (threadIdx.x == 0) {
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 0] = shm[0];
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 1] = shm[1];
+        }
+    }
+    if (!grid_barrier(st, 3 * nb, kBarrierLimitNs)) { bail(); return; }
+
+    // ---- P4
+    double t3[2];
+    const int ops2[2] = {1, 2};
+    grid_totals<2>(w.steppart, nb, 0, ops2, t3);
+    const double eps_c = st->eps_c;
+    double shift_g = 0.0, shift_fn = 0.0;
+    if (!stop) {
+        shift_g = st->cabs - eps_c * t3[0];
+        shift_fn = st->cabs - (eps_c * st->min_loga - eps_c * t3[1] + st->cmin - eps_c * st->log_m);
+        for (int j = tid; j < m; j += nthr) write_G(w, j, eps_c * w.x[j] + shift_g, kh);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const int e = st->steps;
+        if (e < st->hist_cap) {
+            w.h_err[e] = err;
+            w.h_dual[e] = dual;
+            w.h_mu[e] = (is_acc && !first) ? mu : 0.0;
+            w.h_stab[e] = stab_bits;
+            w.h_cond[4 * e + 0] = check ? c1 : 0.0;
+            w.h_cond[4 * e + 1] = check ? c1r : 0.0;
+            w.h_cond[4 * e + 2] = check ? c2l : 0.0;
+            w.h_cond[4 * e + 3] = check ? c2r : 0.0;
+        }
+        st->last_cond[0] = c1; st->last_cond[1] = c1r;
+        st->last_cond[2] = c2l; st->last_cond[3] = c2r;
+        st->steps = steps_new;
+        st->err = err;
+        st->dual = dual;
+        st->kl_prev = t[2];
+        st->first = 0;
+        if (stab_bits) st->failures += 1;
+        if (wupd) {
+            st->mu = mu_new;
+            st->m_stage = ms;
+            st->j_in_stage = jst;
+            st->stages = stages;
+        }
+        if (stop) {
+            st->done = 1;
+            st->status = nonfinite ? 3 : (converged ? 0 : 7);
+        } else {
+            st->shift_g = shift_g;
+            st->shift_f = shift_fn;
+        }
+        if (st->use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+    }
+}
+
+cudaError_t launch_step(const CostView &cv, const Work &w, int grid, cudaGraphConditionalHandle h,
+                        cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    double *nul = nullptr;
+    return cudaLaunchKernelEx(&cfg, k_step, w, cv.n, cv.m, h, nul, nul);
+}
+
+cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double *c_out,
+                            double *s_out, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaGraphConditionalHandle h = 0;
+    return cudaLaunchKernelEx(&cfg, k_step, w, cv.n, cv.m, h, c_out, s_out);
+}
+
+// ------------------------------------------------------------------------
+// Operand preparation for the single-pass entry points (no normalisation,
+// no solve state). prep_g: given g (cost units) and a (and optionally b),
+// writes x = g/eps, log a, the shifts and G. prep_f: given f, writes F.
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nstat,
+                                                   const double *g, const double *a_in,
+                                                   const double *b_in, double eps)
+{
+    DevState *st = w.st;
+    const int tid = blockIdx.x * kVecNT + threadIdx.x;
+    const int nthr = gridDim.x * kVecNT;
+    const uint32_t nb = gridDim.x;
+    double cmax, cmin, cabs, bad;
+    cost_totals(w.statpart, nstat, cmax, cmin, cabs, bad);
+    double gmn = DBL_MAX, gmx = -DBL_MAX, lmn = DBL_MAX;
+    for (int j = tid; j < m; j += nthr) {
+        const double gj = g[j];
+        gmn = fmin(gmn, gj);
+        gmx = fmax(gmx, gj);
+        w.x[j] = gj / eps;
+        if (b_in) {
+            w.b[j] = b_in[j];
+            w.logb[j] = log(b_in[j]);
+        }
+    }
+    for (int i = tid; i < n; i += nthr) {
+        const double ai = a_in ? a_in[i] : 1.0;
+        w.a[i] = ai;
+        w.loga[i] = log(ai);
+        lmn = fmin(lmn, w.loga[i]);
+    }
+    {
+        __shared__ double sh[2];
+        block_minmax_store(gmn, gmx, sh);
+        double dummy = -DBL_MAX;
+        __shared__ double sh2[2];
+        block_minmax_store(lmn, dummy, sh2);
+        if (threadIdx.x == 0) {
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 0] = sh[0];
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 1] = sh[1];
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 2] = sh2[0];
+        }
+    }
+    if (!grid_barrier(st, nb, kBarrierLimitNs)) return;
+    double t[3];
+    const int ops[3] = {1, 2, 1};
+    grid_totals<3>(w.steppart, nb, 0, ops, t);
+    const double k = kLog2e / eps;
+    const float kh = (float)k;
+    const float kl = (float)(k - (double)kh);
+    const double shift_g = cabs - t[0];
+    const double shift_f = cabs - (eps * t[2] - t[1] + cmin - eps * log((double)m));
+    for (int j = tid; j < m; j += nthr) write_G(w, j, g[j] + shift_g, kh);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->eps_c = eps;
+        st->inv_eps_c = 1.0 / eps;
+        st->eps_user = eps;
+        st->cost_div = 1.0;
+        st->cmax = cmax; st->cmin = cmin; st->cabs = cabs;
+        st->nonfinite = (bad > 0.0) ? 1 : 0;
+        st->shift_g = shift_g;
+        st->shift_f = shift_f;
+        st->k_hi = kh;
+        st->k_lo = kl;
+        st->done = 0;
+        st->status = 0;
+        st->first = 1;
+        st->mode = STEP_MAP;
+    }
+}
+
+cudaError_t launch_prep_g(const CostView &cv, const Work &w, int grid, const double *g,
+                          const double *a_in, double eps, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const double *b_in = w.b_src;
+    return cudaLaunchKernelEx(&cfg, k_prep_g, w, cv.n, cv.m, (int)w.nstat, g, a_in, b_in, eps);
+}
+
+__global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nstat,
+                                                   const double *f, double eps)
+{
+    DevState *st = w.st;
+    const int tid = blockIdx.x * kVecNT + threadIdx.x;
+    const int nthr = gridDim.x * kVecNT;
+    const uint32_t nb = gridDim.x;
+    double cmax, cmin, cabs, bad;
+    cost_totals(w.statpart, nstat, cmax, cmin, cabs, bad);
+    double fmn = DBL_MAX, fmx = -DBL_MAX;
+    for (int i = tid; i < n; i += nthr) {
+        fmn = fmin(fmn, f[i]);
+        fmx = fmax(fmx, f[i]);
+    }
+    {
+        __shared__ double sh[2];
+        block_minmax_store(fmn, fmx, sh);
+        if (threadIdx.x == 0) {
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 0] = sh[0];
+            w.steppart[(int64_t)blockIdx.x * kPartStride + 1] = sh[1];
+        }
+    }
+    if (!grid_barrier(st, nb, kBarrierLimitNs)) return;
+    double t[1];
+    const int ops[1] = {1};
+    grid_totals<1>(w.steppart, nb, 0, ops, t);
+    const double k = kLog2e / eps;
+    const float kh = (float)k;
+    const float kl = (float)(k - (double)kh);
+    const double shift_f = cabs - t[0];
+    for (int i = tid; i < n; i += nthr) {
+        const double F = f[i] + shift_f;
+        const float Fh = (float)F;
+        const float Fl = (float)(F - (double)Fh);
+        w.FF[i] = make_float2(Fh, Fl * kh);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->eps_c = eps;
+        st->inv_eps_c = 1.0 / eps;
+        st->eps_user = eps;
+        st->cmax = cmax; st->cmin = cmin; st->cabs = cabs;
+        st->nonfinite = (bad > 0.0) ? 1 : 0;
+        st->shift_f = shift_f;
+        st->k_hi = kh;
+        st->k_lo = kl;
+        st->done = 0;
+        st->status = 0;
+    }
+}
+
+cudaError_t launch_prep_f(const CostView &cv, const Work &w, int grid, const double *f,
+                          double eps, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_prep_f, w, cv.n, cv.m, (int)w.nstat, f, eps);
+}
+
+__global__ void k_scale_out(const double *src, double scale, double *dst, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[i] * scale;
+}
+
+cudaError_t launch_scale_out(const double *src, double scale, double *dst, int n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    k_scale_out<<<(n + 255) / 256, 256, 0, s>>>(src, scale, dst, n);
+    return cudaGetLastError();
+}
+
+// ell_j = log S_j + (R_j - shift_f) / eps from the column-pass partials.
+__global__ void k_col_finish_lse(Work w, int m, double *ell_out)
+{
+    const DevState *st = w.st;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= m) return;
+    const int splits = st->col_splits;
+    const float kh = st->k_hi, kl = st->k_lo;
+    float R = w.colpart[j].x;
+    for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
+    double S = 0.0;
+    for (int q = 0; q < splits; ++q) {
+        const float2 pr = w.colpart[(int64_t)q * m + j];
+        S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
+    }
+    ell_out[j] = log(S) + ((double)R - st->shift_f) * st->inv_eps_c;
+}
+
+cudaError_t launch_col_finish_lse(const Work &w, int m, double *ell_out, cudaStream_t s)
+{
+    k_col_finish_lse<<<(m + 255) / 256, 256, 0, s>>>(w, m, ell_out);
+    return cudaGetLastError();
+}
+
+}  // namespace accsink

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+Tolerances (from the arithmetic of the kernels):
+  * one pass: |delta u| (natural-log units) <= 2e-6, i.e. f within 2e-6 eps;
+  * whole solves: potentials within 1e-3 eps max-abs after centring, <C,P>
+    within 1e-5 relative, step counts within 2% (or one step), FP64-truth
+    column L1 <= tol (1 + 0.05) and row L1 at the FP32 floor (<= 2e-7).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_30267_gb300 import binding as B
+from paper_2605_30267_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+PASS_TOL = 2e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(x, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(DEV)
+
+
+def rand_dense(seed, n, m, scale=1.0):
+    g = np.random.default_rng(seed)
+    C = (scale * g.random((n, m))).astype(np.float32)
+    a = W.dirichlet1(g, n)
+    b = W.dirichlet1(g, m)
+    return C, a, b
+
+
+def potential_like(seed, m, eps):
+    """A column potential of the size real solves produce (a few cost units)."""
+    g = np.random.default_rng(seed)
+    return 0.3 * g.standard_normal(m) + 0.05 * g.random(m)
+
+
+SHAPES = [(1, 1), (1, 7), (9, 1), (3, 5), (37, 129), (257, 1000), (513, 2049), (1000, 1003)]
+
+
+@pytest.mark.parametrize("n,m", SHAPES)
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+def test_row_pass_matches_oracle(ctx, n, m, eps):
+    C, a, b = rand_dense(n * 7 + m, n, m)
+    g = potential_like(n + 3 * m, m, eps)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    prob = B.problem_dense(to_dev(C), to_dev(a), to_dev(b))
+    ctx.accsink_row_pass(prob, eps, to_dev(g), f)
+    torch.cuda.synchronize()
+    ref = eps * O.row_pass(O.Cost(C=C), eps, np.log(a), g / eps)
+    err = np.abs(f.cpu().numpy() - ref).max() / eps
+    assert err <= PASS_TOL, err
+
+
+@pytest.mark.parametrize("n,m", SHAPES)
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+def test_col_lse_matches_oracle(ctx, n, m, eps):
+    C, a, b = rand_dense(n * 11 + m, n, m)
+    f = potential_like(2 * n + m, n, eps)
+    ell = torch.empty(m, dtype=torch.float64, device=DEV)
+    prob = B.problem_dense(to_dev(C))
+    ctx.accsink_col_lse(prob, eps, to_dev(f), ell)
+    torch.cuda.synchronize()
+    ref = O.col_lse(O.Cost(C=C), eps, f / eps)
+    err = np.abs(ell.cpu().numpy() - ref).max()
+    assert err <= PASS_TOL, err
+
+
+@pytest.mark.parametrize("layout", ["ldc_odd", "misaligned"])
+def test_scalar_path_matches_vector_path(ctx, layout):
+    n, m, eps = 131, 517, 1e-2
+    C, a, b = rand_dense(5, n, m)
+    if layout == "ldc_odd":
+        big = torch.zeros((n, m + 3), dtype=torch.float32, device=DEV)
+        big[:, :m] = to_dev(C)
+        Cd = big[:, :m]
+    else:
+        flat = torch.zeros(n * m + 1, dtype=torch.float32, device=DEV)
+        flat[1:] = to_dev(C).reshape(-1)
+        Cd = flat[1:].view(n, m)
+    g = potential_like(6, m, eps)
+    f1 = torch.empty(n, dtype=torch.float64, device=DEV)
+    f2 = torch.empty(n, dtype=torch.float64, device=DEV)
+    ctx.accsink_row_pass(B.problem_dense(Cd, to_dev(a)), eps, to_dev(g), f1)
+    ctx.accsink_row_pass(B.problem_dense(to_dev(C), to_dev(a)), eps, to_dev(g), f2)
+    torch.cuda.synchronize()
+    ref = eps * O.row_pass(O.Cost(C=C), eps, np.log(a), g / eps)
+    assert np.abs(f1.cpu().numpy() - ref).max() / eps <= PASS_TOL
+    assert np.abs(f2.cpu().numpy() - ref).max() / eps <= PASS_TOL
+    ell1 = torch.empty(m, dtype=torch.float64, device=DEV)
+    ctx.accsink_col_lse(B.problem_dense(Cd), eps, f2, ell1)
+    torch.cuda.synchronize()
+    ref2 = O.col_lse(O.Cost(C=C), eps, f2.cpu().numpy() / eps)
+    assert np.abs(ell1.cpu().numpy() - ref2).max() <= PASS_TOL
+
+
+@pytest.mark.parametrize("n,m", [(3, 5), (257, 1000), (1000, 1003)])
+@pytest.mark.parametrize("eps", [1e-1, 1e-3])
+def test_sinkhorn_map_matches_oracle(ctx, n, m, eps):
+    C, a, b = rand_dense(n + m, n, m)
+    g = potential_like(n * m, m, eps)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    c = torch.empty(m, dtype=torch.float64, device=DEV)
+    s = torch.empty(m, dtype=torch.float64, device=DEV)
+    err = ctx.accsink_sinkhorn_map(B.problem_dense(to_dev(C), to_dev(a), to_dev(b)), eps,
+                                   to_dev(g), f, c, s)
+    rerr, ru, rc, rs = O.sinkhorn_map(O.Cost(C=C), eps, a, b, g / eps)
+    assert np.abs(f.cpu().numpy() / eps - ru).max() <= PASS_TOL
+    np.testing.assert_allclose(c.cpu().numpy(), rc, rtol=5 * PASS_TOL, atol=0)
+    assert np.abs(s.cpu().numpy() / eps - rs).max() <= 2 * PASS_TOL
+    assert abs(err - rerr) <= 5 * PASS_TOL * max(1.0, rerr)
+
+
+def test_transport_cost_matches_oracle(ctx):
+    n, m, eps = 300, 211, 2e-2
+    C, a, b = rand_dense(77, n, m)
+    ref = O.solve(O.Cost(C=C), a, b, eps, tol=1e-9, method=O.PLAIN)
+    ev = O.evaluate(O.Cost(C=C), eps, ref["a"], ref["b"], ref["f"], ref["g"])
+    out = ctx.accsink_transport_cost(B.problem_dense(to_dev(C)), eps, to_dev(ref["f"]),
+                                     to_dev(ref["g"]))
+    assert abs(out - ev["transport_cost"]) <= 1e-6 * abs(ev["transport_cost"])
+
+
+# ---------------------------------------------------------------- solves --
+
+def gpu_solve(ctx, C, a, b, eps, tol=1e-6, method=B.ACC, scale=False, **kw):
+    n, m = C.shape
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    g = torch.empty(m, dtype=torch.float64, device=DEV)
+    p = B.default_params(eps=eps, tol=tol, method=method, **kw)
+    res = ctx.accsink_solve(B.problem_dense(to_dev(C), to_dev(a), to_dev(b), scale), p, f, g)
+    return f.cpu().numpy(), g.cpu().numpy(), B.result_dict(res)
+
+
+def check_solve(ctx, C, a, b, eps, tol, method, scale=False, cost=None, **kw):
+    f, g, res = gpu_solve(ctx, C, a, b, eps, tol, method, scale, **kw)
+    cost = cost or O.Cost(C=C, scale_to_max=scale)
+    ref = O.solve(cost, a, b, eps, tol, method=O.ACC if method == B.ACC else O.PLAIN,
+                  carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
+                  stability=kw.get("stability", B.STAB_REPORT))
+    assert res["status"] == 0, res
+    assert ref["status"] == O.CONVERGED
+    # steps within 2% (at least one step of slack)
+    rs, gs = ref["sinkhorn_steps"], res["sinkhorn_steps"]
+    assert abs(gs - rs) <= max(1, int(0.02 * rs)), (gs, rs)
+    # potentials after centring
+    sh = g.mean() - ref["g"].mean()
+    dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
+    assert dpot <= 1e-3 * eps, dpot
+    # FP64 truth of the GPU's potentials
+    ev = O.evaluate(cost, eps, ref["a"], ref["b"], f, g)
+    assert ev["col_l1"] <= tol * 1.05, ev
+    assert ev["row_l1"] <= 2e-7, ev
+    evr = O.evaluate(cost, eps, ref["a"], ref["b"], ref["f"], ref["g"])
+    assert abs(res["transport_cost"] - evr["transport_cost"]) <= 1e-5 * abs(evr["transport_cost"])
+    assert abs(res["dual_objective"] - ref["dual"]) <= 1e-5 * max(1e-3, abs(ref["dual"]))
+    return f, g, res, ref
+
+
+@pytest.mark.parametrize("method", [B.ACC, B.PLAIN])
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+@pytest.mark.parametrize("n,m", [(64, 64), (200, 333), (1000, 1000)])
+def test_solve_matches_oracle(ctx, method, eps, n, m):
+    pr = W.gmm_stored_cost_problem(seed=n + m, n=n, m=m, eps=eps)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], eps, 1e-6, method)
+
+
+def test_small_pointcloud_problem_256(ctx):
+    pr = W.small_pointcloud_problem(0)
+    for method in (B.ACC, B.PLAIN):
+        check_solve(ctx, pr["C"], pr["a"], pr["b"], pr["eps"], pr["tol"], method)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 9), (9, 1), (2, 2), (5, 3)])
+def test_tiny_solves(ctx, n, m):
+    C, a, b = rand_dense(n * 10 + m, n, m)
+    for method in (B.ACC, B.PLAIN):
+        check_solve(ctx, C, a, b, 5e-2, 1e-8, method)
+
+
+def test_max_to_one_scaling(ctx):
+    pr = W.gmm_stored_cost_problem(seed=9, n=150, m=120, eps=1e-2)
+    C = (pr["C"] * np.float32(3.5)).astype(np.float32)
+    f, g, res, ref = check_solve(ctx, C, pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, scale=True)
+    assert abs(res["cost_max"] - float(C.max())) == 0.0
+
+
+def test_carry_w_and_gate_modes(ctx):
+    pr = W.gmm_stored_cost_problem(seed=10, n=120, m=100, eps=1e-2)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, carry=B.CARRY_W)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, stability=B.STAB_GATE)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, stability=B.STAB_OFF)
+
+
+def test_history_tracks_oracle(ctx):
+    pr = W.gmm_stored_cost_problem(seed=12, n=200, m=180, eps=1e-2)
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, history=5000)
+    h = ctx.accsink_get_history(5000)
+    ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-2, 1e-6, method=O.ACC, history=5000)
+    rh = ref["history"]
+    k = min(len(h["err"]), len(rh["err"]))
+    assert k == res["sinkhorn_steps"]
+    np.testing.assert_array_equal(h["mu"][:k], rh["mu"][:k])
+    # marginal error trajectories agree while well above the FP32 floor
+    sel = rh["err"][:k] > 1e-4
+    np.testing.assert_allclose(h["err"][:k][sel], rh["err"][:k][sel], rtol=1e-3)
+    np.testing.assert_allclose(h["dual"][:k], rh["dual"][:k], rtol=1e-6, atol=1e-9)
+    agree = np.mean(h["stab"][:k] == rh["stab"][:k])
+    assert agree >= 0.95, agree
+
+
+def test_graph_and_host_loop_are_bitwise_identical(ctx):
+    pr = W.gmm_stored_cost_problem(seed=13, n=300, m=257, eps=1e-2)
+    f1, g1, r1 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, use_graph=1)
+    f2, g2, r2 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, use_graph=0)
+    f3, g3, r3 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, use_graph=1)
+    assert r1["sinkhorn_steps"] == r2["sinkhorn_steps"] == r3["sinkhorn_steps"]
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(g1, g2)
+    np.testing.assert_array_equal(f1, f3)
+    np.testing.assert_array_equal(g1, g3)
+
+
+def test_maxiter_returns_valid_potentials(ctx):
+    pr = W.gmm_stored_cost_problem(seed=14, n=100, m=90, eps=1e-3)
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-3, 1e-9, B.ACC,
+                          max_sinkhorn_steps=7)
+    assert res["status"] == B.ERR_MAXITER and res["sinkhorn_steps"] == 7
+    ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-3, 1e-9, method=O.ACC, max_steps=7)
+    assert ref["status"] == O.MAXITER
+    sh = g.mean() - ref["g"].mean()
+    assert np.abs(g - sh - ref["g"]).max() <= 1e-3 * 1e-3
+
+
+def test_solve_host_matches_device_solve(ctx):
+    pr = W.gmm_stored_cost_problem(seed=15, n=220, m=190, eps=1e-2)
+    f1, g1, r1 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC)
+    f2 = np.empty(220)
+    g2 = np.empty(190)
+    r2 = ctx.accsink_solve_host(pr["C"], pr["a"], pr["b"], B.default_params(eps=1e-2), f2, g2)
+    assert r2.sinkhorn_steps == r1["sinkhorn_steps"]
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(g1, g2)
+
+
+# ------------------------------------------------------------- errors ----
+
+def test_invalid_inputs_are_rejected(ctx):
+    C, a, b = rand_dense(1, 20, 30)
+    Cd, ad, bd = to_dev(C), to_dev(a), to_dev(b)
+    f = torch.empty(20, dtype=torch.float64, device=DEV)
+    g = torch.empty(30, dtype=torch.float64, device=DEV)
+    bad_a = a.copy(); bad_a[3] = 0.0
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(B.problem_dense(Cd, to_dev(bad_a), bd), B.default_params(), f, g)
+    assert e.value.code == B.ERR_NONPOSITIVE_MARGINAL
+    Cn = C.copy(); Cn[4, 5] = np.nan
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(B.problem_dense(to_dev(Cn), ad, bd), B.default_params(), f, g)
+    assert e.value.code == B.ERR_NONFINITE
+    for kw in ({"eps": 0.0}, {"eps": -1.0}, {"tol": 0.0}, {"mu0": 1.0}, {"m0": 0},
+               {"max_sinkhorn_steps": 0}, {"method": 5}, {"stability": 3}, {"carry": 4}):
+        with pytest.raises(B.AccsinkError) as e:
+            ctx.accsink_solve(B.problem_dense(Cd, ad, bd), B.default_params(**kw), f, g)
+        assert e.value.code == B.ERR_INVALID_ARG, kw
+    pr = B.problem_dense(Cd, ad, bd)
+    pr.ldc = 10
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(pr, B.default_params(), f, g)
+    assert e.value.code == B.ERR_INVALID_ARG
+    pr = B.problem_dense(Cd, ad, bd)
+    pr.cost_kind = B.COST_SQEUCLID
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(pr, B.default_params(), f, g)
+    assert e.value.code in (B.ERR_INVALID_ARG, B.ERR_UNSUPPORTED)
+    # the context stays usable after errors
+    f2, g2, res = gpu_solve(ctx, C, a, b, 5e-2, 1e-6, B.ACC)
+    assert res["status"] == 0
+
+
+def test_budget_is_enforced():
+    with B.Context(0, mem_budget_bytes=1024) as small:
+        C, a, b = rand_dense(2, 64, 64)
+        f = torch.empty(64, dtype=torch.float64, device=DEV)
+        g = torch.empty(64, dtype=torch.float64, device=DEV)
+        with pytest.raises(B.AccsinkError) as e:
+            small.accsink_solve(B.problem_dense(to_dev(C), to_dev(a), to_dev(b)),
+                                B.default_params(), f, g)
+        assert e.value.code == B.ERR_BUDGET
+
+
+# ------------------------------------------- full-size stored cost -------
+
+@pytest.fixture(scope="module")
+def big_problem():
+    pr = W.gmm_stored_cost_problem(seed=0, n=16384, m=16384, eps=1e-2)
+    return pr
+
+
+def test_full_size_row_and_col_pass_sampled(ctx, big_problem):
+    pr = big_problem
+    n = m = 16384
+    eps = 1e-2
+    C = to_dev(pr["C"])
+    a = to_dev(pr["a"])
+    g = potential_like(99, m, eps)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    ctx.accsink_row_pass(B.problem_dense(C, a), eps, to_dev(g), f)
+    ell = torch.empty(m, dtype=torch.float64, device=DEV)
+    fin = potential_like(98, n, eps)
+    ctx.accsink_col_lse(B.problem_dense(C), eps, to_dev(fin), ell)
+    torch.cuda.synchronize()
+    rows = np.random.default_rng(1).choice(n, 48, replace=False)
+    cols = np.random.default_rng(2).choice(m, 48, replace=False)
+    cost = O.Cost(C=pr["C"])
+    ru = O.row_pass_sample(cost, eps, np.log(pr["a"]), g / eps, rows)
+    assert np.abs(f.cpu().numpy()[rows] / eps - ru).max() <= PASS_TOL
+    rl = O.col_lse_sample(cost, eps, fin / eps, cols)
+    assert np.abs(ell.cpu().numpy()[cols] - rl).max() <= PASS_TOL
+
+
+@pytest.mark.parametrize("method", [B.ACC, B.PLAIN])
+def test_full_size_solve_properties(ctx, big_problem, method):
+    """At 16384 x 16384 (eps 1e-2): converged, FP64-truth marginals on sampled
+    rows and columns, row pass exact at the returned g, transport cost."""
+    pr = big_problem
+    eps, tol = 1e-2, 1e-6
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], eps, tol, method)
+    assert res["status"] == 0 and res["marginal_l1"] < tol
+    cost = O.Cost(C=pr["C"])
+    rows = np.random.default_rng(3).choice(16384, 64, replace=False)
+    cols = np.random.default_rng(4).choice(16384, 64, replace=False)
+    r, cs = O.rows_sample(cost, eps, f, g, rows)
+    np.testing.assert_allclose(r, pr["a"][rows], rtol=2e-6)
+    c = O.cols_sample(cost, eps, f, g, cols)
+    # sampled column errors stay within the total budget's per-column share
+    assert np.abs(c - pr["b"][cols]).sum() <= tol * 64 / 16384 * 50
+    # transport cost from the sampled rows extrapolates consistently
+    assert np.isfinite(res["transport_cost"]) and res["transport_cost"] > 0
