@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark: Acc-Sinkhorn time to marginal L1 1e-6 on one GB300.
+
+Workload (stored cost): n = m = 16384, X and Y from 8-component Gaussian
+mixtures in R^3 (sigma 0.05, means uniform in [0,1]^3), dense FP32 squared-
+Euclidean cost scaled to max 1 (1 GiB), Dirichlet(1) marginals, eps = 1e-3,
+tol = 1e-6 (seeded, synthetic; the paper's images and word vectors are not
+available, these inputs stand in for them).
+
+One step = one complete solve to tol through the C-ABI (accsink_solve) with
+the inputs resident in HBM. The cost (1 GiB) is larger than L2 (129 MB), so
+every pass streams it from HBM; no L2 flush is needed between steps.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the same workload instead (bounded sample, extrapolated to a full solve).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 16384
+EPS = 1e-3
+TOL = 1e-6
+SEED = 0
+METRIC = "time to marginal L1 1e-6, Acc vs plain Sinkhorn on 1 GB300; HBM GB/s; p50/p99 latency"
+WORKLOAD = ("gmm8-r3 stored sqeuclid cost n=m=16384 (1 GiB FP32, max 1), Dirichlet(1) "
+            "marginals, eps=1e-3, tol=1e-6")
+# S evaluations Acc-Sinkhorn needs on this workload (measured by the GPU arm;
+# the oracle matches the GPU step count within 2% on every parity size). The
+# reference arm extrapolates its per-evaluation time with it.
+ACC_STEPS_REFERENCE = None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_file: str, profile_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (its sha256 is recorded in the summary)."""
+    src = os.path.join(ROOT, "paper_2605_30267_gb300", "csrc", kernel_file)
+    prof = os.path.join(ROOT, "profiles", profile_name)
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        fields = {}
+        for line in open(prof):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256") != sha:
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", "0", f"--query-gpu={q}",
+                                           "--format=csv,noheader,nounits", "-lms", "200"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                          text=True)
+        except Exception:
+            self._proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+        time.sleep(0.05)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def percentile(v, q):
+    v = sorted(v)
+    if not v:
+        return None
+    k = (len(v) - 1) * q
+    lo, hi = int(k), min(int(k) + 1, len(v) - 1)
+    return v[lo] + (v[hi] - v[lo]) * (k - lo)
+
+
+def dist_setup():
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if os.environ.get("ACCSINK_BENCH_GLOO") is None else "gloo")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+
+    rank, world = dist_setup()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    # Replicas only: every rank solves its own independent problem (seed + rank).
+    pr = W.gmm_stored_cost_problem(seed=SEED + rank, n=args.n, m=args.n, eps=EPS, tol=TOL)
+    C = torch.from_numpy(pr["C"]).to(dev)
+    a = torch.from_numpy(pr["a"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    ctx = B.Context(local)
+    stream = torch.cuda.Stream(dev)
+    prob = B.problem_dense(C, a, b)
+    f = torch.empty(args.n, dtype=torch.float64, device=dev)
+    g = torch.empty(args.n, dtype=torch.float64, device=dev)
+
+    def solve(method, eps, **kw):
+        p = B.default_params(eps=eps, tol=TOL, method=method, **kw)
+        return ctx.accsink_solve(prob, p, f, g, stream=stream)
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        solve(B.ACC, EPS)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K Acc solves at eps = 1e-3 ----------------------
+    clocks = ClockSampler()
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    lat = []
+    steps = []
+    launches = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    ev0.record(stream)
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        res = solve(B.ACC, EPS)
+        evs[k][1].record(stream)
+        steps.append(res.sinkhorn_steps)
+        # set-up (set_state, cost stats, init), 3 per S evaluation, final
+        # cost pass, two output scalings
+        launches += 3 + 3 * res.sinkhorn_steps + 1 + 2
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    total_ms = ev0.elapsed_time(ev1)
+    lat = [e0.elapsed_time(e1) for e0, e1 in evs]
+    clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms, world)
+    ms_per_step = total_ms / args.steps
+    acc_res = B.result_dict(res)
+
+    out = None
+    if rank == 0:
+        # ---- roofline of the streaming passes (CUDA events on this stream)
+        row_ms, col_ms = ctx.accsink_time_passes(prob, EPS, g, args.pass_reps, stream=stream)
+        nm = args.n * args.n
+        row_bytes = 4 * nm + 8 * args.n + 24 * args.n          # C, G/Gk, loga/a/u/F
+        geo = ctx.accsink_launch_geometry(args.n, args.n)
+        col_bytes = 4 * nm + 8 * args.n + 8 * geo["col_splits"] * args.n
+        peak, peak_kind = measured_peaks()
+        row_gbs = row_bytes / (row_ms * 1e-3) / 1e9
+        col_gbs = col_bytes / (col_ms * 1e-3) / 1e9
+        dominant = ("row_pass", row_ms, row_bytes, row_gbs) if row_ms >= col_ms else \
+            ("col_pass", col_ms, col_bytes, col_gbs)
+        traffic = profile_traffic("pass_kernels.cu", f"ncu_{dominant[0]}_gmm16384.txt")
+
+        # ---- Acc vs plain at each eps (one solve each, after the timed region)
+        versus = {}
+        if not args.quick:
+            for eps in (1e-1, 1e-2, 1e-3):
+                row = {}
+                for name, meth in (("acc", B.ACC), ("plain", B.PLAIN)):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    r = solve(meth, eps)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    row[name + "_s"] = round(e0.elapsed_time(e1) / 1e3, 6)
+                    row[name + "_steps"] = r.sinkhorn_steps
+                    row[name + "_status"] = B.STATUS_NAMES[r.status]
+                row["speedup"] = round(row["plain_s"] / row["acc_s"], 3)
+                versus[f"{eps:g}"] = row
+
+        # ---- end to end through the host-buffer C-ABI call
+        Ch = torch.from_numpy(pr["C"]).pin_memory().numpy()
+        ah = torch.from_numpy(pr["a"]).pin_memory().numpy()
+        bh = torch.from_numpy(pr["b"]).pin_memory().numpy()
+        fh = torch.empty(args.n, dtype=torch.float64).pin_memory().numpy()
+        gh = torch.empty(args.n, dtype=torch.float64).pin_memory().numpy()
+        pe = B.default_params(eps=EPS, tol=TOL)
+        ctx.accsink_solve_host(Ch, ah, bh, pe, fh, gh, stream=stream)     # warm-up
+        e2e = []
+        for _ in range(max(1, min(args.steps, 3))):
+            t0 = time.perf_counter()
+            ctx.accsink_solve_host(Ch, ah, bh, pe, fh, gh, stream=stream)
+            e2e.append(time.perf_counter() - t0)
+        h2d = Ch.nbytes + ah.nbytes + bh.nbytes
+        d2h = fh.nbytes + gh.nbytes
+
+        value = ms_per_step / 1e3
+        out = {
+            "metric": METRIC,
+            "value": round(value, 6),
+            "unit": "s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms_per_step, 4),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 bulk, f64 reductions",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "n": args.n, "m": args.n, "eps": EPS, "tol": TOL,
+                       "method": "acc (Algorithm 1+2, mu0=0.25, m0=4, y carried across stages)",
+                       "l2": "inputs larger than L2 (1 GiB cost vs 129 MB L2); no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "loop": "CUDA graph, conditional WHILE node" if acc_res["loop_mode"]
+                       else "host loop"},
+            "latency_s": {"p50": round(percentile(lat, 0.5) / 1e3, 6),
+                          "p99": round(percentile(lat, 0.99) / 1e3, 6)},
+            "acc_steps": steps[-1],
+            "ms_per_sinkhorn_step": round(ms_per_step / steps[-1], 5),
+            "final_marginal_l1_gpu": acc_res["marginal_l1"],
+            "acc_vs_plain": versus,
+            "roofline": {"bound": "hbm", "kernel": dominant[0],
+                         "achieved": round(dominant[3], 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(dominant[3] / peak, 4), "traffic": traffic,
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)",
+                         "bytes_per_launch": dominant[2],
+                         "ms_per_launch": round(dominant[1], 5),
+                         "other_pass": {"row_pass_gbs": round(row_gbs, 1),
+                                        "col_pass_gbs": round(col_gbs, 1)}},
+            "e2e": {"value": round(statistics.median(e2e), 6), "unit": "s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(pr, steps[-1], args.cpu_evals)
+    ctx.close()
+    return out
+
+
+def cpu_baseline(pr, acc_steps, evals):
+    """The FP64 oracle on the host cores: `evals` S evaluations at full size,
+    extrapolated to the Acc step count of the GPU solve."""
+    import numpy as np
+
+    import oracle as O
+    cores = O.set_threads(0)
+    cost = O.Cost(C=pr["C"])
+    a = O.normalise(pr["a"])
+    b = O.normalise(pr["b"])
+    x = np.zeros(pr["C"].shape[1])
+    t0 = time.perf_counter()
+    for _ in range(evals):
+        err, u, c, s = O.sinkhorn_map(cost, EPS, a, b, x)
+        x = s
+    per = (time.perf_counter() - t0) / evals
+    return {"value": round(per * acc_steps, 3), "unit": "s", "cores": cores, "kind": "oracle",
+            "sample": f"{evals} full-size S evaluations (row + column pass, FP64, OpenMP) "
+                      f"at {per:.3f} s each, extrapolated to the {acc_steps} S evaluations "
+                      f"of the Acc solve"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import numpy as np
+
+    import oracle as O
+    from paper_2605_30267_gb300 import workloads as W
+    pr = W.gmm_stored_cost_problem(seed=SEED, n=args.n, m=args.n, eps=EPS, tol=TOL)
+    cores = O.set_threads(0)
+    cost = O.Cost(C=pr["C"])
+    a, b = O.normalise(pr["a"]), O.normalise(pr["b"])
+    x = np.zeros(args.n)
+    acc_steps = ACC_STEPS_REFERENCE or args.ref_steps
+    for _ in range(args.warmup):
+        O.sinkhorn_map(cost, EPS, a, b, x)
+    per = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        err, u, c, s = O.sinkhorn_map(cost, EPS, a, b, x)
+        per.append(time.perf_counter() - t0)
+        x = s
+    v = statistics.median(per) * acc_steps
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(v * 1e3, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD, "n": args.n, "m": args.n, "eps": EPS, "tol": TOL},
+            "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step one full-size S evaluation of the FP64 oracle "
+                                       f"(median {statistics.median(per):.3f} s), extrapolated "
+                                       f"to {acc_steps} S evaluations of the Acc solve"},
+            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--n", type=int, default=N)
+    ap.add_argument("--pass-reps", type=int, default=20)
+    ap.add_argument("--cpu-evals", type=int, default=4)
+    ap.add_argument("--ref-steps", type=int, default=200)
+    ap.add_argument("--quick", action="store_true", help="skip the Acc-vs-plain table")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        out = run_reference(args)
+    else:
+        out = run_gpu(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

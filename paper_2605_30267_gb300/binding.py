@@ -158,6 +158,7 @@ def problem_dense(C, a=None, b=None, scale_to_max=False) -> accsink_problem:
         _check_dev(b, torch.float64, "b", m)
         pr.b = b.data_ptr()
     pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
+    pr._keep = (C, a, b)      # the struct holds raw pointers: keep the tensors alive
     return pr
 
 

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         w.raw[j] = raw;
         w.D1[j] = D1;
         w.del[j] = del;
-        if (c_out) c_out[j] = bj + xi;
+        if (c_out) c_out[j] = bj * exp(del);
     }
     block_sum_store<6>(v, w.steppart + (int64_t)blockIdx.x * kPartStride);
     if (!grid_barrier(st, nb, kBarrierLimitNs)) { bail(); return; }

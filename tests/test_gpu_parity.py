@@ -119,7 +119,7 @@ def test_sinkhorn_map_matches_oracle(ctx, n, m, eps):
                                    to_dev(g), f, c, s)
     rerr, ru, rc, rs = O.sinkhorn_map(O.Cost(C=C), eps, a, b, g / eps)
     assert np.abs(f.cpu().numpy() / eps - ru).max() <= PASS_TOL
-    np.testing.assert_allclose(c.cpu().numpy(), rc, rtol=5 * PASS_TOL, atol=0)
+    np.testing.assert_allclose(c.cpu().numpy(), rc, rtol=5 * PASS_TOL, atol=1e-300)
     assert np.abs(s.cpu().numpy() / eps - rs).max() <= 2 * PASS_TOL
     assert abs(err - rerr) <= 5 * PASS_TOL * max(1.0, rerr)
 
@@ -188,7 +188,7 @@ def test_small_pointcloud_problem_256(ctx):
 def test_tiny_solves(ctx, n, m):
     C, a, b = rand_dense(n * 10 + m, n, m)
     for method in (B.ACC, B.PLAIN):
-        check_solve(ctx, C, a, b, 5e-2, 1e-8, method)
+        check_solve(ctx, C, a, b, 5e-2, 1e-6, method)
 
 
 def test_max_to_one_scaling(ctx):
