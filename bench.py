@@ -174,7 +174,8 @@ def run_gpu(args):
     g = torch.empty(args.n, dtype=torch.float64, device=dev)
 
     def solve(method, eps, **kw):
-        p = B.default_params(eps=eps, tol=TOL, method=method, **kw)
+        p = B.default_params(eps=eps, tol=TOL, method=method,
+                             use_graph=0 if args.host_loop else 1, **kw)
         return ctx.accsink_solve(prob, p, f, g, stream=stream)
 
     # warm-up (untimed)
@@ -219,8 +220,9 @@ def run_gpu(args):
         row_ms, col_ms = ctx.accsink_time_passes(prob, EPS, g, args.pass_reps, stream=stream)
         nm = args.n * args.n
         row_bytes = 4 * nm + 8 * args.n + 24 * args.n          # C, G/Gk, loga/a/u/F
-        geo = ctx.accsink_launch_geometry(args.n, args.n)
-        col_bytes = 4 * nm + 8 * args.n + 8 * geo["col_splits"] * args.n
+        # column pass over the transposed copy: C^T once, F pair (8 B/row),
+        # ell out (8 B/column)
+        col_bytes = 4 * nm + 8 * args.n + 8 * args.n
         peak, peak_kind = measured_peaks()
         row_gbs = row_bytes / (row_ms * 1e-3) / 1e9
         col_gbs = col_bytes / (col_ms * 1e-3) / 1e9
@@ -377,6 +379,8 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=200)
     ap.add_argument("--quick", action="store_true", help="skip the Acc-vs-plain table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive iterations from the host instead of the graph loop")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

@@ -89,7 +89,8 @@ typedef struct {
 
 /* Solver parameters. accsink_params_default() fills:
  *   method ACC, eps 1e-2, tol 1e-6, mu0 0.25, m0 4, max_sinkhorn_steps
- *   100000, stability REPORT, carry Y, evaluate 1, use_graph 1, history 0.
+ *   100000, stability REPORT, carry Y, evaluate 1, use_graph 1, history 0,
+ *   col_transpose 1.
  * mu0 in (0, 1), m0 >= 1 (Algorithm 2). tol is the l1 marginal tolerance of
  * Sec. 5 eq. (l1tol). carry selects how a homotopy stage hands w to the next
  * one: CARRY_Y keeps y = w / alpha (the state Theorem 1 follows), CARRY_W
@@ -108,6 +109,11 @@ typedef struct {
     int32_t evaluate;    /* 1: one extra pass computes <C, P> at the end     */
     int32_t use_graph;   /* 1: device-side loop in a CUDA graph; 0: host loop */
     int32_t history;     /* keep per-step history for this many steps (0: no) */
+    int32_t col_transpose; /* 1: the context keeps a transposed copy of C
+                              (another 4 n m bytes, made once per solve) so
+                              the column pass streams rows too, when the
+                              budget and the device allow; 0: never */
+    int32_t reserved;
 } accsink_params;
 
 /* Result of a solve (host struct, filled by the library). */
@@ -206,10 +212,11 @@ int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob,
 
 /* Times the two streaming passes alone on `stream` with CUDA events: after
  * one untimed row pass and column pass at g (device, m, cost units), runs
- * `reps` row passes back to back, then `reps` column passes, and writes the
- * mean device milliseconds per launch to *row_ms and *col_ms (host). Used for
- * the HBM roofline of the passes; the data they move is 4 n m bytes of C
- * per launch plus O(n + m) operands. */
+ * `reps` row passes back to back, then `reps` column passes (over the
+ * transposed copy when the context can hold it, as the solver does), and
+ * writes the mean device milliseconds per launch to *row_ms and *col_ms
+ * (host). Used for the HBM roofline of the passes; each launch reads the
+ * 4 n m bytes of the cost once plus O(n + m) operands. */
 int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double eps,
                         const double *g, int reps, void *stream, float *row_ms,
                         float *col_ms);

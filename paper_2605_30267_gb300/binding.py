@@ -46,7 +46,7 @@ class accsink_params(ct.Structure):
                 ("tol", ct.c_double), ("mu0", ct.c_double),
                 ("max_sinkhorn_steps", ct.c_int32), ("stability", ct.c_int32),
                 ("carry", ct.c_int32), ("evaluate", ct.c_int32), ("use_graph", ct.c_int32),
-                ("history", ct.c_int32)]
+                ("history", ct.c_int32), ("col_transpose", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class accsink_result(ct.Structure):

@@ -59,8 +59,9 @@ struct DevState {
     int32_t first, done, status, use_cond;
     int32_t hist_cap, row_grid, col_splits, nonfinite;
     int32_t mode;              // step-kernel mode (solve / single map)
+    int32_t col_mode;          // 0: column partials (strip pass); 1: ell from C^T
     uint32_t barrier;          // grid-barrier arrival counter (reset by the row pass)
-    int32_t pad[2];
+    int32_t pad[1];
 };
 
 enum StepMode { STEP_SOLVE = 0, STEP_MAP = 1 };
@@ -78,6 +79,8 @@ struct Work {
     // double-float operands
     float *G, *Gk;            // m (row pass)
     float2 *FF;               // n (column pass): (F_hi, F_lo * k_hi)
+    float *Fh, *Fk;           // n: the same pair as two arrays (transposed column pass)
+    double *ell;              // m: column log-sum-exp (transposed column pass)
     // partials
     float2 *colpart;          // splits x m : (R, S) per column per row split
     double *rowpart;          // row-grid x 2 : (sum a_i u_i, sum cost) per CTA
@@ -214,6 +217,19 @@ cudaError_t launch_scale_out(const double *src, double scale, double *dst, int n
                              cudaStream_t s);
 cudaError_t launch_col_finish_lse(const Work &w, int m, double *ell_out, cudaStream_t s);
 int occupancy_row_pass(int vec);
+cudaError_t launch_row_pass_tma(const CostView &cv, const Work &w, int grid, bool with_cost,
+                                cudaStream_t s);
+cudaError_t setup_row_pass_tma();
+int row_pass_tma_smem_bytes();
+cudaError_t launch_row_pass_warp(const CostView &cv, const Work &w, int grid, bool with_cost,
+                                 cudaStream_t s);
+int occupancy_row_pass_warp();
+cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int m,
+                                       const Work &w, int grid, cudaStream_t s);
+cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaStream_t s);
+// Which kernel serves 128-bit-aligned row passes: 0 warp-per-row, 1 TMA.
+int row_kernel_choice();
 int occupancy_col_pass(int vec);
+void setup_col_pass();
 
 }  // namespace accsink

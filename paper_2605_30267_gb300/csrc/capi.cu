@@ -23,13 +23,14 @@ namespace {
 struct GraphKey {
     const float *C = nullptr;
     int64_t ldc = 0;
-    int n = 0, m = 0, vec = 0, row_grid = 0, splits = 0, step_grid = 0;
+    int n = 0, m = 0, vec = 0, row_grid = 0, splits = 0, step_grid = 0, colt_grid = 0;
     void *ws = nullptr;
+    const float *ct = nullptr;
     bool operator==(const GraphKey &o) const
     {
         return C == o.C && ldc == o.ldc && n == o.n && m == o.m && vec == o.vec &&
                row_grid == o.row_grid && splits == o.splits && step_grid == o.step_grid &&
-               ws == o.ws;
+               colt_grid == o.colt_grid && ws == o.ws && ct == o.ct;
     }
 };
 
@@ -42,7 +43,7 @@ struct accsink_ctx {
     size_t budget = 0;
     std::string err;
     int num_sms = 1;
-    int occ_row[2] = {1, 1}, occ_col[2] = {1, 1};
+    int occ_row[2] = {1, 1}, occ_col[2] = {1, 1}, occ_row_warp = 1;
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -63,6 +64,9 @@ struct accsink_ctx {
     int last_hist_count = 0;
     bool graph_broken = false;
     std::string graph_error;
+    // transposed copy of the cost for the column pass
+    float *ct = nullptr;
+    size_t ct_bytes = 0;
 };
 
 namespace {
@@ -94,23 +98,70 @@ void free_graph(accsink_ctx *ctx)
 }
 
 struct Geometry {
-    int stat_grid, row_grid, splits, step_grid, vec_grid;
+    int stat_grid, row_grid, splits, step_grid, vec_grid, colt_grid;
 };
+
+// Grid of the warp-per-row kernel for `rows` rows: k rows per warp with
+// k = ceil(rows / resident warps), and just enough warps for that, so every
+// warp gets k or k - 1 rows.
+int warp_rows_grid(const accsink_ctx *ctx, int rows);
 
 Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
 {
     Geometry g;
     const int S = ctx->num_sms;
     g.stat_grid = std::max(1, std::min(n, 4 * S));
-    g.row_grid = std::max(1, std::min(S * ctx->occ_row[vec], (n + 1) / 2));
+    if (vec && row_kernel_choice() == 1) {
+        // TMA row pass: one CTA per SM
+        g.row_grid = std::max(1, std::min(S, n));
+    } else if (vec) {
+        g.row_grid = warp_rows_grid(ctx, n);
+    } else {
+        g.row_grid = std::max(1, std::min(S * ctx->occ_row[vec], (n + 1) / 2));
+    }
     const int strips = (m + kColStrip - 1) / kColStrip;
     const int target = S * ctx->occ_col[vec];
     int splits = target / strips;
     splits = std::max(1, std::min(splits, std::max(1, n / 8)));
     g.splits = splits;
-    g.step_grid = std::max(1, std::min(S, (m + 255) / 256));
+    // the step kernel's FP64 column work is spread over every SM
+    g.step_grid = std::max(1, std::min(S, (m + 63) / 64));
     g.vec_grid = std::max(1, std::min(S, (std::max(n, m) + 255) / 256));
+    g.colt_grid = warp_rows_grid(ctx, m);
     return g;
+}
+
+int warp_rows_grid(const accsink_ctx *ctx, int rows)
+{
+    const int64_t max_warps = (int64_t)ctx->num_sms * ctx->occ_row_warp * 8;
+    const int64_t k = (rows + max_warps - 1) / max_warps;
+    const int64_t warps = (rows + k - 1) / k;
+    return (int)std::max<int64_t>(1, (warps + 7) / 8);
+}
+
+// Row stride (elements) of the transposed copy: n rounded up to 4 so every
+// row starts on a 16-byte boundary.
+int64_t ct_ld(int n) { return (n + 3) / 4 * 4; }
+
+// Makes room for C^T (m x ct_ld(n) floats). Returns false, without error,
+// when the budget or the device cannot hold it (the strip column pass is
+// used then).
+bool ensure_ct(accsink_ctx *ctx, int n, int m)
+{
+    const size_t need = (size_t)m * (size_t)ct_ld(n) * sizeof(float);
+    if (ctx->ct && ctx->ct_bytes >= need) return true;
+    if (ctx->budget && ctx->ws_bytes + ctx->stage_bytes + need > ctx->budget) return false;
+    if (ctx->ct) cudaFree(ctx->ct);
+    ctx->ct = nullptr;
+    ctx->ct_bytes = 0;
+    free_graph(ctx);
+    if (cudaMalloc(&ctx->ct, need) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->ct = nullptr;
+        return false;
+    }
+    ctx->ct_bytes = need;
+    return true;
 }
 
 // (Re)allocates the workspace for n x m with the given partial counts.
@@ -133,6 +184,8 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
         (size_t)N * 8,                                                         // u
         (size_t)Mp * 4, (size_t)Mp * 4,                                        // G Gk
         (size_t)N * 8,                                                         // FF
+        (size_t)((N + 3) / 4 * 4) * 4, (size_t)((N + 3) / 4 * 4) * 4,          // Fh Fk
+        (size_t)M * 8,                                                         // ell
         (size_t)SP * (size_t)M * 8,                                            // colpart
         (size_t)RG * 16,                                                       // rowpart
         (size_t)std::max(S, 1) * kPartStride * 8 * 2,                          // steppart
@@ -177,6 +230,8 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
     w.u = (double *)take();
     w.G = (float *)take(); w.Gk = (float *)take();
     w.FF = (float2 *)take();
+    w.Fh = (float *)take(); w.Fk = (float *)take();
+    w.ell = (double *)take();
     w.colpart = (float2 *)take();
     w.rowpart = (double *)take();
     w.steppart = (double *)take();
@@ -247,11 +302,22 @@ cudaError_t set_state(accsink_ctx *ctx, const DevState &hs, cudaStream_t s)
 }
 
 // Builds (or reuses) the graph: WHILE(cond) { row pass; column pass; step }.
-int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g)
+// One S evaluation: row pass, then the column pass (on C^T when `ct`).
+cudaError_t launch_passes(const CostView &cv, const Work &w, const Geometry &g, const float *ct,
+                          cudaStream_t s)
+{
+    cudaError_t e = launch_row_pass(cv, w, g.row_grid, false, s);
+    if (e != cudaSuccess) return e;
+    if (ct) return launch_col_pass_transposed(ct, ct_ld(cv.n), cv.n, cv.m, w, g.colt_grid, s);
+    return launch_col_pass(cv, w, g.splits, s);
+}
+
+int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const float *ct)
 {
     GraphKey key;
     key.C = cv.C; key.ldc = cv.ldc; key.n = cv.n; key.m = cv.m; key.vec = cv.vec;
     key.row_grid = g.row_grid; key.splits = g.splits; key.step_grid = g.step_grid;
+    key.colt_grid = g.colt_grid; key.ct = ct;
     key.ws = ctx->ws;
     if (ctx->exec && ctx->key == key) return ACCSINK_OK;
     free_graph(ctx);
@@ -274,8 +340,8 @@ int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g)
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
     Work w = ctx->w;
     w.ignore_done = 0;
-    cudaError_t e1 = launch_row_pass(cv, w, g.row_grid, false, ctx->cap_stream);
-    cudaError_t e2 = launch_col_pass(cv, w, g.splits, ctx->cap_stream);
+    cudaError_t e1 = launch_passes(cv, w, g, ct, ctx->cap_stream);
+    cudaError_t e2 = cudaSuccess;
     cudaError_t e3 = launch_step(cv, w, g.step_grid, handle, ctx->cap_stream);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &out);
@@ -323,11 +389,16 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     hs.col_splits = g.splits;
     hs.use_cond = prm->use_graph ? 1 : 0;
     hs.first = 1;
+    // column pass on a transposed copy when it fits (see ensure_ct)
+    const float *ct = nullptr;
+    if (prm->col_transpose && ensure_ct(ctx, n, m)) ct = ctx->ct;
+    hs.col_mode = ct ? 1 : 0;
 
     CK(cudaEventRecord(ctx->ev0, s));
     CK(set_state(ctx, hs, s));
     CK(launch_cost_stats(cv, w, g.stat_grid, s));
     CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, s));
+    if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(n), s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_state->done) {
@@ -344,7 +415,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
 
     bool use_graph = prm->use_graph && !ctx->graph_broken;
     if (use_graph) {
-        rc = get_graph(ctx, cv, g);
+        rc = get_graph(ctx, cv, g, ct);
         if (rc != ACCSINK_OK) {
             // The device-side loop needs conditional graph nodes with
             // cooperative kernels; if this driver refuses, remember it and
@@ -362,8 +433,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
         const int unroll = 8;
         for (;;) {
             for (int u = 0; u < unroll; ++u) {
-                CK(launch_row_pass(cv, w, g.row_grid, false, s));
-                CK(launch_col_pass(cv, w, g.splits, s));
+                CK(launch_passes(cv, w, g, ct, s));
                 CK(launch_step(cv, w, g.step_grid, 0, s));
             }
             CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
@@ -471,6 +541,7 @@ void accsink_params_default(accsink_params *p)
     p->evaluate = 1;
     p->use_graph = 1;
     p->history = 0;
+    p->col_transpose = 1;
 }
 
 int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
@@ -487,9 +558,16 @@ int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
     ctx->device = device;
     ctx->budget = mem_budget_bytes;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    setup_col_pass();
     for (int v = 0; v < 2; ++v) {
         ctx->occ_row[v] = occupancy_row_pass(v);
         ctx->occ_col[v] = occupancy_col_pass(v);
+    }
+    ctx->occ_row_warp = occupancy_row_pass_warp();
+    if (setup_row_pass_tma() != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return ACCSINK_ERR_CUDA;
     }
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
@@ -509,6 +587,7 @@ void accsink_destroy(accsink_ctx *ctx)
     free_graph(ctx);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
+    if (ctx->ct) cudaFree(ctx->ct);
     if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -720,9 +799,11 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     rc = pass_setup(ctx, prob, eps, s, &geo, &w);
     if (rc != ACCSINK_OK) return rc;
     const CostView cv = make_view(prob);
+    // the column pass the solver would use: on C^T when it fits
+    const float *ct = ensure_ct(ctx, prob->n, prob->m) ? ctx->ct : nullptr;
     CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
-    CK(launch_row_pass(cv, w, geo.row_grid, false, s));   // warm-up, writes F
-    CK(launch_col_pass(cv, w, geo.splits, s));
+    if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(prob->n), s));
+    CK(launch_passes(cv, w, geo, ct, s));                 // warm-up, writes F
     CK(cudaEventRecord(ctx->ev0, s));
     for (int r = 0; r < reps; ++r) CK(launch_row_pass(cv, w, geo.row_grid, false, s));
     CK(cudaEventRecord(ctx->ev1, s));
@@ -731,7 +812,11 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (row_ms) *row_ms = ms / reps;
     CK(cudaEventRecord(ctx->ev0, s));
-    for (int r = 0; r < reps; ++r) CK(launch_col_pass(cv, w, geo.splits, s));
+    for (int r = 0; r < reps; ++r) {
+        if (ct) CK(launch_col_pass_transposed(ct, ct_ld(prob->n), prob->n, prob->m, w,
+                                              geo.colt_grid, s));
+        else CK(launch_col_pass(cv, w, geo.splits, s));
+    }
     CK(cudaEventRecord(ctx->ev1, s));
     CK(cudaEventSynchronize(ctx->ev1));
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));

@@ -8,6 +8,7 @@
 // potentials as double-float pairs) is a few KB to a few hundred KB that
 // stays in L1/L2. See accsink_internal.cuh for the precision argument.
 #include <float.h>
+#include <cstdlib>
 
 #include "accsink_internal.cuh"
 
@@ -103,6 +104,17 @@ __device__ __forceinline__ void kahan_add(Acc &a, float x)
 __device__ __forceinline__ float lse_term(float G, float gk, float c, float R, float kh, float kl)
 {
     const float s = G - c;
+    const float z = s - G;
+    const float e = -c - z;
+    const float q = fmaf(e, kh, gk);
+    const float t = s - R;
+    return ex2_approx(fmaf(t, kh, fmaf(t, kl, q)));
+}
+
+// Same with s = fl(G - c) already formed.
+__device__ __forceinline__ float lse_term_s(float s, float G, float gk, float c, float R,
+                                            float kh, float kl)
+{
     const float z = s - G;
     const float e = -c - z;
     const float q = fmaf(e, kh, gk);
@@ -285,6 +297,8 @@ __global__ void __launch_bounds__(kRowNT) k_row_pass(CostView cv, Work w)
                 const float Fh = (float)F;
                 const float Fl = (float)(F - (double)Fh);
                 w.FF[i] = make_float2(Fh, Fl * kh);
+                w.Fh[i] = Fh;
+                w.Fk[i] = Fl * kh;
                 my_dual += w.a[i] * ui;
                 // P_ij = a_i 2^{(s_ij - R) k} / S after the row pass, so
                 // sum_j C_ij P_ij = a_i CS / S; for given potentials f the
@@ -316,6 +330,12 @@ constexpr int kRowU = 4;
 cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, bool with_cost,
                             cudaStream_t s)
 {
+    // 128-bit-aligned costs stream through the TMA pipeline (row_tma.cu);
+    // the plain kernel below serves the unaligned layouts.
+    if (cv.vec) {
+        if (row_kernel_choice() == 1) return launch_row_pass_tma(cv, w, grid, with_cost, s);
+        return launch_row_pass_warp(cv, w, grid, with_cost, s);
+    }
     if (cv.vec) {
         if (with_cost) k_row_pass<kRowRG, kRowU, true, true><<<grid, kRowNT, 0, s>>>(cv, w);
         else k_row_pass<kRowRG, kRowU, true, false><<<grid, kRowNT, 0, s>>>(cv, w);
@@ -458,5 +478,7 @@ int occupancy_col_pass(int vec)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_col_pass<kColU, false>, kColNT, 0);
     return b > 0 ? b : 1;
 }
+
+void setup_col_pass() {}
 
 }  // namespace accsink

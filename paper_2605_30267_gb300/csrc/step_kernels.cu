@@ -67,47 +67,69 @@ __device__ __forceinline__ void block_minmax_store(double mn, double mx, double 
     __syncthreads();
 }
 
+// Reduces K values held by every thread over the whole block (op per value:
+// 0 sum, 1 min, 2 max) and returns the totals to every thread. Fixed
+// shuffle tree and fixed warp order, so the result is deterministic.
+template <int K>
+__device__ __forceinline__ void block_allreduce(double (&v)[K], const int (&op)[K])
+{
+    __shared__ double sh[K][kVecNT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = (op[k] == 0) ? x + y : (op[k] == 1 ? fmin(x, y) : fmax(x, y));
+        }
+        if (lane == 0) sh[k][wid] = x;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double x = sh[k][0];
+        for (int q = 1; q < kVecNT / 32; ++q)
+            x = (op[k] == 0) ? x + sh[k][q] : (op[k] == 1 ? fmin(x, sh[k][q]) : fmax(x, sh[k][q]));
+        v[k] = x;
+    }
+    __syncthreads();
+}
+
 // Totals of K consecutive slots of every block's partial record (stride
-// kPartStride), computed identically by every block; result broadcast via
-// shared memory into tot[0..K-1]. op: 0 sum, 1 min, 2 max (per slot).
+// kPartStride), computed identically by every block: thread t reads the
+// records t, t + blockDim, ... (bypassing L1, they were written by other
+// blocks) and the block reduces them in a fixed order.
 template <int K>
 __device__ __forceinline__ void grid_totals(const double *part, int nblocks, int slot0,
                                             const int (&op)[K], double (&tot)[K])
 {
-    __shared__ double sh[K];
-    if (threadIdx.x < K) {
-        const int k = threadIdx.x;
-        double acc = (op[k] == 0) ? 0.0 : (op[k] == 1 ? DBL_MAX : -DBL_MAX);
-        for (int b = 0; b < nblocks; ++b) {
-            const double v = *(volatile const double *)&part[(int64_t)b * kPartStride + slot0 + k];
-            acc = (op[k] == 0) ? acc + v : (op[k] == 1 ? fmin(acc, v) : fmax(acc, v));
-        }
-        sh[k] = acc;
-    }
-    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < K; ++k) tot[k] = sh[k];
-    __syncthreads();
+    for (int k = 0; k < K; ++k) tot[k] = (op[k] == 0) ? 0.0 : (op[k] == 1 ? DBL_MAX : -DBL_MAX);
+    for (int b = threadIdx.x; b < nblocks; b += kVecNT) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double x = __ldcg(&part[(int64_t)b * kPartStride + slot0 + k]);
+            tot[k] = (op[k] == 0) ? tot[k] + x : (op[k] == 1 ? fmin(tot[k], x) : fmax(tot[k], x));
+        }
+    }
+    block_allreduce<K>(tot, op);
 }
 
 // Reduction of the cost-statistics partials (max C, min C, max|C|, #bad).
 __device__ __forceinline__ void cost_totals(const double *statpart, int nstat, double &cmax,
                                             double &cmin, double &cabs, double &bad)
 {
-    __shared__ double sh[4];
-    if (threadIdx.x == 0) {
-        double a0 = -DBL_MAX, a1 = DBL_MAX, a2 = 0.0, a3 = 0.0;
-        for (int b = 0; b < nstat; ++b) {
-            a0 = fmax(a0, statpart[4 * b + 0]);
-            a1 = fmin(a1, statpart[4 * b + 1]);
-            a2 = fmax(a2, statpart[4 * b + 2]);
-            a3 += statpart[4 * b + 3];
-        }
-        sh[0] = a0; sh[1] = a1; sh[2] = a2; sh[3] = a3;
+    double v[4] = {-DBL_MAX, DBL_MAX, 0.0, 0.0};
+    const int op[4] = {2, 1, 2, 0};
+    for (int b = threadIdx.x; b < nstat; b += kVecNT) {
+        v[0] = fmax(v[0], __ldcg(&statpart[4 * b + 0]));
+        v[1] = fmin(v[1], __ldcg(&statpart[4 * b + 1]));
+        v[2] = fmax(v[2], __ldcg(&statpart[4 * b + 2]));
+        v[3] += __ldcg(&statpart[4 * b + 3]);
     }
-    __syncthreads();
-    cmax = sh[0]; cmin = sh[1]; cabs = sh[2]; bad = sh[3];
-    __syncthreads();
+    block_allreduce<4>(v, op);
+    cmax = v[0]; cmin = v[1]; cabs = v[2]; bad = v[3];
 }
 
 // Writes G_j + gamma_j = g_j + shift_g as (hi, gamma * k_hi).
@@ -289,15 +311,21 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
 
     // ---- P1
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l
+    const int col_mode = st->col_mode;
     for (int j = tid; j < m; j += nthr) {
-        float R = w.colpart[j].x;
-        for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
-        double S = 0.0;
-        for (int q = 0; q < splits; ++q) {
-            const float2 pr = w.colpart[(int64_t)q * m + j];
-            S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
+        double ell;
+        if (col_mode == 1) {
+            ell = w.ell[j];
+        } else {
+            float R = w.colpart[j].x;
+            for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
+            double S = 0.0;
+            for (int q = 0; q < splits; ++q) {
+                const float2 pr = w.colpart[(int64_t)q * m + j];
+                S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
+            }
+            ell = log(S) + ((double)R - shift_f) * inv_eps;
         }
-        const double ell = log(S) + ((double)R - shift_f) * inv_eps;
         const double xj = w.x[j];
         const double bj = w.b[j];
         const double del = xj + ell - w.logb[j];
@@ -331,14 +359,12 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     const double rbar = t[1] / (double)m;
     double sum_au = 0.0;
     {
-        __shared__ double sh_au;
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int b = 0; b < st->row_grid; ++b) s += w.rowpart[2 * b];
-            sh_au = s;
-        }
-        __syncthreads();
-        sum_au = sh_au;
+        double au[1] = {0.0};
+        const int op1[1] = {0};
+        const int rg = st->row_grid;
+        for (int b = threadIdx.x; b < rg; b += kVecNT) au[0] += __ldcg(&w.rowpart[2 * b]);
+        block_allreduce<1>(au, op1);
+        sum_au = au[0];
     }
     const double dual = st->eps_user * (sum_au + t[3] - 1.0);
     if (mode == STEP_MAP) {

@@ -205,6 +205,18 @@ def test_carry_w_and_gate_modes(ctx):
     check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, stability=B.STAB_OFF)
 
 
+@pytest.mark.parametrize("n,m", [(257, 1000), (1000, 257), (33, 4099)])
+def test_column_pass_layouts_agree(ctx, n, m):
+    # column pass over the transposed copy vs the strip pass over C itself
+    pr = W.gmm_stored_cost_problem(seed=n * 3 + m, n=n, m=m, eps=1e-2)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, col_transpose=1)
+    check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, col_transpose=0)
+    f1, g1, r1 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, col_transpose=1)
+    f0, g0, r0 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, col_transpose=0)
+    assert abs(r1["sinkhorn_steps"] - r0["sinkhorn_steps"]) <= 1
+    assert np.abs((g1 - g1.mean()) - (g0 - g0.mean())).max() <= 1e-6 * 1e-2
+
+
 def test_history_tracks_oracle(ctx):
     pr = W.gmm_stored_cost_problem(seed=12, n=200, m=180, eps=1e-2)
     f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, history=5000)
