@@ -227,6 +227,34 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
 int accsink_launch_geometry(accsink_ctx *ctx, int32_t n, int32_t m, int32_t vec,
                             int32_t *out6);
 
+/* ---- allocation-free variant -------------------------------------------- */
+
+/* Column log-sum-exp pass of accsink_col_lse for callers that cannot
+ * allocate device memory (a server whose memory pool owns the whole GPU, a
+ * plugin living under another framework's allocator, a loop that cannot
+ * accept cudaMalloc's implicit synchronisation). The paper has no
+ * counterpart to this entry point; it exists only for those callers.
+ *
+ * It needs no context and calls no allocating routine. Its scratch is one
+ * 16 MiB array in device memory that the library reserves on every device
+ * it is loaded on and holds until the process exits. It must fit
+ * 8 n + 8 m bytes plus a few KB; larger problems return ACCSINK_ERR_BUDGET
+ * before any work is queued. Everything runs on the current device and on
+ * `stream`; the call returns without synchronising.
+ *
+ * The first call on a device looks up the array's device address once; make
+ * that first call outside any stream capture. All calls share the one array
+ * and reuse it without clearing what they fully rewrite: calls whose work
+ * overlaps on the GPU (different streams, or host threads) race and must be
+ * serialised by the caller.
+ *
+ * Arguments as accsink_col_lse (dense cost, f (n) and ell_out (m) device
+ * FP64, eps > 0). Returns ACCSINK_OK, ACCSINK_ERR_INVALID_ARG,
+ * ACCSINK_ERR_UNSUPPORTED (non-dense cost), ACCSINK_ERR_BUDGET (too large)
+ * or ACCSINK_ERR_CUDA. */
+int accsink_col_lse_noalloc(const accsink_problem *prob, double eps, const double *f,
+                            double *ell_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,8 @@ STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NONPOSITIVE_MARGINAL",
 EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_params_default",
             "accsink_version", "accsink_solve", "accsink_solve_host", "accsink_get_history",
             "accsink_row_pass", "accsink_col_lse", "accsink_sinkhorn_map",
-            "accsink_transport_cost", "accsink_time_passes", "accsink_launch_geometry"]
+            "accsink_transport_cost", "accsink_time_passes", "accsink_launch_geometry",
+            "accsink_col_lse_noalloc"]
 
 
 class accsink_problem(ct.Structure):
@@ -99,6 +100,7 @@ def lib():
         L.accsink_time_passes.argtypes = [vp, P(accsink_problem), dbl, vp, ct.c_int, vp,
                                           P(ct.c_float), P(ct.c_float)]
         L.accsink_launch_geometry.argtypes = [vp, i32, i32, i32, P(i32)]
+        L.accsink_col_lse_noalloc.argtypes = [P(accsink_problem), dbl, vp, vp, vp]
         for name in EXPORTED:
             if name not in ("accsink_destroy", "accsink_params_default", "accsink_last_error",
                             "accsink_version"):
@@ -274,6 +276,13 @@ class Context:
         self._raise(lib().accsink_launch_geometry(self._h, int(n), int(m), int(vec), out))
         keys = ["num_sms", "row_grid", "col_splits", "col_strips", "step_grid", "stat_grid"]
         return dict(zip(keys, list(out)))
+
+
+def accsink_col_lse_noalloc(prob: accsink_problem, eps, f, ell_out, stream=None) -> int:
+    """Context-free column log-sum-exp pass that allocates nothing (see the
+    header); returns the accsink status code."""
+    return lib().accsink_col_lse_noalloc(ct.byref(prob), float(eps), _ptr(f), _ptr(ell_out),
+                                         _stream_ptr(stream))
 
 
 def result_dict(res: accsink_result) -> dict:
