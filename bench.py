@@ -39,7 +39,7 @@ WORKLOAD = ("gmm8-r3 stored sqeuclid cost n=m=16384 (1 GiB FP32, max 1), Dirichl
 # S evaluations Acc-Sinkhorn needs on this workload (measured by the GPU arm;
 # the oracle matches the GPU step count within 2% on every parity size). The
 # reference arm extrapolates its per-evaluation time with it.
-ACC_STEPS_REFERENCE = None
+ACC_STEPS_REFERENCE = 156
 
 
 def measured_peaks():
@@ -142,13 +142,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Max of a host scalar over the ranks (time of the slowest replica)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Replicas only: every rank solves its own independent problem."""
+    return SEED + rank
 
 
 def run_gpu(args):
@@ -162,8 +169,7 @@ def run_gpu(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    # Replicas only: every rank solves its own independent problem (seed + rank).
-    pr = W.gmm_stored_cost_problem(seed=SEED + rank, n=args.n, m=args.n, eps=EPS, tol=TOL)
+    pr = W.gmm_stored_cost_problem(seed=replica_seed(rank), n=args.n, m=args.n, eps=EPS, tol=TOL)
     C = torch.from_numpy(pr["C"]).to(dev)
     a = torch.from_numpy(pr["a"]).to(dev)
     b = torch.from_numpy(pr["b"]).to(dev)

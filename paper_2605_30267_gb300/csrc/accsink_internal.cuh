@@ -29,7 +29,10 @@ namespace accsink {
 constexpr double kLog2e = 1.44269504088896340736;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr int kColStrip = 128;      // columns per column-pass CTA (32 lanes x 4)
-constexpr int kPartStride = 8;      // doubles per block partial in the step kernel
+constexpr int kPartStride = 16;     // doubles per block partial in the step kernel
+constexpr int kMaxStages = 64;      // homotopy stages tabulated (mu0 / 2^63 at the last)
+constexpr int kStageSlots = 8;      // alpha, 1/alpha, 1/(1+alpha), alpha^2-2, kappa1,
+                                    // alpha^1.5, alpha_next/alpha, 1/(1+alpha_next)
 
 // Device-resident solver state. Written only by the init kernel, by block 0
 // of the step kernel (after its last grid barrier) and by the host before a
@@ -86,6 +89,8 @@ struct Work {
     double *rowpart;          // row-grid x 2 : (sum a_i u_i, sum cost) per CTA
     double *steppart;         // step-grid x 3 x kPartStride
     double *statpart;         // cost-stats grid x 4
+    // per-stage constants of Algorithm 1/2 (kStageSlots doubles per stage)
+    const double *stage_table;
     // history (hist_cap each)
     double *h_err, *h_dual, *h_mu, *h_cond;
     int32_t *h_stab;

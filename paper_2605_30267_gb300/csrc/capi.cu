@@ -16,6 +16,14 @@ using namespace accsink;
 
 namespace accsink {
 __global__ void k_set_state(DevState v, DevState *dst) { *dst = v; }
+
+struct StageTable {
+    double v[kMaxStages * kStageSlots];
+};
+__global__ void k_set_table(StageTable t, double *dst)
+{
+    for (int i = threadIdx.x; i < kMaxStages * kStageSlots; i += blockDim.x) dst[i] = t.v[i];
+}
 }  // namespace accsink
 
 namespace {
@@ -126,7 +134,7 @@ Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
     g.splits = splits;
     // the step kernel's FP64 column work is spread over every SM
     g.step_grid = std::max(1, std::min(S, (m + 63) / 64));
-    g.vec_grid = std::max(1, std::min(S, (std::max(n, m) + 255) / 256));
+    g.vec_grid = std::max(1, std::min(S, (std::max(n, m) + 63) / 64));
     g.colt_grid = warp_rows_grid(ctx, m);
     return g;
 }
@@ -188,10 +196,11 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
         (size_t)M * 8,                                                         // ell
         (size_t)SP * (size_t)M * 8,                                            // colpart
         (size_t)RG * 16,                                                       // rowpart
-        (size_t)std::max(S, 1) * kPartStride * 8 * 2,                          // steppart
+        (size_t)std::max(S, 1) * kPartStride * 8,                              // steppart
         (size_t)4 * S * 32,                                                    // statpart
         (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8,
         (size_t)std::max(H, 1) * 32, (size_t)std::max(H, 1) * 4,               // history
+        (size_t)kMaxStages * kStageSlots * 8,                                  // stage table
         sizeof(DevState)};
     size_t total = 0;
     for (size_t s : sizes) total += align_up(s, 256);
@@ -238,6 +247,7 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
     w.statpart = (double *)take();
     w.h_err = (double *)take(); w.h_dual = (double *)take(); w.h_mu = (double *)take();
     w.h_cond = (double *)take(); w.h_stab = (int32_t *)take();
+    w.stage_table = (const double *)take();
     w.st = (DevState *)take();
     ctx->n_cap = N; ctx->m_cap = M; ctx->splits_cap = SP; ctx->rowgrid_cap = RG; ctx->hist_cap = H;
     return ACCSINK_OK;
@@ -394,8 +404,28 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     if (prm->col_transpose && ensure_ct(ctx, n, m)) ct = ctx->ct;
     hs.col_mode = ct ? 1 : 0;
 
+    // Algorithm 2's stages: mu_s = mu0 / 2^s, alpha_s = sqrt(2 mu_s) and the
+    // alpha-dependent constants of Algorithm 1 and Theorem 4, per stage.
+    StageTable tab;
+    for (int st_i = 0; st_i < kMaxStages; ++st_i) {
+        const double mu_s = prm->mu0 * std::ldexp(1.0, -st_i);
+        const double a = std::sqrt(2.0 * mu_s);
+        const double an = std::sqrt(2.0 * (mu_s / 2.0));
+        double *r = tab.v + st_i * kStageSlots;
+        r[0] = a;
+        r[1] = 1.0 / a;
+        r[2] = 1.0 / (1.0 + a);
+        r[3] = a * a - 2.0;
+        r[4] = (4.0 - a * a - 2.0 * std::sqrt(a)) / (2.0 * a * (1.0 + a) * (1.0 + a));
+        r[5] = std::pow(a, 1.5);
+        r[6] = an / a;
+        r[7] = 1.0 / (1.0 + an);
+    }
+
     CK(cudaEventRecord(ctx->ev0, s));
     CK(set_state(ctx, hs, s));
+    k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
+    CK(cudaGetLastError());
     CK(launch_cost_stats(cv, w, g.stat_grid, s));
     CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, s));
     if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(n), s));

@@ -69,7 +69,7 @@ extern "C" int accsink_col_lse_noalloc(const accsink_problem *prob, double eps,
         return ACCSINK_ERR_CUDA;
     const int n = cv.n, m = cv.m;
     const int stat_grid = std::max(1, std::min(n, 4 * sms));
-    const int vec_grid = std::max(1, std::min(sms, (std::max(n, m) + 255) / 256));
+    const int vec_grid = std::max(1, std::min(sms, (std::max(n, m) + 63) / 64));
     const int strips = (m + kColStrip - 1) / kColStrip;
     int splits = (sms * occupancy_col_pass(cv.vec)) / strips;
     splits = std::max(1, std::min(splits, std::max(1, n / 8)));

@@ -12,7 +12,7 @@
 
 namespace accsink {
 
-constexpr int kVecNT = 256;
+constexpr int kVecNT = 64;   // two warps: FP64 block reductions stay short
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;   // 2 s per barrier
 
 // Sum K per-thread doubles over the block; thread k < K writes the k-th sum
@@ -269,19 +269,63 @@ cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const doubl
 // ------------------------------------------------------------------------
 // The per-iteration step, run after the row and column passes at x (the
 // iterate being evaluated, x_{k+1} in Algorithm 1's indexing):
-//   P1  merge the column partials -> ell_j = LSE_i(u_i - C_ij/eps),
-//       p_j = log(c_j/b_j) = x_j + ell_j - log b_j, raw_j = x_j - p_j
+//   P1  ell_j (merged column partials, or read from the transposed column
+//       pass), p_j = log(c_j/b_j) = x_j + ell_j - log b_j, raw_j = x_j - p_j
 //       (v-update), c_j - b_j = b_j expm1(p_j), D_j = (c_j - b_j)/p_j
 //       (eq. D), KL term b_j (e^p - 1 - p); block partials of the L1 error,
-//       sum raw, KL, <b, x>, Cond 1 lhs and Cond 2 lhs (Theorem 4).
+//       sum raw, KL, <b, x>, Cond 1 lhs and Cond 2 lhs (Theorem 4), and FP32
+//       outward-rounded bounds of raw, x, w.
 //   P2  S(x) = raw - mean(raw) (Sec. 3); Algorithm 1 w-update
-//       w+ = (w + (alpha^2 - 2) x + 2 S(x)) / (1 + alpha); Cond 2 rhs.
+//       w+ = (w + (alpha^2 - 2) x + 2 S(x)) / (1 + alpha); Cond 2 rhs and
+//       bounds of w+.
 //   P3  stop test (Sec. 5 eq. l1tol), stability verdict and gate, homotopy
-//       (Algorithm 2), next x = (w+ + S(x)) / (1 + alpha_next) (or S(x)
-//       for plain Sinkhorn); block min/max of the new x.
-//   P4  operand shifts and G for the next row pass; block 0 records the
-//       scalars, the history entry and the graph loop condition.
+//       (Algorithm 2), next x = (w+ + S(x)) / (1 + alpha_next) (or S(x) for
+//       plain Sinkhorn) and its operand G. The operand shifts only need
+//       bounds of the next x, which the P1/P2 bounds give, so no third grid
+//       barrier is needed. Block 0 records the scalars, the history entry and
+//       the graph loop condition.
 // ------------------------------------------------------------------------
+namespace {
+
+// Record slots of a block: sums (FP64) then FP32 bounds stored as doubles.
+enum {
+    R_ERR = 0, R_RAW, R_KL, R_XB, R_C1, R_C2L,          // P1 sums
+    R_RAWLO, R_RAWHI, R_XLO, R_XHI, R_WLO, R_WHI,       // P1 bounds
+    R_C2R, R_W1LO, R_W1HI,                              // P2
+    R_NSLOTS
+};
+static_assert(R_NSLOTS <= kPartStride, "step-kernel record too long");
+
+__device__ __forceinline__ float lo_f(double v) { return __double2float_rd(v); }
+__device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
+
+// Block min and max of floats (exact; ALU pipe).
+__device__ __forceinline__ void block_minmax_f(float (&lo)[3], float (&hi)[3])
+{
+    __shared__ float sh[6][kVecNT / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        if (lane == 0) { sh[k][wid] = lo[k]; sh[3 + k][wid] = hi[k]; }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float a = sh[k][0], b = sh[3 + k][0];
+        for (int q = 1; q < kVecNT / 32; ++q) { a = fminf(a, sh[k][q]); b = fmaxf(b, sh[3 + k][q]); }
+        lo[k] = a;
+        hi[k] = b;
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
 __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
                                                  cudaGraphConditionalHandle h,
                                                  double *c_out, double *s_out)
@@ -296,21 +340,31 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     const int tid = blockIdx.x * kVecNT + threadIdx.x;
     const int nthr = gridDim.x * kVecNT;
     const uint32_t nb = gridDim.x;
+    double *rec = w.steppart + (int64_t)blockIdx.x * kPartStride;
 
     const int method = st->method, first = st->first, stab = st->stability;
     const int mode = st->mode, splits = st->col_splits;
     const double mu = st->mu;
-    const double alpha = sqrt(2.0 * mu);
-    const double inv_alpha = 1.0 / alpha;
+    // alpha-dependent constants of the current stage, tabulated on the host
+    // (FP64 transcendentals are slow on this part; every warp would
+    // recompute them)
+    const bool acc_solve = (method == 1) && (mode == STEP_SOLVE);
+    const int stage = min(st->stages, kMaxStages - 1);
+    const double one[kStageSlots] = {1.0, 1.0, 0.5, -1.0, 0.0, 1.0, 1.0, 0.5};
+    const double *T = acc_solve ? w.stage_table + stage * kStageSlots : one;
+    const double alpha = T[0];
+    const double inv_alpha = T[1];
+    const double inv_1pa = T[2];
     const double inv_eps = st->inv_eps_c;
     const double shift_f = st->shift_f;
     const float kh = st->k_hi, kl = st->k_lo;
-    const bool is_acc = (method == 1) && (mode == STEP_SOLVE);
+    const bool is_acc = acc_solve;
     const bool check = is_acc && !first && stab != 0;
     const bool wupd = is_acc && !first;
 
     // ---- P1
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l
+    float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int col_mode = st->col_mode;
     for (int j = tid; j < m; j += nthr) {
         double ell;
@@ -328,35 +382,88 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         }
         const double xj = w.x[j];
         const double bj = w.b[j];
+        const double wj = w.w[j];
         const double del = xj + ell - w.logb[j];
         const double raw = xj - del;
-        const double e = expm1(del);
-        const double xi = bj * e;
-        const double D1 = (del != 0.0) ? xi / del : bj;
+        // p = log(c/b) is formed in FP64; e^p - 1, D(p)/b = (e^p - 1)/p and
+        // e^p - 1 - p are then needed to ~1e-7 relative, which FP32 gives
+        // (series for the last one at small p, where the difference cancels).
+        double xi, D1, klt;
+        const float dl = (float)del;
+        if (fabsf(dl) <= 80.0f) {
+            const float e = expm1f(dl);
+            float km;   // e^p - 1 - p
+            if (fabsf(dl) < 0.0625f) {
+                km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
+                                                     1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+            } else {
+                km = e - dl;
+            }
+            const float dr = (dl != 0.0f) ? e / dl : 1.0f;
+            xi = bj * (double)e;
+            D1 = bj * (double)dr;
+            klt = bj * (double)km;
+        } else {
+            const double e = expm1(del);
+            xi = bj * e;
+            D1 = xi / del;
+            klt = bj * (e - del);
+        }
         v[0] += fabs(xi);
         v[1] += raw;
-        v[2] += bj * (e - del);
+        v[2] += klt;
         v[3] += bj * xj;
         if (check) {
             const double p0 = w.p_prev[j];
-            const double v0 = w.w[j] * inv_alpha - w.x_prev[j];
+            const double v0 = wj * inv_alpha - w.x_prev[j];
             v[4] += p0 * p0 * D1;
             v[5] += v0 * v0 * (D1 - w.D_prev[j]);
         }
+        blo[0] = fminf(blo[0], lo_f(raw)); bhi[0] = fmaxf(bhi[0], hi_f(raw));
+        blo[1] = fminf(blo[1], lo_f(xj));  bhi[1] = fmaxf(bhi[1], hi_f(xj));
+        blo[2] = fminf(blo[2], lo_f(wj));  bhi[2] = fmaxf(bhi[2], hi_f(wj));
         w.raw[j] = raw;
         w.D1[j] = D1;
         w.del[j] = del;
         if (c_out) c_out[j] = bj * exp(del);
     }
-    block_sum_store<6>(v, w.steppart + (int64_t)blockIdx.x * kPartStride);
+    {
+        __shared__ double shs[6];
+        block_sum_store<6>(v, shs);
+        block_minmax_f(blo, bhi);
+        if (threadIdx.x < 6) rec[R_ERR + threadIdx.x] = shs[threadIdx.x];
+        if (threadIdx.x == 0) {
+            rec[R_RAWLO] = blo[0]; rec[R_RAWHI] = bhi[0];
+            rec[R_XLO] = blo[1];   rec[R_XHI] = bhi[1];
+            rec[R_WLO] = blo[2];   rec[R_WHI] = bhi[2];
+        }
+    }
     if (!grid_barrier(st, nb, kBarrierLimitNs)) { bail(); return; }
 
     // ---- P2
-    double t[6];
-    const int ops6[6] = {0, 0, 0, 0, 0, 0};
-    grid_totals<6>(w.steppart, nb, 0, ops6, t);
-    const double err = t[0];
-    const double rbar = t[1] / (double)m;
+    double t[12];
+    {
+        double t6[6];
+        const int ops6[6] = {0, 0, 0, 0, 0, 0};
+        grid_totals<6>(w.steppart, nb, R_ERR, ops6, t6);
+        float blo2[3] = {INFINITY, INFINITY, INFINITY}, bhi2[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
+            const double *r = w.steppart + (int64_t)b * kPartStride;
+            blo2[0] = fminf(blo2[0], (float)__ldcg(&r[R_RAWLO]));
+            bhi2[0] = fmaxf(bhi2[0], (float)__ldcg(&r[R_RAWHI]));
+            blo2[1] = fminf(blo2[1], (float)__ldcg(&r[R_XLO]));
+            bhi2[1] = fmaxf(bhi2[1], (float)__ldcg(&r[R_XHI]));
+            blo2[2] = fminf(blo2[2], (float)__ldcg(&r[R_WLO]));
+            bhi2[2] = fmaxf(bhi2[2], (float)__ldcg(&r[R_WHI]));
+        }
+        block_minmax_f(blo2, bhi2);
+        for (int k = 0; k < 6; ++k) t[k] = t6[k];
+        t[R_RAWLO] = blo2[0]; t[R_RAWHI] = bhi2[0];
+        t[R_XLO] = blo2[1];   t[R_XHI] = bhi2[1];
+        t[R_WLO] = blo2[2];   t[R_WHI] = bhi2[2];
+    }
+    const double err = t[R_ERR];
+    const double rbar = t[R_RAW] / (double)m;
     double sum_au = 0.0;
     {
         double au[1] = {0.0};
@@ -366,7 +473,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         block_allreduce<1>(au, op1);
         sum_au = au[0];
     }
-    const double dual = st->eps_user * (sum_au + t[3] - 1.0);
+    const double dual = st->eps_user * (sum_au + t[R_XB] - 1.0);
     if (mode == STEP_MAP) {
         for (int j = tid; j < m; j += nthr) s_out[j] = st->eps_user * (w.raw[j] - rbar);
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -377,33 +484,53 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         return;
     }
     double v2[1] = {0.0};
+    float wlo[3] = {INFINITY, INFINITY, INFINITY}, whi[3] = {-INFINITY, -INFINITY, -INFINITY};
     if (wupd) {
-        const double a2 = alpha * alpha - 2.0;
+        const double a2 = T[3];
         for (int j = tid; j < m; j += nthr) {
             const double s = w.raw[j] - rbar;
             const double xj = w.x[j];
-            const double w1 = (w.w[j] + a2 * xj + 2.0 * s) / (1.0 + alpha);
+            const double w1 = (w.w[j] + a2 * xj + 2.0 * s) * inv_1pa;
             w.w1[j] = w1;
             const double v1 = w1 * inv_alpha - xj;
             v2[0] += v1 * v1 * w.D1[j];
+            wlo[0] = fminf(wlo[0], lo_f(w1));
+            whi[0] = fmaxf(whi[0], hi_f(w1));
         }
     }
     {
         __shared__ double shv[1];
         block_sum_store<1>(v2, shv);
-        if (threadIdx.x == 0) w.steppart[(int64_t)blockIdx.x * kPartStride + 6] = shv[0];
+        block_minmax_f(wlo, whi);
+        if (threadIdx.x == 0) {
+            rec[R_C2R] = shv[0];
+            rec[R_W1LO] = wlo[0];
+            rec[R_W1HI] = whi[0];
+        }
     }
     if (!grid_barrier(st, 2 * nb, kBarrierLimitNs)) { bail(); return; }
 
     // ---- P3
-    double t2[1];
-    const int ops1[1] = {0};
-    grid_totals<1>(w.steppart, nb, 6, ops1, t2);
-    const double c1 = t[4], c2l = t[5], c2r_sum = t2[0];
-    const double kappa1 = (4.0 - alpha * alpha - 2.0 * sqrt(alpha)) /
-                          (2.0 * alpha * (1.0 + alpha) * (1.0 + alpha));
+    double t2[3];
+    {
+        double c2[1];
+        const int op1[1] = {0};
+        grid_totals<1>(w.steppart, nb, R_C2R, op1, c2);
+        float wl[3] = {INFINITY, INFINITY, INFINITY}, wh[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
+            const double *r = w.steppart + (int64_t)b * kPartStride;
+            wl[0] = fminf(wl[0], (float)__ldcg(&r[R_W1LO]));
+            wh[0] = fmaxf(wh[0], (float)__ldcg(&r[R_W1HI]));
+        }
+        block_minmax_f(wl, wh);
+        t2[0] = c2[0];
+        t2[1] = wl[0];
+        t2[2] = wh[0];
+    }
+    const double c1 = t[R_C1], c2l = t[R_C2L], c2r_sum = t2[0];
+    const double kappa1 = T[4];
     const double c1r = kappa1 * st->kl_prev;
-    const double c2r = pow(alpha, 1.5) * c2r_sum;
+    const double c2r = T[5] * c2r_sum;
     int stab_bits = 0;
     if (check) stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
     const bool gate = (stab == 2) && (stab_bits != 0);
@@ -425,9 +552,30 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             stages += 1;
         }
     }
-    const double alpha_new = sqrt(2.0 * mu_new);
-    const double ratio = (stage_end && st->carry == 0) ? alpha_new / alpha : 1.0;
-    double xmn = DBL_MAX, xmx = -DBL_MAX;
+    // the next iterate uses the next stage's alpha after a stage change
+    const double inv_1pa_new = stage_end ? T[7] : inv_1pa;
+    const double ratio = (stage_end && st->carry == 0) ? T[6] : 1.0;
+    // bounds of the next iterate from the P1/P2 bounds (all factors > 0)
+    const double slo = t[R_RAWLO] - rbar, shi = t[R_RAWHI] - rbar;
+    double xlo, xhi;
+    if (is_acc) {
+        double w1lo, w1hi;
+        if (!wupd) { w1lo = t[R_WLO]; w1hi = t[R_WHI]; }
+        else if (gate) { w1lo = alpha * t[R_XLO]; w1hi = alpha * t[R_XHI]; }
+        else { w1lo = t2[1]; w1hi = t2[2]; }
+        xlo = (w1lo * ratio + slo) * inv_1pa_new;
+        xhi = (w1hi * ratio + shi) * inv_1pa_new;
+    } else {
+        xlo = slo;
+        xhi = shi;
+    }
+    // widen by a relative margin that covers the FP64 rounding of the bounds
+    xlo -= 1e-12 * (1.0 + fabs(xlo));
+    xhi += 1e-12 * (1.0 + fabs(xhi));
+    const double eps_c = st->eps_c;
+    const double shift_g = st->cabs - eps_c * xlo;
+    const double shift_fn = st->cabs - (eps_c * st->min_loga - eps_c * xhi + st->cmin -
+                                        eps_c * st->log_m);
     if (!stop) {
         for (int j = tid; j < m; j += nthr) {
             const double s = w.raw[j] - rbar;
@@ -436,7 +584,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             if (is_acc) {
                 double w1 = wupd ? (gate ? alpha * xj : w.w1[j]) : w.w[j];
                 w1 *= ratio;
-                xn = (w1 + s) / (1.0 + alpha_new);
+                xn = (w1 + s) * inv_1pa_new;
                 w.w[j] = w1;
             } else {
                 xn = s;
@@ -445,30 +593,8 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             w.x[j] = xn;
             w.p_prev[j] = w.del[j];
             w.D_prev[j] = w.D1[j];
-            xmn = fmin(xmn, xn);
-            xmx = fmax(xmx, xn);
+            write_G(w, j, eps_c * xn + shift_g, kh);
         }
-    }
-    {
-        __shared__ double shm[2];
-        block_minmax_store(xmn, xmx, shm);
-        if (threadIdx.x == 0) {
-            w.steppart[(int64_t)blockIdx.x * kPartStride + 0] = shm[0];
-            w.steppart[(int64_t)blockIdx.x * kPartStride + 1] = shm[1];
-        }
-    }
-    if (!grid_barrier(st, 3 * nb, kBarrierLimitNs)) { bail(); return; }
-
-    // ---- P4
-    double t3[2];
-    const int ops2[2] = {1, 2};
-    grid_totals<2>(w.steppart, nb, 0, ops2, t3);
-    const double eps_c = st->eps_c;
-    double shift_g = 0.0, shift_fn = 0.0;
-    if (!stop) {
-        shift_g = st->cabs - eps_c * t3[0];
-        shift_fn = st->cabs - (eps_c * st->min_loga - eps_c * t3[1] + st->cmin - eps_c * st->log_m);
-        for (int j = tid; j < m; j += nthr) write_G(w, j, eps_c * w.x[j] + shift_g, kh);
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const int e = st->steps;
@@ -487,7 +613,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         st->steps = steps_new;
         st->err = err;
         st->dual = dual;
-        st->kl_prev = t[2];
+        st->kl_prev = t[R_KL];
         st->first = 0;
         if (stab_bits) st->failures += 1;
         if (wupd) {
