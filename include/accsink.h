@@ -152,12 +152,17 @@ const char *accsink_version(void);
  * and g_out (m) are caller-allocated device arrays that receive the
  * potentials in cost units at the returned iterate; f is the row pass at
  * that g, so the row marginal is exact up to rounding. res (host) receives
- * the summary. Returns res->status (ACCSINK_ERR_MAXITER if not converged). */
+ * the summary. Returns res->status (ACCSINK_ERR_MAXITER if not converged).
+ * Every cost kind is served: DENSE reads C; SQEUCLID and COSINE form each
+ * C_ij from X and Y inside the passes (1 <= d <= 64), never storing an
+ * n x m matrix, with the device workspace O((n + m) d). Non-finite points
+ * give ACCSINK_ERR_NONFINITE. */
 int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob,
                   const accsink_params *params, void *stream,
                   double *f_out, double *g_out, accsink_result *res);
 
-/* Same solve with every problem pointer and f_out/g_out in HOST memory:
+/* Same solve (any cost kind) with every problem pointer and f_out/g_out in
+ * HOST memory:
  * the library copies the inputs to its workspace, solves, and copies the
  * potentials back, all on `stream`. Host buffers may be pageable or pinned
  * (pinned copies are faster). */
@@ -178,17 +183,21 @@ int accsink_get_history(accsink_ctx *ctx, int32_t capacity, double *err,
 
 /* ---- single passes (the hot path's steps, for tests and roofline timing) */
 
+/* Every single-pass call serves every cost kind and honours cost_scale: with
+ * MAX_TO_ONE the cost is C / max C and potentials are in its units. For
+ * point clouds each call first forms the O((n + m) d) point workspace. */
+
 /* Row pass, Sec. 2 u-update in cost units (Sec. 8 step "row LSE"):
  *   f_i = eps log a_i - eps LSE_j((g_j - C_ij) / eps).
  * a is used as given (not renormalised). g (m), a (n) and f_out (n) are
- * device FP64 arrays. DENSE costs only. */
+ * device FP64 arrays. */
 int accsink_row_pass(accsink_ctx *ctx, const accsink_problem *prob,
                      double eps, const double *g, double *f_out, void *stream);
 
 /* Column log-sum-exp of the v-update (Sec. 2, eq. v-update):
  *   ell_j = LSE_i((f_i - C_ij) / eps),
  * so that the column sums of P(f, g) are c_j = exp(g_j / eps + ell_j).
- * f (n) and ell_out (m) are device FP64 arrays. DENSE costs only. */
+ * f (n) and ell_out (m) are device FP64 arrays. */
 int accsink_col_lse(accsink_ctx *ctx, const accsink_problem *prob,
                     double eps, const double *f, double *ell_out, void *stream);
 
@@ -203,7 +212,7 @@ int accsink_sinkhorn_map(accsink_ctx *ctx, const accsink_problem *prob,
 
 /* Transport cost <C, P> (eq. EOT) of the plan P_ij = exp((f_i + g_j - C_ij)
  * / eps) for device potentials f (n), g (m); result in *cost_out (host),
- * accumulated in FP64. DENSE costs only. */
+ * accumulated in FP64. */
 int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob,
                            double eps, const double *f, const double *g,
                            double *cost_out, void *stream);
@@ -216,7 +225,9 @@ int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob,
  * transposed copy when the context can hold it, as the solver does), and
  * writes the mean device milliseconds per launch to *row_ms and *col_ms
  * (host). Used for the HBM roofline of the passes; each launch reads the
- * 4 n m bytes of the cost once plus O(n + m) operands. */
+ * 4 n m bytes of the cost once plus O(n + m) operands. For point clouds the
+ * two on-the-fly passes are timed (a must be given; n m cost entries each,
+ * bound by FP32 arithmetic rather than by memory). */
 int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double eps,
                         const double *g, int reps, void *stream, float *row_ms,
                         float *col_ms);

@@ -164,6 +164,35 @@ def problem_dense(C, a=None, b=None, scale_to_max=False) -> accsink_problem:
     return pr
 
 
+def problem_points(X, Y, kind="sqeuclid", a=None, b=None, scale_to_max=False) -> accsink_problem:
+    """Problem struct for a point-cloud cost formed on the fly from FP32 CUDA
+    point clouds X (n x d) and Y (m x d), row-major and contiguous:
+    kind "sqeuclid" (||x_i - y_j||^2) or "cosine" (1 - <x_i, y_j>)."""
+    import torch
+    _check_dev(X, torch.float32, "X")
+    _check_dev(Y, torch.float32, "Y")
+    if X.dim() != 2 or Y.dim() != 2 or X.shape[1] != Y.shape[1]:
+        raise ValueError("X and Y must be 2-D with the same number of columns")
+    if not (X.is_contiguous() and Y.is_contiguous()):
+        raise ValueError("X and Y must be contiguous")
+    n, d = X.shape
+    m = Y.shape[0]
+    pr = accsink_problem()
+    pr.n, pr.m, pr.d = n, m, d
+    pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+    pr.X = X.data_ptr()
+    pr.Y = Y.data_ptr()
+    if a is not None:
+        _check_dev(a, torch.float64, "a", n)
+        pr.a = a.data_ptr()
+    if b is not None:
+        _check_dev(b, torch.float64, "b", m)
+        pr.b = b.data_ptr()
+    pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
+    pr._keep = (X, Y, a, b)
+    return pr
+
+
 class Context:
     """An accsink context on one CUDA device (wraps accsink_create/destroy)."""
 
@@ -209,14 +238,25 @@ class Context:
         return res
 
     def accsink_solve_host(self, C, a, b, params: accsink_params, f_out, g_out,
-                           scale_to_max=False, stream=None, allow_maxiter=True) -> accsink_result:
-        """C, a, b, f_out, g_out: host numpy arrays (FP32 C, FP64 vectors)."""
+                           scale_to_max=False, stream=None, allow_maxiter=True,
+                           X=None, Y=None, kind="sqeuclid") -> accsink_result:
+        """C, a, b, f_out, g_out: host numpy arrays (FP32 C, FP64 vectors).
+        With C None, the cost is formed from the FP32 host point clouds X, Y."""
         import numpy as np
-        assert C.dtype == np.float32 and C.flags.c_contiguous
-        n, m = C.shape
         pr = accsink_problem()
-        pr.n, pr.m, pr.cost_kind, pr.ldc = n, m, COST_DENSE, m
-        pr.C = C.ctypes.data
+        if C is not None:
+            assert C.dtype == np.float32 and C.flags.c_contiguous
+            n, m = C.shape
+            pr.n, pr.m, pr.cost_kind, pr.ldc = n, m, COST_DENSE, m
+            pr.C = C.ctypes.data
+        else:
+            assert X.dtype == np.float32 and X.flags.c_contiguous
+            assert Y.dtype == np.float32 and Y.flags.c_contiguous
+            pr.n, pr.d = X.shape
+            pr.m = Y.shape[0]
+            pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+            pr.X = X.ctypes.data
+            pr.Y = Y.ctypes.data
         pr.a = np.ascontiguousarray(a, np.float64).ctypes.data if a.dtype == np.float64 and a.flags.c_contiguous else None
         pr.b = np.ascontiguousarray(b, np.float64).ctypes.data if b.dtype == np.float64 and b.flags.c_contiguous else None
         if pr.a is None or pr.b is None:
@@ -287,6 +327,27 @@ def accsink_col_lse_noalloc(prob: accsink_problem, eps, f, ell_out, stream=None)
 
 def result_dict(res: accsink_result) -> dict:
     return {k: getattr(res, k) for k, _ in accsink_result._fields_}
+
+
+def solve_points(X, Y, a, b, eps, kind="sqeuclid", tol=1e-6, method="acc", scale_to_max=False,
+                 ctx: Context | None = None, stream=None, **params):
+    """Convenience: solve a point-cloud problem held in CUDA tensors.
+
+    Returns (f, g, result dict) with f, g FP64 CUDA tensors in cost units."""
+    import torch
+    own = ctx is None
+    ctx = ctx or Context(X.device.index or 0)
+    try:
+        prob = problem_points(X, Y, kind, a, b, scale_to_max)
+        p = default_params(eps=float(eps), tol=float(tol),
+                           method=ACC if method in ("acc", ACC) else PLAIN, **params)
+        f = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
+        g = torch.empty(Y.shape[0], dtype=torch.float64, device=X.device)
+        res = ctx.accsink_solve(prob, p, f, g, stream=stream)
+        return f, g, result_dict(res)
+    finally:
+        if own:
+            ctx.close()
 
 
 def solve(C, a, b, eps, tol=1e-6, method="acc", scale_to_max=False, ctx: Context | None = None,

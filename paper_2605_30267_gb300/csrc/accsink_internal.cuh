@@ -95,11 +95,29 @@ struct Work {
     double *h_err, *h_dual, *h_mu, *h_cond;
     int32_t *h_stab;
     DevState *st;
+    // point-cloud costs (NULL for a dense cost): Bx = s||x||^2 (or 0), By =
+    // s||y||^2 (or s) in FP64 and as pairs; scaled points in SoA pairs
+    double *Bx64, *By64;
+    float *Bxh, *Bxl, *Byh, *Byl;
+    float *PXh, *PXl, *PYh, *PYl;
+    int64_t ldx, ldy;         // SoA row strides (n, m rounded up to 4)
+    double *rowmax;           // n: row maxima of the cost (scaling)
     // inputs of the single-pass entry points
     const double *b_src;      // column marginal to copy (may be NULL)
     const double *f_given;    // row potentials weighting the cost sum (may be NULL)
     int32_t nstat;            // number of cost-statistics partials
     int32_t ignore_done;      // row pass runs even when the solve has stopped
+};
+
+// One pass over a point-cloud cost: rows of P (AoS, nr x d) against columns
+// whose scaled points are Qh/Ql (SoA, d x ldq); A (per column) and B (per
+// row) are the expansion terms as pairs; Ch (per column, hi) serves the
+// transport-cost sum.
+struct PointView {
+    const float *P;
+    const float *Ah, *Al, *Bh, *Bl, *Qh, *Ql, *Ch;
+    int64_t ldq;
+    int32_t nr, nc, d, pad;
 };
 
 struct CostView {
@@ -215,9 +233,9 @@ cudaError_t launch_step(const CostView &cv, const Work &w, int grid,
 cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double *c_out,
                             double *s_out, cudaStream_t s);
 cudaError_t launch_prep_g(const CostView &cv, const Work &w, int grid, const double *g,
-                          const double *a_in, double eps, cudaStream_t s);
+                          const double *a_in, double eps, int scale_max, cudaStream_t s);
 cudaError_t launch_prep_f(const CostView &cv, const Work &w, int grid, const double *f,
-                          double eps, cudaStream_t s);
+                          double eps, int scale_max, cudaStream_t s);
 cudaError_t launch_scale_out(const double *src, double scale, double *dst, int n,
                              cudaStream_t s);
 cudaError_t launch_col_finish_lse(const Work &w, int m, double *ell_out, cudaStream_t s);
@@ -235,6 +253,14 @@ cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaSt
 // Which kernel serves 128-bit-aligned row passes: 0 warp-per-row, 1 TMA.
 int row_kernel_choice();
 int occupancy_col_pass(int vec);
+cudaError_t launch_points_pass(const PointView &pv, const Work &w, int grid, int mode,
+                               bool with_cost, cudaStream_t s);
+int occupancy_points_pass();
+cudaError_t launch_points_rowmax(const float *X, const float *Y, int n, int m, int d, int kind,
+                                 double *rowmax, int grid, cudaStream_t s);
+cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, int d, int kind,
+                                int scale_max, const Work &w, double *scal, double *blockmax,
+                                int nblk, cudaStream_t s);
 void setup_col_pass();
 
 }  // namespace accsink

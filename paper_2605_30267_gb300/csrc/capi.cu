@@ -24,6 +24,26 @@ __global__ void k_set_table(StageTable t, double *dst)
 {
     for (int i = threadIdx.x; i < kMaxStages * kStageSlots; i += blockDim.x) dst[i] = t.v[i];
 }
+
+// Algorithm 2's stages: mu_s = mu0 / 2^s, alpha_s = sqrt(2 mu_s), and the
+// alpha-dependent constants of Algorithm 1 and Theorem 4, per stage.
+void fill_stage_table(StageTable &tab, double mu0)
+{
+    for (int st_i = 0; st_i < kMaxStages; ++st_i) {
+        const double mu_s = mu0 * std::ldexp(1.0, -st_i);
+        const double a = std::sqrt(2.0 * mu_s);
+        const double an = std::sqrt(2.0 * (mu_s / 2.0));
+        double *r = tab.v + st_i * kStageSlots;
+        r[0] = a;
+        r[1] = 1.0 / a;
+        r[2] = 1.0 / (1.0 + a);
+        r[3] = a * a - 2.0;
+        r[4] = (4.0 - a * a - 2.0 * std::sqrt(a)) / (2.0 * a * (1.0 + a) * (1.0 + a));
+        r[5] = std::pow(a, 1.5);
+        r[6] = an / a;
+        r[7] = 1.0 / (1.0 + an);
+    }
+}
 }  // namespace accsink
 
 namespace {
@@ -75,6 +95,10 @@ struct accsink_ctx {
     // transposed copy of the cost for the column pass
     float *ct = nullptr;
     size_t ct_bytes = 0;
+    // point-cloud workspace
+    void *pts = nullptr;
+    size_t pts_bytes = 0;
+    int occ_pts = 1;
 };
 
 namespace {
@@ -258,12 +282,18 @@ int validate_problem(accsink_ctx *ctx, const accsink_problem *p, bool need_cost_
     if (!p) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "problem is NULL");
     if (p->n < 1 || p->m < 1) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "n and m must be >= 1");
     if (p->cost_kind != ACCSINK_COST_DENSE) {
-        if (p->cost_kind == ACCSINK_COST_SQEUCLID || p->cost_kind == ACCSINK_COST_COSINE)
+        if (p->cost_kind != ACCSINK_COST_SQEUCLID && p->cost_kind != ACCSINK_COST_COSINE)
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_kind");
+        if (need_cost_dense)
             return fail(ctx, ACCSINK_ERR_UNSUPPORTED,
-                        "point-cloud costs are not served by this entry point yet");
-        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_kind");
+                        "this entry point serves dense costs only");
+        if (!p->X || !p->Y) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "X and Y must be given");
+        if (p->d < 1 || p->d > 64)
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "point dimension d must be in 1..64");
+        if (p->cost_scale != ACCSINK_SCALE_NONE && p->cost_scale != ACCSINK_SCALE_MAX_TO_ONE)
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_scale");
+        return ACCSINK_OK;
     }
-    (void)need_cost_dense;
     if (!p->C) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "C is NULL");
     const int64_t ldc = p->ldc ? p->ldc : p->m;
     if (ldc < p->m) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "ldc < m");
@@ -322,6 +352,9 @@ cudaError_t launch_passes(const CostView &cv, const Work &w, const Geometry &g, 
     return launch_col_pass(cv, w, g.splits, s);
 }
 
+template <class Body>
+int build_loop_graph(accsink_ctx *ctx, const GraphKey &key, Body body);
+
 int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const float *ct)
 {
     GraphKey key;
@@ -329,6 +362,20 @@ int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const flo
     key.row_grid = g.row_grid; key.splits = g.splits; key.step_grid = g.step_grid;
     key.colt_grid = g.colt_grid; key.ct = ct;
     key.ws = ctx->ws;
+    Work w = ctx->w;
+    w.ignore_done = 0;
+    return build_loop_graph(ctx, key, [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        cudaError_t e = launch_passes(cv, w, g, ct, cs);
+        if (e != cudaSuccess) return e;
+        return launch_step(cv, w, g.step_grid, h, cs);
+    });
+}
+
+// WHILE(cond) { body } with the body captured from `body(stream, handle)`;
+// reuses the cached executable when `key` matches.
+template <class Body>
+int build_loop_graph(accsink_ctx *ctx, const GraphKey &key, Body body)
+{
     if (ctx->exec && ctx->key == key) return ACCSINK_OK;
     free_graph(ctx);
     cudaGraph_t graph = nullptr;
@@ -344,21 +391,16 @@ int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const flo
     cudaGraphNode_t node;
     e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaGraphAddNode"); }
-    cudaGraph_t body = cp.conditional.phGraph_out[0];
-    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body, nullptr, nullptr, 0,
+    cudaGraph_t body_graph = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(ctx->cap_stream, body_graph, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
-    Work w = ctx->w;
-    w.ignore_done = 0;
-    cudaError_t e1 = launch_passes(cv, w, g, ct, ctx->cap_stream);
-    cudaError_t e2 = cudaSuccess;
-    cudaError_t e3 = launch_step(cv, w, g.step_grid, handle, ctx->cap_stream);
+    cudaError_t e1 = body(ctx->cap_stream, handle);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &out);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess) {
+    if (e1 != cudaSuccess || e != cudaSuccess) {
         cudaGraphDestroy(graph);
-        cudaError_t bad = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e));
-        return cuda_fail(ctx, bad, "capturing the solve loop");
+        return cuda_fail(ctx, e1 != cudaSuccess ? e1 : e, "capturing the solve loop");
     }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
@@ -404,23 +446,8 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     if (prm->col_transpose && ensure_ct(ctx, n, m)) ct = ctx->ct;
     hs.col_mode = ct ? 1 : 0;
 
-    // Algorithm 2's stages: mu_s = mu0 / 2^s, alpha_s = sqrt(2 mu_s) and the
-    // alpha-dependent constants of Algorithm 1 and Theorem 4, per stage.
     StageTable tab;
-    for (int st_i = 0; st_i < kMaxStages; ++st_i) {
-        const double mu_s = prm->mu0 * std::ldexp(1.0, -st_i);
-        const double a = std::sqrt(2.0 * mu_s);
-        const double an = std::sqrt(2.0 * (mu_s / 2.0));
-        double *r = tab.v + st_i * kStageSlots;
-        r[0] = a;
-        r[1] = 1.0 / a;
-        r[2] = 1.0 / (1.0 + a);
-        r[3] = a * a - 2.0;
-        r[4] = (4.0 - a * a - 2.0 * std::sqrt(a)) / (2.0 * a * (1.0 + a) * (1.0 + a));
-        r[5] = std::pow(a, 1.5);
-        r[6] = an / a;
-        r[7] = 1.0 / (1.0 + an);
-    }
+    fill_stage_table(tab, prm->mu0);
 
     CK(cudaEventRecord(ctx->ev0, s));
     CK(set_state(ctx, hs, s));
@@ -510,6 +537,226 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     return ACCSINK_OK;
 }
 
+// A point-cloud problem's launch plan: grids, workspace views and the two
+// pass views (row pass: rows of X against Y; column pass: rows of Y
+// against X).
+struct PointPlan {
+    CostView cv;
+    Geometry g;
+    Work w;
+    PointView pr, pc;
+    int prow = 1, pcol = 1, kind = 1, nblk = 1;
+    double *blockmax = nullptr, *scal = nullptr;
+};
+
+int points_grid(const accsink_ctx *ctx, int rows)
+{
+    const int64_t max_warps = (int64_t)ctx->num_sms * ctx->occ_pts * 8;
+    const int64_t k = (rows + max_warps - 1) / max_warps;
+    const int64_t warps = (rows + k - 1) / k;
+    return (int)std::max<int64_t>(1, (warps + 7) / 8);
+}
+
+// Allocates the solve workspace and the O((n + m) d) point workspace and
+// fills `pl`. Launches nothing.
+int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPlan &pl)
+{
+    const int n = prob->n, m = prob->m, d = prob->d;
+    pl.kind = prob->cost_kind == ACCSINK_COST_SQEUCLID ? 1 : 2;
+    pl.cv.C = nullptr;
+    pl.cv.ldc = m;
+    pl.cv.n = n;
+    pl.cv.m = m;
+    pl.cv.vec = 1;
+    pl.g = geometry(ctx, n, m, 1);
+    pl.prow = points_grid(ctx, n);
+    pl.pcol = points_grid(ctx, m);
+    int rc = ensure_workspace(ctx, n, m, 1, pl.prow, hist);
+    if (rc != ACCSINK_OK) return rc;
+    const int64_t ldx = (n + 3) / 4 * 4, ldy = (m + 3) / 4 * 4;
+    pl.nblk = std::max(1, std::min(ctx->num_sms, (std::max(n, m) + 255) / 256));
+    std::vector<size_t> sizes = {(size_t)n * 8, (size_t)m * 8, (size_t)ldx * 4, (size_t)ldx * 4,
+                                 (size_t)ldy * 4, (size_t)ldy * 4, (size_t)d * ldx * 4,
+                                 (size_t)d * ldx * 4, (size_t)d * ldy * 4, (size_t)d * ldy * 4,
+                                 (size_t)n * 8, (size_t)pl.nblk * 40, 16};
+    size_t need = 0;
+    for (size_t z : sizes) need += align_up(z, 256);
+    if (need > ctx->pts_bytes) {
+        if (ctx->budget && ctx->ws_bytes + ctx->stage_bytes + ctx->ct_bytes + need > ctx->budget)
+            return fail(ctx, ACCSINK_ERR_BUDGET, "point-cloud workspace exceeds the budget");
+        if (ctx->pts) cudaFree(ctx->pts);
+        ctx->pts = nullptr;
+        ctx->pts_bytes = 0;
+        free_graph(ctx);
+        if (cudaMalloc(&ctx->pts, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, ACCSINK_ERR_OOM, "cudaMalloc of the point-cloud workspace failed");
+        }
+        ctx->pts_bytes = need;
+    }
+    char *p = (char *)ctx->pts;
+    size_t k = 0;
+    auto take = [&]() -> void * {
+        void *r = p;
+        p += align_up(sizes[k++], 256);
+        return r;
+    };
+    Work &w = pl.w;
+    w = ctx->w;
+    w.Bx64 = (double *)take(); w.By64 = (double *)take();
+    w.Bxh = (float *)take(); w.Bxl = (float *)take();
+    w.Byh = (float *)take(); w.Byl = (float *)take();
+    w.PXh = (float *)take(); w.PXl = (float *)take();
+    w.PYh = (float *)take(); w.PYl = (float *)take();
+    w.rowmax = (double *)take();
+    pl.blockmax = (double *)take();
+    pl.scal = (double *)take();
+    w.ldx = ldx;
+    w.ldy = ldy;
+    w.nstat = 1;
+    w.b_src = nullptr;
+    w.f_given = nullptr;
+    w.ignore_done = 0;
+    PointView &pr = pl.pr, &pc = pl.pc;
+    pr.P = prob->X; pr.Ah = w.G; pr.Al = w.Gk; pr.Bh = w.Bxh; pr.Bl = w.Bxl;
+    pr.Qh = w.PYh; pr.Ql = w.PYl; pr.Ch = w.Byh; pr.ldq = ldy; pr.nr = n; pr.nc = m; pr.d = d;
+    pc.P = prob->Y; pc.Ah = w.Fh; pc.Al = w.Fk; pc.Bh = w.Byh; pc.Bl = w.Byl;
+    pc.Qh = w.PXh; pc.Ql = w.PXl; pc.Ch = w.Bxh; pc.ldq = ldx; pc.nr = m; pc.nc = n; pc.d = d;
+    return ACCSINK_OK;
+}
+
+// Row maxima (for max C and the MAX_TO_ONE scale), then the FP64 norms, the
+// scaled SoA copies of the points and the cost-statistics record.
+cudaError_t points_prologue(const accsink_problem *prob, const PointPlan &pl, cudaStream_t s)
+{
+    cudaError_t e = launch_points_rowmax(prob->X, prob->Y, prob->n, prob->m, prob->d, pl.kind,
+                                         pl.w.rowmax, pl.prow, s);
+    if (e != cudaSuccess) return e;
+    return launch_points_setup(prob->X, prob->Y, prob->n, prob->m, prob->d, pl.kind,
+                               prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, pl.w, pl.scal,
+                               pl.blockmax, pl.nblk, s);
+}
+
+// Point-cloud costs (squared Euclidean, cosine) built on the fly: the same
+// loop as solve_device with the two point passes of points.cu.
+int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *prm,
+                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res)
+{
+    const int n = prob->n, m = prob->m;
+    PointPlan pl;
+    int rc = points_plan(ctx, prob, prm->history, pl);
+    if (rc != ACCSINK_OK) return rc;
+    const CostView &cv = pl.cv;
+    const Geometry &g = pl.g;
+    const Work &w = pl.w;
+    const PointView &pr = pl.pr, &pc = pl.pc;
+    const int prow = pl.prow, pcol = pl.pcol, kind = pl.kind;
+
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.eps_user = prm->eps;
+    hs.tol = prm->tol;
+    hs.mu = prm->mu0;
+    hs.method = prm->method;
+    hs.stability = prm->stability;
+    hs.carry = prm->carry;
+    hs.max_steps = prm->max_sinkhorn_steps;
+    hs.m_stage = prm->m0;
+    hs.hist_cap = prm->history;
+    hs.row_grid = prow;
+    hs.col_splits = 1;
+    hs.use_cond = prm->use_graph ? 1 : 0;
+    hs.first = 1;
+    hs.col_mode = 1;
+    StageTable tab;
+    fill_stage_table(tab, prm->mu0);
+
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(set_state(ctx, hs, s));
+    k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
+    CK(cudaGetLastError());
+    CK(points_prologue(prob, pl, s));
+    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, 0, s));
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ctx->h_state->done) {
+        const int st = ctx->h_state->status;
+        std::memset(res, 0, sizeof(*res));
+        res->status = st;
+        if (st == ACCSINK_ERR_NONFINITE) return fail(ctx, st, "X, Y, a or b holds NaN or Inf");
+        if (st == ACCSINK_ERR_NONPOSITIVE_MARGINAL)
+            return fail(ctx, st, "every a_i and b_j must be > 0");
+        return fail(ctx, st == 0 ? ACCSINK_ERR_INVALID_ARG : st, "set-up failed");
+    }
+    auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle h) {
+        cudaError_t e = launch_points_pass(pr, w, prow, 0, false, cs);
+        if (e != cudaSuccess) return e;
+        e = launch_points_pass(pc, w, pcol, 1, false, cs);
+        if (e != cudaSuccess) return e;
+        return launch_step(cv, w, g.step_grid, h, cs);
+    };
+    bool use_graph = prm->use_graph && !ctx->graph_broken;
+    if (use_graph) {
+        GraphKey key;
+        key.C = prob->X; key.ct = prob->Y; key.ldc = prob->d; key.n = n; key.m = m;
+        key.vec = 100 + kind; key.row_grid = prow; key.colt_grid = pcol;
+        key.step_grid = g.step_grid; key.ws = ctx->pts;
+        rc = build_loop_graph(ctx, key, body);
+        if (rc != ACCSINK_OK) {
+            ctx->graph_broken = true;
+            ctx->graph_error = ctx->err;
+            ctx->err.clear();
+            use_graph = false;
+            CK(cudaMemsetAsync(&w.st->use_cond, 0, sizeof(int32_t), s));
+        }
+    }
+    if (use_graph) {
+        CK(cudaGraphLaunch(ctx->exec, s));
+    } else {
+        for (;;) {
+            for (int u = 0; u < 8; ++u) CK(body(s, 0));
+            CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            if (ctx->h_state->done) break;
+        }
+    }
+    if (prm->evaluate) {
+        Work we = w;
+        we.ignore_done = 1;
+        CK(launch_points_pass(pr, we, prow, 0, true, s));
+    }
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(launch_scale_out(w.u, prm->eps, f_out, n, s));
+    CK(launch_scale_out(w.x, prm->eps, g_out, m, s));
+    CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)prow * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaStreamSynchronize(s));
+    const DevState &fs = *ctx->h_state;
+    std::memset(res, 0, sizeof(*res));
+    res->status = fs.status;
+    res->sinkhorn_steps = fs.steps;
+    res->outer_stages = fs.stages;
+    res->stability_failures = fs.failures;
+    res->marginal_l1 = fs.err;
+    res->dual_objective = fs.dual;
+    res->cost_max = fs.cmax;
+    res->transport_cost = NAN;
+    if (prm->evaluate) {
+        double c = 0.0;
+        for (int b = 0; b < prow; ++b) c += ctx->h_rowpart[2 * b + 1];
+        res->transport_cost = c;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    res->gpu_ms = ms;
+    res->loop_mode = use_graph ? 1 : 0;
+    ctx->last_hist_count = std::min(fs.steps, prm->history);
+    if (fs.status == ACCSINK_ERR_MAXITER)
+        return fail(ctx, ACCSINK_ERR_MAXITER, "not converged within max_sinkhorn_steps");
+    if (fs.status != ACCSINK_OK) return fail(ctx, fs.status, "solve stopped with an error status");
+    return ACCSINK_OK;
+}
+
 int begin(accsink_ctx *ctx)
 {
     if (!ctx) return ACCSINK_ERR_INVALID_ARG;
@@ -519,33 +766,75 @@ int begin(accsink_ctx *ctx)
     return ACCSINK_OK;
 }
 
-// Shared set-up of the single-pass entry points: workspace, state, cost
-// statistics. Returns the geometry through *g.
+// Launch plan of the single-pass calls, dense or point-cloud. pass_setup
+// makes the workspace, resets the state and computes the cost statistics.
+struct PassPlan {
+    bool pts = false;
+    int scale = 0;        // dense MAX_TO_ONE: eps_c = eps max C in the prep kernels
+    CostView cv;
+    Geometry geo;
+    Work w;
+    PointPlan pp;
+    int row_grid() const { return pts ? pp.prow : geo.row_grid; }
+};
+
 int pass_setup(accsink_ctx *ctx, const accsink_problem *prob, double eps, cudaStream_t s,
-               Geometry *g, Work *w)
+               PassPlan &pl)
 {
-    int rc = validate_problem(ctx, prob, true);
+    int rc = validate_problem(ctx, prob, false);
     if (rc != ACCSINK_OK) return rc;
     if (!(eps > 0.0) || !std::isfinite(eps))
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "eps must be positive and finite");
-    const CostView cv = make_view(prob);
-    *g = geometry(ctx, prob->n, prob->m, cv.vec);
-    rc = ensure_workspace(ctx, prob->n, prob->m, g->splits, g->row_grid, 0);
-    if (rc != ACCSINK_OK) return rc;
-    *w = ctx->w;
-    w->nstat = g->stat_grid;
-    w->b_src = nullptr;
-    w->f_given = nullptr;
-    w->ignore_done = 1;
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     hs.eps_user = eps;
-    hs.row_grid = g->row_grid;
-    hs.col_splits = g->splits;
     hs.mode = STEP_MAP;
+    pl.pts = prob->cost_kind != ACCSINK_COST_DENSE;
+    if (pl.pts) {
+        rc = points_plan(ctx, prob, 0, pl.pp);
+        if (rc != ACCSINK_OK) return rc;
+        pl.cv = pl.pp.cv;
+        pl.geo = pl.pp.g;
+        pl.w = pl.pp.w;
+        pl.w.ignore_done = 1;
+        pl.scale = 0;   // the point set-up applies the scale inside the cost
+        hs.row_grid = pl.pp.prow;
+        hs.col_splits = 1;
+        hs.col_mode = 1;
+        CK(set_state(ctx, hs, s));
+        CK(points_prologue(prob, pl.pp, s));
+        return ACCSINK_OK;
+    }
+    pl.cv = make_view(prob);
+    pl.geo = geometry(ctx, prob->n, prob->m, pl.cv.vec);
+    rc = ensure_workspace(ctx, prob->n, prob->m, pl.geo.splits, pl.geo.row_grid, 0);
+    if (rc != ACCSINK_OK) return rc;
+    pl.scale = prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE;
+    Work &w = pl.w;
+    w = ctx->w;
+    w.nstat = pl.geo.stat_grid;
+    w.b_src = nullptr;
+    w.f_given = nullptr;
+    w.ignore_done = 1;
+    hs.row_grid = pl.geo.row_grid;
+    hs.col_splits = pl.geo.splits;
     CK(set_state(ctx, hs, s));
-    CK(launch_cost_stats(cv, *w, g->stat_grid, s));
+    CK(launch_cost_stats(pl.cv, w, pl.geo.stat_grid, s));
     return ACCSINK_OK;
+}
+
+cudaError_t plan_row_pass(const PassPlan &pl, const Work &w, bool with_cost, cudaStream_t s)
+{
+    if (pl.pts) return launch_points_pass(pl.pp.pr, w, pl.pp.prow, 0, with_cost, s);
+    return launch_row_pass(pl.cv, w, pl.geo.row_grid, with_cost, s);
+}
+
+// Column pass in the layout the step kernel reads (partials for a dense
+// cost, ell for point clouds).
+cudaError_t plan_col_pass(const PassPlan &pl, const Work &w, cudaStream_t s)
+{
+    if (pl.pts) return launch_points_pass(pl.pp.pc, w, pl.pp.pcol, 1, false, s);
+    return launch_col_pass(pl.cv, w, pl.geo.splits, s);
 }
 
 }  // namespace
@@ -594,6 +883,7 @@ int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
         ctx->occ_col[v] = occupancy_col_pass(v);
     }
     ctx->occ_row_warp = occupancy_row_pass_warp();
+    ctx->occ_pts = occupancy_points_pass();
     if (setup_row_pass_tma() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -618,6 +908,7 @@ void accsink_destroy(accsink_ctx *ctx)
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ct) cudaFree(ctx->ct);
+    if (ctx->pts) cudaFree(ctx->pts);
     if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -639,14 +930,17 @@ int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob, const accsink_p
     if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
     std::memset(res, 0, sizeof(*res));
     res->status = ACCSINK_ERR_INVALID_ARG;
-    rc = validate_problem(ctx, prob, true);
+    rc = validate_problem(ctx, prob, false);
     if (rc == ACCSINK_OK) rc = validate_params(ctx, params);
     if (rc == ACCSINK_OK && (!prob->a || !prob->b))
         rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "a and b must be given");
     if (rc == ACCSINK_OK && (!f_out || !g_out))
         rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "f_out and g_out must be given");
     if (rc != ACCSINK_OK) { res->status = rc; return rc; }
-    rc = solve_device(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res);
+    if (prob->cost_kind == ACCSINK_COST_DENSE)
+        rc = solve_device(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res);
+    else
+        rc = solve_points(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res);
     res->status = rc;
     return rc;
 }
@@ -659,14 +953,19 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
     if (rc != ACCSINK_OK) return rc;
     if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
     std::memset(res, 0, sizeof(*res));
-    rc = validate_problem(ctx, prob_host, true);
+    rc = validate_problem(ctx, prob_host, false);
     if (rc == ACCSINK_OK) rc = validate_params(ctx, params);
     if (rc == ACCSINK_OK && (!prob_host->a || !prob_host->b || !f_out_host || !g_out_host))
         rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "a, b, f_out and g_out must be given");
     if (rc != ACCSINK_OK) { res->status = rc; return rc; }
     const int n = prob_host->n, m = prob_host->m;
+    const bool dense = prob_host->cost_kind == ACCSINK_COST_DENSE;
     const int64_t ldc = prob_host->ldc ? prob_host->ldc : m;
-    const size_t cbytes = ((size_t)(n - 1) * (size_t)ldc + (size_t)m) * sizeof(float);
+    // dense: C; point clouds: X (n x d) then Y (m x d)
+    const size_t xbytes = dense ? 0 : (size_t)n * (size_t)prob_host->d * sizeof(float);
+    const size_t ybytes = dense ? 0 : (size_t)m * (size_t)prob_host->d * sizeof(float);
+    const size_t cbytes = dense ? ((size_t)(n - 1) * (size_t)ldc + (size_t)m) * sizeof(float)
+                                : align_up(xbytes, 256) + ybytes;
     const size_t need = align_up(cbytes, 256) + align_up((size_t)n * 8, 256) * 2 +
                         align_up((size_t)m * 8, 256) * 2;
     if (need > ctx->stage_bytes) {
@@ -691,15 +990,24 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
     double *db = (double *)p; p += align_up((size_t)m * 8, 256);
     double *dg = (double *)p;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(cudaMemcpyAsync(dC, prob_host->C, cbytes, cudaMemcpyHostToDevice, s));
+    accsink_problem pd = *prob_host;
+    if (dense) {
+        CK(cudaMemcpyAsync(dC, prob_host->C, cbytes, cudaMemcpyHostToDevice, s));
+        pd.C = dC;
+        pd.ldc = ldc;
+    } else {
+        float *dY = (float *)((char *)dC + align_up(xbytes, 256));
+        CK(cudaMemcpyAsync(dC, prob_host->X, xbytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(dY, prob_host->Y, ybytes, cudaMemcpyHostToDevice, s));
+        pd.X = dC;
+        pd.Y = dY;
+    }
     CK(cudaMemcpyAsync(da, prob_host->a, (size_t)n * 8, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(db, prob_host->b, (size_t)m * 8, cudaMemcpyHostToDevice, s));
-    accsink_problem pd = *prob_host;
-    pd.C = dC;
     pd.a = da;
     pd.b = db;
-    pd.ldc = ldc;
-    rc = solve_device(ctx, &pd, params, s, df, dg, res);
+    rc = dense ? solve_device(ctx, &pd, params, s, df, dg, res)
+               : solve_points(ctx, &pd, params, s, df, dg, res);
     if (rc != ACCSINK_OK && rc != ACCSINK_ERR_MAXITER) { res->status = rc; return rc; }
     CK(cudaMemcpyAsync(f_out_host, df, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(g_out_host, dg, (size_t)m * 8, cudaMemcpyDeviceToHost, s));
@@ -733,14 +1041,12 @@ int accsink_row_pass(accsink_ctx *ctx, const accsink_problem *prob, double eps, 
     if (!prob || !g || !f_out || !prob->a)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "g, f_out and a must be given");
     cudaStream_t s = (cudaStream_t)stream;
-    Geometry geo;
-    Work w;
-    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    PassPlan pl;
+    rc = pass_setup(ctx, prob, eps, s, pl);
     if (rc != ACCSINK_OK) return rc;
-    const CostView cv = make_view(prob);
-    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
-    CK(launch_row_pass(cv, w, geo.row_grid, false, s));
-    CK(launch_scale_out(w.u, eps, f_out, prob->n, s));
+    CK(launch_prep_g(pl.cv, pl.w, pl.geo.vec_grid, g, prob->a, eps, pl.scale, s));
+    CK(plan_row_pass(pl, pl.w, false, s));
+    CK(launch_scale_out(pl.w.u, eps, f_out, prob->n, s));
     return ACCSINK_OK;
 }
 
@@ -751,14 +1057,15 @@ int accsink_col_lse(accsink_ctx *ctx, const accsink_problem *prob, double eps, c
     if (rc != ACCSINK_OK) return rc;
     if (!prob || !f || !ell_out) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "f and ell_out must be given");
     cudaStream_t s = (cudaStream_t)stream;
-    Geometry geo;
-    Work w;
-    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    PassPlan pl;
+    rc = pass_setup(ctx, prob, eps, s, pl);
     if (rc != ACCSINK_OK) return rc;
-    const CostView cv = make_view(prob);
-    CK(launch_prep_f(cv, w, geo.vec_grid, f, eps, s));
-    CK(launch_col_pass(cv, w, geo.splits, s));
-    CK(launch_col_finish_lse(w, prob->m, ell_out, s));
+    CK(launch_prep_f(pl.cv, pl.w, pl.geo.vec_grid, f, eps, pl.scale, s));
+    CK(plan_col_pass(pl, pl.w, s));
+    if (pl.pts)
+        CK(cudaMemcpyAsync(ell_out, pl.w.ell, (size_t)prob->m * 8, cudaMemcpyDeviceToDevice, s));
+    else
+        CK(launch_col_finish_lse(pl.w, prob->m, ell_out, s));
     return ACCSINK_OK;
 }
 
@@ -771,21 +1078,21 @@ int accsink_sinkhorn_map(accsink_ctx *ctx, const accsink_problem *prob, double e
     if (!prob || !g || !f_out || !c_out || !s_out || !err_out || !prob->a || !prob->b)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "every pointer argument must be given");
     cudaStream_t s = (cudaStream_t)stream;
-    Geometry geo;
-    Work w;
-    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    PassPlan pl;
+    rc = pass_setup(ctx, prob, eps, s, pl);
     if (rc != ACCSINK_OK) return rc;
-    const CostView cv = make_view(prob);
+    Work w = pl.w;
     w.b_src = prob->b;
-    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
-    CK(launch_row_pass(cv, w, geo.row_grid, false, s));
-    CK(launch_col_pass(cv, w, geo.splits, s));
-    CK(launch_step_map(cv, w, geo.step_grid, c_out, s_out, s));
+    CK(launch_prep_g(pl.cv, w, pl.geo.vec_grid, g, prob->a, eps, pl.scale, s));
+    CK(plan_row_pass(pl, w, false, s));
+    CK(plan_col_pass(pl, w, s));
+    CK(launch_step_map(pl.cv, w, pl.geo.step_grid, c_out, s_out, s));
     CK(launch_scale_out(w.u, eps, f_out, prob->n, s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     *err_out = ctx->h_state->err;
-    if (ctx->h_state->nonfinite) return fail(ctx, ACCSINK_ERR_NONFINITE, "C holds NaN or Inf");
+    if (ctx->h_state->nonfinite)
+        return fail(ctx, ACCSINK_ERR_NONFINITE, "the cost or the points hold NaN or Inf");
     return ACCSINK_OK;
 }
 
@@ -797,22 +1104,22 @@ int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob, double
     if (!prob || !f || !g || !cost_out)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "f, g and cost_out must be given");
     cudaStream_t s = (cudaStream_t)stream;
-    Geometry geo;
-    Work w;
-    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    PassPlan pl;
+    rc = pass_setup(ctx, prob, eps, s, pl);
     if (rc != ACCSINK_OK) return rc;
-    const CostView cv = make_view(prob);
     // The row pass at g weighs row i by w_i = exp(f_i/eps + LSE_i), so that
     // w_i * (sum_j C_ij t_ij) / (sum_j t_ij) = sum_j C_ij P_ij.
+    Work w = pl.w;
     w.f_given = f;
-    CK(launch_prep_g(cv, w, geo.vec_grid, g, nullptr, eps, s));
-    CK(launch_row_pass(cv, w, geo.row_grid, true, s));
-    CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)geo.row_grid * 16,
-                       cudaMemcpyDeviceToHost, s));
+    CK(launch_prep_g(pl.cv, w, pl.geo.vec_grid, g, nullptr, eps, pl.scale, s));
+    CK(plan_row_pass(pl, w, true, s));
+    const int rg = pl.row_grid();
+    CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)rg * 16, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     double c = 0.0;
-    for (int b = 0; b < geo.row_grid; ++b) c += ctx->h_rowpart[2 * b + 1];
-    *cost_out = c;
+    for (int b = 0; b < rg; ++b) c += ctx->h_rowpart[2 * b + 1];
+    *cost_out = c / ctx->h_state->cost_div;   // in units of the scaled cost
     return ACCSINK_OK;
 }
 
@@ -824,14 +1131,35 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     if (!prob || !g || !prob->a || reps < 1)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "g and a must be given and reps >= 1");
     cudaStream_t s = (cudaStream_t)stream;
-    Geometry geo;
-    Work w;
-    rc = pass_setup(ctx, prob, eps, s, &geo, &w);
+    PassPlan pl;
+    rc = pass_setup(ctx, prob, eps, s, pl);
     if (rc != ACCSINK_OK) return rc;
-    const CostView cv = make_view(prob);
+    const CostView &cv = pl.cv;
+    const Geometry &geo = pl.geo;
+    const Work &w = pl.w;
+    if (pl.pts) {
+        // the two point passes, as the solver launches them
+        CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, 0, s));
+        CK(plan_row_pass(pl, w, false, s));                 // warm-up, writes A'
+        CK(plan_col_pass(pl, w, s));
+        float ms = 0.0f;
+        CK(cudaEventRecord(ctx->ev0, s));
+        for (int r = 0; r < reps; ++r) CK(plan_row_pass(pl, w, false, s));
+        CK(cudaEventRecord(ctx->ev1, s));
+        CK(cudaEventSynchronize(ctx->ev1));
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (row_ms) *row_ms = ms / reps;
+        CK(cudaEventRecord(ctx->ev0, s));
+        for (int r = 0; r < reps; ++r) CK(plan_col_pass(pl, w, s));
+        CK(cudaEventRecord(ctx->ev1, s));
+        CK(cudaEventSynchronize(ctx->ev1));
+        CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+        if (col_ms) *col_ms = ms / reps;
+        return ACCSINK_OK;
+    }
     // the column pass the solver would use: on C^T when it fits
     const float *ct = ensure_ct(ctx, prob->n, prob->m) ? ctx->ct : nullptr;
-    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, s));
+    CK(launch_prep_g(cv, w, geo.vec_grid, g, prob->a, eps, pl.scale, s));
     if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(prob->n), s));
     CK(launch_passes(cv, w, geo, ct, s));                 // warm-up, writes F
     CK(cudaEventRecord(ctx->ev0, s));

@@ -119,7 +119,9 @@ extern "C" int accsink_col_lse_noalloc(const accsink_problem *prob, double eps,
     k_noalloc_state<<<1, 1, 0, s>>>(hs, w.st);
     if (cudaGetLastError() != cudaSuccess) return ACCSINK_ERR_CUDA;
     if (launch_cost_stats(cv, w, stat_grid, s) != cudaSuccess) return ACCSINK_ERR_CUDA;
-    if (launch_prep_f(cv, w, vec_grid, f, eps, s) != cudaSuccess) return ACCSINK_ERR_CUDA;
+    if (launch_prep_f(cv, w, vec_grid, f, eps, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, s) !=
+        cudaSuccess)
+        return ACCSINK_ERR_CUDA;
     if (launch_col_pass(cv, w, splits, s) != cudaSuccess) return ACCSINK_ERR_CUDA;
     if (launch_col_finish_lse(w, m, ell_out, s) != cudaSuccess) return ACCSINK_ERR_CUDA;
     return ACCSINK_OK;

@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(kRowNT) k_row_pass(CostView cv, Work w)
                 // sum_j C_ij P_ij = a_i CS / S; for given potentials f the
                 // row weight is exp(f_i / eps + LSE_i) instead of a_i.
                 if (WITH_COST) {
-                    const double wi = w.f_given ? exp(w.f_given[i] * st->inv_eps_c + lse) : w.a[i];
+                    const double wi = w.f_given ? exp(w.f_given[i] / st->eps_user + lse) : w.a[i];
                     my_cost += wi * (CS / S);
                 }
             }

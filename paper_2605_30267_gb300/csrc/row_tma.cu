@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work 
                 w.FF[i] = make_float2(Fh, Fl * kh);
                 my_dual += w.a[i] * ui;
                 if (WITH_COST) {
-                    const double wi = w.f_given ? exp(w.f_given[i] * inv_eps + lse) : w.a[i];
+                    const double wi = w.f_given ? exp(w.f_given[i] / st->eps_user + lse) : w.a[i];
                     my_cost += wi * (CS / S);
                 }
             }

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
             my_dual += w.a[i] * ui;
             if (WITH_COST) {
                 const double CS = (double)chi + (double)clo;
-                const double wi = w.f_given ? exp(w.f_given[i] * st->inv_eps_c + lse) : w.a[i];
+                const double wi = w.f_given ? exp(w.f_given[i] / st->eps_user + lse) : w.a[i];
                 my_cost += wi * (CS / S);
             }
         }

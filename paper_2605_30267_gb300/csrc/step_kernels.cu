@@ -132,9 +132,18 @@ __device__ __forceinline__ void cost_totals(const double *statpart, int nstat, d
     cmax = v[0]; cmin = v[1]; cabs = v[2]; bad = v[3];
 }
 
-// Writes G_j + gamma_j = g_j + shift_g as (hi, gamma * k_hi).
+// Writes the row-pass operand for column j from g_j + shift_g: for a dense
+// cost the pair (hi, lo k_hi) of G_j; for a point-cloud cost the pair
+// (hi, lo) of A_j = G_j - By_j (the expansion term of points.cu).
 __device__ __forceinline__ void write_G(const Work &w, int j, double gshift, float kh)
 {
+    if (w.By64) {
+        const double a = gshift - w.By64[j];
+        const float hi = (float)a;
+        w.G[j] = hi;
+        w.Gk[j] = (float)(a - (double)hi);
+        return;
+    }
     const float hi = (float)gshift;
     const float lo = (float)(gshift - (double)hi);
     w.G[j] = hi;
@@ -672,7 +681,8 @@ cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double 
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nstat,
                                                    const double *g, const double *a_in,
-                                                   const double *b_in, double eps)
+                                                   const double *b_in, double eps,
+                                                   int scale_max)
 {
     DevState *st = w.st;
     const int tid = blockIdx.x * kVecNT + threadIdx.x;
@@ -713,17 +723,22 @@ __global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nst
     double t[3];
     const int ops[3] = {1, 2, 1};
     grid_totals<3>(w.steppart, nb, 0, ops, t);
-    const double k = kLog2e / eps;
+    // g is in units of the (possibly scaled) cost; the kernels work in units
+    // of the stored cost, i.e. with eps_c = eps * cost_div and G = cost_div g.
+    const double cost_div = (scale_max && cmax > 0.0) ? cmax : 1.0;
+    const double eps_c = eps * cost_div;
+    const double k = kLog2e / eps_c;
     const float kh = (float)k;
     const float kl = (float)(k - (double)kh);
-    const double shift_g = cabs - t[0];
-    const double shift_f = cabs - (eps * t[2] - t[1] + cmin - eps * log((double)m));
-    for (int j = tid; j < m; j += nthr) write_G(w, j, g[j] + shift_g, kh);
+    const double shift_g = cabs - cost_div * t[0];
+    const double shift_f =
+        cabs - (eps_c * t[2] - cost_div * t[1] + cmin - eps_c * log((double)m));
+    for (int j = tid; j < m; j += nthr) write_G(w, j, cost_div * g[j] + shift_g, kh);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->eps_c = eps;
-        st->inv_eps_c = 1.0 / eps;
+        st->eps_c = eps_c;
+        st->inv_eps_c = 1.0 / eps_c;
         st->eps_user = eps;
-        st->cost_div = 1.0;
+        st->cost_div = cost_div;
         st->cmax = cmax; st->cmin = cmin; st->cabs = cabs;
         st->nonfinite = (bad > 0.0) ? 1 : 0;
         st->shift_g = shift_g;
@@ -738,7 +753,7 @@ __global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nst
 }
 
 cudaError_t launch_prep_g(const CostView &cv, const Work &w, int grid, const double *g,
-                          const double *a_in, double eps, cudaStream_t s)
+                          const double *a_in, double eps, int scale_max, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -750,11 +765,12 @@ cudaError_t launch_prep_g(const CostView &cv, const Work &w, int grid, const dou
     cfg.attrs = at;
     cfg.numAttrs = 1;
     const double *b_in = w.b_src;
-    return cudaLaunchKernelEx(&cfg, k_prep_g, w, cv.n, cv.m, (int)w.nstat, g, a_in, b_in, eps);
+    return cudaLaunchKernelEx(&cfg, k_prep_g, w, cv.n, cv.m, (int)w.nstat, g, a_in, b_in, eps,
+                              scale_max);
 }
 
 __global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nstat,
-                                                   const double *f, double eps)
+                                                   const double *f, double eps, int scale_max)
 {
     DevState *st = w.st;
     const int tid = blockIdx.x * kVecNT + threadIdx.x;
@@ -779,20 +795,31 @@ __global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nst
     double t[1];
     const int ops[1] = {1};
     grid_totals<1>(w.steppart, nb, 0, ops, t);
-    const double k = kLog2e / eps;
+    const double cost_div = (scale_max && cmax > 0.0) ? cmax : 1.0;
+    const double eps_c = eps * cost_div;
+    const double k = kLog2e / eps_c;
     const float kh = (float)k;
     const float kl = (float)(k - (double)kh);
-    const double shift_f = cabs - t[0];
+    const double shift_f = cabs - cost_div * t[0];
     for (int i = tid; i < n; i += nthr) {
-        const double F = f[i] + shift_f;
-        const float Fh = (float)F;
-        const float Fl = (float)(F - (double)Fh);
-        w.FF[i] = make_float2(Fh, Fl * kh);
+        const double F = cost_div * f[i] + shift_f;
+        if (w.Bx64) {
+            // point-cloud column operand A'_i = F_i - Bx_i as (hi, lo)
+            const double A2 = F - w.Bx64[i];
+            const float Ah = (float)A2;
+            w.Fh[i] = Ah;
+            w.Fk[i] = (float)(A2 - (double)Ah);
+        } else {
+            const float Fh = (float)F;
+            const float Fl = (float)(F - (double)Fh);
+            w.FF[i] = make_float2(Fh, Fl * kh);
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->eps_c = eps;
-        st->inv_eps_c = 1.0 / eps;
+        st->eps_c = eps_c;
+        st->inv_eps_c = 1.0 / eps_c;
         st->eps_user = eps;
+        st->cost_div = cost_div;
         st->cmax = cmax; st->cmin = cmin; st->cabs = cabs;
         st->nonfinite = (bad > 0.0) ? 1 : 0;
         st->shift_f = shift_f;
@@ -804,7 +831,7 @@ __global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nst
 }
 
 cudaError_t launch_prep_f(const CostView &cv, const Work &w, int grid, const double *f,
-                          double eps, cudaStream_t s)
+                          double eps, int scale_max, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -815,7 +842,7 @@ cudaError_t launch_prep_f(const CostView &cv, const Work &w, int grid, const dou
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_prep_f, w, cv.n, cv.m, (int)w.nstat, f, eps);
+    return cudaLaunchKernelEx(&cfg, k_prep_f, w, cv.n, cv.m, (int)w.nstat, f, eps, scale_max);
 }
 
 __global__ void k_scale_out(const double *src, double scale, double *dst, int n)

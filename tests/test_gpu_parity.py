@@ -148,14 +148,21 @@ def gpu_solve(ctx, C, a, b, eps, tol=1e-6, method=B.ACC, scale=False, **kw):
 def check_solve(ctx, C, a, b, eps, tol, method, scale=False, cost=None, **kw):
     f, g, res = gpu_solve(ctx, C, a, b, eps, tol, method, scale, **kw)
     cost = cost or O.Cost(C=C, scale_to_max=scale)
-    ref = O.solve(cost, a, b, eps, tol, method=O.ACC if method == B.ACC else O.PLAIN,
-                  carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
-                  stability=kw.get("stability", B.STAB_REPORT))
+    okw = dict(method=O.ACC if method == B.ACC else O.PLAIN,
+               carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
+               stability=kw.get("stability", B.STAB_REPORT))
+    ref = O.solve(cost, a, b, eps, tol, **okw)
     assert res["status"] == 0, res
     assert ref["status"] == O.CONVERGED
     # steps within 2% (at least one step of slack)
     rs, gs = ref["sinkhorn_steps"], res["sinkhorn_steps"]
     assert abs(gs - rs) <= max(1, int(0.02 * rs)), (gs, rs)
+    if gs != rs:
+        # Near the tolerance the error can sit on a plateau where last-bit
+        # differences move the stopping step; the potentials are then compared
+        # with the oracle's iterate at the GPU's step (the oracle run on with
+        # no tolerance), so the bound below measures arithmetic, not stopping.
+        ref = dict(O.solve(cost, a, b, eps, 1e-300, max_steps=gs, **okw), status=ref["status"])
     # potentials after centring
     sh = g.mean() - ref["g"].mean()
     dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())

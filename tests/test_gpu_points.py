@@ -1,0 +1,321 @@
+"""GPU parity of the point-cloud path (costs formed on the fly, Sec. 5's
+colour-transfer and word-alignment costs) against the FP64 oracle, whose cost
+is formed in FP64 from the same FP32 points.
+
+Tolerances as for stored costs: potentials within 1e-3 eps max-abs after
+centring, <C,P> within 1e-5 relative, step counts within 2% (or one step),
+FP64-truth column L1 <= tol (1 + 0.05), row L1 at the FP32 floor.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2605_30267_gb300 import binding as B
+from paper_2605_30267_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def gpu_solve_points(ctx, X, Y, kind, a, b, eps, tol, method, scale, **kw):
+    n, m = X.shape[0], Y.shape[0]
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    g = torch.empty(m, dtype=torch.float64, device=DEV)
+    p = B.default_params(eps=eps, tol=tol, method=method, **kw)
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind, to_dev(a), to_dev(b), scale)
+    res = ctx.accsink_solve(prob, p, f, g)
+    return f.cpu().numpy(), g.cpu().numpy(), B.result_dict(res)
+
+
+def check_points(ctx, X, Y, kind, a, b, eps, tol=1e-6, method=B.ACC, scale=False, **kw):
+    f, g, res = gpu_solve_points(ctx, X, Y, kind, a, b, eps, tol, method, scale, **kw)
+    cost = O.Cost(X=X, Y=Y, kind=kind, scale_to_max=scale)
+    okw = dict(method=O.ACC if method == B.ACC else O.PLAIN,
+               carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
+               stability=kw.get("stability", B.STAB_REPORT))
+    ref = O.solve(cost, a, b, eps, tol, **okw)
+    assert res["status"] == 0, res
+    assert ref["status"] == O.CONVERGED
+    rs, gs = ref["sinkhorn_steps"], res["sinkhorn_steps"]
+    assert abs(gs - rs) <= max(1, int(0.02 * rs)), (gs, rs)
+    if gs != rs:
+        # Near the tolerance the error can sit on a plateau where last-bit
+        # differences move the stopping step; the potentials are then compared
+        # with the oracle's iterate at the GPU's step (the oracle run on with
+        # no tolerance), so the bound below measures arithmetic, not stopping.
+        ref = dict(O.solve(cost, a, b, eps, 1e-300, max_steps=gs, **okw), status=ref["status"])
+    sh = g.mean() - ref["g"].mean()
+    dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
+    assert dpot <= 1e-3 * eps, dpot
+    ev = O.evaluate(cost, eps, ref["a"], ref["b"], f, g)
+    assert ev["col_l1"] <= tol * 1.05, ev
+    assert ev["row_l1"] <= 2e-7, ev
+    evr = O.evaluate(cost, eps, ref["a"], ref["b"], ref["f"], ref["g"])
+    assert abs(res["transport_cost"] - evr["transport_cost"]) <= \
+        1e-5 * abs(evr["transport_cost"]), (res["transport_cost"], evr["transport_cost"])
+    assert abs(res["dual_objective"] - ref["dual"]) <= 1e-5 * max(1e-3, abs(ref["dual"]))
+    return f, g, res, ref
+
+
+def sqeuclid_points(seed, n, m, d, spread=1.0):
+    g = np.random.default_rng(seed)
+    X = (spread * g.random((n, d))).astype(np.float32)
+    Y = (spread * g.random((m, d))).astype(np.float32)
+    return X, Y, W.dirichlet1(g, n), W.dirichlet1(g, m)
+
+
+def cosine_points(seed, n, m, d):
+    g = np.random.default_rng(seed)
+    X = W.unit_gaussian_points(g, n, d)
+    Y = W.unit_gaussian_points(g, m, d)
+    return X, Y, W.dirichlet1(g, n), W.dirichlet1(g, m)
+
+
+# ------------------------------------------------------ single passes --
+
+PASS_TOL = 2e-6
+PT_SHAPES = [(1, 1), (3, 5), (9, 1), (37, 129), (513, 2049), (1000, 1003)]
+
+
+def points_for(kind, seed, n, m, d):
+    return sqeuclid_points(seed, n, m, d) if kind == "sqeuclid" else cosine_points(seed, n, m, d)
+
+
+def potential_like(seed, k):
+    g = np.random.default_rng(seed)
+    return 0.3 * g.standard_normal(k) + 0.05 * g.random(k)
+
+
+@pytest.mark.parametrize("n,m", PT_SHAPES)
+@pytest.mark.parametrize("kind,d", [("sqeuclid", 3), ("sqeuclid", 9), ("cosine", 16),
+                                    ("cosine", 64)])
+@pytest.mark.parametrize("eps", [1e-1, 1e-3])
+def test_point_row_pass_matches_oracle(ctx, n, m, kind, d, eps):
+    X, Y, a, b = points_for(kind, n * 7 + m + d, n, m, d)
+    g = potential_like(n + 3 * m, m)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind, to_dev(a), to_dev(b))
+    ctx.accsink_row_pass(prob, eps, to_dev(g), f)
+    torch.cuda.synchronize()
+    ref = eps * O.row_pass(O.Cost(X=X, Y=Y, kind=kind), eps, np.log(a), g / eps)
+    err = np.abs(f.cpu().numpy() - ref).max() / eps
+    assert err <= PASS_TOL, err
+
+
+@pytest.mark.parametrize("n,m", PT_SHAPES)
+@pytest.mark.parametrize("kind,d", [("sqeuclid", 3), ("cosine", 33)])
+@pytest.mark.parametrize("eps", [1e-1, 1e-3])
+def test_point_col_lse_matches_oracle(ctx, n, m, kind, d, eps):
+    X, Y, a, b = points_for(kind, n * 11 + m + d, n, m, d)
+    f = potential_like(2 * n + m, n)
+    ell = torch.empty(m, dtype=torch.float64, device=DEV)
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind)
+    ctx.accsink_col_lse(prob, eps, to_dev(f), ell)
+    torch.cuda.synchronize()
+    ref = O.col_lse(O.Cost(X=X, Y=Y, kind=kind), eps, f / eps)
+    err = np.abs(ell.cpu().numpy() - ref).max()
+    assert err <= PASS_TOL, err
+
+
+@pytest.mark.parametrize("kind,d", [("sqeuclid", 3), ("cosine", 20)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_point_sinkhorn_map_matches_oracle(ctx, kind, d, scale):
+    n, m, eps = 257, 1000, 1e-2
+    X, Y, a, b = points_for(kind, d + 3, n, m, d)
+    g = potential_like(17, m)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    c = torch.empty(m, dtype=torch.float64, device=DEV)
+    s = torch.empty(m, dtype=torch.float64, device=DEV)
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind, to_dev(a), to_dev(b), scale)
+    err = ctx.accsink_sinkhorn_map(prob, eps, to_dev(g), f, c, s)
+    cost = O.Cost(X=X, Y=Y, kind=kind, scale_to_max=scale)
+    rerr, ru, rc, rs = O.sinkhorn_map(cost, eps, a, b, g / eps)
+    assert np.abs(f.cpu().numpy() / eps - ru).max() <= PASS_TOL
+    np.testing.assert_allclose(c.cpu().numpy(), rc, rtol=5 * PASS_TOL, atol=1e-300)
+    assert np.abs(s.cpu().numpy() / eps - rs).max() <= 2 * PASS_TOL
+    assert abs(err - rerr) <= 5 * PASS_TOL * max(1.0, rerr)
+
+
+@pytest.mark.parametrize("kind,d", [("sqeuclid", 3), ("cosine", 12)])
+@pytest.mark.parametrize("scale", [False, True])
+def test_point_transport_cost_matches_oracle(ctx, kind, d, scale):
+    n, m, eps = 300, 211, 2e-2
+    X, Y, a, b = points_for(kind, 77 + d, n, m, d)
+    cost = O.Cost(X=X, Y=Y, kind=kind, scale_to_max=scale)
+    ref = O.solve(cost, a, b, eps, tol=1e-9, method=O.PLAIN)
+    ev = O.evaluate(cost, eps, ref["a"], ref["b"], ref["f"], ref["g"])
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind, None, None, scale)
+    out = ctx.accsink_transport_cost(prob, eps, to_dev(ref["f"]), to_dev(ref["g"]))
+    assert abs(out - ev["transport_cost"]) <= 1e-6 * abs(ev["transport_cost"])
+
+
+def test_dense_single_passes_honour_max_to_one(ctx):
+    """The dense single-pass calls read C / max C under MAX_TO_ONE."""
+    n, m, eps = 120, 340, 1e-2
+    g0 = np.random.default_rng(4)
+    C = (3.0 * g0.random((n, m))).astype(np.float32)
+    a, b = W.dirichlet1(g0, n), W.dirichlet1(g0, m)
+    cost = O.Cost(C=C, scale_to_max=True)
+    g = potential_like(5, m)
+    f = torch.empty(n, dtype=torch.float64, device=DEV)
+    ctx.accsink_row_pass(B.problem_dense(to_dev(C), to_dev(a), to_dev(b), True), eps,
+                         to_dev(g), f)
+    torch.cuda.synchronize()
+    ref = eps * O.row_pass(cost, eps, np.log(a), g / eps)
+    assert np.abs(f.cpu().numpy() - ref).max() / eps <= PASS_TOL
+    ell = torch.empty(m, dtype=torch.float64, device=DEV)
+    ctx.accsink_col_lse(B.problem_dense(to_dev(C), None, None, True), eps, f, ell)
+    torch.cuda.synchronize()
+    ref2 = O.col_lse(cost, eps, f.cpu().numpy() / eps)
+    assert np.abs(ell.cpu().numpy() - ref2).max() <= PASS_TOL
+    ref3 = O.solve(cost, a, b, eps, tol=1e-9, method=O.PLAIN)
+    ev = O.evaluate(cost, eps, ref3["a"], ref3["b"], ref3["f"], ref3["g"])
+    out = ctx.accsink_transport_cost(B.problem_dense(to_dev(C), None, None, True), eps,
+                                     to_dev(ref3["f"]), to_dev(ref3["g"]))
+    assert abs(out - ev["transport_cost"]) <= 1e-6 * abs(ev["transport_cost"])
+
+
+# -------------------------------------------------------------- solves --
+
+def test_uniform_2d_256_matches_oracle(ctx):
+    """The 256-point uniform [0,1]^2 problem, cost scaled to max 1, eps 1e-2."""
+    pr = W.small_pointcloud_problem(0)
+    for method in (B.ACC, B.PLAIN):
+        check_points(ctx, pr["X"], pr["Y"], "sqeuclid", pr["a"], pr["b"], pr["eps"],
+                     pr["tol"], method, scale=True)
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+@pytest.mark.parametrize("n,m,d", [(333, 200, 3), (64, 1031, 2), (517, 515, 5)])
+def test_sqeuclid_solves_match_oracle(ctx, eps, n, m, d):
+    X, Y, a, b = sqeuclid_points(n * 3 + m + d, n, m, d)
+    check_points(ctx, X, Y, "sqeuclid", a, b, eps, scale=True)
+
+
+@pytest.mark.parametrize("n,m,d", [(300, 257, 16), (129, 250, 64), (200, 180, 7)])
+@pytest.mark.parametrize("eps", [5e-3, 5e-2])
+def test_cosine_solves_match_oracle(ctx, n, m, d, eps):
+    X, Y, a, b = cosine_points(n + 5 * m + d, n, m, d)
+    check_points(ctx, X, Y, "cosine", a, b, eps)
+
+
+def test_unscaled_sqeuclid_with_large_coordinates(ctx):
+    """Costs of size ~50 without scaling: the operand shifts stay exact."""
+    X, Y, a, b = sqeuclid_points(41, 150, 170, 3, spread=4.0)
+    f, g, res, ref = check_points(ctx, X, Y, "sqeuclid", a, b, 0.5)
+    cost = O.Cost(X=X, Y=Y, kind="sqeuclid")
+    assert abs(res["cost_max"] - cost.unscaled_max()) <= 1e-12 * cost.unscaled_max()
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (1, 9), (9, 1), (5, 3)])
+def test_tiny_point_solves(ctx, n, m):
+    X, Y, a, b = sqeuclid_points(n * 10 + m, n, m, 2)
+    for method in (B.ACC, B.PLAIN):
+        check_points(ctx, X, Y, "sqeuclid", a, b, 5e-2, method=method, scale=True)
+
+
+def test_point_solve_host_matches_device(ctx):
+    X, Y, a, b = sqeuclid_points(8, 210, 190, 3)
+    eps = 1e-2
+    f1, g1, r1 = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, eps, 1e-6, B.ACC, True)
+    f2 = np.empty(210)
+    g2 = np.empty(190)
+    p = B.default_params(eps=eps, tol=1e-6)
+    res = ctx.accsink_solve_host(None, a, b, p, f2, g2, scale_to_max=True, X=X, Y=Y,
+                                 kind="sqeuclid")
+    assert res.status == 0
+    assert res.sinkhorn_steps == r1["sinkhorn_steps"]
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(g1, g2)
+
+
+def test_point_graph_and_host_loop_agree(ctx):
+    X, Y, a, b = sqeuclid_points(12, 140, 260, 3)
+    out = []
+    for use_graph in (1, 0):
+        f, g, res = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True,
+                                     use_graph=use_graph)
+        assert res["loop_mode"] == use_graph
+        out.append((f, g, res["sinkhorn_steps"]))
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+def test_point_and_dense_problems_alternate_on_one_context(ctx):
+    """A dense solve between two point solves leaves both paths' results
+    unchanged (workspaces and cached graphs are told apart)."""
+    X, Y, a, b = sqeuclid_points(14, 120, 100, 3)
+    first = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True)
+    C = W.sqeuclid_cost_fp32(X, Y)
+    f = torch.empty(120, dtype=torch.float64, device=DEV)
+    g = torch.empty(100, dtype=torch.float64, device=DEV)
+    ctx.accsink_solve(B.problem_dense(to_dev(C), to_dev(a), to_dev(b), True),
+                      B.default_params(eps=1e-2, tol=1e-6), f, g)
+    second = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True)
+    np.testing.assert_array_equal(first[0], second[0])
+    np.testing.assert_array_equal(first[1], second[1])
+
+
+def test_point_inputs_are_validated(ctx):
+    X, Y, a, b = sqeuclid_points(3, 20, 30, 3)
+    f = torch.empty(20, dtype=torch.float64, device=DEV)
+    g = torch.empty(30, dtype=torch.float64, device=DEV)
+    p = B.default_params(eps=1e-2)
+    bad = X.copy()
+    bad[4, 1] = np.nan
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(B.problem_points(to_dev(bad), to_dev(Y), "sqeuclid", to_dev(a),
+                                           to_dev(b)), p, f, g)
+    assert e.value.code == B.ERR_NONFINITE
+    pr = B.problem_points(to_dev(X), to_dev(Y), "sqeuclid", to_dev(a), to_dev(b))
+    pr.d = 65
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(pr, p, f, g)
+    assert e.value.code == B.ERR_INVALID_ARG
+    pr = B.problem_points(to_dev(X), to_dev(Y), "sqeuclid", to_dev(a), to_dev(b))
+    pr.cost_kind = 7
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_row_pass(pr, 1e-2, g, f)
+    assert e.value.code == B.ERR_INVALID_ARG
+    # the context still solves afterwards
+    check_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, scale=True)
+
+
+# ------------------------------------- colour-transfer shape, full size --
+
+@pytest.fixture(scope="module")
+def colour_problem():
+    return W.color_transfer_problem(seed=0, n=65536, eps=1e-3)
+
+
+def test_full_size_colour_transfer_solve(ctx, colour_problem):
+    """n = m = 65536 RGB points, eps 1e-3, tol 1e-6 (cost scaled to max 1):
+    converged, and on sampled rows and columns the FP64 oracle's marginals of
+    the returned potentials agree with a and b."""
+    pr = colour_problem
+    eps, tol = pr["eps"], pr["tol"]
+    f, g, res = gpu_solve_points(ctx, pr["X"], pr["Y"], "sqeuclid", pr["a"], pr["b"], eps,
+                                 tol, B.ACC, True)
+    assert res["status"] == 0 and res["marginal_l1"] < tol, res
+    cost = O.Cost(X=pr["X"], Y=pr["Y"], kind="sqeuclid", scale_to_max=True)
+    n = m = 65536
+    rows = np.random.default_rng(5).choice(n, 32, replace=False)
+    cols = np.random.default_rng(6).choice(m, 32, replace=False)
+    r, _ = O.rows_sample(cost, eps, f, g, rows)
+    np.testing.assert_allclose(r, pr["a"][rows], rtol=2e-6)
+    c = O.cols_sample(cost, eps, f, g, cols)
+    assert np.abs(c - pr["b"][cols]).sum() <= tol * 32 / m * 50
