@@ -51,6 +51,7 @@ struct DevState {
     // double-float operand constants
     double shift_g, shift_f;
     float k_hi, k_lo;          // log2(e)/eps_c = k_hi + k_lo
+    double k2;                 // log2(e)/eps_c in FP64 (point-cloud operands)
     // Algorithm 1/2 state
     double mu;
     double kl_prev;            // D_phi*(0, grad f(x_k)) of the previous iterate
@@ -113,11 +114,18 @@ struct Work {
 // whose scaled points are Qh/Ql (SoA, d x ldq); A (per column) and B (per
 // row) are the expansion terms as pairs; Ch (per column, hi) serves the
 // transport-cost sum.
+// One point-cloud pass: rows r of P (nr x d, row-major FP32) against the
+// columns c of Q (d x ldq SoA, (hi, lo) FP32 pairs, pre-scaled to log2
+// units), with the per-column operand A (pairs) and the rows' FP64 norm term
+// B64 (applied in the finish). Pc (the columns' points, nc x d) and scal
+// ({max C, s}) are only read when the transport cost is accumulated, which
+// forms each C_ij directly from the points.
 struct PointView {
-    const float *P;
-    const float *Ah, *Al, *Bh, *Bl, *Qh, *Ql, *Ch;
+    const float *P, *Pc;
+    const float *Ah, *Al, *Qh, *Ql;
+    const double *B64, *scal;
     int64_t ldq;
-    int32_t nr, nc, d, pad;
+    int32_t nr, nc, d, kind;
 };
 
 struct CostView {
@@ -259,8 +267,9 @@ int occupancy_points_pass();
 cudaError_t launch_points_rowmax(const float *X, const float *Y, int n, int m, int d, int kind,
                                  double *rowmax, int grid, cudaStream_t s);
 cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, int d, int kind,
-                                int scale_max, const Work &w, double *scal, double *blockmax,
-                                int nblk, cudaStream_t s);
+                                int scale_max, double eps, const Work &w, double *scal,
+                                double *blockmax, int nblk, cudaStream_t s);
+int points_rows_per_warp(int d);
 void setup_col_pass();
 
 }  // namespace accsink

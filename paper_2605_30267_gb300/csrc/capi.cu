@@ -549,8 +549,10 @@ struct PointPlan {
     double *blockmax = nullptr, *scal = nullptr;
 };
 
-int points_grid(const accsink_ctx *ctx, int rows)
+int points_grid(const accsink_ctx *ctx, int n_rows, int d)
 {
+    const int rw = points_rows_per_warp(d);
+    const int rows = (n_rows + rw - 1) / rw;   // row tiles, one per warp pass
     const int64_t max_warps = (int64_t)ctx->num_sms * ctx->occ_pts * 8;
     const int64_t k = (rows + max_warps - 1) / max_warps;
     const int64_t warps = (rows + k - 1) / k;
@@ -569,8 +571,8 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     pl.cv.m = m;
     pl.cv.vec = 1;
     pl.g = geometry(ctx, n, m, 1);
-    pl.prow = points_grid(ctx, n);
-    pl.pcol = points_grid(ctx, m);
+    pl.prow = points_grid(ctx, n, d);
+    pl.pcol = points_grid(ctx, m, d);
     int rc = ensure_workspace(ctx, n, m, 1, pl.prow, hist);
     if (rc != ACCSINK_OK) return rc;
     const int64_t ldx = (n + 3) / 4 * 4, ldy = (m + 3) / 4 * 4;
@@ -618,23 +620,26 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     w.f_given = nullptr;
     w.ignore_done = 0;
     PointView &pr = pl.pr, &pc = pl.pc;
-    pr.P = prob->X; pr.Ah = w.G; pr.Al = w.Gk; pr.Bh = w.Bxh; pr.Bl = w.Bxl;
-    pr.Qh = w.PYh; pr.Ql = w.PYl; pr.Ch = w.Byh; pr.ldq = ldy; pr.nr = n; pr.nc = m; pr.d = d;
-    pc.P = prob->Y; pc.Ah = w.Fh; pc.Al = w.Fk; pc.Bh = w.Byh; pc.Bl = w.Byl;
-    pc.Qh = w.PXh; pc.Ql = w.PXl; pc.Ch = w.Bxh; pc.ldq = ldx; pc.nr = m; pc.nc = n; pc.d = d;
+    pr.P = prob->X; pr.Pc = prob->Y; pr.Ah = w.G; pr.Al = w.Gk; pr.B64 = w.Bx64;
+    pr.Qh = w.PYh; pr.Ql = w.PYl; pr.scal = pl.scal; pr.ldq = ldy;
+    pr.nr = n; pr.nc = m; pr.d = d; pr.kind = pl.kind;
+    pc.P = prob->Y; pc.Pc = prob->X; pc.Ah = w.Fh; pc.Al = w.Fk; pc.B64 = w.By64;
+    pc.Qh = w.PXh; pc.Ql = w.PXl; pc.scal = pl.scal; pc.ldq = ldx;
+    pc.nr = m; pc.nc = n; pc.d = d; pc.kind = pl.kind;
     return ACCSINK_OK;
 }
 
 // Row maxima (for max C and the MAX_TO_ONE scale), then the FP64 norms, the
 // scaled SoA copies of the points and the cost-statistics record.
-cudaError_t points_prologue(const accsink_problem *prob, const PointPlan &pl, cudaStream_t s)
+cudaError_t points_prologue(const accsink_problem *prob, const PointPlan &pl, double eps,
+                            cudaStream_t s)
 {
     cudaError_t e = launch_points_rowmax(prob->X, prob->Y, prob->n, prob->m, prob->d, pl.kind,
                                          pl.w.rowmax, pl.prow, s);
     if (e != cudaSuccess) return e;
     return launch_points_setup(prob->X, prob->Y, prob->n, prob->m, prob->d, pl.kind,
-                               prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, pl.w, pl.scal,
-                               pl.blockmax, pl.nblk, s);
+                               prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, eps, pl.w,
+                               pl.scal, pl.blockmax, pl.nblk, s);
 }
 
 // Point-cloud costs (squared Euclidean, cosine) built on the fly: the same
@@ -675,7 +680,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     CK(set_state(ctx, hs, s));
     k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
     CK(cudaGetLastError());
-    CK(points_prologue(prob, pl, s));
+    CK(points_prologue(prob, pl, prm->eps, s));
     CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, 0, s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -802,7 +807,7 @@ int pass_setup(accsink_ctx *ctx, const accsink_problem *prob, double eps, cudaSt
         hs.col_splits = 1;
         hs.col_mode = 1;
         CK(set_state(ctx, hs, s));
-        CK(points_prologue(prob, pl.pp, s));
+        CK(points_prologue(prob, pl.pp, eps, s));
         return ACCSINK_OK;
     }
     pl.cv = make_view(prob);

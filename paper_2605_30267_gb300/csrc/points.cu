@@ -4,17 +4,20 @@
 //
 // Precision. The problem is the cost formed in FP64 from the FP32 points, and
 // at eps = 1e-3 every exponent must be right to ~1e-7, so each s C_ij (s the
-// scale, 1 or 1 / max C) must be right to ~1e-10. FP32 products (or TF32
-// tensor-core tiles) are four orders short. Instead the kernels use the exact
-// expansion
+// scale, 1 or 1 / max C) must be right to ~1e-10. FP32 products (or 3xTF32
+// tensor-core tiles, ~2^-24 relative) are orders short. Instead the kernels
+// use the exact expansion
 //     G_j - s C_ij = (G_j - By_j) - Bx_i + sum_k x_ik Q_jk,
 // with Bx_i = s ||x_i||^2, By_j = s ||y_j||^2, Q_j = 2 s y_j (squared
-// Euclidean) or Bx_i = 0, By_j = s, Q_j = s y_j (cosine). Bx, By, Q and the
-// operand (G_j - By_j) are precomputed in FP64 and held as FP32 (hi, lo)
-// pairs; each product x_ik Q_jk is formed exactly with an FMA and accumulated
-// with Fast2Sum into a double-float sum. The operand shifts make the running
-// sum dominate every product (see setup), so Fast2Sum is exact at every step.
-// The column pass is the same kernel with the roles of X and Y swapped.
+// Euclidean) or Bx_i = 0, By_j = s, Q_j = s y_j (cosine), everything
+// multiplied by k = log2(e) / eps so that the sum is the exponent in log2
+// units. Q and the column operand k (G_j - By_j) are precomputed in FP64 and
+// held as FP32 (hi, lo) pairs; each product x_ik Q_jk is formed exactly with
+// an FMA and added with Fast2Sum into a double-float sum. The operand shifts
+// make the running sum dominate every product (see the set-up), so Fast2Sum
+// is exact at every step. The row term Bx_i is constant along a row and is
+// applied once, in FP64, when the row is finished. The column pass is the
+// same kernel with the roles of X and Y swapped.
 #include <float.h>
 
 #include "accsink_internal.cuh"
@@ -47,156 +50,235 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 
 }  // namespace
 
-// rows r of P (AoS, nr x d) against columns c of Q (SoA hi/lo, d x ldq):
-//   h + l = A_c - B_r + sum_k P_rk Q_kc   (A = Ah + Al per column, B per row)
-// MODE 0 (row pass): A = G - By, B = Bx, finish u_i, the column operand
-//   A'_i = F_i - Bx_i and the CTA partials (dual, cost).
-// MODE 1 (column pass): A = A', B = By, finish ell_j.
-template <int MODE, int DMAX, bool WITH_COST>
+// One slot (4 consecutive columns) of one row: h + l = A_c + sum_k p_k Q_kc
+// in log2 units, each product formed exactly (FMA) and added by Fast2Sum
+// (exact: the operand shift makes |h| >= |p_k Q_kc| at every step, see the
+// set-up).
+// Small DMAX: the slot's Q columns were loaded into qh/ql once for all RW
+// rows (PRE). Larger DMAX: they are read per k from Qh/Ql (L1-resident).
+template <int DMAX, bool PRE>
+__device__ __forceinline__ void slot_dot(const float *p, int d, const float4 &ah,
+                                         const float4 &al, const float4 *qh, const float4 *ql,
+                                         const float *Qh, const float *Ql, int64_t ldq, int v,
+                                         float h[4], float l[4])
+{
+    h[0] = ah.x; h[1] = ah.y; h[2] = ah.z; h[3] = ah.w;
+    l[0] = al.x; l[1] = al.y; l[2] = al.z; l[3] = al.w;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) {
+        if (k < d) {
+            float4 a4, b4;
+            if (PRE) {
+                a4 = qh[k];
+                b4 = ql[k];
+            } else {
+                a4 = __ldg(reinterpret_cast<const float4 *>(Qh + k * ldq) + v);
+                b4 = __ldg(reinterpret_cast<const float4 *>(Ql + k * ldq) + v);
+            }
+            const float qv[4] = {a4.x, a4.y, a4.z, a4.w};
+            const float qlv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float pr = p[k] * qv[e];
+                float pe = fmaf(p[k], qv[e], -pr);     // exact product error
+                pe = fmaf(p[k], qlv[e], pe);
+                const float hn = h[e] + pr;             // Fast2Sum
+                const float z = hn - h[e];
+                l[e] += (pr - z) + pe;
+                h[e] = hn;
+            }
+        }
+    }
+}
+
+// Cost entries C_ij (scaled by s) of one slot, formed directly from the
+// points in FP32 for the transport cost: sum_k (x_k - y_k)^2 for squared
+// Euclidean (no cancellation between norms), 1 - <x, y> for cosine.
+template <int DMAX>
+__device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float s,
+                                          const float *Pc, int c0, int nc, float cst[4])
+{
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int c = min(c0 + e, nc - 1);
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) {
+            if (k < d) {
+                const float y = __ldg(Pc + (int64_t)c * d + k);
+                if (kind == 1) {
+                    const float df = p[k] - y;
+                    acc = fmaf(df, df, acc);
+                } else {
+                    acc = fmaf(p[k], y, acc);
+                }
+            }
+        }
+        cst[e] = s * (kind == 1 ? acc : 1.0f - acc);
+    }
+}
+
+// Folds one slot's terms 2^(h + l - R) into a row accumulator; raises R to
+// the slot maximum first (rare after the first slots).
+template <bool WC>
+__device__ __forceinline__ void slot_accumulate(Acc &acc, Acc &cacc, const float h[4],
+                                                const float l[4], const float cst[4])
+{
+    const float m4 = fmaxf(fmaxf(h[0], h[1]), fmaxf(h[2], h[3]));
+    if (m4 > acc.R) {
+        const float f = ex2_approx(acc.R - m4);
+        acc.S *= f;
+        acc.K *= f;
+        if (WC) { cacc.S *= f; cacc.K *= f; }
+        acc.R = m4;
+    }
+    float s = 0.0f, cs = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float t = ex2_approx((h[e] - acc.R) + l[e]);   // h - R exact (Sterbenz)
+        s += t;
+        if (WC) cs = fmaf(cst[e], t, cs);
+    }
+    kahan(acc, s);
+    if (WC) kahan(cacc, cs);
+}
+
+// Rows r of P against all columns of Q (see PointView), RW rows per warp so
+// each column slot is loaded once per RW rows:
+//   MODE 0 (row pass): A = k (G - By), rows of X, B64 = Bx; finishes u_i,
+//     the column operand A'_i = k (F_i - Bx_i) and the CTA partials.
+//   MODE 1 (column pass): A = A', rows of Y, B64 = By; finishes ell_j.
+// With h_rc = k (A-term + x.Q) the row's log-sum-exp in natural units is
+//   (R + log2 S) ln 2 - (B_r + shift) / eps_c.
+template <int MODE, int DMAX, int RW, bool WC>
 __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 {
     DevState *st = w.st;
     if (!w.ignore_done && *(volatile int32_t *)&st->done) return;
     if (MODE == 0 && blockIdx.x == 0 && threadIdx.x == 0) st->barrier = 0u;
 
-    const float kh = st->k_hi, kl = st->k_lo;
     const int nr = pv.nr, nc = pv.nc, d = pv.d;
     const int64_t ldq = pv.ldq;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * kPtNT + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * kPtNT) >> 5;
-    const int nc4 = (nc + 3) >> 2;   // float4 groups (arrays padded to 4)
-    constexpr int kStep = 32 * kPtU;
+    const int nc4 = (nc + 3) >> 2;             // float4 slots (operands padded to 4)
+    const int nfull = (nc >> 2) & ~31;         // slots in whole, unmasked 32-lane chunks
+    const float cs_scale = WC ? (float)pv.scal[1] : 0.0f;
+    constexpr bool PRE = DMAX <= 4;
+    const float4 *Ah4 = reinterpret_cast<const float4 *>(pv.Ah);
+    const float4 *Al4 = reinterpret_cast<const float4 *>(pv.Al);
 
     double my_dual = 0.0, my_cost = 0.0;
-    for (int r = gwarp; r < nr; r += nwarps) {
-        float p[DMAX];
+    for (int r0 = gwarp * RW; r0 < nr; r0 += nwarps * RW) {
+        float p[RW][DMAX];
 #pragma unroll
-        for (int k = 0; k < DMAX; ++k) p[k] = (k < d) ? pv.P[(int64_t)r * d + k] : 0.0f;
-        const float bh = pv.Bh[r], bl = pv.Bl[r];
-        Acc acc = {0.0f, 0.0f, 0.0f};
-        Acc cacc = {0.0f, 0.0f, 0.0f};
-        for (int vb = 0; vb < nc4; vb += kStep) {
-            float hh[kPtU][4], ll[kPtU][4], cc[kPtU][4];
-            float cm = acc.R;
+        for (int q = 0; q < RW; ++q) {
+            const int rr = min(r0 + q, nr - 1);
 #pragma unroll
-            for (int u = 0; u < kPtU; ++u) {
-                const int v = vb + lane + 32 * u;
-                if (v < nc4) {
-                    const float4 ah = __ldg(reinterpret_cast<const float4 *>(pv.Ah) + v);
-                    const float4 al = __ldg(reinterpret_cast<const float4 *>(pv.Al) + v);
-                    float h[4] = {ah.x, ah.y, ah.z, ah.w};
-                    float l[4] = {al.x, al.y, al.z, al.w};
-                    float dt[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < DMAX; ++k) p[q][k] = (k < d) ? pv.P[(int64_t)rr * d + k] : 0.0f;
+        }
+        Acc acc[RW], cacc[RW];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        // h - B: Fast2Sum (|A| >= |B| by the operand shift)
-                        const float hn = h[e] - bh;
-                        const float z = hn - h[e];
-                        l[e] += (-bh - z) - bl;
-                        h[e] = hn;
-                    }
+        for (int q = 0; q < RW; ++q) {
+            acc[q] = {-INFINITY, 0.0f, 0.0f};
+            cacc[q] = {0.0f, 0.0f, 0.0f};
+        }
+        // whole chunks: every element valid
+        for (int v = lane; v < nfull; v += 32) {
+            const float4 ah = __ldg(Ah4 + v), al = __ldg(Al4 + v);
+            float4 qh[PRE ? DMAX : 1], ql[PRE ? DMAX : 1];
+            if (PRE) {
 #pragma unroll
-                    for (int k = 0; k < DMAX; ++k) {
-                        if (k < d) {
-                            const float4 qh = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
-                            const float4 ql = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
-                            const float qhv[4] = {qh.x, qh.y, qh.z, qh.w};
-                            const float qlv[4] = {ql.x, ql.y, ql.z, ql.w};
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float pr = p[k] * qhv[e];
-                                float pe = fmaf(p[k], qhv[e], -pr);    // exact product error
-                                pe = fmaf(p[k], qlv[e], pe);
-                                const float hn = h[e] + pr;            // Fast2Sum, |h| >= |pr|
-                                const float z = hn - h[e];
-                                l[e] += (pr - z) + pe;
-                                h[e] = hn;
-                                if (WITH_COST) dt[e] = fmaf(p[k], qhv[e], dt[e]);
-                            }
-                        }
-                    }
-                    const int c0 = 4 * v;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const bool ok = c0 + e < nc;
-                        hh[u][e] = ok ? h[e] : 0.0f;
-                        ll[u][e] = ok ? l[e] : -INFINITY;
-                        if (WITH_COST) cc[u][e] = ok ? (bh + pv.Ch[c0 + e] - dt[e]) : 0.0f;
-                        cm = fmaxf(cm, hh[u][e]);
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        hh[u][e] = 0.0f;
-                        ll[u][e] = -INFINITY;
-                        cc[u][e] = 0.0f;
+                for (int k = 0; k < DMAX; ++k) {
+                    if (k < d) {
+                        qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
+                        ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
                     }
                 }
             }
-            if (cm > acc.R) {
-                const float f = exp2_scaled(acc.R - cm, kh, kl);
-                acc.S *= f;
-                acc.K *= f;
-                if (WITH_COST) { cacc.S *= f; cacc.K *= f; }
-                acc.R = cm;
-            }
-            const float R = acc.R;
-            float cs = 0.0f, ccs = 0.0f;
 #pragma unroll
-            for (int u = 0; u < kPtU; ++u) {
+            for (int q = 0; q < RW; ++q) {
+                float h[4], l[4], cst[4];
+                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l);
+                if (WC) slot_cost<DMAX>(p[q], d, pv.kind, cs_scale, pv.Pc, 4 * v, nc, cst);
+                slot_accumulate<WC>(acc[q], cacc[q], h, l, cst);
+            }
+        }
+        // ragged tail: at most one slot per lane, masked per element
+        for (int v = nfull + lane; v < nc4; v += 32) {
+            const float4 ah = __ldg(Ah4 + v), al = __ldg(Al4 + v);
+            float4 qh[PRE ? DMAX : 1], ql[PRE ? DMAX : 1];
+            if (PRE) {
+#pragma unroll
+                for (int k = 0; k < DMAX; ++k) {
+                    if (k < d) {
+                        qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
+                        ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
+                    }
+                }
+            }
+            const int c0 = 4 * v;
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                float h[4], l[4], cst[4];
+                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l);
+                if (WC) slot_cost<DMAX>(p[q], d, pv.kind, cs_scale, pv.Pc, c0, nc, cst);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const float t = hh[u][e] - R;
-                    const float pterm = ex2_approx(fmaf(t, kh, fmaf(t, kl, ll[u][e] * kh)));
-                    cs += pterm;
-                    if (WITH_COST) ccs = fmaf(cc[u][e], pterm, ccs);
+                    if (c0 + e >= nc) { h[e] = -INFINITY; l[e] = 0.0f; }
+                }
+                slot_accumulate<WC>(acc[q], cacc[q], h, l, cst);
+            }
+        }
+        // per row: lane merge (double-float tree), FP64 finish by lane 0
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int r = r0 + q;
+            const float Rrow = warp_max(acc[q].R);
+            const float sc = ex2_approx(acc[q].R - Rrow);
+            float hi, lo, chi = 0.f, clo = 0.f;
+            two_sum(acc[q].S * sc, -acc[q].K * sc, hi, lo);
+            if (WC) two_sum(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+                const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+                float s2, e2;
+                two_sum(hi, ohi, s2, e2);
+                lo = lo + olo + e2;
+                two_sum(s2, lo, hi, lo);
+                if (WC) {
+                    const float ochi = __shfl_xor_sync(0xffffffffu, chi, o);
+                    const float oclo = __shfl_xor_sync(0xffffffffu, clo, o);
+                    two_sum(chi, ochi, s2, e2);
+                    clo = clo + oclo + e2;
+                    two_sum(s2, clo, chi, clo);
                 }
             }
-            kahan(acc, cs);
-            if (WITH_COST) kahan(cacc, ccs);
-        }
-        // lane merge (double-float tree), FP64 finish by lane 0
-        const float Rrow = warp_max(acc.R);
-        const float sc = exp2_scaled(acc.R - Rrow, kh, kl);
-        float hi, lo, chi = 0.f, clo = 0.f;
-        two_sum(acc.S * sc, -acc.K * sc, hi, lo);
-        if (WITH_COST) two_sum(cacc.S * sc, -cacc.K * sc, chi, clo);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
-            float s2, e2;
-            two_sum(hi, ohi, s2, e2);
-            lo = lo + olo + e2;
-            two_sum(s2, lo, hi, lo);
-            if (WITH_COST) {
-                const float ochi = __shfl_xor_sync(0xffffffffu, chi, o);
-                const float oclo = __shfl_xor_sync(0xffffffffu, clo, o);
-                two_sum(chi, ochi, s2, e2);
-                clo = clo + oclo + e2;
-                two_sum(s2, clo, chi, clo);
-            }
-        }
-        if (lane == 0) {
-            const double S = (double)hi + (double)lo;
-            if (MODE == 1) {
-                w.ell[r] = ((double)Rrow - st->shift_f) * st->inv_eps_c + log(S);
-            } else {
-                const double lse = ((double)Rrow - st->shift_g) * st->inv_eps_c + log(S);
-                const double ui = w.loga[r] - lse;
-                w.u[r] = ui;
-                // column-pass operand A'_r = F_r - Bx_r, F = eps u + shift_f
-                const double A2 = st->eps_c * ui + st->shift_f - w.Bx64[r];
-                const float A2h = (float)A2;
-                w.Fh[r] = A2h;
-                w.Fk[r] = (float)(A2 - (double)A2h);
-                my_dual += w.a[r] * ui;
-                if (WITH_COST) {
-                    // row weight: a_r after the row pass, or the mass of row r
-                    // under given potentials f (f_r / eps + LSE_r)
-                    const double wr = w.f_given ? exp(w.f_given[r] / st->eps_user + lse) : w.a[r];
-                    my_cost += wr * (((double)chi + (double)clo) / S);
+            if (lane == 0 && r < nr) {
+                const double S = (double)hi + (double)lo;
+                const double l2 = (double)Rrow * kLn2 + log(S);
+                if (MODE == 1) {
+                    w.ell[r] = l2 - (pv.B64[r] + st->shift_f) * st->inv_eps_c;
+                } else {
+                    const double bx = pv.B64[r];
+                    const double lse = l2 - (bx + st->shift_g) * st->inv_eps_c;
+                    const double ui = w.loga[r] - lse;
+                    w.u[r] = ui;
+                    // column-pass operand A'_r = k (F_r - Bx_r), F = eps u + shift_f
+                    const double A2 = st->k2 * (st->eps_c * ui + st->shift_f - bx);
+                    const float A2h = (float)A2;
+                    w.Fh[r] = A2h;
+                    w.Fk[r] = (float)(A2 - (double)A2h);
+                    my_dual += w.a[r] * ui;
+                    if (WC) {
+                        // row mass: a_r after the row pass, or f_r / eps + LSE_r
+                        // under given potentials f
+                        const double wr =
+                            w.f_given ? exp(w.f_given[r] / st->eps_user + lse) : w.a[r];
+                        my_cost += wr * (((double)chi + (double)clo) / S);
+                    }
                 }
             }
         }
@@ -216,12 +298,18 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
     }
 }
 
+// Rows per warp for a dimension bound: enough registers for RW rows of
+// points plus one slot of column operands.
+template <int DMAX>
+constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
+
 template <int MODE, bool WC>
 static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cudaStream_t s)
 {
-    if (pv.d <= 4) k_lse_points<MODE, 4, WC><<<grid, kPtNT, 0, s>>>(pv, w);
-    else if (pv.d <= 16) k_lse_points<MODE, 16, WC><<<grid, kPtNT, 0, s>>>(pv, w);
-    else k_lse_points<MODE, 64, WC><<<grid, kPtNT, 0, s>>>(pv, w);
+    if (pv.d <= 4) k_lse_points<MODE, 4, rows_per_warp<4>(), WC><<<grid, kPtNT, 0, s>>>(pv, w);
+    else if (pv.d <= 8) k_lse_points<MODE, 8, rows_per_warp<8>(), WC><<<grid, kPtNT, 0, s>>>(pv, w);
+    else if (pv.d <= 16) k_lse_points<MODE, 16, rows_per_warp<16>(), WC><<<grid, kPtNT, 0, s>>>(pv, w);
+    else k_lse_points<MODE, 64, rows_per_warp<64>(), WC><<<grid, kPtNT, 0, s>>>(pv, w);
     return cudaGetLastError();
 }
 
@@ -236,8 +324,13 @@ cudaError_t launch_points_pass(const PointView &pv, const Work &w, int grid, int
 int occupancy_points_pass()
 {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lse_points<0, 4, false>, kPtNT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lse_points<0, 4, 4, false>, kPtNT, 0);
     return b > 0 ? b : 1;
+}
+
+int points_rows_per_warp(int d)
+{
+    return d <= 8 ? rows_per_warp<4>() : (d <= 16 ? rows_per_warp<16>() : rows_per_warp<64>());
 }
 
 // ------------------------------------------------------------------------
@@ -326,13 +419,15 @@ __global__ void k_points_scale(const double *rowmax, int n, int scale_max, doubl
     }
 }
 
-// Bx, By in FP64 and as pairs; Q (scaled Y) and Q' (scaled X) in SoA pairs;
+// Bx, By in FP64 and as pairs; Q (scaled Y) and Q' (scaled X), both times
+// k = log2(e) / eps, in SoA pairs;
 // per-block maxima for the shift bound and a count of non-finite coordinates. `scal` = {max C, s}.
 __global__ void k_points_setup(const float *X, const float *Y, int n, int m, int d, int kind,
-                               const double *scal, Work w, double *blockmax)
+                               const double *scal, double eps, Work w, double *blockmax)
 {
     const double s = scal[1];
     const double qs = (kind == 1) ? 2.0 * s : s;
+    const double kq = (kLog2e / eps) * qs;   // Q in log2 units
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     double mbx = 0.0, mby = 0.0, mdot = 0.0, nbad = 0.0;
@@ -344,7 +439,7 @@ __global__ void k_points_setup(const float *X, const float *Y, int n, int m, int
             if (!isfinite(xv)) nbad += 1.0;
             nx += xv * xv;
             ax = fmax(ax, fabs(xv));
-            const double q = qs * xv;
+            const double q = kq * xv;
             const float qh = (float)q;
             w.PXh[(int64_t)k * w.ldx + i] = qh;
             w.PXl[(int64_t)k * w.ldx + i] = (float)(q - (double)qh);
@@ -365,7 +460,7 @@ __global__ void k_points_setup(const float *X, const float *Y, int n, int m, int
             if (!isfinite(yv)) nbad += 1.0;
             ny += yv * yv;
             ay = fmax(ay, fabs(yv));
-            const double q = qs * yv;
+            const double q = kq * yv;
             const float qh = (float)q;
             w.PYh[(int64_t)k * w.ldy + j] = qh;
             w.PYl[(int64_t)k * w.ldy + j] = (float)(q - (double)qh);
@@ -429,11 +524,11 @@ __global__ void k_points_stats(const double *blockmax, int nblk, int d, int kind
 }
 
 cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, int d, int kind,
-                                int scale_max, const Work &w, double *scal, double *blockmax,
-                                int nblk, cudaStream_t s)
+                                int scale_max, double eps, const Work &w, double *scal,
+                                double *blockmax, int nblk, cudaStream_t s)
 {
     k_points_scale<<<1, 256, 0, s>>>(w.rowmax, n, scale_max, scal);
-    k_points_setup<<<nblk, 256, 0, s>>>(X, Y, n, m, d, kind, scal, w, blockmax);
+    k_points_setup<<<nblk, 256, 0, s>>>(X, Y, n, m, d, kind, scal, eps, w, blockmax);
     k_points_stats<<<1, 32, 0, s>>>(blockmax, nblk, d, kind, scal, w.statpart);
     return cudaGetLastError();
 }

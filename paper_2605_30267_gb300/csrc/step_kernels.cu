@@ -134,11 +134,12 @@ __device__ __forceinline__ void cost_totals(const double *statpart, int nstat, d
 
 // Writes the row-pass operand for column j from g_j + shift_g: for a dense
 // cost the pair (hi, lo k_hi) of G_j; for a point-cloud cost the pair
-// (hi, lo) of A_j = G_j - By_j (the expansion term of points.cu).
-__device__ __forceinline__ void write_G(const Work &w, int j, double gshift, float kh)
+// (hi, lo) of A_j = k (G_j - By_j) in log2 units (k = log2(e)/eps_c, the
+// expansion term of points.cu).
+__device__ __forceinline__ void write_G(const Work &w, int j, double gshift, float kh, double k)
 {
     if (w.By64) {
-        const double a = gshift - w.By64[j];
+        const double a = k * (gshift - w.By64[j]);
         const float hi = (float)a;
         w.G[j] = hi;
         w.Gk[j] = (float)(a - (double)hi);
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
     // eps_c u_i >= eps_c min log a - eps_c max x + min C - eps_c log m.
     const double shift_g = cabs;
     const double shift_f = cabs - (eps_c * min_loga - 0.0 + cmin - eps_c * log_m);
-    for (int j = tid; j < m; j += nthr) write_G(w, j, shift_g, kh);
+    for (int j = tid; j < m; j += nthr) write_G(w, j, shift_g, kh, k);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->eps_c = eps_c;
         st->inv_eps_c = 1.0 / eps_c;
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
         st->shift_f = shift_f;
         st->k_hi = kh;
         st->k_lo = kl;
+        st->k2 = k;
         st->steps = 0; st->stages = 0; st->failures = 0; st->j_in_stage = 0;
         st->first = 1; st->done = 0; st->status = 0;
         st->err = INFINITY; st->dual = 0.0; st->kl_prev = 0.0;
@@ -586,6 +588,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     const double shift_fn = st->cabs - (eps_c * st->min_loga - eps_c * xhi + st->cmin -
                                         eps_c * st->log_m);
     if (!stop) {
+        const double k2 = st->k2;
         for (int j = tid; j < m; j += nthr) {
             const double s = w.raw[j] - rbar;
             const double xj = w.x[j];
@@ -602,7 +605,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             w.x[j] = xn;
             w.p_prev[j] = w.del[j];
             w.D_prev[j] = w.D1[j];
-            write_G(w, j, eps_c * xn + shift_g, kh);
+            write_G(w, j, eps_c * xn + shift_g, kh, k2);
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -733,7 +736,7 @@ __global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nst
     const double shift_g = cabs - cost_div * t[0];
     const double shift_f =
         cabs - (eps_c * t[2] - cost_div * t[1] + cmin - eps_c * log((double)m));
-    for (int j = tid; j < m; j += nthr) write_G(w, j, cost_div * g[j] + shift_g, kh);
+    for (int j = tid; j < m; j += nthr) write_G(w, j, cost_div * g[j] + shift_g, kh, k);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->eps_c = eps_c;
         st->inv_eps_c = 1.0 / eps_c;
@@ -745,6 +748,7 @@ __global__ void __launch_bounds__(kVecNT) k_prep_g(Work w, int n, int m, int nst
         st->shift_f = shift_f;
         st->k_hi = kh;
         st->k_lo = kl;
+        st->k2 = k;
         st->done = 0;
         st->status = 0;
         st->first = 1;
@@ -804,8 +808,8 @@ __global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nst
     for (int i = tid; i < n; i += nthr) {
         const double F = cost_div * f[i] + shift_f;
         if (w.Bx64) {
-            // point-cloud column operand A'_i = F_i - Bx_i as (hi, lo)
-            const double A2 = F - w.Bx64[i];
+            // point-cloud column operand A'_i = k (F_i - Bx_i) as (hi, lo)
+            const double A2 = k * (F - w.Bx64[i]);
             const float Ah = (float)A2;
             w.Fh[i] = Ah;
             w.Fk[i] = (float)(A2 - (double)Ah);
@@ -825,6 +829,7 @@ __global__ void __launch_bounds__(kVecNT) k_prep_f(Work w, int n, int m, int nst
         st->shift_f = shift_f;
         st->k_hi = kh;
         st->k_lo = kl;
+        st->k2 = k;
         st->done = 0;
         st->status = 0;
     }
