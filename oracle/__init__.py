@@ -28,7 +28,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "acc_sinkhorn_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-DENSE, SQEUCLID, COSINE = 0, 1, 2
+DENSE, SQEUCLID, COSINE, DENSE64 = 0, 1, 2, 3
 PLAIN, ACC = 0, 1
 STAB_OFF, STAB_REPORT, STAB_GATE = 0, 1, 2
 CONVERGED, MAXITER = 0, 7
@@ -58,7 +58,7 @@ class _Cost(ct.Structure):
     _fields_ = [("kind", ct.c_int), ("n", ct.c_long), ("m", ct.c_long),
                 ("d", ct.c_long), ("ldc", ct.c_long),
                 ("C", ct.c_void_p), ("X", ct.c_void_p), ("Y", ct.c_void_p),
-                ("scale", ct.c_double)]
+                ("scale", ct.c_double), ("C64", ct.c_void_p)]
 
 
 class _Problem(ct.Structure):
@@ -162,6 +162,23 @@ class Cost:
 
     def unscaled_max(self):
         return _L().orc_cost_max(self.ref)
+
+    def materialised(self):
+        """The same cost formed once as an FP64 matrix (entries identical to
+        ``entry``, scale applied), so that each pass reads instead of forming
+        them: much faster for high-dimensional point clouds."""
+        return MaterialisedCost(self.matrix())
+
+
+class MaterialisedCost(Cost):
+    """A cost given as an FP64 n x m matrix (already scaled)."""
+
+    def __init__(self, C64):
+        C64 = np.ascontiguousarray(C64, dtype=np.float64)
+        self.C64, self.C, self.X, self.Y = C64, None, None, None
+        self.kind, self.n, self.m, self.d = DENSE64, C64.shape[0], C64.shape[1], 0
+        self._s = _Cost(DENSE64, self.n, self.m, 0, self.m, None, None, None, 1.0, _p(C64))
+        self.scale = 1.0
 
 
 def normalise(v):

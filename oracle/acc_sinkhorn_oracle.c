@@ -36,16 +36,18 @@
 /* cosine 1 - <x,y> for word alignment).                                       */
 /* ------------------------------------------------------------------------- */
 
-enum { ORC_DENSE = 0, ORC_SQEUCLID = 1, ORC_COSINE = 2 };
+enum { ORC_DENSE = 0, ORC_SQEUCLID = 1, ORC_COSINE = 2, ORC_DENSE64 = 3 };
 
 typedef struct {
-    int kind;         /* ORC_DENSE, ORC_SQEUCLID, ORC_COSINE                  */
+    int kind;         /* ORC_DENSE, ORC_SQEUCLID, ORC_COSINE, ORC_DENSE64     */
     long n, m, d;     /* rows, columns, point dimension (point clouds only)   */
     long ldc;         /* row stride of C in elements (dense only)             */
     const float *C;   /* n x m row-major FP32 cost (dense)                    */
     const float *X;   /* n x d row-major FP32 points                          */
     const float *Y;   /* m x d row-major FP32 points                          */
     double scale;     /* multiply every entry by this (1/max C, or 1)         */
+    const double *C64; /* n x m row-major FP64 cost (ORC_DENSE64): a cost     */
+                       /* already formed once, e.g. by orc_cost_matrix        */
 } orc_cost;
 
 /* One entry of the cost, formed in double from the FP32 inputs. */
@@ -54,6 +56,8 @@ double orc_cost_entry(const orc_cost *c, long i, long j)
     double v = 0.0;
     if (c->kind == ORC_DENSE) {
         v = (double)c->C[i * c->ldc + j];
+    } else if (c->kind == ORC_DENSE64) {
+        v = c->C64[i * c->ldc + j];
     } else if (c->kind == ORC_SQEUCLID) {
         /* C_ij = ||x_i - y_j||^2 (Sec. 5, colour transfer) */
         for (long k = 0; k < c->d; ++k) {

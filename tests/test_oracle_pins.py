@@ -490,3 +490,27 @@ def test_sampled_passes_match_full_passes():
     ell = O.col_lse(cost, 0.05, u)
     es = O.col_lse_sample(cost, 0.05, u, [29, 0])
     np.testing.assert_array_equal(es, ell[[29, 0]])
+
+
+def test_materialised_cost_reproduces_the_point_cloud_cost():
+    """A cost formed once as an FP64 matrix is the same problem: entries equal
+    to the definition (checked against numpy), transposition-sensitive, and a
+    whole solve on it is bitwise identical to the solve on the points."""
+    g = np.random.default_rng(71)
+    X = W.unit_gaussian_points(g, 9, 40)
+    Y = W.unit_gaussian_points(g, 6, 40)
+    cost = O.Cost(X=X, Y=Y, kind="cosine")
+    mc = cost.materialised()
+    direct = 1.0 - X.astype(np.float64) @ Y.astype(np.float64).T
+    np.testing.assert_allclose(mc.matrix(), direct, rtol=0, atol=1e-15)
+    assert mc.entry(8, 5) == cost.entry(8, 5) and mc.entry(5, 2) == cost.entry(5, 2)
+    assert mc.entry(1, 4) != mc.entry(4, 1) or direct[1, 4] == direct[4, 1]
+    a, b = W.dirichlet1(g, 9), W.dirichlet1(g, 6)
+    r1 = O.solve(cost, a, b, 0.02, 1e-9, method=O.ACC)
+    r2 = O.solve(mc, a, b, 0.02, 1e-9, method=O.ACC)
+    assert r1["sinkhorn_steps"] == r2["sinkhorn_steps"]
+    np.testing.assert_array_equal(r1["f"], r2["f"])
+    np.testing.assert_array_equal(r1["g"], r2["g"])
+    # the scale is carried by the matrix
+    cs = O.Cost(X=X, Y=Y, kind="sqeuclid", scale_to_max=True)
+    np.testing.assert_array_equal(cs.materialised().matrix(), cs.matrix())
