@@ -129,7 +129,8 @@ typedef struct {
     double cost_max;             /* max_ij C_ij of the input                 */
     double gpu_ms;               /* device time of the solve (CUDA events)   */
     int32_t loop_mode;           /* 1: CUDA-graph device loop ran; 0: host loop
-                                    (requested, or the graph could not be built) */
+                                    (requested, or the graph could not be built);
+                                    2: batched persistent launch */
     int32_t reserved;
 } accsink_result;
 
@@ -180,6 +181,58 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
 int accsink_get_history(accsink_ctx *ctx, int32_t capacity, double *err,
                         double *dual, double *mu, int32_t *stab, double *cond,
                         int32_t *count);
+
+/* ---- batches: many independent problems in one persistent launch -------- */
+
+/* Work split of a batch (zero fields take the defaults):
+ *   small_max_nm   problems with n*m at most this are solved whole by one
+ *                  CTA (default 65536);
+ *   row_tile_elems cost entries per row-pass work item of larger problems
+ *                  (default 65536; column items are 128 columns);
+ *   ctas_per_sm    persistent CTAs per SM (0: as many as fit). */
+typedef struct {
+    int32_t small_max_nm;
+    int32_t row_tile_elems;
+    int32_t ctas_per_sm;
+    int32_t reserved;
+} accsink_batch_config;
+
+/* Solves `count` independent problems (Sec. 1, eq. EOT, each with its own
+ * a, b, cost, eps and parameters) in one persistent launch, each exactly as
+ * accsink_solve would (same stopping rule, Algorithm 1 + 2, stability modes;
+ * params.history and use_graph are ignored). probs, params and res are host
+ * arrays of `count` records; the pointers inside probs are device pointers;
+ * f_out and g_out are host arrays of `count` device pointers (n_k and m_k
+ * doubles). Each problem's cost is formed once in the context's batch
+ * workspace (8 bytes per entry, FP64-accurate), so point clouds of any
+ * dimension 1 <= d <= 4096 are accepted. Returns OK when every problem
+ * converged, ACCSINK_ERR_MAXITER when some did not (their results are still
+ * valid), another code for the first failed problem (see res[k].status), or
+ * ACCSINK_ERR_TIMEOUT if a device-side wait of the scheduler ran out. */
+int accsink_solve_batch(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
+                        const accsink_params *params, void *stream,
+                        double *const *f_out, double *const *g_out,
+                        accsink_result *res);
+
+/* The context's batch work split (NULL resets to the defaults). */
+int accsink_batch_set_config(accsink_ctx *ctx, const accsink_batch_config *cfg);
+int accsink_batch_get_config(const accsink_ctx *ctx, accsink_batch_config *cfg);
+
+/* Autotuner: solves the batch once with each candidate work split, keeps the
+ * fastest in the context and writes it to *best. times_ms (host, capacity
+ * cap, may be NULL) receives each candidate's time and *tried their number.
+ * Arguments otherwise as accsink_solve_batch (the outputs hold the last
+ * candidate's solve). */
+int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
+                           const accsink_params *params, void *stream,
+                           double *const *f_out, double *const *g_out,
+                           accsink_result *res, accsink_batch_config *best,
+                           float *times_ms, int32_t cap, int32_t *tried);
+
+/* Device times of the last batch on this context: total, cost formation and
+ * persistent solve, in milliseconds (host pointers, any may be NULL). */
+int accsink_batch_last_timing(const accsink_ctx *ctx, float *total_ms, float *form_ms,
+                              float *solve_ms);
 
 /* ---- single passes (the hot path's steps, for tests and roofline timing) */
 

@@ -31,7 +31,8 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_version", "accsink_solve", "accsink_solve_host", "accsink_get_history",
             "accsink_row_pass", "accsink_col_lse", "accsink_sinkhorn_map",
             "accsink_transport_cost", "accsink_time_passes", "accsink_launch_geometry",
-            "accsink_col_lse_noalloc"]
+            "accsink_col_lse_noalloc", "accsink_solve_batch", "accsink_batch_set_config",
+            "accsink_batch_get_config", "accsink_batch_autotune", "accsink_batch_last_timing"]
 
 
 class accsink_problem(ct.Structure):
@@ -56,6 +57,11 @@ class accsink_result(ct.Structure):
                 ("marginal_l1", ct.c_double), ("transport_cost", ct.c_double),
                 ("dual_objective", ct.c_double), ("cost_max", ct.c_double),
                 ("gpu_ms", ct.c_double), ("loop_mode", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class accsink_batch_config(ct.Structure):
+    _fields_ = [("small_max_nm", ct.c_int32), ("row_tile_elems", ct.c_int32),
+                ("ctas_per_sm", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class AccsinkError(RuntimeError):
@@ -101,6 +107,14 @@ def lib():
                                           P(ct.c_float), P(ct.c_float)]
         L.accsink_launch_geometry.argtypes = [vp, i32, i32, i32, P(i32)]
         L.accsink_col_lse_noalloc.argtypes = [P(accsink_problem), dbl, vp, vp, vp]
+        L.accsink_solve_batch.argtypes = [vp, i32, P(accsink_problem), P(accsink_params), vp,
+                                          P(vp), P(vp), P(accsink_result)]
+        L.accsink_batch_set_config.argtypes = [vp, P(accsink_batch_config)]
+        L.accsink_batch_get_config.argtypes = [vp, P(accsink_batch_config)]
+        L.accsink_batch_autotune.argtypes = [vp, i32, P(accsink_problem), P(accsink_params), vp,
+                                             P(vp), P(vp), P(accsink_result),
+                                             P(accsink_batch_config), P(ct.c_float), i32, P(i32)]
+        L.accsink_batch_last_timing.argtypes = [vp, P(ct.c_float), P(ct.c_float), P(ct.c_float)]
         for name in EXPORTED:
             if name not in ("accsink_destroy", "accsink_params_default", "accsink_last_error",
                             "accsink_version"):
@@ -268,6 +282,54 @@ class Context:
                                       ct.c_void_p(g_out.ctypes.data), ct.byref(res))
         self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
         return res
+
+    # ---- batches ------------------------------------------------------
+    @staticmethod
+    def _batch_arrays(probs, params, f_outs, g_outs):
+        k = len(probs)
+        if not (len(params) == len(f_outs) == len(g_outs) == k):
+            raise ValueError("probs, params, f_outs and g_outs must have the same length")
+        pa = (accsink_problem * k)(*probs)
+        qa = (accsink_params * k)(*params)
+        fa = (ct.c_void_p * k)(*[_ptr(t) for t in f_outs])
+        ga = (ct.c_void_p * k)(*[_ptr(t) for t in g_outs])
+        ra = (accsink_result * k)()
+        return k, pa, qa, fa, ga, ra
+
+    def accsink_solve_batch(self, probs, params, f_outs, g_outs, stream=None,
+                            allow_maxiter=True):
+        """probs/params: lists of structs (device pointers inside); f_outs,
+        g_outs: lists of FP64 CUDA tensors. Returns the list of results."""
+        k, pa, qa, fa, ga, ra = self._batch_arrays(probs, params, f_outs, g_outs)
+        rc = lib().accsink_solve_batch(self._h, k, pa, qa, _stream_ptr(stream), fa, ga, ra)
+        self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+        return [ra[i] for i in range(k)]
+
+    def accsink_batch_set_config(self, small_max_nm=0, row_tile_elems=0, ctas_per_sm=0):
+        c = accsink_batch_config(small_max_nm, row_tile_elems, ctas_per_sm, 0)
+        self._raise(lib().accsink_batch_set_config(self._h, ct.byref(c)))
+
+    def accsink_batch_get_config(self) -> dict:
+        c = accsink_batch_config()
+        self._raise(lib().accsink_batch_get_config(self._h, ct.byref(c)))
+        return {"small_max_nm": c.small_max_nm, "row_tile_elems": c.row_tile_elems,
+                "ctas_per_sm": c.ctas_per_sm}
+
+    def accsink_batch_autotune(self, probs, params, f_outs, g_outs, stream=None):
+        k, pa, qa, fa, ga, ra = self._batch_arrays(probs, params, f_outs, g_outs)
+        best = accsink_batch_config()
+        times = (ct.c_float * 64)()
+        tried = ct.c_int32()
+        rc = lib().accsink_batch_autotune(self._h, k, pa, qa, _stream_ptr(stream), fa, ga, ra,
+                                          ct.byref(best), times, 64, ct.byref(tried))
+        self._raise(rc)
+        return ({"small_max_nm": best.small_max_nm, "row_tile_elems": best.row_tile_elems,
+                 "ctas_per_sm": best.ctas_per_sm}, list(times)[:tried.value])
+
+    def accsink_batch_last_timing(self):
+        t, f, s = ct.c_float(), ct.c_float(), ct.c_float()
+        self._raise(lib().accsink_batch_last_timing(self._h, ct.byref(t), ct.byref(f), ct.byref(s)))
+        return {"total_ms": t.value, "form_ms": f.value, "solve_ms": s.value}
 
     def accsink_get_history(self, capacity: int):
         import numpy as np

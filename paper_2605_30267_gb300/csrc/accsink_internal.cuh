@@ -187,6 +187,53 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// Running log2-sum-exp accumulator of one lane: sum = (S - K) 2^R (Kahan
+// pair S, K about the running maximum R).
+struct Lse2 {
+    float R, S, K;
+};
+
+__device__ __forceinline__ void lse2_kahan(Lse2 &a, float x)
+{
+    const float y = x - a.K;
+    const float t = a.S + y;
+    a.K = (t - a.S) - y;
+    a.S = t;
+}
+
+// Knuth's TwoSum: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Folds one slot's terms 2^(h + l - R) into a row accumulator; raises R to
+// the slot maximum first (rare after the first slots).
+template <bool WC>
+__device__ __forceinline__ void slot_accumulate(Lse2 &acc, Lse2 &cacc, const float h[4],
+                                                const float l[4], const float cst[4])
+{
+    const float m4 = fmaxf(fmaxf(h[0], h[1]), fmaxf(h[2], h[3]));
+    if (m4 > acc.R) {
+        const float f = ex2_approx(acc.R - m4);
+        acc.S *= f;
+        acc.K *= f;
+        if (WC) { cacc.S *= f; cacc.K *= f; }
+        acc.R = m4;
+    }
+    float s = 0.0f, cs = 0.0f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const float t = ex2_approx((h[e] - acc.R) + l[e]);   // h - R exact (Sterbenz)
+        s += t;
+        if (WC) cs = fmaf(cst[e], t, cs);
+    }
+    lse2_kahan(acc, s);
+    if (WC) lse2_kahan(cacc, cs);
+}
+
 // Grid-wide barrier for cooperatively launched kernels (all blocks resident).
 // `target` is the arrival count to wait for (k * gridDim for the k-th
 // barrier of a launch; the counter is zeroed by the kernel that runs before).

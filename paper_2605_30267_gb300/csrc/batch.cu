@@ -1,0 +1,978 @@
+// Batched solver kernels: cost formation, scaling and the persistent solve.
+//
+// The arithmetic of a pass is the single-problem path's, in log2 units on a
+// stored double-float cost: with G'_j = k (eps_c x_j + shift_g) and
+// K_ij = k C_ij as (hi, lo) pairs, the exponent G'_j - K_ij is formed
+// exactly (Fast2Sum on the hi parts, valid because the shift makes
+// G' >= k max|C|, plus the lo parts), each row keeps a running maximum R and
+// a Kahan pair, lanes merge in double-float and each row finishes in FP64:
+//   LSE_j(x_j - C_ij / eps_c) = (R + log2 S) ln 2 - shift_g / eps_c.
+// The step is Algorithm 1 + 2 with Theorem 4's test, as in the single-problem
+// step kernel, reduced over one CTA.
+#include <float.h>
+
+#include "accsink_internal.cuh"
+#include "batch_internal.cuh"
+
+namespace accsink {
+
+namespace {
+
+constexpr int kBW = kBatchThreads / 32;            // warps per CTA
+constexpr uint64_t kQueueWaitNs = 20000000000ull;  // 20 s for one queue wait
+
+// ---------------------------------------------------------------- helpers --
+
+// Order-preserving map of doubles to unsigned 64-bit integers (for atomic
+// min / max of FP64 values).
+__device__ __forceinline__ unsigned long long enc_d(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double dec_d(unsigned long long e)
+{
+    const unsigned long long b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t *p)
+{
+    return *(const volatile int32_t *)p;
+}
+
+// The scale k = log2(e) / eps_c of a problem, from its formation statistics.
+__device__ __forceinline__ double batch_cost_div(const BatchProb *P)
+{
+    const double cmax = dec_d(P->cmax_enc);
+    return (P->scale && cmax > 0.0) ? cmax : 1.0;
+}
+
+__device__ __forceinline__ double batch_k(const BatchProb *P)
+{
+    return kLog2e / (P->eps * batch_cost_div(P));
+}
+
+// CTA-wide sums of N doubles (fixed order); every thread gets the totals.
+template <int N>
+__device__ __forceinline__ void cta_sum(double (&v)[N])
+{
+    __shared__ double sh[N][kBW];
+    __shared__ double tot[N];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const double s = warp_sum(v[k]);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double s = 0.0;
+        for (int q = 0; q < kBW; ++q) s += sh[threadIdx.x][q];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = tot[k];
+    __syncthreads();
+}
+
+// CTA-wide min (lo) and max (hi) of N doubles each.
+template <int N>
+__device__ __forceinline__ void cta_minmax(double (&lo)[N], double (&hi)[N])
+{
+    __shared__ double sl[N][kBW], shh[N][kBW];
+    __shared__ double tl[N], th[N];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        double a = lo[k], b = hi[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) { sl[k][wid] = a; shh[k][wid] = b; }
+    }
+    __syncthreads();
+    if (threadIdx.x < N) {
+        double a = sl[threadIdx.x][0], b = shh[threadIdx.x][0];
+        for (int q = 1; q < kBW; ++q) { a = fmin(a, sl[threadIdx.x][q]); b = fmax(b, shh[threadIdx.x][q]); }
+        tl[threadIdx.x] = a;
+        th[threadIdx.x] = b;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; ++k) { lo[k] = tl[k]; hi[k] = th[k]; }
+    __syncthreads();
+}
+
+// Writes a double-float (hi, lo) of v.
+__device__ __forceinline__ void put_df(float *hp, float *lp, int64_t i, double v)
+{
+    const float h = (float)v;
+    hp[i] = h;
+    lp[i] = (float)(v - (double)h);
+}
+
+// Lane-tree merge of a warp's (R, S, K) accumulators into one double-float
+// sum about the warp maximum; every lane gets (Rw, hi, lo).
+__device__ __forceinline__ void warp_merge(const Lse2 &a, float &Rw, float &hi, float &lo)
+{
+    Rw = warp_max(a.R);
+    const float sc = (a.R == -INFINITY) ? 0.0f : ex2_approx(a.R - Rw);
+    two_sum_f(a.S * sc, -a.K * sc, hi, lo);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s2, e2;
+        two_sum_f(hi, ohi, s2, e2);
+        lo = lo + olo + e2;
+        two_sum_f(s2, lo, hi, lo);
+    }
+}
+
+// ---------------------------------------------------------------- passes --
+
+// Row pass over rows [r0, r1) of problem P: u_i, the column operand F'_i and
+// the CTA's partials (sum a u, and with WC the transport cost in K units).
+template <bool WC>
+__device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int m = P->m;
+    const int64_t ldm = P->ldm;
+    const int m4 = (m + 3) >> 2, mfull = m >> 2;
+    const double k2 = __ldcg(&P->k2), eps_c = __ldcg(&P->eps_c);
+    const double shift_g = __ldcg(&P->shift_g), shift_f = __ldcg(&P->shift_f);
+    const double inv_eps = 1.0 / eps_c;
+    const float4 *G4h = reinterpret_cast<const float4 *>(P->Gh);
+    const float4 *G4l = reinterpret_cast<const float4 *>(P->Gl);
+    double my_dual = 0.0, my_cost = 0.0;
+    for (int r = r0 + wid; r < r1; r += kBW) {
+        const float4 *K4h = reinterpret_cast<const float4 *>(P->Kh + (int64_t)r * ldm);
+        const float4 *K4l = reinterpret_cast<const float4 *>(P->Kl + (int64_t)r * ldm);
+        Lse2 acc = {-INFINITY, 0.0f, 0.0f}, cacc = {0.0f, 0.0f, 0.0f};
+        for (int v = lane; v < m4; v += 32) {
+            const float4 kh = __ldg(K4h + v), kl = __ldg(K4l + v);
+            const float4 gh = __ldcg(G4h + v), gl = __ldcg(G4l + v);
+            const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
+            const float ga[4] = {gh.x, gh.y, gh.z, gh.w}, gb[4] = {gl.x, gl.y, gl.z, gl.w};
+            float h[4], l[4], cst[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float hn = ga[e] - ka[e];        // Fast2Sum: |G'| >= |K|
+                const float z = hn - ga[e];
+                l[e] = (gb[e] - kb[e]) + (-ka[e] - z);
+                h[e] = hn;
+                if (WC) cst[e] = ka[e] + kb[e];
+            }
+            if (v >= mfull) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (4 * v + e >= m) { h[e] = -INFINITY; l[e] = 0.0f; if (WC) cst[e] = 0.0f; }
+            }
+            slot_accumulate<WC>(acc, cacc, h, l, cst);
+        }
+        float Rw, hi, lo;
+        warp_merge(acc, Rw, hi, lo);
+        float chi = 0.0f, clo = 0.0f;
+        if (WC) {
+            // the cost accumulator shares R with the row accumulator
+            const float sc = ex2_approx(acc.R - Rw);
+            two_sum_f(cacc.S * sc, -cacc.K * sc, chi, clo);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float ohi = __shfl_xor_sync(0xffffffffu, chi, o);
+                const float olo = __shfl_xor_sync(0xffffffffu, clo, o);
+                float s2, e2;
+                two_sum_f(chi, ohi, s2, e2);
+                clo = clo + olo + e2;
+                two_sum_f(s2, clo, chi, clo);
+            }
+        }
+        if (lane == 0) {
+            const double S = (double)hi + (double)lo;
+            const double lse = (double)Rw * kLn2 + log(S) - shift_g * inv_eps;
+            const double ui = __ldcg(&P->loga[r]) - lse;
+            P->u[r] = ui;
+            put_df(P->Fh, P->Fl, r, k2 * (eps_c * ui + shift_f));
+            const double ar = __ldcg(&P->a[r]);
+            my_dual += ar * ui;
+            if (WC) my_cost += ar * (((double)chi + (double)clo) / S);
+        }
+    }
+    double v[2] = {my_dual, my_cost};
+    cta_sum<2>(v);
+    part2[0] = v[0];
+    part2[1] = v[1];
+}
+
+// Column pass over columns [c0, c0 + 128) of problem P: ell_j. Each lane owns
+// four columns, warps split the rows in groups of four, and the warps'
+// accumulators are merged per column in a fixed order.
+__device__ void cta_cols(BatchProb *P, int c0)
+{
+    __shared__ float sR[kBW][kBatchColTile], sH[kBW][kBatchColTile], sL[kBW][kBatchColTile];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = P->n, m = P->m;
+    const int64_t ldm = P->ldm;
+    const int cb = c0 + 4 * lane;
+    const bool any = cb < m;
+    Lse2 acc[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[e] = {-INFINITY, 0.0f, 0.0f};
+    if (any) {
+        for (int rg = 4 * wid; rg < n; rg += 4 * kBW) {
+            float h[4][4], l[4][4];     // [column][row]
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int r = rg + q;
+                if (r < n) {
+                    const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->Kh + (int64_t)r * ldm + cb));
+                    const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->Kl + (int64_t)r * ldm + cb));
+                    const float fh = __ldcg(P->Fh + r), fl = __ldcg(P->Fl + r);
+                    const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float hn = fh - ka[e];
+                        const float z = hn - fh;
+                        l[e][q] = (fl - kb[e]) + (-ka[e] - z);
+                        h[e][q] = hn;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) { h[e][q] = -INFINITY; l[e][q] = 0.0f; }
+                }
+            }
+            float dummy[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                Lse2 none;
+                slot_accumulate<false>(acc[e], none, h[e], l[e], dummy);
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        float hi, lo;
+        two_sum_f(acc[e].S, -acc[e].K, hi, lo);
+        sR[wid][4 * lane + e] = acc[e].R;
+        sH[wid][4 * lane + e] = hi;
+        sL[wid][4 * lane + e] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBatchColTile) {
+        const int t = threadIdx.x, c = c0 + t;
+        if (c < m) {
+            float R = -INFINITY;
+            for (int q = 0; q < kBW; ++q) R = fmaxf(R, sR[q][t]);
+            double S = 0.0;
+            for (int q = 0; q < kBW; ++q) {
+                if (sR[q][t] == -INFINITY) continue;
+                const double f = (double)ex2_approx(sR[q][t] - R);
+                S += ((double)sH[q][t] + (double)sL[q][t]) * f;
+            }
+            const double shift_f = __ldcg(&P->shift_f), eps_c = __ldcg(&P->eps_c);
+            P->ell[c] = (double)R * kLn2 + log(S) - shift_f / eps_c;
+        }
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ init, step --
+
+// Validates and normalises the marginals, derives eps_c, k and the operand
+// shifts, and writes x_0 = w_0 = 0 with its operand G'. Returns false (and
+// records the status) for invalid inputs.
+__device__ bool cta_init(BatchProb *P)
+{
+    __shared__ int st_s;
+    const int n = P->n, m = P->m;
+    const double cmax = dec_d(P->cmax_enc), cmin = dec_d(P->cmin_enc), cabs = dec_d(P->cabs_enc);
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // sum a, sum b, #a<=0, #b<=0, #nonfinite
+    for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+        const double ai = P->a_in[i];
+        v[0] += ai;
+        if (!(ai > 0.0)) v[2] += 1.0;
+        if (!isfinite(ai)) v[4] += 1.0;
+    }
+    for (int j = threadIdx.x; j < m; j += kBatchThreads) {
+        const double bj = P->b_in[j];
+        v[1] += bj;
+        if (!(bj > 0.0)) v[3] += 1.0;
+        if (!isfinite(bj)) v[4] += 1.0;
+    }
+    cta_sum<5>(v);
+    if (threadIdx.x == 0) {
+        int status = 0;
+        if (P->nonfinite || v[4] > 0.0 || !isfinite(cmax) || !isfinite(cmin)) status = 3;
+        else if (v[2] > 0.0 || v[3] > 0.0) status = 2;
+        else if (P->scale && !(cmax > 0.0)) status = 1;
+        st_s = status;
+        if (status) { P->status = status; P->cmax = cmax; }
+    }
+    __syncthreads();
+    if (st_s != 0) return false;
+    const double sa = v[0], sb = v[1];
+    const double cost_div = batch_cost_div(P);
+    const double eps_c = P->eps * cost_div;
+    const double k2 = batch_k(P);
+    double mn[1] = {DBL_MAX}, mx[1] = {-DBL_MAX};
+    for (int i = threadIdx.x; i < n; i += kBatchThreads) {
+        const double ai = P->a_in[i] / sa;
+        const double la = log(ai);
+        P->a[i] = ai;
+        P->loga[i] = la;
+        mn[0] = fmin(mn[0], la);
+    }
+    cta_minmax<1>(mn, mx);
+    const double min_loga = mn[0];
+    const double log_m = log((double)m);
+    const double shift_g = cabs;
+    const double shift_f = cabs - (eps_c * min_loga + cmin - eps_c * log_m);
+    for (int j = threadIdx.x; j < m; j += kBatchThreads) {
+        const double bj = P->b_in[j] / sb;
+        P->b[j] = bj;
+        P->logb[j] = log(bj);
+        P->x[j] = 0.0;
+        P->x_prev[j] = 0.0;
+        P->w[j] = 0.0;
+        P->p_prev[j] = 0.0;
+        P->D_prev[j] = bj;
+        put_df(P->Gh, P->Gl, j, k2 * shift_g);
+    }
+    if (threadIdx.x == 0) {
+        P->k2 = k2;
+        P->eps_c = eps_c;
+        P->cost_div = cost_div;
+        P->cmax = cmax; P->cmin = cmin; P->cabs = cabs;
+        P->min_loga = min_loga;
+        P->log_m = log_m;
+        P->shift_g = shift_g;
+        P->shift_f = shift_f;
+        P->mu = P->mu0;
+        P->m_stage = P->m0;
+        P->j_in_stage = 0;
+        P->steps = 0; P->stages = 0; P->failures = 0;
+        P->first = 1; P->status = 0; P->done = 0;
+        P->err = INFINITY; P->dual = 0.0; P->kl_prev = 0.0; P->cost = NAN;
+    }
+    __syncthreads();
+    return true;
+}
+
+// One step after the row and column passes at x (see the single-problem step
+// kernel for the phases P1-P3). Returns true when the solve stops.
+__device__ bool cta_step(BatchProb *P)
+{
+    __shared__ int stop_s;
+    const int m = P->m;
+    const int method = P->method, stab = P->stability;
+    const int first = __ldcg(&P->first);
+    const double mu = __ldcg(&P->mu);
+    const bool is_acc = method == 1;
+    // Algorithm 1's alpha-dependent constants for this stage
+    double alpha = 1.0, inv_alpha = 1.0, inv_1pa = 0.5, a2 = -1.0, kappa1 = 0.0, c2f = 1.0;
+    double ratio_next = 1.0, inv_1pa_next = 0.5;
+    if (is_acc) {
+        alpha = sqrt(2.0 * mu);
+        const double an = sqrt(mu);             // alpha of the next stage (mu / 2)
+        inv_alpha = 1.0 / alpha;
+        inv_1pa = 1.0 / (1.0 + alpha);
+        a2 = alpha * alpha - 2.0;
+        kappa1 = (4.0 - alpha * alpha - 2.0 * sqrt(alpha)) /
+                 (2.0 * alpha * (1.0 + alpha) * (1.0 + alpha));
+        c2f = alpha * sqrt(alpha);
+        ratio_next = an / alpha;
+        inv_1pa_next = 1.0 / (1.0 + an);
+    }
+    const bool check = is_acc && !first && stab != 0;
+    const bool wupd = is_acc && !first;
+
+    // ---- P1
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // err, raw, kl, <b,x>, c1, c2l
+    double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int j = threadIdx.x; j < m; j += kBatchThreads) {
+        const double ell = __ldcg(&P->ell[j]);
+        const double xj = __ldcg(&P->x[j]);
+        const double bj = __ldcg(&P->b[j]);
+        const double wj = __ldcg(&P->w[j]);
+        const double del = xj + ell - __ldcg(&P->logb[j]);
+        const double raw = xj - del;
+        double xi, D1, klt;
+        const float dl = (float)del;
+        if (fabsf(dl) <= 80.0f) {
+            const float e = expm1f(dl);
+            float km;
+            if (fabsf(dl) < 0.0625f) {
+                km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
+                                                     1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+            } else {
+                km = e - dl;
+            }
+            const float dr = (dl != 0.0f) ? e / dl : 1.0f;
+            xi = bj * (double)e;
+            D1 = bj * (double)dr;
+            klt = bj * (double)km;
+        } else {
+            const double e = expm1(del);
+            xi = bj * e;
+            D1 = xi / del;
+            klt = bj * (e - del);
+        }
+        v[0] += fabs(xi);
+        v[1] += raw;
+        v[2] += klt;
+        v[3] += bj * xj;
+        if (check) {
+            const double p0 = __ldcg(&P->p_prev[j]);
+            const double v0 = wj * inv_alpha - __ldcg(&P->x_prev[j]);
+            v[4] += p0 * p0 * D1;
+            v[5] += v0 * v0 * (D1 - __ldcg(&P->D_prev[j]));
+        }
+        lo3[0] = fmin(lo3[0], raw); hi3[0] = fmax(hi3[0], raw);
+        lo3[1] = fmin(lo3[1], xj);  hi3[1] = fmax(hi3[1], xj);
+        lo3[2] = fmin(lo3[2], wj);  hi3[2] = fmax(hi3[2], wj);
+        P->raw[j] = raw;
+        P->D1[j] = D1;
+        P->del[j] = del;
+    }
+    cta_sum<6>(v);
+    cta_minmax<3>(lo3, hi3);
+    const double err = v[0];
+    const double rbar = v[1] / (double)m;
+    double au[1] = {0.0};
+    {
+        const int rt = P->row_tiles;
+        for (int t = threadIdx.x; t < rt; t += kBatchThreads) au[0] += __ldcg(&P->rowpart[2 * t]);
+        cta_sum<1>(au);
+    }
+    const double dual = P->eps * (au[0] + v[3] - 1.0);
+
+    // ---- P2
+    double v2[1] = {0.0};
+    double wl[1] = {DBL_MAX}, wh[1] = {-DBL_MAX};
+    if (wupd) {
+        for (int j = threadIdx.x; j < m; j += kBatchThreads) {
+            const double s = P->raw[j] - rbar;
+            const double xj = __ldcg(&P->x[j]);
+            const double w1 = (__ldcg(&P->w[j]) + a2 * xj + 2.0 * s) * inv_1pa;
+            P->w1[j] = w1;
+            const double v1 = w1 * inv_alpha - xj;
+            v2[0] += v1 * v1 * P->D1[j];
+            wl[0] = fmin(wl[0], w1);
+            wh[0] = fmax(wh[0], w1);
+        }
+    }
+    cta_sum<1>(v2);
+    cta_minmax<1>(wl, wh);
+
+    // ---- P3
+    const double c1 = v[4], c2l = v[5];
+    const double c1r = kappa1 * __ldcg(&P->kl_prev);
+    const double c2r = c2f * v2[0];
+    int stab_bits = 0;
+    if (check) stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
+    const bool gate = (stab == 2) && (stab_bits != 0);
+    const int steps_new = __ldcg(&P->steps) + 1;
+    const bool nonfinite = !isfinite(err);
+    const bool converged = err < P->tol;
+    const bool stop = converged || nonfinite || steps_new >= P->max_steps;
+    double mu_new = mu;
+    int ms = __ldcg(&P->m_stage), jst = __ldcg(&P->j_in_stage), stages = __ldcg(&P->stages);
+    bool stage_end = false;
+    if (wupd) {
+        jst += 1;
+        if (jst == ms) {
+            stage_end = true;
+            mu_new = mu / 2.0;
+            ms = (int)floor(sqrt(2.0) * (double)ms) + 1;
+            jst = 0;
+            stages += 1;
+        }
+    }
+    const double inv_1pa_new = stage_end ? inv_1pa_next : inv_1pa;
+    const double ratio = (stage_end && P->carry == 0) ? ratio_next : 1.0;
+    const double slo = lo3[0] - rbar, shi = hi3[0] - rbar;
+    double xlo, xhi;
+    if (is_acc) {
+        double w1lo, w1hi;
+        if (!wupd) { w1lo = lo3[2]; w1hi = hi3[2]; }
+        else if (gate) { w1lo = alpha * lo3[1]; w1hi = alpha * hi3[1]; }
+        else { w1lo = wl[0]; w1hi = wh[0]; }
+        xlo = (w1lo * ratio + slo) * inv_1pa_new;
+        xhi = (w1hi * ratio + shi) * inv_1pa_new;
+    } else {
+        xlo = slo;
+        xhi = shi;
+    }
+    xlo -= 1e-12 * (1.0 + fabs(xlo));
+    xhi += 1e-12 * (1.0 + fabs(xhi));
+    const double eps_c = P->eps_c, k2 = P->k2;
+    const double shift_g = P->cabs - eps_c * xlo;
+    const double shift_fn = P->cabs - (eps_c * P->min_loga - eps_c * xhi + P->cmin - eps_c * P->log_m);
+    if (!stop) {
+        for (int j = threadIdx.x; j < m; j += kBatchThreads) {
+            const double s = P->raw[j] - rbar;
+            const double xj = __ldcg(&P->x[j]);
+            double xn;
+            if (is_acc) {
+                double w1 = wupd ? (gate ? alpha * xj : P->w1[j]) : __ldcg(&P->w[j]);
+                w1 *= ratio;
+                xn = (w1 + s) * inv_1pa_new;
+                P->w[j] = w1;
+            } else {
+                xn = s;
+            }
+            P->x_prev[j] = xj;
+            P->x[j] = xn;
+            P->p_prev[j] = P->del[j];
+            P->D_prev[j] = P->D1[j];
+            put_df(P->Gh, P->Gl, j, k2 * (eps_c * xn + shift_g));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P->steps = steps_new;
+        P->err = err;
+        P->dual = dual;
+        P->kl_prev = v[2];
+        P->first = 0;
+        if (stab_bits) P->failures += 1;
+        if (wupd) {
+            P->mu = mu_new;
+            P->m_stage = ms;
+            P->j_in_stage = jst;
+            P->stages = stages;
+        }
+        if (stop) {
+            P->status = nonfinite ? 3 : (converged ? 0 : 7);
+        } else {
+            P->shift_g = shift_g;
+            P->shift_f = shift_fn;
+        }
+        stop_s = stop ? 1 : 0;
+    }
+    __syncthreads();
+    return stop_s != 0;
+}
+
+// Outputs of a finished problem: f = eps u, g = eps x, the result record.
+__device__ void cta_finish(BatchProb *P, BatchResult *R, bool ok)
+{
+    const int n = P->n, m = P->m;
+    const double eps = P->eps;
+    if (ok) {
+        for (int i = threadIdx.x; i < n; i += kBatchThreads) P->f_out[i] = eps * __ldcg(&P->u[i]);
+        for (int j = threadIdx.x; j < m; j += kBatchThreads) P->g_out[j] = eps * __ldcg(&P->x[j]);
+    }
+    double c[1] = {0.0};
+    if (ok && P->evaluate) {
+        for (int t = threadIdx.x; t < P->row_tiles; t += kBatchThreads)
+            c[0] += __ldcg(&P->rowpart[2 * t + 1]);
+    }
+    cta_sum<1>(c);
+    if (threadIdx.x == 0) {
+        R->status = P->status;
+        R->steps = ok ? P->steps : 0;
+        R->stages = ok ? P->stages : 0;
+        R->failures = ok ? P->failures : 0;
+        R->marginal_l1 = ok ? P->err : NAN;
+        R->transport_cost = (ok && P->evaluate) ? c[0] / (P->k2 * P->cost_div) : NAN;
+        R->dual = ok ? P->dual : NAN;
+        R->cost_max = P->cmax;
+        P->done = 1;
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------- queue --
+
+// Pops one item (thread 0). Returns false when the batch is finished or a
+// wait ran out.
+__device__ bool q_pop(BatchQueue *q, unsigned long long &item)
+{
+    const unsigned long long pos = atomicAdd(&q->head, 1ull);
+    const unsigned long long slot = pos & (q->cap - 1);
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        const unsigned long long s = ld_acquire_u64(&q->seq[slot]);
+        if (s == pos + 1) break;
+        if (ld_volatile_i32(&q->all_done)) return false;
+        if (globaltimer_ns() - t0 > kQueueWaitNs) {
+            atomicExch(&q->error, 6 /* ACCSINK_ERR_TIMEOUT */);
+            atomicExch(&q->all_done, 1);
+            return false;
+        }
+        __nanosleep(200);
+    }
+    item = *(volatile unsigned long long *)&q->items[slot];
+    st_release_u64(&q->seq[slot], pos + q->cap);
+    return true;
+}
+
+// Pushes k items (all threads of the CTA call it; item(t) gives item t).
+template <class F>
+__device__ void q_push(BatchQueue *q, int k, F item)
+{
+    __shared__ unsigned long long base_s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) base_s = atomicAdd(&q->tail, (unsigned long long)k);
+    __syncthreads();
+    const unsigned long long base = base_s;
+    for (int t = threadIdx.x; t < k; t += kBatchThreads) {
+        const unsigned long long pos = base + t;
+        const unsigned long long slot = pos & (q->cap - 1);
+        const uint64_t t0 = globaltimer_ns();
+        bool ok = true;
+        while (ld_acquire_u64(&q->seq[slot]) != pos) {
+            if (globaltimer_ns() - t0 > kQueueWaitNs || ld_volatile_i32(&q->all_done)) {
+                atomicExch(&q->error, 6);
+                atomicExch(&q->all_done, 1);
+                ok = false;
+                break;
+            }
+            __nanosleep(200);
+        }
+        if (!ok) continue;
+        *(volatile unsigned long long *)&q->items[slot] = item(t);
+        st_release_u64(&q->seq[slot], pos + 1);
+    }
+    __syncthreads();
+}
+
+// Arrival at the end of a phase tile; true for the last of `ntiles`.
+__device__ bool arrive_last(BatchProb *P, int ntiles)
+{
+    __shared__ int last_s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int old = atomicAdd(&P->arrive, 1);
+        const bool last = old == ntiles - 1;
+        if (last) {
+            P->arrive = 0;
+            __threadfence();
+        }
+        last_s = last ? 1 : 0;
+    }
+    __syncthreads();
+    return last_s != 0;
+}
+
+__device__ void problem_done(BatchQueue *q)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int d = atomicAdd(&q->done_count, 1) + 1;
+        if (d == q->count) atomicExch(&q->all_done, 1);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// ------------------------------------------------------- cost formation --
+
+// One 64 x 64 tile of C_ij for one problem, unscaled, as (hi, lo): squared
+// Euclidean sum_k (x_k - y_k)^2 and cosine 1 - <x, y> accumulated exactly
+// (TwoSum on each exact product or square) and rounded once; dense costs are
+// copied. Per-problem min / max / max|C| and non-finite entries are folded
+// in with atomics. Problems without scaling get k C directly.
+__global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const BatchTile *tiles)
+{
+    constexpr int T = kBatchFormTile, KC = 32;
+    __shared__ float Xs[T][KC + 1], Ys[T][KC + 1];
+    const BatchTile tl = tiles[blockIdx.x];
+    BatchProb *P = Pall + tl.prob;
+    const int n = P->n, m = P->m, d = P->d, kind = P->kind;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    const int rb = tl.row0 + 4 * ty, cb = tl.col0 + 4 * tx;
+    double vals[4][4];
+    if (kind == 0) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int r = rb + a, c = cb + b;
+                vals[a][b] = (r < n && c < m) ? (double)P->C[(int64_t)r * P->ldc + c] : 0.0;
+            }
+    } else {
+        float s[4][4], e[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) { s[a][b] = 0.0f; e[a][b] = 0.0f; }
+        for (int k0 = 0; k0 < d; k0 += KC) {
+            for (int t = threadIdx.x; t < T * KC; t += 256) {
+                const int rr = t / KC, kk = t % KC;
+                const int gx = tl.row0 + rr, gy = tl.col0 + rr, k = k0 + kk;
+                Xs[rr][kk] = (gx < n && k < d) ? P->X[(int64_t)gx * d + k] : 0.0f;
+                Ys[rr][kk] = (gy < m && k < d) ? P->Y[(int64_t)gy * d + k] : 0.0f;
+            }
+            __syncthreads();
+            const int kn = min(KC, d - k0);
+            for (int kk = 0; kk < kn; ++kk) {
+                float xa[4], yb[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a) xa[a] = Xs[4 * ty + a][kk];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) yb[b] = Ys[4 * tx + b][kk];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        float p, pe;
+                        if (kind == 1) {
+                            float dh, de;
+                            two_sum_f(xa[a], -yb[b], dh, de);       // exact difference
+                            p = dh * dh;
+                            pe = fmaf(dh, dh, -p) + 2.0f * dh * de;  // + de^2 (negligible)
+                        } else {
+                            p = xa[a] * yb[b];
+                            pe = fmaf(xa[a], yb[b], -p);             // exact product error
+                        }
+                        float t, te;
+                        two_sum_f(s[a][b], p, t, te);
+                        s[a][b] = t;
+                        e[a][b] += te + pe;
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const double sum = (double)s[a][b] + (double)e[a][b];
+                vals[a][b] = (kind == 1) ? sum : 1.0 - sum;
+            }
+    }
+    // statistics and store
+    const bool direct = !P->scale;
+    const double k = direct ? kLog2e / P->eps : 1.0;
+    double mx = -DBL_MAX, mn = DBL_MAX, ab = 0.0;
+    int bad = 0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = rb + a;
+        if (r >= n) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int c = cb + b;
+            if (c < m) {
+                const double v = vals[a][b];
+                if (!isfinite(v)) bad = 1;
+                mx = fmax(mx, v);
+                mn = fmin(mn, v);
+                ab = fmax(ab, fabs(v));
+                put_df(P->Kh, P->Kl, (int64_t)r * P->ldm + c, k * v);
+            } else if (c < P->ldm) {
+                P->Kh[(int64_t)r * P->ldm + c] = 0.0f;
+                P->Kl[(int64_t)r * P->ldm + c] = 0.0f;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        ab = fmax(ab, __shfl_xor_sync(0xffffffffu, ab, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (mx != -DBL_MAX) atomicMax(&P->cmax_enc, enc_d(mx));
+        if (mn != DBL_MAX) atomicMin(&P->cmin_enc, enc_d(mn));
+        atomicMax(&P->cabs_enc, enc_d(ab));
+        if (bad) atomicOr(&P->nonfinite, 1u);
+    }
+}
+
+// k C in place for problems scaled by their maximum (k needs max C).
+__global__ void __launch_bounds__(256) k_batch_scale(BatchProb *Pall, const BatchTile *tiles)
+{
+    const BatchTile tl = tiles[blockIdx.x];
+    BatchProb *P = Pall + tl.prob;
+    if (!P->scale) return;
+    const double k = batch_k(P);
+    const int n = P->n, m = P->m;
+    for (int t = threadIdx.x; t < kBatchFormTile * kBatchFormTile; t += 256) {
+        const int r = tl.row0 + t / kBatchFormTile, c = tl.col0 + t % kBatchFormTile;
+        if (r < n && c < m) {
+            const int64_t i = (int64_t)r * P->ldm + c;
+            const double v = (double)P->Kh[i] + (double)P->Kl[i];
+            put_df(P->Kh, P->Kl, i, k * v);
+        }
+    }
+}
+
+// ---------------------------------------------------------- the solver --
+
+__global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, BatchQueue *q,
+                                                               BatchResult *res)
+{
+    __shared__ unsigned long long item_s;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            unsigned long long it;
+            item_s = q_pop(q, it) ? it : ~0ull;
+        }
+        __syncthreads();
+        const unsigned long long item = item_s;
+        __syncthreads();
+        if (item == ~0ull) break;
+        const int p = (int)(item >> 32);
+        const int kind = (int)((item >> 28) & 0xf);
+        const int tile = (int)(item & 0x0fffffffu);
+        BatchProb *P = Pall + p;
+        BatchResult *R = res + p;
+        if (kind == BI_SMALL) {
+            // the whole solve in this CTA
+            // (each phase reads what the previous one wrote through L2, so a
+            // device-scope fence separates them)
+            bool ok = cta_init(P);
+            if (ok) {
+                for (;;) {
+                    __threadfence();
+                    __syncthreads();
+                    double part[2];
+                    cta_rows<false>(P, 0, P->n, part);
+                    if (threadIdx.x == 0) { P->rowpart[0] = part[0]; P->rowpart[1] = part[1]; }
+                    __threadfence();
+                    __syncthreads();
+                    for (int c0 = 0; c0 < P->m; c0 += kBatchColTile) cta_cols(P, c0);
+                    __threadfence();
+                    __syncthreads();
+                    if (cta_step(P)) break;
+                }
+                __threadfence();
+                __syncthreads();
+                if (P->evaluate) {
+                    double part[2];
+                    cta_rows<true>(P, 0, P->n, part);
+                    if (threadIdx.x == 0) { P->rowpart[0] = part[0]; P->rowpart[1] = part[1]; }
+                    __syncthreads();
+                }
+            }
+            cta_finish(P, R, ok);
+            problem_done(q);
+        } else if (kind == BI_INIT) {
+            const bool ok = cta_init(P);
+            if (ok) {
+                q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
+            } else {
+                cta_finish(P, R, false);
+                problem_done(q);
+            }
+        } else if (kind == BI_ROW || kind == BI_FINAL) {
+            const int r0 = tile * P->rows_per_tile;
+            const int r1 = min(P->n, r0 + P->rows_per_tile);
+            double part[2];
+            if (kind == BI_ROW) cta_rows<false>(P, r0, r1, part);
+            else cta_rows<true>(P, r0, r1, part);
+            if (threadIdx.x == 0) {
+                P->rowpart[2 * tile] = part[0];
+                P->rowpart[2 * tile + 1] = part[1];
+            }
+            if (arrive_last(P, P->row_tiles)) {
+                if (kind == BI_ROW) {
+                    q_push(q, P->col_tiles, [&](int t) { return batch_item(BI_COL, p, t); });
+                } else {
+                    cta_finish(P, R, true);
+                    problem_done(q);
+                }
+            }
+        } else if (kind == BI_COL) {
+            cta_cols(P, tile * kBatchColTile);
+            if (arrive_last(P, P->col_tiles)) {
+                const bool stop = cta_step(P);
+                if (!stop) {
+                    q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
+                } else if (P->evaluate) {
+                    q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_FINAL, p, t); });
+                } else {
+                    cta_finish(P, R, true);
+                    problem_done(q);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int ntiles, int dmax,
+                              cudaStream_t s)
+{
+    (void)dmax;
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_form<<<ntiles, 256, 0, s>>>(const_cast<BatchProb *>(P), tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_scale(BatchProb *P, const BatchTile *tiles, int ntiles, cudaStream_t s)
+{
+    if (ntiles <= 0) return cudaSuccess;
+    k_batch_scale<<<ntiles, 256, 0, s>>>(P, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_solve(BatchProb *P, BatchQueue *q, BatchResult *res, int grid,
+                               cudaStream_t s)
+{
+    k_batch_solve<<<grid, kBatchThreads, 0, s>>>(P, q, res);
+    return cudaGetLastError();
+}
+
+int occupancy_batch_solve()
+{
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_batch_solve, kBatchThreads, 0);
+    return b > 0 ? b : 1;
+}
+
+}  // namespace accsink
+
+namespace accsink {
+
+// Sets every queue slot free for its first position, then publishes the
+// initial items (one per problem) at positions 0 .. count - 1.
+__global__ void k_queue_init(BatchQueue *q, const unsigned long long *items0, int count)
+{
+    const unsigned long long cap = q->cap;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < cap;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        if (i < (unsigned long long)count) {
+            q->items[i] = items0[i];
+            q->seq[i] = i + 1;
+        } else {
+            q->seq[i] = i;
+        }
+    }
+}
+
+cudaError_t launch_queue_init(BatchQueue *q, const unsigned long long *items0, int count,
+                              unsigned long long cap, cudaStream_t s)
+{
+    const int grid = (int)std::min<unsigned long long>(1024, (cap + 255) / 256);
+    k_queue_init<<<grid, 256, 0, s>>>(q, items0, count);
+    return cudaGetLastError();
+}
+
+}  // namespace accsink

@@ -1,0 +1,264 @@
+// Host side of the batched solver: plans a batch (work split, workspace
+// layout, initial queue), launches the formation and the persistent solve,
+// and collects the results. Called by accsink_solve_batch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "accsink.h"
+#include "accsink_internal.cuh"
+#include "batch_internal.cuh"
+#include "batch_host.h"
+
+namespace accsink {
+
+namespace {
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Sizes of one problem's arrays, in the order they are carved.
+struct ProbLayout {
+    size_t kh, kl, a, loga, u, fh, fl, mvec, gh, gl, rowpart;
+    size_t total() const { return kh + kl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart; }
+};
+
+ProbLayout layout(int64_t n, int64_t m, int row_tiles)
+{
+    const int64_t ldm = (m + 3) / 4 * 4, n4 = (n + 3) / 4 * 4;
+    ProbLayout L;
+    L.kh = L.kl = up256((size_t)n * ldm * 4);
+    L.a = L.loga = L.u = up256((size_t)n * 8);
+    L.fh = L.fl = up256((size_t)n4 * 4);
+    L.mvec = up256((size_t)m * 8);
+    L.gh = L.gl = up256((size_t)ldm * 4);
+    L.rowpart = up256((size_t)row_tiles * 16);
+    return L;
+}
+
+unsigned long long pow2_at_least(unsigned long long v)
+{
+    unsigned long long c = 1;
+    while (c < v) c <<= 1;
+    return c;
+}
+
+}  // namespace
+
+BatchTuning batch_default_tuning(int num_sms)
+{
+    BatchTuning t;
+    t.small_max_nm = 1 << 16;
+    t.row_tile_elems = 1 << 16;
+    t.ctas_per_sm = 0;          // occupancy
+    (void)num_sms;
+    return t;
+}
+
+int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, int count,
+              const accsink_problem *probs, const accsink_params *params, double *const *f_out,
+              double *const *g_out, accsink_result *res, cudaStream_t s, std::string &err,
+              BatchTiming *timing)
+{
+    // ---- plan
+    std::vector<BatchProb> hp(count);
+    std::vector<ProbLayout> lay(count);
+    std::vector<BatchTile> tiles;
+    size_t data_bytes = 0;
+    size_t outstanding = 0;
+    for (int k = 0; k < count; ++k) {
+        const accsink_problem &q = probs[k];
+        const accsink_params &pp = params[k];
+        BatchProb &P = hp[k];
+        std::memset(&P, 0, sizeof(P));
+        P.C = q.C; P.X = q.X; P.Y = q.Y;
+        P.a_in = q.a; P.b_in = q.b;
+        P.f_out = f_out[k]; P.g_out = g_out[k];
+        P.ldc = q.ldc ? q.ldc : q.m;
+        P.n = q.n; P.m = q.m; P.d = q.d; P.kind = q.cost_kind;
+        P.scale = q.cost_scale == ACCSINK_SCALE_MAX_TO_ONE ? 1 : 0;
+        P.method = pp.method; P.stability = pp.stability; P.carry = pp.carry;
+        P.max_steps = pp.max_sinkhorn_steps; P.m0 = pp.m0; P.evaluate = pp.evaluate ? 1 : 0;
+        P.eps = pp.eps; P.tol = pp.tol; P.mu0 = pp.mu0;
+        P.ldm = ((int64_t)q.m + 3) / 4 * 4;
+        const int64_t nm = (int64_t)q.n * q.m;
+        P.small = nm <= tn.small_max_nm ? 1 : 0;
+        if (P.small) {
+            P.rows_per_tile = q.n;
+            P.row_tiles = 1;
+        } else {
+            int rpt = (int)std::max<int64_t>(1, tn.row_tile_elems / std::max(1, q.m));
+            rpt = std::min(rpt, q.n);
+            P.rows_per_tile = rpt;
+            P.row_tiles = (q.n + rpt - 1) / rpt;
+        }
+        P.col_tiles = (q.m + kBatchColTile - 1) / kBatchColTile;
+        P.cmax_enc = 0ull;             // below every encoded value
+        P.cmin_enc = ~0ull;            // above every encoded value
+        P.cabs_enc = 0ull;
+        lay[k] = layout(q.n, q.m, P.row_tiles);
+        data_bytes += lay[k].total();
+        outstanding += (size_t)std::max(P.row_tiles, P.col_tiles);
+        for (int r = 0; r < q.n; r += kBatchFormTile)
+            for (int c = 0; c < q.m; c += kBatchFormTile) tiles.push_back({k, r, c, 0});
+    }
+    const unsigned long long cap = pow2_at_least(std::max<unsigned long long>(
+        4096, 2 * (unsigned long long)(outstanding + count)));
+    const size_t head_bytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchResult) * count) +
+                              up256(sizeof(BatchQueue)) + up256(cap * 8) + up256(cap * 8) +
+                              up256(sizeof(BatchTile) * tiles.size()) + up256(8 * (size_t)count);
+    const size_t need = head_bytes + data_bytes;
+    if (need > ws.bytes) {
+        if (env.budget_left && need > env.budget_left) {
+            err = "batch workspace of " + std::to_string(need) + " bytes exceeds the budget";
+            return ACCSINK_ERR_BUDGET;
+        }
+        if (ws.dev) cudaFree(ws.dev);
+        ws.dev = nullptr;
+        ws.bytes = 0;
+        if (cudaMalloc(&ws.dev, need) != cudaSuccess) {
+            cudaGetLastError();
+            err = "cudaMalloc of the batch workspace failed";
+            return ACCSINK_ERR_OOM;
+        }
+        ws.bytes = need;
+    }
+    // ---- carve
+    char *p = (char *)ws.dev;
+    BatchProb *dP = (BatchProb *)p;        p += up256(sizeof(BatchProb) * count);
+    BatchResult *dR = (BatchResult *)p;    p += up256(sizeof(BatchResult) * count);
+    BatchQueue *dQ = (BatchQueue *)p;      p += up256(sizeof(BatchQueue));
+    unsigned long long *dItems = (unsigned long long *)p;  p += up256(cap * 8);
+    unsigned long long *dSeq = (unsigned long long *)p;    p += up256(cap * 8);
+    BatchTile *dT = (BatchTile *)p;        p += up256(sizeof(BatchTile) * tiles.size());
+    unsigned long long *dInit = (unsigned long long *)p;   p += up256(8 * (size_t)count);
+    for (int k = 0; k < count; ++k) {
+        BatchProb &P = hp[k];
+        const ProbLayout &L = lay[k];
+        auto take = [&](size_t b) { char *r = p; p += b; return r; };
+        P.Kh = (float *)take(L.kh); P.Kl = (float *)take(L.kl);
+        P.a = (double *)take(L.a); P.loga = (double *)take(L.loga); P.u = (double *)take(L.u);
+        P.Fh = (float *)take(L.fh); P.Fl = (float *)take(L.fl);
+        double **mv[12] = {&P.b, &P.logb, &P.x, &P.x_prev, &P.w, &P.w1, &P.p_prev, &P.D_prev,
+                           &P.raw, &P.D1, &P.del, &P.ell};
+        for (double **v : mv) *v = (double *)take(L.mvec);
+        P.Gh = (float *)take(L.gh); P.Gl = (float *)take(L.gl);
+        P.rowpart = (double *)take(L.rowpart);
+    }
+    // initial items, largest problems first
+    std::vector<int> order(count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (int64_t)hp[x].n * hp[x].m > (int64_t)hp[y].n * hp[y].m;
+    });
+    std::vector<unsigned long long> init(count);
+    for (int i = 0; i < count; ++i) {
+        const int k = order[i];
+        init[i] = batch_item(hp[k].small ? BI_SMALL : BI_INIT, k, 0);
+    }
+    BatchQueue hq;
+    std::memset(&hq, 0, sizeof(hq));
+    hq.head = 0;
+    hq.tail = (unsigned long long)count;
+    hq.items = dItems;
+    hq.seq = dSeq;
+    hq.cap = cap;
+    hq.count = count;
+    // ---- stage the host records (pinned) and launch
+    const size_t hbytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchTile) * tiles.size()) +
+                          up256(8 * (size_t)count) + up256(sizeof(BatchQueue)) +
+                          up256(sizeof(BatchResult) * count);
+    if (hbytes > ws.host_bytes) {
+        if (ws.host) cudaFreeHost(ws.host);
+        ws.host = nullptr;
+        ws.host_bytes = 0;
+        if (cudaMallocHost(&ws.host, hbytes) != cudaSuccess) {
+            cudaGetLastError();
+            err = "cudaMallocHost of the batch staging failed";
+            return ACCSINK_ERR_OOM;
+        }
+        ws.host_bytes = hbytes;
+    }
+    char *h = (char *)ws.host;
+    BatchProb *hP = (BatchProb *)h;        h += up256(sizeof(BatchProb) * count);
+    BatchTile *hT = (BatchTile *)h;        h += up256(sizeof(BatchTile) * tiles.size());
+    unsigned long long *hI = (unsigned long long *)h;  h += up256(8 * (size_t)count);
+    BatchQueue *hQ = (BatchQueue *)h;      h += up256(sizeof(BatchQueue));
+    BatchResult *hR = (BatchResult *)h;
+    std::memcpy(hP, hp.data(), sizeof(BatchProb) * count);
+    if (!tiles.empty()) std::memcpy(hT, tiles.data(), sizeof(BatchTile) * tiles.size());
+    std::memcpy(hI, init.data(), 8 * (size_t)count);
+    std::memcpy(hQ, &hq, sizeof(hq));
+
+#define BK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            err = std::string(#call) + ": " + cudaGetErrorString(e_);   \
+            return ACCSINK_ERR_CUDA;                                    \
+        }                                                               \
+    } while (0)
+
+    BK(cudaEventRecord(env.ev0, s));
+    BK(cudaMemcpyAsync(dP, hP, sizeof(BatchProb) * count, cudaMemcpyHostToDevice, s));
+    if (!tiles.empty())
+        BK(cudaMemcpyAsync(dT, hT, sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(dInit, hI, 8 * (size_t)count, cudaMemcpyHostToDevice, s));
+    BK(cudaMemcpyAsync(dQ, hQ, sizeof(BatchQueue), cudaMemcpyHostToDevice, s));
+    BK(launch_batch_form(dP, dT, (int)tiles.size(), 0, s));
+    BK(launch_batch_scale(dP, dT, (int)tiles.size(), s));
+    BK(launch_queue_init(dQ, dInit, count, cap, s));
+    BK(cudaEventRecord(env.ev_mid, s));
+    const int per_sm = tn.ctas_per_sm > 0 ? std::min(tn.ctas_per_sm, env.occ_solve) : env.occ_solve;
+    const int grid = std::max(1, env.num_sms * per_sm);
+    BK(launch_batch_solve(dP, dQ, dR, grid, s));
+    BK(cudaEventRecord(env.ev1, s));
+    BK(cudaMemcpyAsync(hR, dR, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, s));
+    BK(cudaMemcpyAsync(hQ, dQ, sizeof(BatchQueue), cudaMemcpyDeviceToHost, s));
+    BK(cudaStreamSynchronize(s));
+    float ms_all = 0.0f, ms_form = 0.0f;
+    cudaEventElapsedTime(&ms_all, env.ev0, env.ev1);
+    cudaEventElapsedTime(&ms_form, env.ev0, env.ev_mid);
+    if (timing) {
+        timing->total_ms = ms_all;
+        timing->form_ms = ms_form;
+        timing->solve_ms = ms_all - ms_form;
+        timing->grid = grid;
+    }
+#undef BK
+    if (hQ->error) {
+        err = "a batch queue wait ran out of time";
+        for (int k = 0; k < count; ++k) {
+            std::memset(&res[k], 0, sizeof(res[k]));
+            res[k].status = ACCSINK_ERR_TIMEOUT;
+        }
+        return ACCSINK_ERR_TIMEOUT;
+    }
+    int rc = ACCSINK_OK;
+    for (int k = 0; k < count; ++k) {
+        const BatchResult &r = hR[k];
+        accsink_result &o = res[k];
+        std::memset(&o, 0, sizeof(o));
+        o.status = r.status;
+        o.sinkhorn_steps = r.steps;
+        o.outer_stages = r.stages;
+        o.stability_failures = r.failures;
+        o.marginal_l1 = r.marginal_l1;
+        o.transport_cost = r.transport_cost;
+        o.dual_objective = r.dual;
+        o.cost_max = r.cost_max;
+        o.gpu_ms = ms_all;
+        o.loop_mode = 2;
+        if (r.status != ACCSINK_OK) {
+            if (rc == ACCSINK_OK || (rc == ACCSINK_ERR_MAXITER && r.status != ACCSINK_ERR_MAXITER))
+                rc = r.status;
+        }
+    }
+    if (rc == ACCSINK_ERR_MAXITER) err = "some problems did not converge within max_sinkhorn_steps";
+    else if (rc != ACCSINK_OK) err = "some problems stopped with an error status (see res[k].status)";
+    return rc;
+}
+
+}  // namespace accsink

@@ -1,0 +1,50 @@
+// Host-side interface of the batched solver (used by the C-ABI layer).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "accsink.h"
+
+namespace accsink {
+
+// Device workspace of a context's batches (grow-only) and its pinned staging.
+struct BatchWorkspace {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    void *host = nullptr;
+    size_t host_bytes = 0;
+};
+
+// Work split of a batch. small_max_nm: problems with n m at most this are
+// solved whole by one CTA; row_tile_elems: cost entries per row-pass item of
+// the larger ones; ctas_per_sm: persistent CTAs per SM (0: occupancy).
+struct BatchTuning {
+    int small_max_nm = 1 << 16;
+    int row_tile_elems = 1 << 16;
+    int ctas_per_sm = 0;
+};
+
+struct BatchEnv {
+    int num_sms = 1;
+    int occ_solve = 1;
+    size_t budget_left = 0;      // 0: no cap
+    cudaEvent_t ev0 = nullptr, ev_mid = nullptr, ev1 = nullptr;
+};
+
+struct BatchTiming {
+    float total_ms = 0, form_ms = 0, solve_ms = 0;
+    int grid = 0;
+};
+
+BatchTuning batch_default_tuning(int num_sms);
+
+// Plans, launches and waits for one batch on stream s. Returns an ACCSINK_*
+// code; res[k] receives each problem's record; err the message on failure.
+int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, int count,
+              const accsink_problem *probs, const accsink_params *params, double *const *f_out,
+              double *const *g_out, accsink_result *res, cudaStream_t s, std::string &err,
+              BatchTiming *timing);
+
+}  // namespace accsink

@@ -1,0 +1,102 @@
+// Internal declarations of the batched solver (many independent problems in
+// one persistent launch).
+//
+// Each problem's cost is formed once into the workspace as a double-float
+// pair (Kh + Kl = k C, k = log2(e) / eps_c, so that the passes work in log2
+// units), then a persistent kernel solves every problem. Its CTAs pull work
+// items from a device queue: a whole solve for a small problem, or one
+// phase tile (rows of the row pass, columns of the column pass, rows of the
+// final pass) of a large one. The last CTA to finish a phase of a problem
+// (per-problem arrival counter) runs the step of Algorithm 1 for it and
+// queues the next phase, so no CTA ever waits for another to make progress;
+// a CTA only waits, bounded, for the next item to be published.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+namespace accsink {
+
+// One problem of a batch (device-resident). Inputs are the caller's device
+// pointers; the rest points into the batch workspace.
+struct BatchProb {
+    // ---- inputs
+    const float *C, *X, *Y;
+    const double *a_in, *b_in;
+    double *f_out, *g_out;
+    int64_t ldc;
+    int32_t n, m, d, kind, scale;
+    int32_t method, stability, carry, max_steps, m0, evaluate;
+    int32_t pad_in;
+    double eps, tol, mu0;
+    // ---- workspace
+    float *Kh, *Kl;          // n x ldm, k C as (hi, lo); C before scaling
+    int64_t ldm;             // m rounded up to 4
+    double *a, *loga, *u;    // n
+    float *Fh, *Fl;          // n (padded): k (eps_c u + shift_f) as (hi, lo)
+    double *b, *logb, *x, *x_prev, *w, *w1, *p_prev, *D_prev, *raw, *D1, *del, *ell;  // m
+    float *Gh, *Gl;          // m (padded): k (eps_c x + shift_g) as (hi, lo)
+    double *rowpart;         // row tiles x 2 (sum a u, sum cost)
+    // ---- schedule
+    int32_t small;           // 1: the whole solve is one work item
+    int32_t row_tiles, rows_per_tile, col_tiles;
+    int32_t arrive;          // arrival counter of the phase in flight
+    int32_t pad_s;
+    // ---- cost statistics from the formation (ordered encodings of FP64)
+    unsigned long long cmax_enc, cmin_enc, cabs_enc;
+    uint32_t nonfinite, pad_c;
+    // ---- solver state (written by the CTA that owns the current phase)
+    double k2, eps_c, cost_div, cmax, cmin, cabs, min_loga, log_m;
+    double shift_g, shift_f, mu, kl_prev, err, dual, cost;
+    int32_t steps, stages, m_stage, j_in_stage, failures, first, status, done;
+};
+
+// Result record of one problem (device, copied back to the host).
+struct BatchResult {
+    int32_t status, steps, stages, failures;
+    double marginal_l1, transport_cost, dual, cost_max;
+};
+
+// Work queue: a ring of 64-bit items with a per-slot sequence word
+// (published when seq == pos + 1, free for position pos when seq == pos).
+struct BatchQueue {
+    unsigned long long head, tail;
+    unsigned long long *items;
+    unsigned long long *seq;
+    unsigned long long cap;      // power of two
+    int32_t count;               // problems in the batch
+    int32_t done_count;
+    int32_t all_done;
+    int32_t error;               // ACCSINK_ERR_TIMEOUT on a wait that ran out
+};
+
+// Work item kinds.
+enum BatchItem { BI_SMALL = 0, BI_INIT = 1, BI_ROW = 2, BI_COL = 3, BI_FINAL = 4 };
+
+__host__ __device__ inline unsigned long long batch_item(int kind, int prob, int tile)
+{
+    return ((unsigned long long)(uint32_t)prob << 32) | ((unsigned long long)kind << 28) |
+           (unsigned long long)(uint32_t)tile;
+}
+
+// A 64 x 64 tile of one problem's cost for the formation kernels.
+struct BatchTile {
+    int32_t prob, row0, col0, pad;
+};
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchColTile = 128;     // columns per column-pass item (32 lanes x 4)
+constexpr int kBatchFormTile = 64;     // formation tile edge
+
+cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int ntiles,
+                              int dmax, cudaStream_t s);
+cudaError_t launch_batch_scale(BatchProb *P, const BatchTile *tiles, int ntiles, cudaStream_t s);
+cudaError_t launch_batch_solve(BatchProb *P, BatchQueue *q, BatchResult *res, int grid,
+                               cudaStream_t s);
+int occupancy_batch_solve();
+cudaError_t launch_queue_init(BatchQueue *q, const unsigned long long *items0, int count,
+                              unsigned long long cap, cudaStream_t s);
+
+}  // namespace accsink

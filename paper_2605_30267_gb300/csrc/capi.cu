@@ -11,6 +11,8 @@
 
 #include "accsink.h"
 #include "accsink_internal.cuh"
+#include "batch_host.h"
+#include "batch_internal.cuh"
 
 using namespace accsink;
 
@@ -99,6 +101,12 @@ struct accsink_ctx {
     void *pts = nullptr;
     size_t pts_bytes = 0;
     int occ_pts = 1;
+    // batches
+    BatchWorkspace batch;
+    BatchTuning batch_tuning;
+    BatchTiming batch_timing;
+    int occ_batch = 1;
+    cudaEvent_t ev_mid = nullptr;
 };
 
 namespace {
@@ -889,6 +897,8 @@ int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
     }
     ctx->occ_row_warp = occupancy_row_pass_warp();
     ctx->occ_pts = occupancy_points_pass();
+    ctx->occ_batch = occupancy_batch_solve();
+    ctx->batch_tuning = batch_default_tuning(ctx->num_sms);
     if (setup_row_pass_tma() != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -896,6 +906,7 @@ int accsink_create(accsink_ctx **out, int device, size_t mem_budget_bytes)
     }
     if (cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaEventCreate(&ctx->ev_mid) != cudaSuccess ||
         cudaMallocHost(&ctx->h_state, sizeof(DevState)) != cudaSuccess) {
         cudaGetLastError();
         delete ctx;
@@ -914,6 +925,9 @@ void accsink_destroy(accsink_ctx *ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ct) cudaFree(ctx->ct);
     if (ctx->pts) cudaFree(ctx->pts);
+    if (ctx->batch.dev) cudaFree(ctx->batch.dev);
+    if (ctx->batch.host) cudaFreeHost(ctx->batch.host);
+    if (ctx->ev_mid) cudaEventDestroy(ctx->ev_mid);
     if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -1199,6 +1213,157 @@ int accsink_launch_geometry(accsink_ctx *ctx, int32_t n, int32_t m, int32_t vec,
     out6[3] = (m + kColStrip - 1) / kColStrip;
     out6[4] = g.step_grid;
     out6[5] = g.stat_grid;
+    return ACCSINK_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------- batches --
+
+namespace {
+
+int validate_batch(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
+                   const accsink_params *params, double *const *f_out, double *const *g_out,
+                   accsink_result *res)
+{
+    if (count < 0) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "count must be >= 0");
+    if (count > 0 && (!probs || !params || !f_out || !g_out || !res))
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "probs, params, f_out, g_out and res must be given");
+    for (int k = 0; k < count; ++k) {
+        const accsink_problem *p = &probs[k];
+        const std::string at = " (problem " + std::to_string(k) + ")";
+        if (p->n < 1 || p->m < 1) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "n and m must be >= 1" + at);
+        if (p->cost_kind == ACCSINK_COST_DENSE) {
+            if (!p->C) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "C is NULL" + at);
+            if (p->ldc && p->ldc < p->m) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "ldc < m" + at);
+        } else if (p->cost_kind == ACCSINK_COST_SQEUCLID || p->cost_kind == ACCSINK_COST_COSINE) {
+            if (!p->X || !p->Y) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "X and Y must be given" + at);
+            if (p->d < 1 || p->d > 4096)
+                return fail(ctx, ACCSINK_ERR_INVALID_ARG, "point dimension d must be in 1..4096" + at);
+        } else {
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_kind" + at);
+        }
+        if (p->cost_scale != ACCSINK_SCALE_NONE && p->cost_scale != ACCSINK_SCALE_MAX_TO_ONE)
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown cost_scale" + at);
+        if (!p->a || !p->b) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "a and b must be given" + at);
+        if (!f_out[k] || !g_out[k])
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "f_out and g_out must be given" + at);
+        const int rc = validate_params(ctx, &params[k]);
+        if (rc != ACCSINK_OK) { ctx->err += at; return rc; }
+    }
+    return ACCSINK_OK;
+}
+
+int run_batch(accsink_ctx *ctx, const BatchTuning &tn, int32_t count, const accsink_problem *probs,
+              const accsink_params *params, void *stream, double *const *f_out,
+              double *const *g_out, accsink_result *res)
+{
+    if (count == 0) return ACCSINK_OK;
+    BatchEnv env;
+    env.num_sms = ctx->num_sms;
+    env.occ_solve = ctx->occ_batch;
+    const size_t used = ctx->ws_bytes + ctx->stage_bytes + ctx->ct_bytes + ctx->pts_bytes;
+    env.budget_left = ctx->budget ? (ctx->budget > used ? ctx->budget - used : 1) : 0;
+    env.ev0 = ctx->ev0;
+    env.ev_mid = ctx->ev_mid;
+    env.ev1 = ctx->ev1;
+    std::string err;
+    const int rc = batch_run(env, ctx->batch, tn, count, probs, params, f_out, g_out, res,
+                             (cudaStream_t)stream, err, &ctx->batch_timing);
+    if (rc != ACCSINK_OK) return fail(ctx, rc, err);
+    return ACCSINK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int accsink_solve_batch(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
+                        const accsink_params *params, void *stream, double *const *f_out,
+                        double *const *g_out, accsink_result *res)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    rc = validate_batch(ctx, count, probs, params, f_out, g_out, res);
+    if (rc != ACCSINK_OK) return rc;
+    return run_batch(ctx, ctx->batch_tuning, count, probs, params, stream, f_out, g_out, res);
+}
+
+int accsink_batch_set_config(accsink_ctx *ctx, const accsink_batch_config *cfg)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    BatchTuning t = batch_default_tuning(ctx->num_sms);
+    if (cfg) {
+        if (cfg->small_max_nm < 0 || cfg->row_tile_elems < 0 || cfg->ctas_per_sm < 0)
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "batch config fields must be >= 0");
+        if (cfg->small_max_nm) t.small_max_nm = cfg->small_max_nm;
+        if (cfg->row_tile_elems) t.row_tile_elems = cfg->row_tile_elems;
+        t.ctas_per_sm = cfg->ctas_per_sm;
+    }
+    ctx->batch_tuning = t;
+    return ACCSINK_OK;
+}
+
+int accsink_batch_get_config(const accsink_ctx *ctx, accsink_batch_config *cfg)
+{
+    if (!ctx || !cfg) return ACCSINK_ERR_INVALID_ARG;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->small_max_nm = ctx->batch_tuning.small_max_nm;
+    cfg->row_tile_elems = ctx->batch_tuning.row_tile_elems;
+    cfg->ctas_per_sm = ctx->batch_tuning.ctas_per_sm;
+    return ACCSINK_OK;
+}
+
+int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
+                           const accsink_params *params, void *stream, double *const *f_out,
+                           double *const *g_out, accsink_result *res, accsink_batch_config *best,
+                           float *times_ms, int32_t cap, int32_t *tried)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    rc = validate_batch(ctx, count, probs, params, f_out, g_out, res);
+    if (rc != ACCSINK_OK) return rc;
+    // Candidates: the small-problem cut-off, the row-item size and the
+    // persistent CTAs per SM, around the defaults.
+    const int smalls[] = {1 << 14, 1 << 16, 1 << 18};
+    const int tiles[] = {1 << 14, 1 << 16, 1 << 18};
+    const int per_sm[] = {0, 1};
+    BatchTuning bt = ctx->batch_tuning;
+    float best_ms = INFINITY;
+    int k = 0;
+    for (int sm : smalls)
+        for (int tl : tiles)
+            for (int ps : per_sm) {
+                BatchTuning t;
+                t.small_max_nm = sm;
+                t.row_tile_elems = tl;
+                t.ctas_per_sm = ps;
+                const int r = run_batch(ctx, t, count, probs, params, stream, f_out, g_out, res);
+                if (r != ACCSINK_OK && r != ACCSINK_ERR_MAXITER) return r;
+                const float ms = ctx->batch_timing.total_ms;
+                if (times_ms && k < cap) times_ms[k] = ms;
+                ++k;
+                if (ms < best_ms) { best_ms = ms; bt = t; }
+            }
+    ctx->batch_tuning = bt;
+    if (tried) *tried = k;
+    if (best) {
+        std::memset(best, 0, sizeof(*best));
+        best->small_max_nm = bt.small_max_nm;
+        best->row_tile_elems = bt.row_tile_elems;
+        best->ctas_per_sm = bt.ctas_per_sm;
+    }
+    return ACCSINK_OK;
+}
+
+int accsink_batch_last_timing(const accsink_ctx *ctx, float *total_ms, float *form_ms,
+                              float *solve_ms)
+{
+    if (!ctx) return ACCSINK_ERR_INVALID_ARG;
+    if (total_ms) *total_ms = ctx->batch_timing.total_ms;
+    if (form_ms) *form_ms = ctx->batch_timing.form_ms;
+    if (solve_ms) *solve_ms = ctx->batch_timing.solve_ms;
     return ACCSINK_OK;
 }
 

@@ -27,26 +27,6 @@ namespace accsink {
 namespace {
 
 constexpr int kPtNT = 256;
-constexpr int kPtU = 2;   // float4 column slots per lane per chunk
-
-struct Acc {
-    float R, S, K;
-};
-
-__device__ __forceinline__ void kahan(Acc &a, float x)
-{
-    const float y = x - a.K;
-    const float t = a.S + y;
-    a.K = (t - a.S) - y;
-    a.S = t;
-}
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
 
 }  // namespace
 
@@ -118,31 +98,6 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
     }
 }
 
-// Folds one slot's terms 2^(h + l - R) into a row accumulator; raises R to
-// the slot maximum first (rare after the first slots).
-template <bool WC>
-__device__ __forceinline__ void slot_accumulate(Acc &acc, Acc &cacc, const float h[4],
-                                                const float l[4], const float cst[4])
-{
-    const float m4 = fmaxf(fmaxf(h[0], h[1]), fmaxf(h[2], h[3]));
-    if (m4 > acc.R) {
-        const float f = ex2_approx(acc.R - m4);
-        acc.S *= f;
-        acc.K *= f;
-        if (WC) { cacc.S *= f; cacc.K *= f; }
-        acc.R = m4;
-    }
-    float s = 0.0f, cs = 0.0f;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const float t = ex2_approx((h[e] - acc.R) + l[e]);   // h - R exact (Sterbenz)
-        s += t;
-        if (WC) cs = fmaf(cst[e], t, cs);
-    }
-    kahan(acc, s);
-    if (WC) kahan(cacc, cs);
-}
-
 // Rows r of P against all columns of Q (see PointView), RW rows per warp so
 // each column slot is loaded once per RW rows:
 //   MODE 0 (row pass): A = k (G - By), rows of X, B64 = Bx; finishes u_i,
@@ -178,7 +133,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 #pragma unroll
             for (int k = 0; k < DMAX; ++k) p[q][k] = (k < d) ? pv.P[(int64_t)rr * d + k] : 0.0f;
         }
-        Acc acc[RW], cacc[RW];
+        Lse2 acc[RW], cacc[RW];
 #pragma unroll
         for (int q = 0; q < RW; ++q) {
             acc[q] = {-INFINITY, 0.0f, 0.0f};
@@ -238,22 +193,22 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
             const float Rrow = warp_max(acc[q].R);
             const float sc = ex2_approx(acc[q].R - Rrow);
             float hi, lo, chi = 0.f, clo = 0.f;
-            two_sum(acc[q].S * sc, -acc[q].K * sc, hi, lo);
-            if (WC) two_sum(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
+            two_sum_f(acc[q].S * sc, -acc[q].K * sc, hi, lo);
+            if (WC) two_sum_f(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
                 const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
                 float s2, e2;
-                two_sum(hi, ohi, s2, e2);
+                two_sum_f(hi, ohi, s2, e2);
                 lo = lo + olo + e2;
-                two_sum(s2, lo, hi, lo);
+                two_sum_f(s2, lo, hi, lo);
                 if (WC) {
                     const float ochi = __shfl_xor_sync(0xffffffffu, chi, o);
                     const float oclo = __shfl_xor_sync(0xffffffffu, clo, o);
-                    two_sum(chi, ochi, s2, e2);
+                    two_sum_f(chi, ochi, s2, e2);
                     clo = clo + oclo + e2;
-                    two_sum(s2, clo, chi, clo);
+                    two_sum_f(s2, clo, chi, clo);
                 }
             }
             if (lane == 0 && r < nr) {
@@ -360,7 +315,7 @@ __global__ void __launch_bounds__(kPtNT) k_points_rowmax(const float *X, const f
                     float term, te;
                     if (kind == 1) {
                         float dh, de;
-                        two_sum(x[k], -y, dh, de);          // exact difference
+                        two_sum_f(x[k], -y, dh, de);          // exact difference
                         term = dh * dh;                      // (dh + de)^2 to double-float
                         te = fmaf(dh, dh, -term) + 2.0f * dh * de;
                     } else {
@@ -368,18 +323,18 @@ __global__ void __launch_bounds__(kPtNT) k_points_rowmax(const float *X, const f
                         te = fmaf(x[k], y, -term);
                     }
                     float s2, e2;
-                    two_sum(h, term, s2, e2);
+                    two_sum_f(h, term, s2, e2);
                     l += e2 + te;
                     h = s2;
                 }
             }
             if (kind != 1) {   // cosine: 1 - <x, y>
                 float s2, e2;
-                two_sum(1.0f, -h, s2, e2);
+                two_sum_f(1.0f, -h, s2, e2);
                 h = s2;
                 l = e2 - l;
             }
-            two_sum(h, l, h, l);
+            two_sum_f(h, l, h, l);
             if (h > bh || (h == bh && l > bl)) { bh = h; bl = l; }
         }
 #pragma unroll

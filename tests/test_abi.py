@@ -61,6 +61,8 @@ int main(void) {
          offsetof(accsink_params, max_sinkhorn_steps), offsetof(accsink_params, history));
   printf("%zu %zu %zu\n", sizeof(accsink_result), offsetof(accsink_result, marginal_l1),
          offsetof(accsink_result, gpu_ms));
+  printf("%zu %zu %zu\n", sizeof(accsink_batch_config),
+         offsetof(accsink_batch_config, row_tile_elems), offsetof(accsink_batch_config, ctas_per_sm));
   return 0;
 }
 ''')
@@ -78,6 +80,9 @@ int main(void) {
     r = [int(v) for v in lines[2].split()]
     assert r == [ct.sizeof(B.accsink_result), B.accsink_result.marginal_l1.offset,
                  B.accsink_result.gpu_ms.offset]
+    c = [int(v) for v in lines[3].split()]
+    assert c == [ct.sizeof(B.accsink_batch_config), B.accsink_batch_config.row_tile_elems.offset,
+                 B.accsink_batch_config.ctas_per_sm.offset]
 
 
 def test_host_only_calls(L):

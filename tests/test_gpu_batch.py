@@ -1,0 +1,258 @@
+"""GPU parity of the batched solver (many problems, one persistent launch)
+against the FP64 oracle, problem by problem.
+
+Each problem of a batch must meet the single-solve tolerances: potentials
+within 1e-3 eps max-abs after centring (at the same iterate), <C,P> within
+1e-5 relative, steps within 2% (or one step), FP64-truth column L1 <= tol
+(1 + 0.05) and row L1 at the FP32 floor. The work split (whole-problem items
+or row / column tiles) must not change any potential.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from solve_checks import check_steps, same_iterate
+from paper_2605_30267_gb300 import binding as B
+from paper_2605_30267_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = B.Context(0)
+    yield c
+    c.close()
+
+
+def to_dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+class Prob:
+    """One host problem plus its device tensors and oracle cost."""
+
+    def __init__(self, kind, n, m, seed, eps, d=3, scale=False, method=B.ACC, tol=1e-6,
+                 spread=1.0, **kw):
+        g = np.random.default_rng(seed)
+        self.kind, self.eps, self.tol, self.method, self.scale, self.kw = kind, eps, tol, method, scale, kw
+        if kind == "dense":
+            self.C = (spread * g.random((n, m))).astype(np.float32)
+            self.cost = O.Cost(C=self.C, scale_to_max=scale)
+        elif kind == "sqeuclid":
+            self.X = (spread * g.random((n, d))).astype(np.float32)
+            self.Y = (spread * g.random((m, d))).astype(np.float32)
+            self.cost = O.Cost(X=self.X, Y=self.Y, kind="sqeuclid", scale_to_max=scale)
+        else:
+            self.X = W.unit_gaussian_points(g, n, d)
+            self.Y = W.unit_gaussian_points(g, m, d)
+            self.cost = O.Cost(X=self.X, Y=self.Y, kind="cosine", scale_to_max=scale)
+        self.a = W.dirichlet1(g, n)
+        self.b = W.dirichlet1(g, m)
+        self.n, self.m = n, m
+
+    def struct(self):
+        if self.kind == "dense":
+            return B.problem_dense(to_dev(self.C), to_dev(self.a), to_dev(self.b), self.scale)
+        return B.problem_points(to_dev(self.X), to_dev(self.Y), self.kind, to_dev(self.a),
+                                to_dev(self.b), self.scale)
+
+    def params(self):
+        return B.default_params(eps=self.eps, tol=self.tol, method=self.method, **self.kw)
+
+
+def run_batch(ctx, probs):
+    structs = [p.struct() for p in probs]
+    params = [p.params() for p in probs]
+    fs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in probs]
+    gs = [torch.empty(p.m, dtype=torch.float64, device=DEV) for p in probs]
+    res = ctx.accsink_solve_batch(structs, params, fs, gs)
+    torch.cuda.synchronize()
+    return [f.cpu().numpy() for f in fs], [g.cpu().numpy() for g in gs], \
+        [B.result_dict(r) for r in res]
+
+
+def check_against_oracle(p, f, g, res, cost=None):
+    cost = cost or p.cost
+    okw = dict(method=O.ACC if p.method == B.ACC else O.PLAIN,
+               carry_y=p.kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
+               stability=p.kw.get("stability", B.STAB_REPORT))
+    ref = O.solve(cost, p.a, p.b, p.eps, p.tol, **okw)
+    assert res["status"] == 0, res
+    assert ref["status"] == O.CONVERGED
+    rs, gs_ = ref["sinkhorn_steps"], res["sinkhorn_steps"]
+    check_steps(cost, p.a, p.b, p.eps, p.tol, okw, rs, gs_)
+    ref = same_iterate(cost, p.a, p.b, p.eps, okw, ref, gs_)
+    sh = g.mean() - ref["g"].mean()
+    dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
+    assert dpot <= 1e-3 * p.eps, dpot
+    ev = O.evaluate(cost, p.eps, ref["a"], ref["b"], f, g)
+    assert ev["col_l1"] <= p.tol * 1.05, ev
+    assert ev["row_l1"] <= 2e-7, ev
+    evr = O.evaluate(cost, p.eps, ref["a"], ref["b"], ref["f"], ref["g"])
+    assert abs(res["transport_cost"] - evr["transport_cost"]) <= \
+        1e-5 * abs(evr["transport_cost"]), (res["transport_cost"], evr["transport_cost"])
+    assert abs(res["dual_objective"] - ref["dual"]) <= 1e-5 * max(1e-3, abs(ref["dual"]))
+
+
+def mixed_problems():
+    return [
+        Prob("dense", 1, 1, 1, 5e-2),
+        Prob("dense", 1, 9, 2, 5e-2),
+        Prob("dense", 9, 1, 3, 5e-2, method=B.PLAIN),
+        Prob("dense", 37, 129, 4, 1e-2),
+        Prob("sqeuclid", 200, 333, 5, 1e-3, d=3, scale=True),
+        Prob("sqeuclid", 513, 257, 6, 1e-2, d=2, scale=True, method=B.PLAIN),
+        Prob("cosine", 129, 250, 7, 2e-2, d=40),
+        Prob("cosine", 300, 161, 8, 5e-3, d=17),
+        Prob("dense", 150, 120, 9, 1e-2, scale=True, spread=3.5),
+        Prob("sqeuclid", 64, 1031, 10, 1e-1, d=5, scale=True, stability=B.STAB_GATE),
+        Prob("dense", 257, 300, 11, 1e-2, carry=B.CARRY_W),
+        Prob("sqeuclid", 150, 170, 12, 0.5, d=3, spread=4.0),
+    ]
+
+
+def test_mixed_batch_matches_oracle(ctx):
+    """Dense, squared-Euclidean and cosine problems of ragged sizes, each with
+    its own eps, method and modes, solved whole by one CTA each."""
+    ctx.accsink_batch_set_config()          # defaults: all of these are small
+    probs = mixed_problems()
+    fs, gs, rs = run_batch(ctx, probs)
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        assert r["loop_mode"] == 2
+        check_against_oracle(p, f, g, r)
+
+
+def test_tiled_work_split_gives_identical_potentials(ctx):
+    """Row and column tiles (many CTAs per problem, phase hand-offs through
+    the queue) give the same potentials and steps as whole-problem items."""
+    probs = mixed_problems()
+    ctx.accsink_batch_set_config()
+    f1, g1, r1 = run_batch(ctx, probs)
+    ctx.accsink_batch_set_config(small_max_nm=64, row_tile_elems=700)
+    try:
+        f2, g2, r2 = run_batch(ctx, probs)
+    finally:
+        ctx.accsink_batch_set_config()
+    for k in range(len(probs)):
+        assert r1[k]["sinkhorn_steps"] == r2[k]["sinkhorn_steps"], k
+        np.testing.assert_array_equal(f1[k], f2[k])
+        np.testing.assert_array_equal(g1[k], g2[k])
+        assert abs(r1[k]["dual_objective"] - r2[k]["dual_objective"]) <= \
+            1e-12 * max(1.0, abs(r1[k]["dual_objective"]))
+        assert abs(r1[k]["transport_cost"] - r2[k]["transport_cost"]) <= \
+            1e-9 * abs(r1[k]["transport_cost"])
+
+
+def test_tiled_batch_matches_oracle(ctx):
+    ctx.accsink_batch_set_config(small_max_nm=1000, row_tile_elems=4096)
+    try:
+        probs = mixed_problems()[3:8]
+        fs, gs, rs = run_batch(ctx, probs)
+    finally:
+        ctx.accsink_batch_set_config()
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        check_against_oracle(p, f, g, r)
+
+
+def test_batch_of_one_equals_batch_member(ctx):
+    """A problem's result does not depend on the rest of its batch."""
+    probs = mixed_problems()
+    fs, gs, rs = run_batch(ctx, probs)
+    for k in (4, 7):
+        f1, g1, r1 = run_batch(ctx, [probs[k]])
+        np.testing.assert_array_equal(f1[0], fs[k])
+        np.testing.assert_array_equal(g1[0], gs[k])
+        assert r1[0]["sinkhorn_steps"] == rs[k]["sinkhorn_steps"]
+
+
+def test_word_alignment_shaped_batch(ctx):
+    """24 cosine problems with unit-norm Gaussian points in R^300, n, m
+    log-uniform in [16, 512], eps in [0.005, 0.05] (the oracle reads the cost
+    formed once in FP64)."""
+    batch = W.word_alignment_batch(seed=3, count=24, lo=16, hi=512, d=300)
+    probs = []
+    for k, pr in enumerate(batch):
+        p = Prob.__new__(Prob)
+        p.kind, p.eps, p.tol, p.method, p.scale, p.kw = "cosine", pr["eps"], 1e-6, B.ACC, False, {}
+        p.X, p.Y, p.a, p.b = pr["X"], pr["Y"], pr["a"], pr["b"]
+        p.n, p.m = p.X.shape[0], p.Y.shape[0]
+        p.cost = O.Cost(X=p.X, Y=p.Y, kind="cosine").materialised()
+        probs.append(p)
+    fs, gs, rs = run_batch(ctx, probs)
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        check_against_oracle(p, f, g, r)
+
+
+def test_bad_problem_fails_alone(ctx):
+    probs = mixed_problems()[:6]
+    bad = Prob("sqeuclid", 40, 50, 99, 1e-2, d=3)
+    bad.X = bad.X.copy()
+    bad.X[3, 1] = np.nan
+    zero = Prob("dense", 20, 30, 98, 1e-2)
+    zero.b = zero.b.copy()
+    zero.b[4] = 0.0
+    probs = probs[:3] + [bad] + probs[3:] + [zero]
+    structs = [p.struct() for p in probs]
+    params = [p.params() for p in probs]
+    fs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in probs]
+    gs = [torch.empty(p.m, dtype=torch.float64, device=DEV) for p in probs]
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve_batch(structs, params, fs, gs)
+    assert e.value.code in (B.ERR_NONFINITE, B.ERR_NONPOSITIVE_MARGINAL)
+    # the other problems were still solved: rerun just them and compare
+    good = [p for p in probs if p is not bad and p is not zero]
+    f1, g1, r1 = run_batch(ctx, good)
+    for p, f, g, r in zip(good, f1, g1, r1):
+        assert r["status"] == 0
+
+
+def test_bad_problem_statuses_are_reported(ctx):
+    import ctypes as ct
+    bad = Prob("sqeuclid", 40, 50, 99, 1e-2, d=3)
+    bad.X = bad.X.copy()
+    bad.X[3, 1] = np.inf
+    ok = Prob("dense", 30, 20, 97, 1e-2)
+    probs = [ok, bad]
+    k, pa, qa, fa, ga, ra = B.Context._batch_arrays(
+        [p.struct() for p in probs], [p.params() for p in probs],
+        [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in probs],
+        [torch.empty(p.m, dtype=torch.float64, device=DEV) for p in probs])
+    rc = B.lib().accsink_solve_batch(ctx._h, k, pa, qa, None, fa, ga, ra)
+    assert rc == B.ERR_NONFINITE
+    assert ra[0].status == 0 and ra[1].status == B.ERR_NONFINITE
+
+
+def test_empty_batch_and_invalid_arguments(ctx):
+    assert ctx.accsink_solve_batch([], [], [], []) == []
+    p = Prob("dense", 5, 6, 1, 1e-2)
+    s = p.struct()
+    s.n = 0
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve_batch([s], [p.params()], [torch.empty(5, dtype=torch.float64,
+                                                                 device=DEV)],
+                                [torch.empty(6, dtype=torch.float64, device=DEV)])
+    assert e.value.code == B.ERR_INVALID_ARG
+    q = Prob("cosine", 5, 6, 1, 1e-2, d=8)
+    s = q.struct()
+    s.d = 5000
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve_batch([s], [q.params()], [torch.empty(5, dtype=torch.float64,
+                                                                 device=DEV)],
+                                [torch.empty(6, dtype=torch.float64, device=DEV)])
+    assert e.value.code == B.ERR_INVALID_ARG
+
+
+def test_autotune_picks_a_candidate(ctx):
+    probs = mixed_problems()
+    structs = [p.struct() for p in probs]
+    params = [p.params() for p in probs]
+    fs = [torch.empty(p.n, dtype=torch.float64, device=DEV) for p in probs]
+    gs = [torch.empty(p.m, dtype=torch.float64, device=DEV) for p in probs]
+    best, times = ctx.accsink_batch_autotune(structs, params, fs, gs)
+    assert len(times) == 18 and all(t > 0 for t in times)
+    assert ctx.accsink_batch_get_config() == best
+    ctx.accsink_batch_set_config()
