@@ -311,7 +311,171 @@ def run_gpu(args):
         }
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(pr, steps[-1], args.cpu_evals)
+        if not args.no_points:
+            out["points_workload"] = measure_points(ctx, dev, stream, args.points_n,
+                                                    not args.quick, args.pass_reps,
+                                                    clk.get("sm_max_mhz"), args.host_loop)
+        if not args.no_batch:
+            out["batch_workload"] = measure_batch(ctx, dev, stream, args.batch_count, 3,
+                                                  not args.quick, not args.quick)
     ctx.close()
+    return out
+
+
+def run_batch_only(args):
+    """Only the batched workload (used for profiling the persistent solver)."""
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream(dev)
+    out = measure_batch(ctx, dev, stream, args.batch_count, max(1, args.steps), not args.quick,
+                        not args.quick)
+    ctx.close()
+    return {"metric": METRIC, "batch_workload": out}
+
+
+def run_points_only(args):
+    """Only the point-cloud workload (used for profiling the point passes)."""
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream(dev)
+    out = measure_points(ctx, dev, stream, args.points_n, not args.quick, args.pass_reps, None,
+                         args.host_loop)
+    ctx.close()
+    return {"metric": METRIC, "points_workload": out}
+
+
+POINTS_N = 65536
+POINTS_WORKLOAD = ("colour-transfer-shaped point clouds n=m=65536 in [0,1]^3 (source uniform, "
+                   "target 16-cluster mixture sigma 0.03), squared Euclidean cost formed on the "
+                   "fly and scaled to max 1, uniform marginals, eps=1e-3, tol=1e-6")
+
+
+def measure_points(ctx, dev, stream, n, with_plain, pass_reps, sm_max_mhz, host_loop=False):
+    """Colour-transfer-shaped solve with the cost formed on the fly from the
+    point clouds (no n x m matrix): Acc (and plain) time to tol, and the
+    arithmetic roofline of the two point passes."""
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+    pr = W.color_transfer_problem(seed=SEED, n=n, eps=EPS, tol=TOL)
+    X = torch.from_numpy(pr["X"]).to(dev)
+    Y = torch.from_numpy(pr["Y"]).to(dev)
+    a = torch.from_numpy(pr["a"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    prob = B.problem_points(X, Y, "sqeuclid", a, b, True)
+    f = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float64, device=dev)
+    out = {"workload": POINTS_WORKLOAD.replace("65536", str(n)), "n": n, "m": n, "d": 3,
+           "eps": EPS, "tol": TOL}
+    methods = (("acc", B.ACC), ("plain", B.PLAIN)) if with_plain else (("acc", B.ACC),)
+    for name, meth in methods:
+        p = B.default_params(eps=EPS, tol=TOL, method=meth, use_graph=0 if host_loop else 1)
+        if name == "acc":
+            ctx.accsink_solve(prob, p, f, g, stream=stream)          # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.accsink_solve(prob, p, f, g, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_s"] = round(e0.elapsed_time(e1) / 1e3, 6)
+        out[name + "_steps"] = r.sinkhorn_steps
+        out[name + "_status"] = B.STATUS_NAMES[r.status]
+        out[name + "_marginal_l1"] = r.marginal_l1
+        if name == "acc":
+            gsol = g.clone()
+    if with_plain:
+        out["speedup"] = round(out["plain_s"] / out["acc_s"], 3)
+    row_ms, col_ms = ctx.accsink_time_passes(prob, EPS, gsol, pass_reps, stream=stream)
+    # FP32 work per cost entry of the exact expansion (8 per coordinate:
+    # FMUL, 2 FFMA, 5 FADD) plus the exponent (2 FADD), the accumulation
+    # (1 FADD), the running max and the Kahan fold (~2); ex2 runs on the XU.
+    d = 3
+    ops = 8 * d + 5
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_max_mhz or 2070.0
+    peak = sms * 128 * mhz * 1e6 / 1e9            # FP32 lane operations, G/s
+    ms = max(row_ms, col_ms)
+    achieved = ops * n * n / (ms * 1e-3) / 1e9
+    out["pass_ms"] = {"row": round(row_ms, 4), "col": round(col_ms, 4)}
+    out["roofline"] = {"bound": "alu", "kernel": "row_pass" if row_ms >= col_ms else "col_pass",
+                       "achieved": round(achieved, 1), "peak": round(peak, 1),
+                       "unit": "G FP32 ops/s", "frac": round(achieved / peak, 4),
+                       "ops_per_element": ops, "elements_per_launch": n * n,
+                       "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz",
+                       "cost_entries_per_s": round(n * n / (ms * 1e-3), 1)}
+    return out
+
+
+BATCH_COUNT = 512
+BATCH_WORKLOAD = ("word-alignment-shaped batch: 512 problems, n, m log-uniform in [16, 2048], "
+                  "unit-norm Gaussian points in R^300, cosine cost 1 - x.y, Dirichlet(1) "
+                  "marginals, eps ~ U[0.005, 0.05], tol=1e-6")
+
+
+def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=True):
+    """Many independent problems in one persistent launch (accsink_solve_batch):
+    time to solve the whole batch, the cost formation and the solve phase,
+    after the project's autotuner picked the work split; beside it the same
+    problems solved one at a time through the same engine."""
+    import numpy as np
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+    batch = W.word_alignment_batch(seed=SEED, count=count)
+    structs, params, fs, gs = [], [], [], []
+    nm = 0
+    for pr in batch:
+        X = torch.from_numpy(pr["X"]).to(dev)
+        Y = torch.from_numpy(pr["Y"]).to(dev)
+        a = torch.from_numpy(pr["a"]).to(dev)
+        b = torch.from_numpy(pr["b"]).to(dev)
+        structs.append(B.problem_points(X, Y, "cosine", a, b, False))
+        params.append(B.default_params(eps=pr["eps"], tol=TOL))
+        fs.append(torch.empty(X.shape[0], dtype=torch.float64, device=dev))
+        gs.append(torch.empty(Y.shape[0], dtype=torch.float64, device=dev))
+        nm += X.shape[0] * Y.shape[0]
+    out = {"workload": BATCH_WORKLOAD.replace("512 problems", f"{count} problems"),
+           "count": count, "d": 300, "sum_nm": nm}
+    if autotune:
+        best, times = ctx.accsink_batch_autotune(structs, params, fs, gs, stream=stream)
+        out["autotune"] = {"best": best, "candidates": len(times),
+                           "best_ms": round(min(times), 3), "worst_ms": round(max(times), 3)}
+    res = ctx.accsink_solve_batch(structs, params, fs, gs, stream=stream)   # warm-up
+    tms = []
+    for _ in range(max(1, reps)):
+        res = ctx.accsink_solve_batch(structs, params, fs, gs, stream=stream)
+        tms.append(ctx.accsink_batch_last_timing())
+    steps = [r.sinkhorn_steps for r in res]
+    evals = sum(st * 2 * structs[k].n * structs[k].m for k, st in enumerate(steps))
+    med = sorted(tms, key=lambda t: t["total_ms"])[len(tms) // 2]
+    out.update({
+        "batch_s": round(med["total_ms"] / 1e3, 6),
+        "form_s": round(med["form_ms"] / 1e3, 6),
+        "solve_s": round(med["solve_ms"] / 1e3, 6),
+        "solves_per_s": round(count / (med["total_ms"] / 1e3), 1),
+        "converged": sum(1 for r in res if r.status == 0),
+        "steps": {"min": min(steps), "median": int(np.median(steps)), "max": max(steps)},
+        "cost_entry_evaluations": evals,
+        "solve_entries_per_s": round(evals / (med["solve_ms"] / 1e3), 1),
+    })
+    if one_at_a_time:
+        tot = 0.0
+        for k in range(count):
+            ctx.accsink_solve_batch([structs[k]], [params[k]], [fs[k]], [gs[k]], stream=stream)
+            tot += ctx.accsink_batch_last_timing()["total_ms"]
+        out["one_at_a_time_s"] = round(tot / 1e3, 6)
+        out["batched_speedup"] = round(tot / med["total_ms"], 2)
     return out
 
 
@@ -387,9 +551,24 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive iterations from the host instead of the graph loop")
+    ap.add_argument("--points-n", type=int, default=POINTS_N,
+                    help="size of the colour-transfer point-cloud workload")
+    ap.add_argument("--no-points", action="store_true",
+                    help="skip the point-cloud workload")
+    ap.add_argument("--points-only", action="store_true",
+                    help="run only the point-cloud workload (profiling)")
+    ap.add_argument("--batch-count", type=int, default=BATCH_COUNT,
+                    help="problems in the word-alignment-shaped batch")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched workload (profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
+    elif args.points_only:
+        out = run_points_only(args)
+    elif args.batch_only:
+        out = run_batch_only(args)
     else:
         out = run_gpu(args)
     if out is not None:

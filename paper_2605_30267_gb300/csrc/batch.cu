@@ -37,11 +37,19 @@ __device__ __forceinline__ double dec_d(unsigned long long e)
     return __longlong_as_double((long long)b);
 }
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+// Polling load: no ordering (so it does not invalidate this SM's L1 on every
+// poll); the waiter issues one acquire fence once the value it waits for
+// is seen.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
 {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ void fence_acquire_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
@@ -128,6 +136,17 @@ __device__ __forceinline__ void put_df(float *hp, float *lp, int64_t i, double v
     lp[i] = (float)(v - (double)h);
 }
 
+// Loads of per-problem data written during the solve. When another CTA may
+// have written it (tiled problems) the load goes to L2 (ld.cg); when this
+// CTA owns the whole problem (LOCAL) every write came from this SM, so the
+// L1-cached load is coherent and much faster.
+template <bool LOCAL, class T>
+__device__ __forceinline__ T ldv(const T *p)
+{
+    if constexpr (LOCAL) return *p;
+    else return __ldcg(p);
+}
+
 // Lane-tree merge of a warp's (R, S, K) accumulators into one double-float
 // sum about the warp maximum; every lane gets (Rw, hi, lo).
 __device__ __forceinline__ void warp_merge(const Lse2 &a, float &Rw, float &hi, float &lo)
@@ -150,71 +169,113 @@ __device__ __forceinline__ void warp_merge(const Lse2 &a, float &Rw, float &hi, 
 
 // Row pass over rows [r0, r1) of problem P: u_i, the column operand F'_i and
 // the CTA's partials (sum a u, and with WC the transport cost in K units).
-template <bool WC>
+// Each warp takes four rows at a time (one operand load serves four rows and
+// four rows' loads are in flight); rows go in chunks of one row per thread:
+// the warps reduce each row to (R, hi, lo) in shared memory, then every
+// thread finishes one row in FP64 (so the slow FP64 pipe works on 32 rows
+// per warp instruction).
+template <bool WC, bool LOCAL>
 __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
 {
+    constexpr int RW = 4;
+    __shared__ float sR[kBatchThreads], sH[kBatchThreads], sL[kBatchThreads];
+    __shared__ float sCH[WC ? kBatchThreads : 1], sCL[WC ? kBatchThreads : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int m = P->m;
     const int64_t ldm = P->ldm;
     const int m4 = (m + 3) >> 2, mfull = m >> 2;
-    const double k2 = __ldcg(&P->k2), eps_c = __ldcg(&P->eps_c);
-    const double shift_g = __ldcg(&P->shift_g), shift_f = __ldcg(&P->shift_f);
-    const double inv_eps = 1.0 / eps_c;
+    const double k2 = ldv<LOCAL>(&P->k2), eps_c = ldv<LOCAL>(&P->eps_c);
+    const double shift_g = ldv<LOCAL>(&P->shift_g), shift_f = ldv<LOCAL>(&P->shift_f);
+    const double inv_eps = ldv<LOCAL>(&P->inv_eps);
     const float4 *G4h = reinterpret_cast<const float4 *>(P->Gh);
     const float4 *G4l = reinterpret_cast<const float4 *>(P->Gl);
     double my_dual = 0.0, my_cost = 0.0;
-    for (int r = r0 + wid; r < r1; r += kBW) {
-        const float4 *K4h = reinterpret_cast<const float4 *>(P->Kh + (int64_t)r * ldm);
-        const float4 *K4l = reinterpret_cast<const float4 *>(P->Kl + (int64_t)r * ldm);
-        Lse2 acc = {-INFINITY, 0.0f, 0.0f}, cacc = {0.0f, 0.0f, 0.0f};
-        for (int v = lane; v < m4; v += 32) {
-            const float4 kh = __ldg(K4h + v), kl = __ldg(K4l + v);
-            const float4 gh = __ldcg(G4h + v), gl = __ldcg(G4l + v);
-            const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
-            const float ga[4] = {gh.x, gh.y, gh.z, gh.w}, gb[4] = {gl.x, gl.y, gl.z, gl.w};
-            float h[4], l[4], cst[4];
+    for (int base = r0; base < r1; base += kBatchThreads) {
+        const int rend = min(r1, base + kBatchThreads);
+        for (int r = base + RW * wid; r < rend; r += RW * kBW) {
+            const int nq = min(RW, rend - r);
+            Lse2 acc[RW], cacc[RW];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float hn = ga[e] - ka[e];        // Fast2Sum: |G'| >= |K|
-                const float z = hn - ga[e];
-                l[e] = (gb[e] - kb[e]) + (-ka[e] - z);
-                h[e] = hn;
-                if (WC) cst[e] = ka[e] + kb[e];
+            for (int q = 0; q < RW; ++q) {
+                acc[q] = {-INFINITY, 0.0f, 0.0f};
+                cacc[q] = {0.0f, 0.0f, 0.0f};
             }
-            if (v >= mfull) {
+            for (int v = lane; v < m4; v += 32) {
+                const float4 gh = ldv<LOCAL>(G4h + v), gl = ldv<LOCAL>(G4l + v);
+                const float ga[4] = {gh.x, gh.y, gh.z, gh.w}, gb[4] = {gl.x, gl.y, gl.z, gl.w};
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    if (4 * v + e >= m) { h[e] = -INFINITY; l[e] = 0.0f; if (WC) cst[e] = 0.0f; }
+                for (int q = 0; q < RW; ++q) {
+                    if (q < nq) {
+                        const int64_t off = (int64_t)(r + q) * ldm;
+                        const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->Kh + off) + v);
+                        const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->Kl + off) + v);
+                        const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
+                        float h[4], l[4], cst[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float hn = ga[e] - ka[e];        // Fast2Sum: |G'| >= |K|
+                            const float z = hn - ga[e];
+                            l[e] = (gb[e] - kb[e]) + (-ka[e] - z);
+                            h[e] = hn;
+                            if (WC) cst[e] = ka[e] + kb[e];
+                        }
+                        if (v >= mfull) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * v + e >= m) {
+                                    h[e] = -INFINITY;
+                                    l[e] = 0.0f;
+                                    if (WC) cst[e] = 0.0f;
+                                }
+                        }
+                        slot_accumulate<WC>(acc[q], cacc[q], h, l, cst);
+                    }
+                }
             }
-            slot_accumulate<WC>(acc, cacc, h, l, cst);
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                if (q < nq) {
+                    float Rw, hi, lo;
+                    warp_merge(acc[q], Rw, hi, lo);
+                    float chi = 0.0f, clo = 0.0f;
+                    if (WC) {
+                        // the cost accumulator shares R with the row accumulator
+                        const float sc = (acc[q].R == -INFINITY) ? 0.0f : ex2_approx(acc[q].R - Rw);
+                        two_sum_f(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float ohi = __shfl_xor_sync(0xffffffffu, chi, o);
+                            const float olo = __shfl_xor_sync(0xffffffffu, clo, o);
+                            float s2, e2;
+                            two_sum_f(chi, ohi, s2, e2);
+                            clo = clo + olo + e2;
+                            two_sum_f(s2, clo, chi, clo);
+                        }
+                    }
+                    if (lane == 0) {
+                        const int t = r + q - base;
+                        sR[t] = Rw;
+                        sH[t] = hi;
+                        sL[t] = lo;
+                        if (WC) { sCH[t] = chi; sCL[t] = clo; }
+                    }
+                }
+            }
         }
-        float Rw, hi, lo;
-        warp_merge(acc, Rw, hi, lo);
-        float chi = 0.0f, clo = 0.0f;
-        if (WC) {
-            // the cost accumulator shares R with the row accumulator
-            const float sc = ex2_approx(acc.R - Rw);
-            two_sum_f(cacc.S * sc, -cacc.K * sc, chi, clo);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float ohi = __shfl_xor_sync(0xffffffffu, chi, o);
-                const float olo = __shfl_xor_sync(0xffffffffu, clo, o);
-                float s2, e2;
-                two_sum_f(chi, ohi, s2, e2);
-                clo = clo + olo + e2;
-                two_sum_f(s2, clo, chi, clo);
-            }
-        }
-        if (lane == 0) {
-            const double S = (double)hi + (double)lo;
-            const double lse = (double)Rw * kLn2 + log(S) - shift_g * inv_eps;
-            const double ui = __ldcg(&P->loga[r]) - lse;
+        __syncthreads();
+        const int r = base + threadIdx.x;
+        if (r < rend) {
+            const int t = threadIdx.x;
+            const double S = (double)sH[t] + (double)sL[t];
+            const double lse = (double)sR[t] * kLn2 + log(S) - shift_g * inv_eps;
+            const double ui = ldv<LOCAL>(&P->loga[r]) - lse;
             P->u[r] = ui;
             put_df(P->Fh, P->Fl, r, k2 * (eps_c * ui + shift_f));
-            const double ar = __ldcg(&P->a[r]);
+            const double ar = ldv<LOCAL>(&P->a[r]);
             my_dual += ar * ui;
-            if (WC) my_cost += ar * (((double)chi + (double)clo) / S);
+            if (WC) my_cost += ar * (((double)sCH[t] + (double)sCL[t]) / S);
         }
+        __syncthreads();
     }
     double v[2] = {my_dual, my_cost};
     cta_sum<2>(v);
@@ -222,11 +283,104 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
     part2[1] = v[1];
 }
 
+// Algorithm 1's stage constants for the current mu (see the single-problem
+// step kernel's table): alpha = sqrt(2 mu) and its functions.
+struct StageK {
+    double alpha, inv_alpha, inv_1pa, a2, kappa1, c2f, ratio_next, inv_1pa_next;
+};
+
+__device__ __forceinline__ StageK stage_constants(bool is_acc, double mu)
+{
+    StageK k = {1.0, 1.0, 0.5, -1.0, 0.0, 1.0, 1.0, 0.5};
+    if (is_acc) {
+        const double alpha = sqrt(2.0 * mu);
+        const double an = sqrt(mu);             // alpha of the next stage (mu / 2)
+        k.alpha = alpha;
+        k.inv_alpha = 1.0 / alpha;
+        k.inv_1pa = 1.0 / (1.0 + alpha);
+        k.a2 = alpha * alpha - 2.0;
+        k.kappa1 = (4.0 - alpha * alpha - 2.0 * sqrt(alpha)) /
+                   (2.0 * alpha * (1.0 + alpha) * (1.0 + alpha));
+        k.c2f = alpha * sqrt(alpha);
+        k.ratio_next = an / alpha;
+        k.inv_1pa_next = 1.0 / (1.0 + an);
+    }
+    return k;
+}
+
+// The stage constants computed once by thread 0 and shared with the CTA (FP64
+// square roots and divisions are slow on this part; every thread computing
+// them costs more than a whole small row pass).
+__device__ __forceinline__ StageK cta_stage_constants(bool is_acc, double mu)
+{
+    __shared__ StageK ks;
+    if (threadIdx.x == 0) ks = stage_constants(is_acc, mu);
+    __syncthreads();
+    const StageK k = ks;
+    __syncthreads();
+    return k;
+}
+
+// Step phase P1 for column j, given ell_j from the column pass: p = log(c/b),
+// raw_j = x_j - p (the v-update), c_j - b_j, D_j, the KL term and Theorem 4's
+// Cond 1 / Cond 2 left-hand terms; adds to the sums v and the bounds.
+template <bool LOCAL>
+__device__ __forceinline__ void p1_column(BatchProb *P, int j, double ell, double inv_alpha,
+                                          bool check, double (&v)[6], double (&lo3)[3],
+                                          double (&hi3)[3])
+{
+    const double xj = ldv<LOCAL>(&P->x[j]);
+    const double bj = ldv<LOCAL>(&P->b[j]);
+    const double wj = ldv<LOCAL>(&P->w[j]);
+    const double del = xj + ell - ldv<LOCAL>(&P->logb[j]);
+    const double raw = xj - del;
+    double xi, D1, klt;
+    const float dl = (float)del;
+    if (fabsf(dl) <= 80.0f) {
+        const float e = expm1f(dl);
+        float km;
+        if (fabsf(dl) < 0.0625f) {
+            km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
+                                                 1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+        } else {
+            km = e - dl;
+        }
+        const float dr = (dl != 0.0f) ? e / dl : 1.0f;
+        xi = bj * (double)e;
+        D1 = bj * (double)dr;
+        klt = bj * (double)km;
+    } else {
+        const double e = expm1(del);
+        xi = bj * e;
+        D1 = xi / del;
+        klt = bj * (e - del);
+    }
+    v[0] += fabs(xi);
+    v[1] += raw;
+    v[2] += klt;
+    v[3] += bj * xj;
+    if (check) {
+        const double p0 = ldv<LOCAL>(&P->p_prev[j]);
+        const double v0 = wj * inv_alpha - ldv<LOCAL>(&P->x_prev[j]);
+        v[4] += p0 * p0 * D1;
+        v[5] += v0 * v0 * (D1 - ldv<LOCAL>(&P->D_prev[j]));
+    }
+    lo3[0] = fmin(lo3[0], raw); hi3[0] = fmax(hi3[0], raw);
+    lo3[1] = fmin(lo3[1], xj);  hi3[1] = fmax(hi3[1], xj);
+    lo3[2] = fmin(lo3[2], wj);  hi3[2] = fmax(hi3[2], wj);
+    P->raw[j] = raw;
+    P->D1[j] = D1;
+    P->del[j] = del;
+}
+
 // Column pass over columns [c0, c0 + 128) of problem P: ell_j. Each lane owns
 // four columns, warps split the rows in groups of four, and the warps'
 // accumulators are merged per column in a fixed order.
-__device__ void cta_cols(BatchProb *P, int c0)
+template <bool LOCAL>
+__device__ void cta_cols(BatchProb *P, int tile, const StageK &K, bool check, double (&wsum)[6],
+                         double (&lo3)[3], double (&hi3)[3])
 {
+    const int c0 = tile * kBatchColTile;
     __shared__ float sR[kBW][kBatchColTile], sH[kBW][kBatchColTile], sL[kBW][kBatchColTile];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = P->n, m = P->m;
@@ -245,7 +399,7 @@ __device__ void cta_cols(BatchProb *P, int c0)
                 if (r < n) {
                     const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->Kh + (int64_t)r * ldm + cb));
                     const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->Kl + (int64_t)r * ldm + cb));
-                    const float fh = __ldcg(P->Fh + r), fl = __ldcg(P->Fl + r);
+                    const float fh = ldv<LOCAL>(P->Fh + r), fl = ldv<LOCAL>(P->Fl + r);
                     const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -276,6 +430,12 @@ __device__ void cta_cols(BatchProb *P, int c0)
         sL[wid][4 * lane + e] = lo;
     }
     __syncthreads();
+    // per column: merge the warps, finish ell_j and run step phase P1 on it
+    // here, so the step's per-column FP64 work is spread over the tiles. The
+    // P1 sums of the columns a warp finished are reduced over its lanes (fixed
+    // tree) and added to that warp's running sums `wsum`; the bounds stay
+    // per thread (the caller reduces them).
+    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     if (threadIdx.x < kBatchColTile) {
         const int t = threadIdx.x, c = c0 + t;
         if (c < m) {
@@ -287,8 +447,33 @@ __device__ void cta_cols(BatchProb *P, int c0)
                 const double f = (double)ex2_approx(sR[q][t] - R);
                 S += ((double)sH[q][t] + (double)sL[q][t]) * f;
             }
-            const double shift_f = __ldcg(&P->shift_f), eps_c = __ldcg(&P->eps_c);
-            P->ell[c] = (double)R * kLn2 + log(S) - shift_f / eps_c;
+            const double shift_f = ldv<LOCAL>(&P->shift_f), inv_eps = ldv<LOCAL>(&P->inv_eps);
+            const double ell = (double)R * kLn2 + log(S) - shift_f * inv_eps;
+            P->ell[c] = ell;
+            p1_column<LOCAL>(P, c, ell, K.inv_alpha, check, v, lo3, hi3);
+        }
+    }
+    if (threadIdx.x < kBatchColTile) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) wsum[q] += warp_sum(v[q]);
+    }
+    __syncthreads();
+}
+
+// Writes record `rec`: the finishing warps' P1 sums and the CTA's bounds.
+__device__ void cta_colrec(BatchProb *P, int rec, const double (&wsum)[6], double (&lo3)[3],
+                           double (&hi3)[3])
+{
+    cta_minmax<3>(lo3, hi3);
+    double *r = P->colrec + (int64_t)rec * kBatchColRec;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0 && wid < kBatchColWarps) {
+        for (int q = 0; q < 6; ++q) r[6 * wid + q] = wsum[q];
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 3; ++q) {
+            r[6 * kBatchColWarps + q] = lo3[q];
+            r[6 * kBatchColWarps + 3 + q] = hi3[q];
         }
     }
     __syncthreads();
@@ -359,6 +544,7 @@ __device__ bool cta_init(BatchProb *P)
     if (threadIdx.x == 0) {
         P->k2 = k2;
         P->eps_c = eps_c;
+        P->inv_eps = 1.0 / eps_c;
         P->cost_div = cost_div;
         P->cmax = cmax; P->cmin = cmin; P->cabs = cabs;
         P->min_loga = min_loga;
@@ -377,89 +563,63 @@ __device__ bool cta_init(BatchProb *P)
 }
 
 // One step after the row and column passes at x (see the single-problem step
-// kernel for the phases P1-P3). Returns true when the solve stops.
-__device__ bool cta_step(BatchProb *P)
+// kernel for the phases P1-P3; P1 ran in the column tiles, which left `nrec`
+// records of sums and bounds). Returns true when the solve stops.
+template <bool LOCAL>
+__device__ bool cta_step(BatchProb *P, int nrec)
 {
     __shared__ int stop_s;
     const int m = P->m;
     const int method = P->method, stab = P->stability;
-    const int first = __ldcg(&P->first);
-    const double mu = __ldcg(&P->mu);
+    const int first = ldv<LOCAL>(&P->first);
+    const double mu = ldv<LOCAL>(&P->mu);
     const bool is_acc = method == 1;
-    // Algorithm 1's alpha-dependent constants for this stage
-    double alpha = 1.0, inv_alpha = 1.0, inv_1pa = 0.5, a2 = -1.0, kappa1 = 0.0, c2f = 1.0;
-    double ratio_next = 1.0, inv_1pa_next = 0.5;
-    if (is_acc) {
-        alpha = sqrt(2.0 * mu);
-        const double an = sqrt(mu);             // alpha of the next stage (mu / 2)
-        inv_alpha = 1.0 / alpha;
-        inv_1pa = 1.0 / (1.0 + alpha);
-        a2 = alpha * alpha - 2.0;
-        kappa1 = (4.0 - alpha * alpha - 2.0 * sqrt(alpha)) /
-                 (2.0 * alpha * (1.0 + alpha) * (1.0 + alpha));
-        c2f = alpha * sqrt(alpha);
-        ratio_next = an / alpha;
-        inv_1pa_next = 1.0 / (1.0 + an);
-    }
+    const StageK K = cta_stage_constants(is_acc, mu);
+    const double alpha = K.alpha, inv_alpha = K.inv_alpha, inv_1pa = K.inv_1pa, a2 = K.a2;
+    const double kappa1 = K.kappa1, c2f = K.c2f, ratio_next = K.ratio_next;
+    const double inv_1pa_next = K.inv_1pa_next;
     const bool check = is_acc && !first && stab != 0;
     const bool wupd = is_acc && !first;
 
-    // ---- P1
+    // ---- P1 totals from the column records: per finishing warp in record
+    // order, then over the warps (the same order for every work split)
     double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // err, raw, kl, <b,x>, c1, c2l
     double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int j = threadIdx.x; j < m; j += kBatchThreads) {
-        const double ell = __ldcg(&P->ell[j]);
-        const double xj = __ldcg(&P->x[j]);
-        const double bj = __ldcg(&P->b[j]);
-        const double wj = __ldcg(&P->w[j]);
-        const double del = xj + ell - __ldcg(&P->logb[j]);
-        const double raw = xj - del;
-        double xi, D1, klt;
-        const float dl = (float)del;
-        if (fabsf(dl) <= 80.0f) {
-            const float e = expm1f(dl);
-            float km;
-            if (fabsf(dl) < 0.0625f) {
-                km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
-                                                     1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+    {
+        __shared__ double tot_s[12];
+        if (threadIdx.x < 12) {
+            const int q = threadIdx.x;
+            double a;
+            if (q < 6) {
+                a = 0.0;
+                for (int w = 0; w < kBatchColWarps; ++w) {
+                    double aw = 0.0;
+                    for (int t = 0; t < nrec; ++t)
+                        aw += ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec + 6 * w + q]);
+                    a += aw;
+                }
             } else {
-                km = e - dl;
+                const bool mn = q < 9;
+                a = mn ? DBL_MAX : -DBL_MAX;
+                for (int t = 0; t < nrec; ++t) {
+                    const double r = ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec +
+                                                           6 * kBatchColWarps + (q - 6)]);
+                    a = mn ? fmin(a, r) : fmax(a, r);
+                }
             }
-            const float dr = (dl != 0.0f) ? e / dl : 1.0f;
-            xi = bj * (double)e;
-            D1 = bj * (double)dr;
-            klt = bj * (double)km;
-        } else {
-            const double e = expm1(del);
-            xi = bj * e;
-            D1 = xi / del;
-            klt = bj * (e - del);
+            tot_s[q] = a;
         }
-        v[0] += fabs(xi);
-        v[1] += raw;
-        v[2] += klt;
-        v[3] += bj * xj;
-        if (check) {
-            const double p0 = __ldcg(&P->p_prev[j]);
-            const double v0 = wj * inv_alpha - __ldcg(&P->x_prev[j]);
-            v[4] += p0 * p0 * D1;
-            v[5] += v0 * v0 * (D1 - __ldcg(&P->D_prev[j]));
-        }
-        lo3[0] = fmin(lo3[0], raw); hi3[0] = fmax(hi3[0], raw);
-        lo3[1] = fmin(lo3[1], xj);  hi3[1] = fmax(hi3[1], xj);
-        lo3[2] = fmin(lo3[2], wj);  hi3[2] = fmax(hi3[2], wj);
-        P->raw[j] = raw;
-        P->D1[j] = D1;
-        P->del[j] = del;
+        __syncthreads();
+        for (int q = 0; q < 6; ++q) v[q] = tot_s[q];
+        for (int q = 0; q < 3; ++q) { lo3[q] = tot_s[6 + q]; hi3[q] = tot_s[9 + q]; }
+        __syncthreads();
     }
-    cta_sum<6>(v);
-    cta_minmax<3>(lo3, hi3);
     const double err = v[0];
     const double rbar = v[1] / (double)m;
     double au[1] = {0.0};
     {
         const int rt = P->row_tiles;
-        for (int t = threadIdx.x; t < rt; t += kBatchThreads) au[0] += __ldcg(&P->rowpart[2 * t]);
+        for (int t = threadIdx.x; t < rt; t += kBatchThreads) au[0] += ldv<LOCAL>(&P->rowpart[2 * t]);
         cta_sum<1>(au);
     }
     const double dual = P->eps * (au[0] + v[3] - 1.0);
@@ -469,12 +629,12 @@ __device__ bool cta_step(BatchProb *P)
     double wl[1] = {DBL_MAX}, wh[1] = {-DBL_MAX};
     if (wupd) {
         for (int j = threadIdx.x; j < m; j += kBatchThreads) {
-            const double s = P->raw[j] - rbar;
-            const double xj = __ldcg(&P->x[j]);
-            const double w1 = (__ldcg(&P->w[j]) + a2 * xj + 2.0 * s) * inv_1pa;
+            const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
+            const double xj = ldv<LOCAL>(&P->x[j]);
+            const double w1 = (ldv<LOCAL>(&P->w[j]) + a2 * xj + 2.0 * s) * inv_1pa;
             P->w1[j] = w1;
             const double v1 = w1 * inv_alpha - xj;
-            v2[0] += v1 * v1 * P->D1[j];
+            v2[0] += v1 * v1 * ldv<LOCAL>(&P->D1[j]);
             wl[0] = fmin(wl[0], w1);
             wh[0] = fmax(wh[0], w1);
         }
@@ -482,57 +642,75 @@ __device__ bool cta_step(BatchProb *P)
     cta_sum<1>(v2);
     cta_minmax<1>(wl, wh);
 
-    // ---- P3
-    const double c1 = v[4], c2l = v[5];
-    const double c1r = kappa1 * __ldcg(&P->kl_prev);
-    const double c2r = c2f * v2[0];
-    int stab_bits = 0;
-    if (check) stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
-    const bool gate = (stab == 2) && (stab_bits != 0);
-    const int steps_new = __ldcg(&P->steps) + 1;
-    const bool nonfinite = !isfinite(err);
-    const bool converged = err < P->tol;
-    const bool stop = converged || nonfinite || steps_new >= P->max_steps;
-    double mu_new = mu;
-    int ms = __ldcg(&P->m_stage), jst = __ldcg(&P->j_in_stage), stages = __ldcg(&P->stages);
-    bool stage_end = false;
-    if (wupd) {
-        jst += 1;
-        if (jst == ms) {
-            stage_end = true;
-            mu_new = mu / 2.0;
-            ms = (int)floor(sqrt(2.0) * (double)ms) + 1;
-            jst = 0;
-            stages += 1;
+    // ---- P3: the scalar decisions by thread 0, shared with the CTA
+    struct P3 {
+        double inv_1pa_new, ratio, shift_g, shift_fn, mu_new;
+        int stab_bits, gate, stop, steps_new, ms, jst, stages, status;
+    };
+    __shared__ P3 p3s;
+    if (threadIdx.x == 0) {
+        P3 r;
+        const double c1 = v[4], c2l = v[5];
+        const double c1r = kappa1 * ldv<LOCAL>(&P->kl_prev);
+        const double c2r = c2f * v2[0];
+        r.stab_bits = 0;
+        if (check) r.stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
+        r.gate = (stab == 2) && (r.stab_bits != 0);
+        r.steps_new = ldv<LOCAL>(&P->steps) + 1;
+        const bool nonfinite = !isfinite(err);
+        const bool converged = err < P->tol;
+        r.stop = converged || nonfinite || r.steps_new >= P->max_steps;
+        r.status = nonfinite ? 3 : (converged ? 0 : 7);
+        r.mu_new = mu;
+        r.ms = ldv<LOCAL>(&P->m_stage);
+        r.jst = ldv<LOCAL>(&P->j_in_stage);
+        r.stages = ldv<LOCAL>(&P->stages);
+        bool stage_end = false;
+        if (wupd) {
+            r.jst += 1;
+            if (r.jst == r.ms) {
+                stage_end = true;
+                r.mu_new = mu / 2.0;
+                r.ms = (int)floor(sqrt(2.0) * (double)r.ms) + 1;
+                r.jst = 0;
+                r.stages += 1;
+            }
         }
+        r.inv_1pa_new = stage_end ? inv_1pa_next : inv_1pa;
+        r.ratio = (stage_end && P->carry == 0) ? ratio_next : 1.0;
+        const double slo = lo3[0] - rbar, shi = hi3[0] - rbar;
+        double xlo, xhi;
+        if (is_acc) {
+            double w1lo, w1hi;
+            if (!wupd) { w1lo = lo3[2]; w1hi = hi3[2]; }
+            else if (r.gate) { w1lo = alpha * lo3[1]; w1hi = alpha * hi3[1]; }
+            else { w1lo = wl[0]; w1hi = wh[0]; }
+            xlo = (w1lo * r.ratio + slo) * r.inv_1pa_new;
+            xhi = (w1hi * r.ratio + shi) * r.inv_1pa_new;
+        } else {
+            xlo = slo;
+            xhi = shi;
+        }
+        // widen by a relative margin that covers the FP64 rounding of the bounds
+        xlo -= 1e-12 * (1.0 + fabs(xlo));
+        xhi += 1e-12 * (1.0 + fabs(xhi));
+        const double eps_c = P->eps_c;
+        r.shift_g = P->cabs - eps_c * xlo;
+        r.shift_fn = P->cabs - (eps_c * P->min_loga - eps_c * xhi + P->cmin - eps_c * P->log_m);
+        p3s = r;
     }
-    const double inv_1pa_new = stage_end ? inv_1pa_next : inv_1pa;
-    const double ratio = (stage_end && P->carry == 0) ? ratio_next : 1.0;
-    const double slo = lo3[0] - rbar, shi = hi3[0] - rbar;
-    double xlo, xhi;
-    if (is_acc) {
-        double w1lo, w1hi;
-        if (!wupd) { w1lo = lo3[2]; w1hi = hi3[2]; }
-        else if (gate) { w1lo = alpha * lo3[1]; w1hi = alpha * hi3[1]; }
-        else { w1lo = wl[0]; w1hi = wh[0]; }
-        xlo = (w1lo * ratio + slo) * inv_1pa_new;
-        xhi = (w1hi * ratio + shi) * inv_1pa_new;
-    } else {
-        xlo = slo;
-        xhi = shi;
-    }
-    xlo -= 1e-12 * (1.0 + fabs(xlo));
-    xhi += 1e-12 * (1.0 + fabs(xhi));
+    __syncthreads();
+    const P3 r = p3s;
+    const bool stop = r.stop, gate = r.gate;
+    const double inv_1pa_new = r.inv_1pa_new, ratio = r.ratio, shift_g = r.shift_g;
     const double eps_c = P->eps_c, k2 = P->k2;
-    const double shift_g = P->cabs - eps_c * xlo;
-    const double shift_fn = P->cabs - (eps_c * P->min_loga - eps_c * xhi + P->cmin - eps_c * P->log_m);
     if (!stop) {
         for (int j = threadIdx.x; j < m; j += kBatchThreads) {
-            const double s = P->raw[j] - rbar;
-            const double xj = __ldcg(&P->x[j]);
+            const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
+            const double xj = ldv<LOCAL>(&P->x[j]);
             double xn;
             if (is_acc) {
-                double w1 = wupd ? (gate ? alpha * xj : P->w1[j]) : __ldcg(&P->w[j]);
+                double w1 = wupd ? (gate ? alpha * xj : P->w1[j]) : ldv<LOCAL>(&P->w[j]);
                 w1 *= ratio;
                 xn = (w1 + s) * inv_1pa_new;
                 P->w[j] = w1;
@@ -541,30 +719,30 @@ __device__ bool cta_step(BatchProb *P)
             }
             P->x_prev[j] = xj;
             P->x[j] = xn;
-            P->p_prev[j] = P->del[j];
-            P->D_prev[j] = P->D1[j];
+            P->p_prev[j] = ldv<LOCAL>(&P->del[j]);
+            P->D_prev[j] = ldv<LOCAL>(&P->D1[j]);
             put_df(P->Gh, P->Gl, j, k2 * (eps_c * xn + shift_g));
         }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        P->steps = steps_new;
+        P->steps = r.steps_new;
         P->err = err;
         P->dual = dual;
         P->kl_prev = v[2];
         P->first = 0;
-        if (stab_bits) P->failures += 1;
+        if (r.stab_bits) P->failures += 1;
         if (wupd) {
-            P->mu = mu_new;
-            P->m_stage = ms;
-            P->j_in_stage = jst;
-            P->stages = stages;
+            P->mu = r.mu_new;
+            P->m_stage = r.ms;
+            P->j_in_stage = r.jst;
+            P->stages = r.stages;
         }
         if (stop) {
-            P->status = nonfinite ? 3 : (converged ? 0 : 7);
+            P->status = r.status;
         } else {
-            P->shift_g = shift_g;
-            P->shift_f = shift_fn;
+            P->shift_g = r.shift_g;
+            P->shift_f = r.shift_fn;
         }
         stop_s = stop ? 1 : 0;
     }
@@ -573,18 +751,19 @@ __device__ bool cta_step(BatchProb *P)
 }
 
 // Outputs of a finished problem: f = eps u, g = eps x, the result record.
+template <bool LOCAL>
 __device__ void cta_finish(BatchProb *P, BatchResult *R, bool ok)
 {
     const int n = P->n, m = P->m;
     const double eps = P->eps;
     if (ok) {
-        for (int i = threadIdx.x; i < n; i += kBatchThreads) P->f_out[i] = eps * __ldcg(&P->u[i]);
-        for (int j = threadIdx.x; j < m; j += kBatchThreads) P->g_out[j] = eps * __ldcg(&P->x[j]);
+        for (int i = threadIdx.x; i < n; i += kBatchThreads) P->f_out[i] = eps * ldv<LOCAL>(&P->u[i]);
+        for (int j = threadIdx.x; j < m; j += kBatchThreads) P->g_out[j] = eps * ldv<LOCAL>(&P->x[j]);
     }
     double c[1] = {0.0};
     if (ok && P->evaluate) {
         for (int t = threadIdx.x; t < P->row_tiles; t += kBatchThreads)
-            c[0] += __ldcg(&P->rowpart[2 * t + 1]);
+            c[0] += ldv<LOCAL>(&P->rowpart[2 * t + 1]);
     }
     cta_sum<1>(c);
     if (threadIdx.x == 0) {
@@ -611,7 +790,7 @@ __device__ bool q_pop(BatchQueue *q, unsigned long long &item)
     const unsigned long long slot = pos & (q->cap - 1);
     const uint64_t t0 = globaltimer_ns();
     for (;;) {
-        const unsigned long long s = ld_acquire_u64(&q->seq[slot]);
+        const unsigned long long s = ld_relaxed_u64(&q->seq[slot]);
         if (s == pos + 1) break;
         if (ld_volatile_i32(&q->all_done)) return false;
         if (globaltimer_ns() - t0 > kQueueWaitNs) {
@@ -621,6 +800,7 @@ __device__ bool q_pop(BatchQueue *q, unsigned long long &item)
         }
         __nanosleep(200);
     }
+    fence_acquire_gpu();
     item = *(volatile unsigned long long *)&q->items[slot];
     st_release_u64(&q->seq[slot], pos + q->cap);
     return true;
@@ -641,7 +821,7 @@ __device__ void q_push(BatchQueue *q, int k, F item)
         const unsigned long long slot = pos & (q->cap - 1);
         const uint64_t t0 = globaltimer_ns();
         bool ok = true;
-        while (ld_acquire_u64(&q->seq[slot]) != pos) {
+        while (ld_relaxed_u64(&q->seq[slot]) != pos) {
             if (globaltimer_ns() - t0 > kQueueWaitNs || ld_volatile_i32(&q->all_done)) {
                 atomicExch(&q->error, 6);
                 atomicExch(&q->all_done, 1);
@@ -844,49 +1024,50 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
         BatchProb *P = Pall + p;
         BatchResult *R = res + p;
         if (kind == BI_SMALL) {
-            // the whole solve in this CTA
-            // (each phase reads what the previous one wrote through L2, so a
-            // device-scope fence separates them)
+            // the whole solve in this CTA (every read of the problem's data
+            // is of this CTA's own writes: L1 loads, CTA barriers)
             bool ok = cta_init(P);
             if (ok) {
+                const bool is_acc = P->method == 1;
                 for (;;) {
-                    __threadfence();
                     __syncthreads();
                     double part[2];
-                    cta_rows<false>(P, 0, P->n, part);
+                    cta_rows<false, true>(P, 0, P->n, part);
                     if (threadIdx.x == 0) { P->rowpart[0] = part[0]; P->rowpart[1] = part[1]; }
-                    __threadfence();
                     __syncthreads();
-                    for (int c0 = 0; c0 < P->m; c0 += kBatchColTile) cta_cols(P, c0);
-                    __threadfence();
-                    __syncthreads();
-                    if (cta_step(P)) break;
+                    const StageK K = cta_stage_constants(is_acc, P->mu);
+                    const bool check = is_acc && !P->first && P->stability != 0;
+                    double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                    double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX};
+                    double hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+                    for (int t = 0; t < P->col_tiles; ++t) cta_cols<true>(P, t, K, check, ws, lo3, hi3);
+                    cta_colrec(P, 0, ws, lo3, hi3);
+                    if (cta_step<true>(P, 1)) break;
                 }
-                __threadfence();
                 __syncthreads();
                 if (P->evaluate) {
                     double part[2];
-                    cta_rows<true>(P, 0, P->n, part);
+                    cta_rows<true, true>(P, 0, P->n, part);
                     if (threadIdx.x == 0) { P->rowpart[0] = part[0]; P->rowpart[1] = part[1]; }
                     __syncthreads();
                 }
             }
-            cta_finish(P, R, ok);
+            cta_finish<true>(P, R, ok);
             problem_done(q);
         } else if (kind == BI_INIT) {
             const bool ok = cta_init(P);
             if (ok) {
                 q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
             } else {
-                cta_finish(P, R, false);
+                cta_finish<false>(P, R, false);
                 problem_done(q);
             }
         } else if (kind == BI_ROW || kind == BI_FINAL) {
             const int r0 = tile * P->rows_per_tile;
             const int r1 = min(P->n, r0 + P->rows_per_tile);
             double part[2];
-            if (kind == BI_ROW) cta_rows<false>(P, r0, r1, part);
-            else cta_rows<true>(P, r0, r1, part);
+            if (kind == BI_ROW) cta_rows<false, false>(P, r0, r1, part);
+            else cta_rows<true, false>(P, r0, r1, part);
             if (threadIdx.x == 0) {
                 P->rowpart[2 * tile] = part[0];
                 P->rowpart[2 * tile + 1] = part[1];
@@ -895,20 +1076,26 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
                 if (kind == BI_ROW) {
                     q_push(q, P->col_tiles, [&](int t) { return batch_item(BI_COL, p, t); });
                 } else {
-                    cta_finish(P, R, true);
+                    cta_finish<false>(P, R, true);
                     problem_done(q);
                 }
             }
         } else if (kind == BI_COL) {
-            cta_cols(P, tile * kBatchColTile);
+            const bool is_acc = P->method == 1;
+            const StageK K = cta_stage_constants(is_acc, __ldcg(&P->mu));
+            const bool check = is_acc && !__ldcg(&P->first) && P->stability != 0;
+            double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+            cta_cols<false>(P, tile, K, check, ws, lo3, hi3);
+            cta_colrec(P, tile, ws, lo3, hi3);
             if (arrive_last(P, P->col_tiles)) {
-                const bool stop = cta_step(P);
+                const bool stop = cta_step<false>(P, P->col_tiles);
                 if (!stop) {
                     q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
                 } else if (P->evaluate) {
                     q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_FINAL, p, t); });
                 } else {
-                    cta_finish(P, R, true);
+                    cta_finish<false>(P, R, true);
                     problem_done(q);
                 }
             }

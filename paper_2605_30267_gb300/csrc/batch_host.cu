@@ -21,11 +21,14 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Sizes of one problem's arrays, in the order they are carved.
 struct ProbLayout {
-    size_t kh, kl, a, loga, u, fh, fl, mvec, gh, gl, rowpart;
-    size_t total() const { return kh + kl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart; }
+    size_t kh, kl, a, loga, u, fh, fl, mvec, gh, gl, rowpart, colrec;
+    size_t total() const
+    {
+        return kh + kl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart + colrec;
+    }
 };
 
-ProbLayout layout(int64_t n, int64_t m, int row_tiles)
+ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles)
 {
     const int64_t ldm = (m + 3) / 4 * 4, n4 = (n + 3) / 4 * 4;
     ProbLayout L;
@@ -35,6 +38,7 @@ ProbLayout layout(int64_t n, int64_t m, int row_tiles)
     L.mvec = up256((size_t)m * 8);
     L.gh = L.gl = up256((size_t)ldm * 4);
     L.rowpart = up256((size_t)row_tiles * 16);
+    L.colrec = up256((size_t)col_tiles * kBatchColRec * 8);
     return L;
 }
 
@@ -98,7 +102,7 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         P.cmax_enc = 0ull;             // below every encoded value
         P.cmin_enc = ~0ull;            // above every encoded value
         P.cabs_enc = 0ull;
-        lay[k] = layout(q.n, q.m, P.row_tiles);
+        lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles);
         data_bytes += lay[k].total();
         outstanding += (size_t)std::max(P.row_tiles, P.col_tiles);
         for (int r = 0; r < q.n; r += kBatchFormTile)
@@ -146,6 +150,7 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         for (double **v : mv) *v = (double *)take(L.mvec);
         P.Gh = (float *)take(L.gh); P.Gl = (float *)take(L.gl);
         P.rowpart = (double *)take(L.rowpart);
+        P.colrec = (double *)take(L.colrec);
     }
     // initial items, largest problems first
     std::vector<int> order(count);

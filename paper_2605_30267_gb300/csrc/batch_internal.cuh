@@ -39,6 +39,7 @@ struct BatchProb {
     double *b, *logb, *x, *x_prev, *w, *w1, *p_prev, *D_prev, *raw, *D1, *del, *ell;  // m
     float *Gh, *Gl;          // m (padded): k (eps_c x + shift_g) as (hi, lo)
     double *rowpart;         // row tiles x 2 (sum a u, sum cost)
+    double *colrec;          // column tiles x kBatchColRec (step P1 sums and bounds)
     // ---- schedule
     int32_t small;           // 1: the whole solve is one work item
     int32_t row_tiles, rows_per_tile, col_tiles;
@@ -48,7 +49,7 @@ struct BatchProb {
     unsigned long long cmax_enc, cmin_enc, cabs_enc;
     uint32_t nonfinite, pad_c;
     // ---- solver state (written by the CTA that owns the current phase)
-    double k2, eps_c, cost_div, cmax, cmin, cabs, min_loga, log_m;
+    double k2, eps_c, inv_eps, cost_div, cmax, cmin, cabs, min_loga, log_m;
     double shift_g, shift_f, mu, kl_prev, err, dual, cost;
     int32_t steps, stages, m_stage, j_in_stage, failures, first, status, done;
 };
@@ -89,6 +90,9 @@ struct BatchTile {
 constexpr int kBatchThreads = 256;
 constexpr int kBatchColTile = 128;     // columns per column-pass item (32 lanes x 4)
 constexpr int kBatchFormTile = 64;     // formation tile edge
+constexpr int kBatchColWarps = kBatchColTile / 32;   // warps that finish a column tile
+// per column tile: 6 sums for each finishing warp, then 3 minima, 3 maxima
+constexpr int kBatchColRec = 6 * kBatchColWarps + 6;
 
 cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int ntiles,
                               int dmax, cudaStream_t s);
