@@ -234,6 +234,56 @@ int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_proble
 int accsink_batch_last_timing(const accsink_ctx *ctx, float *total_ms, float *form_ms,
                               float *solve_ms);
 
+/* ---- request server: admitted by device memory, potentials kept resident */
+
+/* A server owns a worker thread, a CUDA stream and a memory pool on one
+ * device. Its calls are thread-safe (any client thread). Submitted solves
+ * are admitted in FIFO order while their inputs, outputs and batch workspace
+ * fit in mem_budget_bytes next to the potentials still held by clients;
+ * each admitted group runs as one accsink_solve_batch-style persistent
+ * launch. A request moves QUEUED -> RUNNING -> DONE (or FAILED); its
+ * potentials stay on the device until accsink_server_release. */
+typedef struct accsink_server accsink_server;
+typedef uint64_t accsink_ticket;
+enum { ACCSINK_REQ_QUEUED = 0, ACCSINK_REQ_RUNNING = 1, ACCSINK_REQ_DONE = 2,
+       ACCSINK_REQ_FAILED = 3 };
+
+typedef struct {
+    int64_t queued, solved, failed, batches;
+    int64_t resident_bytes;      /* potentials held for DONE tickets          */
+    int64_t peak_bytes;          /* largest admitted footprint                */
+    int64_t budget_bytes;
+    double busy_ms;              /* device time of all batches                */
+} accsink_server_stats;
+
+int accsink_server_create(int device, size_t mem_budget_bytes, accsink_server **out);
+/* Drops queued requests, waits for the running group, frees everything. */
+void accsink_server_destroy(accsink_server *srv);
+const char *accsink_server_last_error(accsink_server *srv);
+/* Queues one solve. prob_host's pointers (C or X, Y, and a, b) are HOST
+ * pointers that must stay valid until the ticket is DONE or FAILED; they are
+ * copied to the device when the request is admitted. Validation failures
+ * return ACCSINK_ERR_INVALID_ARG without a ticket. */
+int accsink_server_submit(accsink_server *srv, const accsink_problem *prob_host,
+                          const accsink_params *params, accsink_ticket *ticket);
+int accsink_server_poll(accsink_server *srv, accsink_ticket ticket, int32_t *state);
+/* Waits for the ticket (timeout_ms < 0: no limit; ACCSINK_ERR_TIMEOUT when it
+ * runs out). Writes the result and the submit-to-done latency (host clock,
+ * ms; may be NULL) and returns the solve's status. */
+int accsink_server_wait(accsink_server *srv, accsink_ticket ticket, int32_t timeout_ms,
+                        accsink_result *res, double *latency_ms);
+/* Device pointers to a DONE ticket's potentials f (n) and g (m), valid until
+ * the ticket is released. */
+int accsink_server_potentials(accsink_server *srv, accsink_ticket ticket,
+                              const double **f_dev, const double **g_dev);
+int accsink_server_copy_potentials(accsink_server *srv, accsink_ticket ticket,
+                                   double *f_host, double *g_host);
+/* Frees a DONE or FAILED ticket and its potentials. */
+int accsink_server_release(accsink_server *srv, accsink_ticket ticket);
+int accsink_server_get_stats(accsink_server *srv, accsink_server_stats *out);
+/* Work split of the server's batches (NULL: defaults). */
+int accsink_server_set_config(accsink_server *srv, const accsink_batch_config *cfg);
+
 /* ---- single passes (the hot path's steps, for tests and roofline timing) */
 
 /* Every single-pass call serves every cost kind and honours cost_scale: with

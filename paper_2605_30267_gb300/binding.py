@@ -32,7 +32,12 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_row_pass", "accsink_col_lse", "accsink_sinkhorn_map",
             "accsink_transport_cost", "accsink_time_passes", "accsink_launch_geometry",
             "accsink_col_lse_noalloc", "accsink_solve_batch", "accsink_batch_set_config",
-            "accsink_batch_get_config", "accsink_batch_autotune", "accsink_batch_last_timing"]
+            "accsink_batch_get_config", "accsink_batch_autotune", "accsink_batch_last_timing",
+            "accsink_server_create", "accsink_server_destroy", "accsink_server_last_error",
+            "accsink_server_submit", "accsink_server_poll", "accsink_server_wait",
+            "accsink_server_potentials", "accsink_server_copy_potentials",
+            "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config"]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
 class accsink_problem(ct.Structure):
@@ -62,6 +67,13 @@ class accsink_result(ct.Structure):
 class accsink_batch_config(ct.Structure):
     _fields_ = [("small_max_nm", ct.c_int32), ("row_tile_elems", ct.c_int32),
                 ("ctas_per_sm", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class accsink_server_stats(ct.Structure):
+    _fields_ = [("queued", ct.c_int64), ("solved", ct.c_int64), ("failed", ct.c_int64),
+                ("batches", ct.c_int64), ("resident_bytes", ct.c_int64),
+                ("peak_bytes", ct.c_int64), ("budget_bytes", ct.c_int64),
+                ("busy_ms", ct.c_double)]
 
 
 class AccsinkError(RuntimeError):
@@ -115,9 +127,24 @@ def lib():
                                              P(vp), P(vp), P(accsink_result),
                                              P(accsink_batch_config), P(ct.c_float), i32, P(i32)]
         L.accsink_batch_last_timing.argtypes = [vp, P(ct.c_float), P(ct.c_float), P(ct.c_float)]
+        u64 = ct.c_uint64
+        L.accsink_server_create.argtypes = [ct.c_int, ct.c_size_t, P(vp)]
+        L.accsink_server_destroy.argtypes = [vp]
+        L.accsink_server_destroy.restype = None
+        L.accsink_server_last_error.argtypes = [vp]
+        L.accsink_server_last_error.restype = ct.c_char_p
+        L.accsink_server_submit.argtypes = [vp, P(accsink_problem), P(accsink_params), P(u64)]
+        L.accsink_server_poll.argtypes = [vp, u64, P(i32)]
+        L.accsink_server_wait.argtypes = [vp, u64, i32, P(accsink_result), P(dbl)]
+        L.accsink_server_potentials.argtypes = [vp, u64, P(vp), P(vp)]
+        L.accsink_server_copy_potentials.argtypes = [vp, u64, vp, vp]
+        L.accsink_server_release.argtypes = [vp, u64]
+        L.accsink_server_get_stats.argtypes = [vp, P(accsink_server_stats)]
+        L.accsink_server_set_config.argtypes = [vp, P(accsink_batch_config)]
         for name in EXPORTED:
             if name not in ("accsink_destroy", "accsink_params_default", "accsink_last_error",
-                            "accsink_version"):
+                            "accsink_version", "accsink_server_destroy",
+                            "accsink_server_last_error"):
                 getattr(L, name).restype = ct.c_int
         _lib = L
     return _lib
@@ -378,6 +405,124 @@ class Context:
         self._raise(lib().accsink_launch_geometry(self._h, int(n), int(m), int(vec), out))
         keys = ["num_sms", "row_grid", "col_splits", "col_strips", "step_grid", "stat_grid"]
         return dict(zip(keys, list(out)))
+
+
+def problem_host(a, b, C=None, X=None, Y=None, kind="sqeuclid", scale_to_max=False):
+    """Problem struct over HOST numpy arrays (for accsink_server_submit): FP32
+    C or point clouds X, Y (row-major, contiguous), FP64 a, b."""
+    import numpy as np
+    pr = accsink_problem()
+    keep = []
+
+    def host(arr, dtype):
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+        keep.append(arr)
+        return arr.ctypes.data
+
+    pr.a = host(a, np.float64)
+    pr.b = host(b, np.float64)
+    if C is not None:
+        pr.n, pr.m = C.shape
+        pr.cost_kind = COST_DENSE
+        pr.ldc = C.shape[1]
+        pr.C = host(C, np.float32)
+    else:
+        pr.n, pr.d = X.shape
+        pr.m = Y.shape[0]
+        pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+        pr.X = host(X, np.float32)
+        pr.Y = host(Y, np.float32)
+    pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
+    pr._keep = keep
+    return pr
+
+
+class Server:
+    """The request server of include/accsink.h (thread-safe). Each submitted
+    problem's host arrays are kept alive here until its ticket is released."""
+
+    def __init__(self, device: int = 0, mem_budget_bytes: int = 64 << 30):
+        self._h = ct.c_void_p()
+        rc = lib().accsink_server_create(int(device), int(mem_budget_bytes), ct.byref(self._h))
+        if rc != OK:
+            raise AccsinkError(rc, "accsink_server_create failed")
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            lib().accsink_server_destroy(self._h)
+            self._h = ct.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib().accsink_server_last_error(self._h).decode()
+
+    def submit(self, prob: accsink_problem, params: accsink_params) -> int:
+        t = ct.c_uint64()
+        rc = lib().accsink_server_submit(self._h, ct.byref(prob), ct.byref(params), ct.byref(t))
+        if rc != OK:
+            raise AccsinkError(rc, "accsink_server_submit rejected the request")
+        self._keep[t.value] = prob
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ct.c_int32()
+        rc = lib().accsink_server_poll(self._h, ticket, ct.byref(st))
+        if rc != OK:
+            raise AccsinkError(rc, "unknown ticket")
+        return st.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """Returns (status, result, latency_ms); status ERR_TIMEOUT when the
+        wait ran out."""
+        res = accsink_result()
+        lat = ct.c_double()
+        rc = lib().accsink_server_wait(self._h, ticket, int(timeout_ms), ct.byref(res),
+                                       ct.byref(lat))
+        return rc, res, lat.value
+
+    def potentials_dev(self, ticket: int):
+        f, g = ct.c_void_p(), ct.c_void_p()
+        rc = lib().accsink_server_potentials(self._h, ticket, ct.byref(f), ct.byref(g))
+        if rc != OK:
+            raise AccsinkError(rc, "ticket is not DONE")
+        return f.value, g.value
+
+    def copy_potentials(self, ticket: int):
+        import numpy as np
+        pr = self._keep[ticket]
+        f = np.empty(pr.n)
+        g = np.empty(pr.m)
+        rc = lib().accsink_server_copy_potentials(self._h, ticket, ct.c_void_p(f.ctypes.data),
+                                                  ct.c_void_p(g.ctypes.data))
+        if rc != OK:
+            raise AccsinkError(rc, "ticket is not DONE")
+        return f, g
+
+    def release(self, ticket: int):
+        rc = lib().accsink_server_release(self._h, ticket)
+        if rc != OK:
+            raise AccsinkError(rc, "ticket cannot be released")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        s = accsink_server_stats()
+        rc = lib().accsink_server_get_stats(self._h, ct.byref(s))
+        if rc != OK:
+            raise AccsinkError(rc, "stats failed")
+        return {k: getattr(s, k) for k, _ in accsink_server_stats._fields_}
+
+    def set_config(self, small_max_nm=0, row_tile_elems=0, ctas_per_sm=0):
+        c = accsink_batch_config(small_max_nm, row_tile_elems, ctas_per_sm, 0)
+        rc = lib().accsink_server_set_config(self._h, ct.byref(c))
+        if rc != OK:
+            raise AccsinkError(rc, "bad config")
 
 
 def accsink_col_lse_noalloc(prob: accsink_problem, eps, f, ell_out, stream=None) -> int:

@@ -61,31 +61,41 @@ BatchTuning batch_default_tuning(int num_sms)
     return t;
 }
 
-int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, int count,
-              const accsink_problem *probs, const accsink_params *params, double *const *f_out,
-              double *const *g_out, accsink_result *res, cudaStream_t s, std::string &err,
-              BatchTiming *timing)
-{
-    // ---- plan
-    std::vector<BatchProb> hp(count);
-    std::vector<ProbLayout> lay(count);
+namespace {
+
+// The work split and sizes of a batch (host records; device pointers are
+// filled in when the workspace is carved).
+struct BatchPlan {
+    std::vector<BatchProb> hp;
+    std::vector<ProbLayout> lay;
     std::vector<BatchTile> tiles;
-    size_t data_bytes = 0;
+    unsigned long long cap = 0;
+    size_t head_bytes = 0, data_bytes = 0;
+};
+
+void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
+                const accsink_params *params, BatchPlan &pl)
+{
+    pl.hp.assign(count, BatchProb{});
+    pl.lay.resize(count);
+    pl.tiles.clear();
+    pl.data_bytes = 0;
     size_t outstanding = 0;
     for (int k = 0; k < count; ++k) {
         const accsink_problem &q = probs[k];
-        const accsink_params &pp = params[k];
-        BatchProb &P = hp[k];
+        BatchProb &P = pl.hp[k];
         std::memset(&P, 0, sizeof(P));
         P.C = q.C; P.X = q.X; P.Y = q.Y;
         P.a_in = q.a; P.b_in = q.b;
-        P.f_out = f_out[k]; P.g_out = g_out[k];
         P.ldc = q.ldc ? q.ldc : q.m;
         P.n = q.n; P.m = q.m; P.d = q.d; P.kind = q.cost_kind;
         P.scale = q.cost_scale == ACCSINK_SCALE_MAX_TO_ONE ? 1 : 0;
-        P.method = pp.method; P.stability = pp.stability; P.carry = pp.carry;
-        P.max_steps = pp.max_sinkhorn_steps; P.m0 = pp.m0; P.evaluate = pp.evaluate ? 1 : 0;
-        P.eps = pp.eps; P.tol = pp.tol; P.mu0 = pp.mu0;
+        if (params) {
+            const accsink_params &pp = params[k];
+            P.method = pp.method; P.stability = pp.stability; P.carry = pp.carry;
+            P.max_steps = pp.max_sinkhorn_steps; P.m0 = pp.m0; P.evaluate = pp.evaluate ? 1 : 0;
+            P.eps = pp.eps; P.tol = pp.tol; P.mu0 = pp.mu0;
+        }
         P.ldm = ((int64_t)q.m + 3) / 4 * 4;
         const int64_t nm = (int64_t)q.n * q.m;
         P.small = nm <= tn.small_max_nm ? 1 : 0;
@@ -102,18 +112,45 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         P.cmax_enc = 0ull;             // below every encoded value
         P.cmin_enc = ~0ull;            // above every encoded value
         P.cabs_enc = 0ull;
-        lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles);
-        data_bytes += lay[k].total();
+        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles);
+        pl.data_bytes += pl.lay[k].total();
         outstanding += (size_t)std::max(P.row_tiles, P.col_tiles);
         for (int r = 0; r < q.n; r += kBatchFormTile)
-            for (int c = 0; c < q.m; c += kBatchFormTile) tiles.push_back({k, r, c, 0});
+            for (int c = 0; c < q.m; c += kBatchFormTile) pl.tiles.push_back({k, r, c, 0});
     }
-    const unsigned long long cap = pow2_at_least(std::max<unsigned long long>(
+    pl.cap = pow2_at_least(std::max<unsigned long long>(
         4096, 2 * (unsigned long long)(outstanding + count)));
-    const size_t head_bytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchResult) * count) +
-                              up256(sizeof(BatchQueue)) + up256(cap * 8) + up256(cap * 8) +
-                              up256(sizeof(BatchTile) * tiles.size()) + up256(8 * (size_t)count);
-    const size_t need = head_bytes + data_bytes;
+    pl.head_bytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchResult) * count) +
+                    up256(sizeof(BatchQueue)) + up256(pl.cap * 8) + up256(pl.cap * 8) +
+                    up256(sizeof(BatchTile) * pl.tiles.size()) + up256(8 * (size_t)count);
+}
+
+}  // namespace
+
+size_t batch_workspace_bytes(const BatchTuning &tn, int count, const accsink_problem *probs)
+{
+    BatchPlan pl;
+    plan_batch(tn, count, probs, nullptr, pl);
+    return pl.head_bytes + pl.data_bytes;
+}
+
+int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, int count,
+              const accsink_problem *probs, const accsink_params *params, double *const *f_out,
+              double *const *g_out, accsink_result *res, cudaStream_t s, std::string &err,
+              BatchTiming *timing)
+{
+    // ---- plan
+    BatchPlan pl;
+    plan_batch(tn, count, probs, params, pl);
+    std::vector<BatchProb> &hp = pl.hp;
+    const std::vector<ProbLayout> &lay = pl.lay;
+    const std::vector<BatchTile> &tiles = pl.tiles;
+    const unsigned long long cap = pl.cap;
+    for (int k = 0; k < count; ++k) {
+        hp[k].f_out = f_out[k];
+        hp[k].g_out = g_out[k];
+    }
+    const size_t need = pl.head_bytes + pl.data_bytes;
     if (need > ws.bytes) {
         if (env.budget_left && need > env.budget_left) {
             err = "batch workspace of " + std::to_string(need) + " bytes exceeds the budget";

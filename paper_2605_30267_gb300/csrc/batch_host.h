@@ -40,6 +40,9 @@ struct BatchTiming {
 
 BatchTuning batch_default_tuning(int num_sms);
 
+// Device workspace bytes batch_run needs for these problems.
+size_t batch_workspace_bytes(const BatchTuning &tn, int count, const accsink_problem *probs);
+
 // Plans, launches and waits for one batch on stream s. Returns an ACCSINK_*
 // code; res[k] receives each problem's record; err the message on failure.
 int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, int count,

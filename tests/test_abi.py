@@ -63,6 +63,8 @@ int main(void) {
          offsetof(accsink_result, gpu_ms));
   printf("%zu %zu %zu\n", sizeof(accsink_batch_config),
          offsetof(accsink_batch_config, row_tile_elems), offsetof(accsink_batch_config, ctas_per_sm));
+  printf("%zu %zu %zu\n", sizeof(accsink_server_stats),
+         offsetof(accsink_server_stats, resident_bytes), offsetof(accsink_server_stats, busy_ms));
   return 0;
 }
 ''')
@@ -83,6 +85,9 @@ int main(void) {
     c = [int(v) for v in lines[3].split()]
     assert c == [ct.sizeof(B.accsink_batch_config), B.accsink_batch_config.row_tile_elems.offset,
                  B.accsink_batch_config.ctas_per_sm.offset]
+    v = [int(x) for x in lines[4].split()]
+    assert v == [ct.sizeof(B.accsink_server_stats), B.accsink_server_stats.resident_bytes.offset,
+                 B.accsink_server_stats.busy_ms.offset]
 
 
 def test_host_only_calls(L):
