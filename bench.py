@@ -318,6 +318,9 @@ def run_gpu(args):
         if not args.no_batch:
             out["batch_workload"] = measure_batch(ctx, dev, stream, args.batch_count, 3,
                                                   not args.quick, not args.quick)
+        if not args.no_serve:
+            out["serving_workload"] = measure_serving(args.serve_rates, args.serve_window,
+                                                      args.serve_max, 64, 16)
     ctx.close()
     return out
 
@@ -335,6 +338,15 @@ def run_batch_only(args):
                         not args.quick)
     ctx.close()
     return {"metric": METRIC, "batch_workload": out}
+
+
+def run_serve_only(args):
+    """Only the serving workload."""
+    import torch
+    torch.cuda.set_device(0)
+    return {"metric": METRIC,
+            "serving_workload": measure_serving(args.serve_rates, args.serve_window,
+                                                args.serve_max, 64, 16)}
 
 
 def run_points_only(args):
@@ -479,6 +491,98 @@ def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=Tr
     return out
 
 
+SERVE_WORKLOAD = ("serving: Poisson arrivals; requests are squared-Euclidean problems, points "
+                  "uniform in [0,1]^d, d in {2..64}, n, m log-uniform in [64, 16384], Dirichlet(1) "
+                  "marginals, eps log-uniform in [1e-3, 1e-1], tol=1e-6, cost scaled to max 1; "
+                  "64 GB admission budget")
+
+
+def measure_serving(rates, window_s, max_requests, pool_size, solo_count):
+    """The request server at offered Poisson rates: sustained solves/s and the
+    submit-to-done latency (p50/p99, queueing included), beside the same
+    requests served one at a time (each submitted after the previous one
+    completed)."""
+    import threading
+
+    import numpy as np
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+    pool = W.serving_requests(seed=SEED, count=pool_size)
+    probs = [B.problem_host(r["a"], r["b"], X=r["X"], Y=r["Y"], kind="sqeuclid",
+                            scale_to_max=True) for r in pool]
+    params = [B.default_params(eps=r["eps"], tol=r["tol"]) for r in pool]
+    srv = B.Server(0, 64 << 30)
+    out = {"workload": SERVE_WORKLOAD, "pool": pool_size,
+           "mean_nm": float(np.mean([r["X"].shape[0] * r["Y"].shape[0] for r in pool]))}
+    try:
+        # warm-up: every pool request once, all at once
+        ts = [srv.submit(probs[k], params[k]) for k in range(pool_size)]
+        steps = []
+        for t in ts:
+            rc, res, _ = srv.wait(t, 600000)
+            steps.append(res.sinkhorn_steps)
+            srv.release(t)
+        out["steps"] = {"median": int(np.median(steps)), "max": int(max(steps))}
+        # one at a time
+        t0 = time.perf_counter()
+        solo = []
+        for k in range(solo_count):
+            t = srv.submit(probs[k % pool_size], params[k % pool_size])
+            rc, res, lat = srv.wait(t, 600000)
+            solo.append(lat)
+            srv.release(t)
+        solo_s = time.perf_counter() - t0
+        out["one_at_a_time"] = {"requests": solo_count,
+                                "solves_per_s": round(solo_count / solo_s, 2),
+                                "latency_ms": {"p50": round(percentile(solo, 0.5), 3),
+                                               "p99": round(percentile(solo, 0.99), 3)}}
+        # offered rates
+        sweep = []
+        for rate in rates:
+            count = int(min(max_requests, max(8, rate * window_s)))
+            arrivals = W.poisson_arrivals(SEED + int(rate), rate, count)
+            tickets = [None] * count
+            lats = [None] * count
+            done_at = [0.0] * count
+            ready = threading.Event()
+
+            def collect():
+                ready.wait()
+                for i in range(count):
+                    while tickets[i] is None:
+                        time.sleep(0.0002)
+                    rc, res, lat = srv.wait(tickets[i], 600000)
+                    lats[i] = lat
+                    done_at[i] = time.perf_counter()
+                    srv.release(tickets[i])
+
+            th = threading.Thread(target=collect)
+            th.start()
+            start = time.perf_counter()
+            ready.set()
+            for i in range(count):
+                delay = start + arrivals[i] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                k = i % pool_size
+                tickets[i] = srv.submit(probs[k], params[k])
+            th.join()
+            elapsed = max(done_at) - start
+            sweep.append({"offered_per_s": rate, "requests": count,
+                          "sustained_per_s": round(count / elapsed, 2),
+                          "latency_ms": {"p50": round(percentile(lats, 0.5), 3),
+                                         "p99": round(percentile(lats, 0.99), 3)}})
+        out["sweep"] = sweep
+        st = srv.stats()
+        out["server"] = {"batches": st["batches"], "solved": st["solved"], "failed": st["failed"],
+                         "peak_gb": round(st["peak_bytes"] / 1e9, 3),
+                         "busy_s": round(st["busy_ms"] / 1e3, 3)}
+    finally:
+        srv.close()
+    return out
+
+
 def cpu_baseline(pr, acc_steps, evals):
     """The FP64 oracle on the host cores: `evals` S evaluations at full size,
     extrapolated to the Acc step count of the GPU solve."""
@@ -562,6 +666,14 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched workload (profiling)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
+    ap.add_argument("--serve-only", action="store_true", help="run only the serving workload")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[25, 50, 100, 200, 2000],
+                    help="offered Poisson rates (requests/s)")
+    ap.add_argument("--serve-window", type=float, default=3.0,
+                    help="seconds of arrivals per offered rate")
+    ap.add_argument("--serve-max", type=int, default=400,
+                    help="cap on requests per offered rate")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)
@@ -569,6 +681,8 @@ def main():
         out = run_points_only(args)
     elif args.batch_only:
         out = run_batch_only(args)
+    elif args.serve_only:
+        out = run_serve_only(args)
     else:
         out = run_gpu(args)
     if out is not None:

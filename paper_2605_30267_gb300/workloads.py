@@ -175,3 +175,29 @@ def paper_synthetic_problem(seed: int = 0, n: int = 100, m: int = 50, eps: float
     C = uniform_dense_cost(g, n, m)
     return {"C": C, "a": a / a.sum(), "b": b / b.sum(), "eps": eps, "tol": tol,
             "name": f"paper-synthetic n={n} m={m}"}
+
+
+def serving_requests(seed: int = 0, count: int = 64, lo: int = 64, hi: int = 16384,
+                     d_lo: int = 2, d_hi: int = 64, eps_lo: float = 1e-3, eps_hi: float = 1e-1,
+                     tol: float = 1e-6) -> list[dict]:
+    """Requests of the serving workload: squared-Euclidean problems with
+    points uniform in [0,1]^d, d uniform in {d_lo..d_hi}, n and m
+    independently log-uniform in [lo, hi], Dirichlet(1) marginals, eps
+    log-uniform in [eps_lo, eps_hi], cost scaled to max 1."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        d = int(g.integers(d_lo, d_hi + 1))
+        n = int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
+        m = int(round(math.exp(g.uniform(math.log(lo), math.log(hi)))))
+        out.append({"X": uniform_points(g, n, d), "Y": uniform_points(g, m, d),
+                    "a": dirichlet1(g, n), "b": dirichlet1(g, m),
+                    "eps": float(math.exp(g.uniform(math.log(eps_lo), math.log(eps_hi)))),
+                    "tol": tol})
+    return out
+
+
+def poisson_arrivals(seed: int, rate: float, count: int) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate."""
+    g = rng(seed)
+    return np.cumsum(g.exponential(1.0 / rate, size=count))
