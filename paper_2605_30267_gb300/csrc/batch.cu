@@ -192,8 +192,10 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
     double my_dual = 0.0, my_cost = 0.0;
     for (int base = r0; base < r1; base += kBatchThreads) {
         const int rend = min(r1, base + kBatchThreads);
-        for (int r = base + RW * wid; r < rend; r += RW * kBW) {
-            const int nq = min(RW, rend - r);
+        // warp w takes rows r, r + kBW, r + 2 kBW, r + 3 kBW (interleaved, so
+        // short tiles still give every warp a row)
+        for (int r = base + wid; r < rend; r += RW * kBW) {
+            const int nq = min(RW, (rend - r + kBW - 1) / kBW);
             Lse2 acc[RW], cacc[RW];
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
@@ -206,7 +208,7 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
 #pragma unroll
                 for (int q = 0; q < RW; ++q) {
                     if (q < nq) {
-                        const int64_t off = (int64_t)(r + q) * ldm;
+                        const int64_t off = (int64_t)(r + kBW * q) * ldm;
                         const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->Kh + off) + v);
                         const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->Kl + off) + v);
                         const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
@@ -253,7 +255,7 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
                         }
                     }
                     if (lane == 0) {
-                        const int t = r + q - base;
+                        const int t = r + kBW * q - base;
                         sR[t] = Rw;
                         sH[t] = hi;
                         sL[t] = lo;
@@ -460,21 +462,133 @@ __device__ void cta_cols(BatchProb *P, int tile, const StageK &K, bool check, do
     __syncthreads();
 }
 
-// Writes record `rec`: the finishing warps' P1 sums and the CTA's bounds.
+// Column pass over K^T rows [j0, j1) (columns of K) of a large problem: the
+// same warp-per-row log-sum-exp as the row pass with F' as the operand, then
+// per thread one column's ell_j and step phase P1. Each warp's 32 columns are
+// summed over lanes (the tree of the strip column pass) and written, with
+// their bounds, to that warp's slot of its 128-column group's record. j0 is a
+// multiple of 32.
+__device__ void cta_colsT(BatchProb *P, int j0, int j1, const StageK &K, bool check)
+{
+    constexpr int RW = 4;
+    __shared__ float sR[kBatchThreads], sH[kBatchThreads], sL[kBatchThreads];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = P->n;
+    const int64_t ldn = P->ldn;
+    const int n4 = (n + 3) >> 2, nfull = n >> 2;
+    const double shift_f = __ldcg(&P->shift_f), inv_eps = __ldcg(&P->inv_eps);
+    const float4 *F4h = reinterpret_cast<const float4 *>(P->Fh);
+    const float4 *F4l = reinterpret_cast<const float4 *>(P->Fl);
+    for (int base = j0; base < j1; base += kBatchThreads) {
+        const int jend = min(j1, base + kBatchThreads);
+        for (int j = base + wid; j < jend; j += RW * kBW) {
+            const int nq = min(RW, (jend - j + kBW - 1) / kBW);
+            Lse2 acc[RW];
+#pragma unroll
+            for (int q = 0; q < RW; ++q) acc[q] = {-INFINITY, 0.0f, 0.0f};
+            for (int v = lane; v < n4; v += 32) {
+                const float4 fh = __ldcg(F4h + v), fl = __ldcg(F4l + v);
+                const float fa[4] = {fh.x, fh.y, fh.z, fh.w}, fb[4] = {fl.x, fl.y, fl.z, fl.w};
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                    if (q < nq) {
+                        const int64_t off = (int64_t)(j + kBW * q) * ldn;
+                        const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->KTh + off) + v);
+                        const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->KTl + off) + v);
+                        const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
+                        float h[4], l[4], dummy[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float hn = fa[e] - ka[e];        // Fast2Sum: |F'| >= |K|
+                            const float z = hn - fa[e];
+                            l[e] = (fb[e] - kb[e]) + (-ka[e] - z);
+                            h[e] = hn;
+                        }
+                        if (v >= nfull) {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (4 * v + e >= n) { h[e] = -INFINITY; l[e] = 0.0f; }
+                        }
+                        Lse2 none;
+                        slot_accumulate<false>(acc[q], none, h, l, dummy);
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                if (q < nq) {
+                    float Rw, hi, lo;
+                    warp_merge(acc[q], Rw, hi, lo);
+                    if (lane == 0) {
+                        const int t = j + kBW * q - base;
+                        sR[t] = Rw;
+                        sH[t] = hi;
+                        sL[t] = lo;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // finish one column per thread, then per-warp P1 sums and bounds
+        double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+        const int c = base + threadIdx.x;
+        if (c < jend) {
+            const int t = threadIdx.x;
+            const double S = (double)sH[t] + (double)sL[t];
+            const double ell = (double)sR[t] * kLn2 + log(S) - shift_f * inv_eps;
+            P->ell[c] = ell;
+            p1_column<false>(P, c, ell, K.inv_alpha, check, v, lo3, hi3);
+        }
+        double ws[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) ws[q] = warp_sum(v[q]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            double a = lo3[q], b = hi3[q];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+                b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+            }
+            lo3[q] = a;
+            hi3[q] = b;
+        }
+        // this warp's 32 columns lie in one 128-column group (items start on
+        // multiples of 32); write its slot of that group's record if the
+        // columns are this item's
+        const int c0w = base + 32 * wid;
+        if (lane == 0 && c0w < jend) {
+            const int group = c0w / kBatchColTile, slot = (c0w % kBatchColTile) / 32;
+            double *r = P->colrec + (int64_t)group * kBatchColRec + 12 * slot;
+            for (int q = 0; q < 6; ++q) r[q] = ws[q];
+            for (int q = 0; q < 3; ++q) { r[6 + q] = lo3[q]; r[9 + q] = hi3[q]; }
+        }
+        __syncthreads();
+    }
+}
+
+// Writes record `rec`: each finishing warp's P1 sums and bounds (the bounds
+// reduced over the warp's lanes).
 __device__ void cta_colrec(BatchProb *P, int rec, const double (&wsum)[6], double (&lo3)[3],
                            double (&hi3)[3])
 {
-    cta_minmax<3>(lo3, hi3);
-    double *r = P->colrec + (int64_t)rec * kBatchColRec;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0 && wid < kBatchColWarps) {
-        for (int q = 0; q < 6; ++q) r[6 * wid + q] = wsum[q];
-    }
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < 3; ++q) {
-            r[6 * kBatchColWarps + q] = lo3[q];
-            r[6 * kBatchColWarps + 3 + q] = hi3[q];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double a = lo3[q], b = hi3[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmin(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
         }
+        lo3[q] = a;
+        hi3[q] = b;
+    }
+    if (lane == 0 && wid < kBatchColWarps) {
+        double *r = P->colrec + (int64_t)rec * kBatchColRec + 12 * wid;
+        for (int q = 0; q < 6; ++q) r[q] = wsum[q];
+        for (int q = 0; q < 3; ++q) { r[6 + q] = lo3[q]; r[9 + q] = hi3[q]; }
     }
     __syncthreads();
 }
@@ -530,6 +644,16 @@ __device__ bool cta_init(BatchProb *P)
     const double log_m = log((double)m);
     const double shift_g = cabs;
     const double shift_f = cabs - (eps_c * min_loga + cmin - eps_c * log_m);
+    // record slots of the last 128-column group that no column reaches (the
+    // transposed column pass never writes them): neutral sums and bounds
+    if (P->KTh && threadIdx.x < kBatchColWarps) {
+        const int w = threadIdx.x, g = P->col_tiles - 1;
+        if (g * kBatchColTile + 32 * w >= m) {
+            double *r = P->colrec + (int64_t)g * kBatchColRec + 12 * w;
+            for (int q = 0; q < 6; ++q) r[q] = 0.0;
+            for (int q = 0; q < 3; ++q) { r[6 + q] = DBL_MAX; r[9 + q] = -DBL_MAX; }
+        }
+    }
     for (int j = threadIdx.x; j < m; j += kBatchThreads) {
         const double bj = P->b_in[j] / sb;
         P->b[j] = bj;
@@ -595,17 +719,17 @@ __device__ bool cta_step(BatchProb *P, int nrec)
                 for (int w = 0; w < kBatchColWarps; ++w) {
                     double aw = 0.0;
                     for (int t = 0; t < nrec; ++t)
-                        aw += ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec + 6 * w + q]);
+                        aw += ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec + 12 * w + q]);
                     a += aw;
                 }
             } else {
                 const bool mn = q < 9;
                 a = mn ? DBL_MAX : -DBL_MAX;
-                for (int t = 0; t < nrec; ++t) {
-                    const double r = ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec +
-                                                           6 * kBatchColWarps + (q - 6)]);
-                    a = mn ? fmin(a, r) : fmax(a, r);
-                }
+                for (int t = 0; t < nrec; ++t)
+                    for (int w = 0; w < kBatchColWarps; ++w) {
+                        const double r = ldv<LOCAL>(&P->colrec[(int64_t)t * kBatchColRec + 12 * w + q]);
+                        a = mn ? fmin(a, r) : fmax(a, r);
+                    }
             }
             tot_s[q] = a;
         }
@@ -964,6 +1088,7 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                 mn = fmin(mn, v);
                 ab = fmax(ab, fabs(v));
                 put_df(P->Kh, P->Kl, (int64_t)r * P->ldm + c, k * v);
+                if (P->KTh) put_df(P->KTh, P->KTl, (int64_t)c * P->ldn + r, k * v);
             } else if (c < P->ldm) {
                 P->Kh[(int64_t)r * P->ldm + c] = 0.0f;
                 P->Kl[(int64_t)r * P->ldm + c] = 0.0f;
@@ -999,6 +1124,11 @@ __global__ void __launch_bounds__(256) k_batch_scale(BatchProb *Pall, const Batc
             const int64_t i = (int64_t)r * P->ldm + c;
             const double v = (double)P->Kh[i] + (double)P->Kl[i];
             put_df(P->Kh, P->Kl, i, k * v);
+            if (P->KTh) {
+                const int64_t it = (int64_t)c * P->ldn + r;
+                const double vt = (double)P->KTh[it] + (double)P->KTl[it];
+                put_df(P->KTh, P->KTl, it, k * vt);
+            }
         }
     }
 }
@@ -1074,7 +1204,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
             }
             if (arrive_last(P, P->row_tiles)) {
                 if (kind == BI_ROW) {
-                    q_push(q, P->col_tiles, [&](int t) { return batch_item(BI_COL, p, t); });
+                    q_push(q, P->col_items, [&](int t) { return batch_item(BI_COL, p, t); });
                 } else {
                     cta_finish<false>(P, R, true);
                     problem_done(q);
@@ -1084,11 +1214,17 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
             const bool is_acc = P->method == 1;
             const StageK K = cta_stage_constants(is_acc, __ldcg(&P->mu));
             const bool check = is_acc && !__ldcg(&P->first) && P->stability != 0;
-            double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-            cta_cols<false>(P, tile, K, check, ws, lo3, hi3);
-            cta_colrec(P, tile, ws, lo3, hi3);
-            if (arrive_last(P, P->col_tiles)) {
+            if (P->KTh) {
+                const int j0 = tile * P->cols_per_item;
+                cta_colsT(P, j0, min(P->m, j0 + P->cols_per_item), K, check);
+            } else {
+                double ws[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+                double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX};
+                double hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+                cta_cols<false>(P, tile, K, check, ws, lo3, hi3);
+                cta_colrec(P, tile, ws, lo3, hi3);
+            }
+            if (arrive_last(P, P->col_items)) {
                 const bool stop = cta_step<false>(P, P->col_tiles);
                 if (!stop) {
                     q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });

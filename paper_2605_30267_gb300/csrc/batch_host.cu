@@ -21,18 +21,20 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Sizes of one problem's arrays, in the order they are carved.
 struct ProbLayout {
-    size_t kh, kl, a, loga, u, fh, fl, mvec, gh, gl, rowpart, colrec;
+    size_t kh, kl, kth, ktl, a, loga, u, fh, fl, mvec, gh, gl, rowpart, colrec;
     size_t total() const
     {
-        return kh + kl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart + colrec;
+        return kh + kl + kth + ktl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart +
+               colrec;
     }
 };
 
-ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles)
+ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles, bool transposed)
 {
     const int64_t ldm = (m + 3) / 4 * 4, n4 = (n + 3) / 4 * 4;
     ProbLayout L;
     L.kh = L.kl = up256((size_t)n * ldm * 4);
+    L.kth = L.ktl = transposed ? up256((size_t)m * n4 * 4) : 0;
     L.a = L.loga = L.u = up256((size_t)n * 8);
     L.fh = L.fl = up256((size_t)n4 * 4);
     L.mvec = up256((size_t)m * 8);
@@ -98,23 +100,40 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
         }
         P.ldm = ((int64_t)q.m + 3) / 4 * 4;
         const int64_t nm = (int64_t)q.n * q.m;
-        P.small = nm <= tn.small_max_nm ? 1 : 0;
+        // problems from kBatchTransposeMin entries are always tiled over K and
+        // K^T, whatever the split, so a problem's layout (and its last bits)
+        // depends only on its size
+        P.small = (nm <= tn.small_max_nm && nm < kBatchTransposeMin) ? 1 : 0;
         if (P.small) {
             P.rows_per_tile = q.n;
             P.row_tiles = 1;
         } else {
-            int rpt = (int)std::max<int64_t>(1, tn.row_tile_elems / std::max(1, q.m));
+            // at least one row for each of the CTA's warps, so none idles
+            int rpt = (int)std::max<int64_t>(kBatchThreads / 32,
+                                             tn.row_tile_elems / std::max(1, q.m));
             rpt = std::min(rpt, q.n);
             P.rows_per_tile = rpt;
             P.row_tiles = (q.n + rpt - 1) / rpt;
         }
         P.col_tiles = (q.m + kBatchColTile - 1) / kBatchColTile;
+        const bool transposed = nm >= kBatchTransposeMin;
+        P.ldn = ((int64_t)q.n + 3) / 4 * 4;
+        if (transposed) {
+            // column items: K^T rows in whole warps (32), about row_tile_elems each
+            int cpi = (int)std::max<int64_t>(1, tn.row_tile_elems / std::max(1, q.n));
+            cpi = std::max(32, cpi / 32 * 32);
+            P.cols_per_item = cpi;
+            P.col_items = (q.m + cpi - 1) / cpi;
+        } else {
+            P.cols_per_item = kBatchColTile;
+            P.col_items = P.col_tiles;
+        }
         P.cmax_enc = 0ull;             // below every encoded value
         P.cmin_enc = ~0ull;            // above every encoded value
         P.cabs_enc = 0ull;
-        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles);
+        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles, transposed);
         pl.data_bytes += pl.lay[k].total();
-        outstanding += (size_t)std::max(P.row_tiles, P.col_tiles);
+        outstanding += (size_t)std::max(P.row_tiles, P.col_items);
         for (int r = 0; r < q.n; r += kBatchFormTile)
             for (int c = 0; c < q.m; c += kBatchFormTile) pl.tiles.push_back({k, r, c, 0});
     }
@@ -180,6 +199,8 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         const ProbLayout &L = lay[k];
         auto take = [&](size_t b) { char *r = p; p += b; return r; };
         P.Kh = (float *)take(L.kh); P.Kl = (float *)take(L.kl);
+        if (L.kth) { P.KTh = (float *)take(L.kth); P.KTl = (float *)take(L.ktl); }
+        else { P.KTh = nullptr; P.KTl = nullptr; }
         P.a = (double *)take(L.a); P.loga = (double *)take(L.loga); P.u = (double *)take(L.u);
         P.Fh = (float *)take(L.fh); P.Fl = (float *)take(L.fl);
         double **mv[12] = {&P.b, &P.logb, &P.x, &P.x_prev, &P.w, &P.w1, &P.p_prev, &P.D_prev,

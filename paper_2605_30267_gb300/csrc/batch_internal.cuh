@@ -34,6 +34,8 @@ struct BatchProb {
     // ---- workspace
     float *Kh, *Kl;          // n x ldm, k C as (hi, lo); C before scaling
     int64_t ldm;             // m rounded up to 4
+    float *KTh, *KTl;        // m x ldn, the transpose (large problems only, else null)
+    int64_t ldn;             // n rounded up to 4
     double *a, *loga, *u;    // n
     float *Fh, *Fl;          // n (padded): k (eps_c u + shift_f) as (hi, lo)
     double *b, *logb, *x, *x_prev, *w, *w1, *p_prev, *D_prev, *raw, *D1, *del, *ell;  // m
@@ -43,6 +45,7 @@ struct BatchProb {
     // ---- schedule
     int32_t small;           // 1: the whole solve is one work item
     int32_t row_tiles, rows_per_tile, col_tiles;
+    int32_t col_items, cols_per_item;   // column-phase work items (over K^T when present)
     int32_t arrive;          // arrival counter of the phase in flight
     int32_t pad_s;
     // ---- cost statistics from the formation (ordered encodings of FP64)
@@ -91,8 +94,9 @@ constexpr int kBatchThreads = 256;
 constexpr int kBatchColTile = 128;     // columns per column-pass item (32 lanes x 4)
 constexpr int kBatchFormTile = 64;     // formation tile edge
 constexpr int kBatchColWarps = kBatchColTile / 32;   // warps that finish a column tile
-// per column tile: 6 sums for each finishing warp, then 3 minima, 3 maxima
-constexpr int kBatchColRec = 6 * kBatchColWarps + 6;
+constexpr int64_t kBatchTransposeMin = 1 << 20;      // n m from which K^T is also stored
+// per 128-column group: for each finishing warp 6 sums, 3 minima, 3 maxima
+constexpr int kBatchColRec = 12 * kBatchColWarps;
 
 cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int ntiles,
                               int dmax, cudaStream_t s);

@@ -169,6 +169,35 @@ def test_batch_of_one_equals_batch_member(ctx):
         assert r1[0]["sinkhorn_steps"] == rs[k]["sinkhorn_steps"]
 
 
+def large_problems():
+    # m = 777 and 1029 leave the last 128-column group partly empty
+    return [Prob("sqeuclid", 1100, 1000, 31, 1e-2, d=3, scale=True),
+            Prob("cosine", 1500, 777, 32, 2e-2, d=24),
+            Prob("dense", 1031, 1029, 33, 5e-3, scale=True)]
+
+
+def test_large_problems_use_the_transposed_column_pass(ctx):
+    """Problems from 2^20 entries keep K^T too and run the column phase as
+    row tiles over it; parity with the oracle, and identical potentials for
+    two work splits."""
+    probs = large_problems()
+    ctx.accsink_batch_set_config()
+    # leave non-zero values in the workspace first (a larger batch of others)
+    run_batch(ctx, mixed_problems() + large_problems()[::-1])
+    f1, g1, r1 = run_batch(ctx, probs)
+    for p, f, g, r in zip(probs, f1, g1, r1):
+        check_against_oracle(p, f, g, r)
+    ctx.accsink_batch_set_config(small_max_nm=64, row_tile_elems=50000)
+    try:
+        f2, g2, r2 = run_batch(ctx, probs)
+    finally:
+        ctx.accsink_batch_set_config()
+    for k in range(len(probs)):
+        assert r1[k]["sinkhorn_steps"] == r2[k]["sinkhorn_steps"]
+        np.testing.assert_array_equal(f1[k], f2[k])
+        np.testing.assert_array_equal(g1[k], g2[k])
+
+
 def test_word_alignment_shaped_batch(ctx):
     """24 cosine problems with unit-norm Gaussian points in R^300, n, m
     log-uniform in [16, 512], eps in [0.005, 0.05] (the oracle reads the cost
