@@ -147,15 +147,16 @@ __device__ __forceinline__ T ldv(const T *p)
     else return __ldcg(p);
 }
 
-// Lane-tree merge of a warp's (R, S, K) accumulators into one double-float
-// sum about the warp maximum; every lane gets (Rw, hi, lo).
-__device__ __forceinline__ void warp_merge(const Lse2 &a, float &Rw, float &hi, float &lo)
+// Lane-tree merge of (R, S, K) accumulators over each aligned segment of L
+// lanes (L a power of two; L = 32 is the whole warp) into one double-float
+// sum about the segment maximum; every lane of a segment gets (Rw, hi, lo).
+__device__ __forceinline__ void seg_merge(const Lse2 &a, int L, float &Rw, float &hi, float &lo)
 {
-    Rw = warp_max(a.R);
+    Rw = a.R;
+    for (int o = L >> 1; o > 0; o >>= 1) Rw = fmaxf(Rw, __shfl_xor_sync(0xffffffffu, Rw, o));
     const float sc = (a.R == -INFINITY) ? 0.0f : ex2_approx(a.R - Rw);
     two_sum_f(a.S * sc, -a.K * sc, hi, lo);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = L >> 1; o > 0; o >>= 1) {
         const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
         const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
         float s2, e2;
@@ -163,6 +164,32 @@ __device__ __forceinline__ void warp_merge(const Lse2 &a, float &Rw, float &hi, 
         lo = lo + olo + e2;
         two_sum_f(s2, lo, hi, lo);
     }
+}
+
+// The same double-float tree for a second sum `a` kept about the lane's
+// reference R of the first one (Ra) and merged about its segment maximum Rw.
+__device__ __forceinline__ void seg_merge_same_r(const Lse2 &a, float Ra, float Rw, int L,
+                                                 float &hi, float &lo)
+{
+    const float sc = (Ra == -INFINITY) ? 0.0f : ex2_approx(Ra - Rw);
+    two_sum_f(a.S * sc, -a.K * sc, hi, lo);
+    for (int o = L >> 1; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s2, e2;
+        two_sum_f(hi, ohi, s2, e2);
+        lo = lo + olo + e2;
+        two_sum_f(s2, lo, hi, lo);
+    }
+}
+
+// Lanes per row: the smallest power of two covering the row's float4 slots
+// (at most 32), so a warp works on 32 / L short rows at once.
+__device__ __forceinline__ int seg_lanes(int slots)
+{
+    int L = 1;
+    while (L < slots && L < 32) L <<= 1;
+    return L;
 }
 
 // ---------------------------------------------------------------- passes --
@@ -189,26 +216,36 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
     const double inv_eps = ldv<LOCAL>(&P->inv_eps);
     const float4 *G4h = reinterpret_cast<const float4 *>(P->Gh);
     const float4 *G4l = reinterpret_cast<const float4 *>(P->Gl);
+    const int L = seg_lanes(m4), sub = lane / L, li = lane % L;
+    const int nvw = kBW * (32 / L), vw = wid * (32 / L) + sub;
     double my_dual = 0.0, my_cost = 0.0;
     for (int base = r0; base < r1; base += kBatchThreads) {
         const int rend = min(r1, base + kBatchThreads);
-        // warp w takes rows r, r + kBW, r + 2 kBW, r + 3 kBW (interleaved, so
-        // short tiles still give every warp a row)
-        for (int r = base + wid; r < rend; r += RW * kBW) {
-            const int nq = min(RW, (rend - r + kBW - 1) / kBW);
+        // Each row is worked by an aligned segment of L lanes; a warp holds
+        // 32 / L segments ("virtual warps"), and virtual warp vw takes rows
+        // rb + vw + nvw q, q < RW (interleaved, so short tiles still give
+        // every warp a row).
+        for (int rb = base; rb < rend; rb += RW * nvw) {
+            int rq[RW];
+            bool ok[RW];
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                rq[q] = rb + vw + nvw * q;
+                ok[q] = rq[q] < rend;
+            }
             Lse2 acc[RW], cacc[RW];
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
                 acc[q] = {-INFINITY, 0.0f, 0.0f};
                 cacc[q] = {0.0f, 0.0f, 0.0f};
             }
-            for (int v = lane; v < m4; v += 32) {
+            for (int v = li; v < m4; v += L) {
                 const float4 gh = ldv<LOCAL>(G4h + v), gl = ldv<LOCAL>(G4l + v);
                 const float ga[4] = {gh.x, gh.y, gh.z, gh.w}, gb[4] = {gl.x, gl.y, gl.z, gl.w};
 #pragma unroll
                 for (int q = 0; q < RW; ++q) {
-                    if (q < nq) {
-                        const int64_t off = (int64_t)(r + kBW * q) * ldm;
+                    if (ok[q]) {
+                        const int64_t off = (int64_t)rq[q] * ldm;
                         const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->Kh + off) + v);
                         const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->Kl + off) + v);
                         const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
@@ -236,31 +273,16 @@ __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
             }
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
-                if (q < nq) {
-                    float Rw, hi, lo;
-                    warp_merge(acc[q], Rw, hi, lo);
-                    float chi = 0.0f, clo = 0.0f;
-                    if (WC) {
-                        // the cost accumulator shares R with the row accumulator
-                        const float sc = (acc[q].R == -INFINITY) ? 0.0f : ex2_approx(acc[q].R - Rw);
-                        two_sum_f(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float ohi = __shfl_xor_sync(0xffffffffu, chi, o);
-                            const float olo = __shfl_xor_sync(0xffffffffu, clo, o);
-                            float s2, e2;
-                            two_sum_f(chi, ohi, s2, e2);
-                            clo = clo + olo + e2;
-                            two_sum_f(s2, clo, chi, clo);
-                        }
-                    }
-                    if (lane == 0) {
-                        const int t = r + kBW * q - base;
-                        sR[t] = Rw;
-                        sH[t] = hi;
-                        sL[t] = lo;
-                        if (WC) { sCH[t] = chi; sCL[t] = clo; }
-                    }
+                float Rw, hi, lo;
+                seg_merge(acc[q], L, Rw, hi, lo);
+                float chi = 0.0f, clo = 0.0f;
+                if (WC) seg_merge_same_r(cacc[q], acc[q].R, Rw, L, chi, clo);
+                if (li == 0 && ok[q]) {
+                    const int t = rq[q] - base;
+                    sR[t] = Rw;
+                    sH[t] = hi;
+                    sL[t] = lo;
+                    if (WC) { sCH[t] = chi; sCL[t] = clo; }
                 }
             }
         }
@@ -479,20 +501,28 @@ __device__ void cta_colsT(BatchProb *P, int j0, int j1, const StageK &K, bool ch
     const double shift_f = __ldcg(&P->shift_f), inv_eps = __ldcg(&P->inv_eps);
     const float4 *F4h = reinterpret_cast<const float4 *>(P->Fh);
     const float4 *F4l = reinterpret_cast<const float4 *>(P->Fl);
+    const int L = seg_lanes(n4), sub = lane / L, li = lane % L;
+    const int nvw = kBW * (32 / L), vw = wid * (32 / L) + sub;
     for (int base = j0; base < j1; base += kBatchThreads) {
         const int jend = min(j1, base + kBatchThreads);
-        for (int j = base + wid; j < jend; j += RW * kBW) {
-            const int nq = min(RW, (jend - j + kBW - 1) / kBW);
+        for (int jb = base; jb < jend; jb += RW * nvw) {
+            int jq[RW];
+            bool ok[RW];
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                jq[q] = jb + vw + nvw * q;
+                ok[q] = jq[q] < jend;
+            }
             Lse2 acc[RW];
 #pragma unroll
             for (int q = 0; q < RW; ++q) acc[q] = {-INFINITY, 0.0f, 0.0f};
-            for (int v = lane; v < n4; v += 32) {
+            for (int v = li; v < n4; v += L) {
                 const float4 fh = __ldcg(F4h + v), fl = __ldcg(F4l + v);
                 const float fa[4] = {fh.x, fh.y, fh.z, fh.w}, fb[4] = {fl.x, fl.y, fl.z, fl.w};
 #pragma unroll
                 for (int q = 0; q < RW; ++q) {
-                    if (q < nq) {
-                        const int64_t off = (int64_t)(j + kBW * q) * ldn;
+                    if (ok[q]) {
+                        const int64_t off = (int64_t)jq[q] * ldn;
                         const float4 kh = __ldg(reinterpret_cast<const float4 *>(P->KTh + off) + v);
                         const float4 kl = __ldg(reinterpret_cast<const float4 *>(P->KTl + off) + v);
                         const float ka[4] = {kh.x, kh.y, kh.z, kh.w}, kb[4] = {kl.x, kl.y, kl.z, kl.w};
@@ -516,15 +546,13 @@ __device__ void cta_colsT(BatchProb *P, int j0, int j1, const StageK &K, bool ch
             }
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
-                if (q < nq) {
-                    float Rw, hi, lo;
-                    warp_merge(acc[q], Rw, hi, lo);
-                    if (lane == 0) {
-                        const int t = j + kBW * q - base;
-                        sR[t] = Rw;
-                        sH[t] = hi;
-                        sL[t] = lo;
-                    }
+                float Rw, hi, lo;
+                seg_merge(acc[q], L, Rw, hi, lo);
+                if (li == 0 && ok[q]) {
+                    const int t = jq[q] - base;
+                    sR[t] = Rw;
+                    sH[t] = hi;
+                    sL[t] = lo;
                 }
             }
         }
