@@ -1047,11 +1047,36 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                 vals[a][b] = (r < n && c < m) ? (double)P->C[(int64_t)r * P->ldc + c] : 0.0;
             }
     } else {
+        // Cosine: every partial sum of <x, y> lies within +-|x||y|, so a
+        // running sum started at off = 2 |x||y| (rounded up) never drops
+        // below |x||y| >= |x_k y_k|: each step can use Fast2Sum (3 ops, exact)
+        // instead of TwoSum (6), and the offset comes off exactly at the end
+        // (Sterbenz). The tile's row norms come from a first sweep over d.
+        __shared__ float sN[2 * T];
+        float off[4][4];
+        if (kind == 2) {
+            if (threadIdx.x < 2 * T) {
+                const int rr = threadIdx.x % T;
+                const bool isx = threadIdx.x < T;
+                const int g = (isx ? tl.row0 : tl.col0) + rr;
+                const float *row = isx ? P->X + (int64_t)g * d : P->Y + (int64_t)g * d;
+                float nn = 0.0f;
+                if (g < (isx ? n : m))
+                    for (int k = 0; k < d; ++k) nn = fmaf(row[k], row[k], nn);
+                sN[threadIdx.x] = sqrtf(nn) * (1.0f + 0x1p-10f) + 0x1p-100f;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    off[a][b] = 2.0f * sN[4 * ty + a] * sN[T + 4 * tx + b] * (1.0f + 0x1p-10f);
+        }
         float s[4][4], e[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) { s[a][b] = 0.0f; e[a][b] = 0.0f; }
+            for (int b = 0; b < 4; ++b) { s[a][b] = (kind == 2) ? off[a][b] : 0.0f; e[a][b] = 0.0f; }
         for (int k0 = 0; k0 < d; k0 += KC) {
             for (int t = threadIdx.x; t < T * KC; t += 256) {
                 const int rr = t / KC, kk = t % KC;
@@ -1067,25 +1092,33 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                 for (int a = 0; a < 4; ++a) xa[a] = Xs[4 * ty + a][kk];
 #pragma unroll
                 for (int b = 0; b < 4; ++b) yb[b] = Ys[4 * tx + b][kk];
+                if (kind == 1) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < 4; ++a)
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        float p, pe;
-                        if (kind == 1) {
+                        for (int b = 0; b < 4; ++b) {
                             float dh, de;
                             two_sum_f(xa[a], -yb[b], dh, de);       // exact difference
-                            p = dh * dh;
-                            pe = fmaf(dh, dh, -p) + 2.0f * dh * de;  // + de^2 (negligible)
-                        } else {
-                            p = xa[a] * yb[b];
-                            pe = fmaf(xa[a], yb[b], -p);             // exact product error
+                            const float p = dh * dh;
+                            const float pe = fmaf(dh, dh, -p) + 2.0f * dh * de;  // + de^2 (negligible)
+                            float t, te;
+                            two_sum_f(s[a][b], p, t, te);
+                            s[a][b] = t;
+                            e[a][b] += te + pe;
                         }
-                        float t, te;
-                        two_sum_f(s[a][b], p, t, te);
-                        s[a][b] = t;
-                        e[a][b] += te + pe;
-                    }
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const float p = xa[a] * yb[b];
+                            const float pe = fmaf(xa[a], yb[b], -p);  // exact product error
+                            const float t = s[a][b] + p;              // Fast2Sum: |s| >= |p|
+                            const float z = t - s[a][b];
+                            e[a][b] += (p - z) + pe;
+                            s[a][b] = t;
+                        }
+                }
             }
             __syncthreads();
         }
@@ -1093,8 +1126,12 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
-                const double sum = (double)s[a][b] + (double)e[a][b];
-                vals[a][b] = (kind == 1) ? sum : 1.0 - sum;
+                if (kind == 1) {
+                    vals[a][b] = (double)s[a][b] + (double)e[a][b];
+                } else {
+                    const float dot_hi = s[a][b] - off[a][b];     // exact (Sterbenz)
+                    vals[a][b] = 1.0 - ((double)dot_hi + (double)e[a][b]);
+                }
             }
     }
     // statistics and store
