@@ -61,7 +61,8 @@ typedef enum {
 enum { ACCSINK_COST_DENSE = 0, ACCSINK_COST_SQEUCLID = 1, ACCSINK_COST_COSINE = 2 };
 enum { ACCSINK_SCALE_NONE = 0, ACCSINK_SCALE_MAX_TO_ONE = 1 };
 enum { ACCSINK_PLAIN = 0, ACCSINK_ACC = 1 };
-enum { ACCSINK_STAB_OFF = 0, ACCSINK_STAB_REPORT = 1, ACCSINK_STAB_GATE = 2 };
+enum { ACCSINK_STAB_OFF = 0, ACCSINK_STAB_REPORT = 1, ACCSINK_STAB_GATE = 2,
+       ACCSINK_STAB_BACKTRACK = 3 };
 enum { ACCSINK_CARRY_Y = 0, ACCSINK_CARRY_W = 1 };
 
 typedef struct accsink_ctx accsink_ctx;
@@ -96,7 +97,8 @@ typedef struct {
  * one: CARRY_Y keeps y = w / alpha (the state Theorem 1 follows), CARRY_W
  * hands w over unchanged as Algorithm 2 is printed. stability: OFF skips the
  * Theorem 4 test, REPORT counts failures, GATE also restarts the momentum
- * (w <- alpha x) after a failed step. */
+ * (w <- alpha x) after a failed step, BACKTRACK instead ends the homotopy
+ * stage at once (mu <- mu / 2, so the next step uses a smaller alpha). */
 typedef struct {
     int32_t method;
     int32_t m0;

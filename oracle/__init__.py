@@ -30,7 +30,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 DENSE, SQEUCLID, COSINE, DENSE64 = 0, 1, 2, 3
 PLAIN, ACC = 0, 1
-STAB_OFF, STAB_REPORT, STAB_GATE = 0, 1, 2
+STAB_OFF, STAB_REPORT, STAB_GATE, STAB_BACKTRACK = 0, 1, 2, 3
 CONVERGED, MAXITER = 0, 7
 
 
@@ -104,6 +104,8 @@ def _L():
         _lib.orc_solve.argtypes = [vp, d, ct.c_int, d, ct.c_int, ct.c_int,
                                    ct.c_int, ct.c_int, vp, vp, vp, vp]
         _lib.orc_evaluate.argtypes = [vp, d, vp, vp, vp, vp, vp]
+        _lib.orc_plan.argtypes = [vp, d, vp, vp, vp]
+        _lib.orc_barycentric.argtypes = [vp, d, vp, vp, vp, lg, vp]
         _lib.orc_rows_sample.argtypes = [vp, d, vp, vp, vp, lg, vp, vp]
         _lib.orc_cols_sample.argtypes = [vp, d, vp, vp, vp, lg, vp]
         _lib.orc_row_pass_sample.argtypes = [vp, d, vp, vp, vp, lg, vp]
@@ -287,6 +289,23 @@ def evaluate(cost: Cost, eps, a, b, f, g):
     _L().orc_evaluate(cost.ref, float(eps), _p(a), _p(b), _p(f), _p(g), _p(out))
     return {"row_l1": out[0], "col_l1": out[1], "transport_cost": out[2],
             "dual": out[3], "primal": out[4], "mass": out[5]}
+
+
+def plan(cost: Cost, eps, f, g):
+    """The plan P(f, g) as an FP64 n x m matrix."""
+    f, g = _f64(f), _f64(g)
+    P = np.empty((cost.n, cost.m))
+    _L().orc_plan(cost.ref, float(eps), _p(f), _p(g), _p(P))
+    return P
+
+
+def barycentric(cost: Cost, eps, f, g, Z):
+    """out_i = sum_j P_ij Z_j / sum_j P_ij for FP32 features Z (m x dz)."""
+    f, g = _f64(f), _f64(g)
+    Z = np.ascontiguousarray(Z, dtype=np.float32)
+    out = np.empty((cost.n, Z.shape[1]))
+    _L().orc_barycentric(cost.ref, float(eps), _p(f), _p(g), _p(Z), int(Z.shape[1]), _p(out))
+    return out
 
 
 def rows_sample(cost: Cost, eps, f, g, rows):

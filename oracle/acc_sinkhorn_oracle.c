@@ -256,7 +256,7 @@ void orc_stability_terms(long m, const double *b, const double *c_k,
 /* ------------------------------------------------------------------------- */
 
 enum { ORC_PLAIN = 0, ORC_ACC = 1 };
-enum { ORC_STAB_OFF = 0, ORC_STAB_REPORT = 1, ORC_STAB_GATE = 2 };
+enum { ORC_STAB_OFF = 0, ORC_STAB_REPORT = 1, ORC_STAB_GATE = 2, ORC_STAB_BACKTRACK = 3 };
 enum { ORC_CONVERGED = 0, ORC_MAXITER = 7, ORC_BADARG = 1 };
 
 typedef struct {
@@ -302,7 +302,10 @@ static void record(orc_history *h, long e, long m, double err, double dual,
  * Both start from x_0 = w_0 = 0 (Sec. 5 starts from the zero dual variable).
  * Stopping (eq. l1tol): after each S evaluation, stop when the marginal L1
  * error of P(u(x), x) is below tol. The stability gate (mode GATE) restarts
- * the momentum, w_{k+1} <- alpha x_{k+1}, when a condition fails.
+ * the momentum, w_{k+1} <- alpha x_{k+1}, when a condition fails; mode
+ * BACKTRACK instead backtracks on alpha: the current homotopy stage ends at
+ * once, so the next step uses alpha = sqrt(2 mu / 2) (our reading of the
+ * backtracking the paper mentions for Theorem 4's conditions).
  * Between homotopy stages Algorithm 2 hands (x, w) to the next stage as is
  * (carry_y = 0). With carry_y = 1 the stage hand-over keeps y = w / alpha
  * instead, w <- w * alpha_new / alpha_old, which is the state (x_k, y_k) that
@@ -382,7 +385,8 @@ int orc_solve(const orc_problem *p, double tol, int method, double mu0,
             tp = u; u = u1; u1 = tp;
             err = err1;
             dual = dual1;
-            if (++j == m_stage) {                         /* Algorithm 2 */
+            const int back = (stab_mode == ORC_STAB_BACKTRACK) && stab;
+            if (++j == m_stage || back) {                 /* Algorithm 2 */
                 if (carry_y) {
                     double ratio = sqrt(2.0 * (mu / 2.0)) / alpha;
                     for (long q = 0; q < m; ++q) w[q] *= ratio;
@@ -447,6 +451,38 @@ void orc_evaluate(const orc_cost *c, double eps, const double *a,
     out[4] = cost + eps * ent;
     out[5] = mass;
     free(col);
+}
+
+/* The transport plan P_ij = exp((f_i + g_j - C_ij) / eps) (eq. P-from-dual)
+ * of given potentials, n x m row-major. */
+void orc_plan(const orc_cost *c, double eps, const double *f, const double *g,
+              double *P)
+{
+    const long n = c->n, m = c->m;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i)
+        for (long j = 0; j < m; ++j)
+            P[i * m + j] = exp((f[i] + g[j] - orc_cost_entry(c, i, j)) / eps);
+}
+
+/* Barycentric projection of a feature matrix Z (m x dz, row-major) through the
+ * plan: out_i = sum_j P_ij Z_j / sum_j P_ij (Sec. 5, colour transfer maps each
+ * source pixel to the plan-weighted mean of the target colours). */
+void orc_barycentric(const orc_cost *c, double eps, const double *f,
+                     const double *g, const float *Z, long dz, double *out)
+{
+    const long n = c->n, m = c->m;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) {
+        double mass = 0.0;
+        for (long k = 0; k < dz; ++k) out[i * dz + k] = 0.0;
+        for (long j = 0; j < m; ++j) {
+            double pij = exp((f[i] + g[j] - orc_cost_entry(c, i, j)) / eps);
+            mass += pij;
+            for (long k = 0; k < dz; ++k) out[i * dz + k] += pij * (double)Z[j * dz + k];
+        }
+        for (long k = 0; k < dz; ++k) out[i * dz + k] /= mass;
+    }
 }
 
 /* Row sums r_i and transport-cost contributions sum_j C_ij P_ij for a list of

@@ -19,7 +19,7 @@ ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, ERR_MAXITER, ERR_CUDA, ERR_UNSUPPORTED = 4, 5,
 COST_DENSE, COST_SQEUCLID, COST_COSINE = 0, 1, 2
 SCALE_NONE, SCALE_MAX_TO_ONE = 0, 1
 PLAIN, ACC = 0, 1
-STAB_OFF, STAB_REPORT, STAB_GATE = 0, 1, 2
+STAB_OFF, STAB_REPORT, STAB_GATE, STAB_BACKTRACK = 0, 1, 2, 3
 CARRY_Y, CARRY_W = 0, 1
 
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NONPOSITIVE_MARGINAL",

@@ -30,7 +30,7 @@ constexpr double kLog2e = 1.44269504088896340736;
 constexpr double kLn2 = 0.69314718055994530942;
 constexpr int kColStrip = 128;      // columns per column-pass CTA (32 lanes x 4)
 constexpr int kPartStride = 16;     // doubles per block partial in the step kernel
-constexpr int kMaxStages = 64;      // homotopy stages tabulated (mu0 / 2^63 at the last)
+constexpr int kMaxStages = 160;     // homotopy stages tabulated (alpha ~ 1e-24 at the last)
 constexpr int kStageSlots = 8;      // alpha, 1/alpha, 1/(1+alpha), alpha^2-2, kappa1,
                                     // alpha^1.5, alpha_next/alpha, 1/(1+alpha_next)
 

@@ -820,7 +820,8 @@ __device__ bool cta_step(BatchProb *P, int nrec)
         bool stage_end = false;
         if (wupd) {
             r.jst += 1;
-            if (r.jst == r.ms) {
+            // BACKTRACK: a failed stability test ends the stage at once
+            if (r.jst == r.ms || (stab == 3 && r.stab_bits != 0)) {
                 stage_end = true;
                 r.mu_new = mu / 2.0;
                 r.ms = (int)floor(sqrt(2.0) * (double)r.ms) + 1;

@@ -335,7 +335,7 @@ int validate_params(accsink_ctx *ctx, const accsink_params *q)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "m0 must be >= 1");
     if (q->max_sinkhorn_steps < 1)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "max_sinkhorn_steps must be >= 1");
-    if (q->stability < 0 || q->stability > 2)
+    if (q->stability < 0 || q->stability > 3)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown stability mode");
     if (q->carry != ACCSINK_CARRY_Y && q->carry != ACCSINK_CARRY_W)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown carry mode");

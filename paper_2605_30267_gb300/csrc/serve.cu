@@ -359,7 +359,7 @@ int accsink_server_submit(accsink_server *S, const accsink_problem *prob_host,
     if (!(q.eps > 0.0) || !(q.tol > 0.0) || q.max_sinkhorn_steps < 1 ||
         (q.method != ACCSINK_PLAIN && q.method != ACCSINK_ACC) ||
         (q.method == ACCSINK_ACC && (!(q.mu0 > 0.0 && q.mu0 < 1.0) || q.m0 < 1)) ||
-        q.stability < 0 || q.stability > 2 ||
+        q.stability < 0 || q.stability > 3 ||
         (q.carry != ACCSINK_CARRY_Y && q.carry != ACCSINK_CARRY_W))
         return ACCSINK_ERR_INVALID_ARG;
     {

@@ -555,7 +555,8 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     bool stage_end = false;
     if (wupd) {
         jst += 1;
-        if (jst == ms) {
+        // BACKTRACK: a failed stability test ends the stage at once
+        if (jst == ms || (stab == 3 && stab_bits != 0)) {
             stage_end = true;
             mu_new = mu / 2.0;
             ms = (int)floor(sqrt(2.0) * (double)ms) + 1;

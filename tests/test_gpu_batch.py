@@ -112,6 +112,7 @@ def mixed_problems():
         Prob("sqeuclid", 64, 1031, 10, 1e-1, d=5, scale=True, stability=B.STAB_GATE),
         Prob("dense", 257, 300, 11, 1e-2, carry=B.CARRY_W),
         Prob("sqeuclid", 150, 170, 12, 0.5, d=3, spread=4.0),
+        Prob("dense", 120, 100, 13, 1e-2, stability=B.STAB_BACKTRACK),
     ]
 
 

@@ -206,6 +206,9 @@ def test_carry_w_and_gate_modes(ctx):
     check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, carry=B.CARRY_W)
     check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, stability=B.STAB_GATE)
     check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, stability=B.STAB_OFF)
+    f, g, res, ref = check_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC,
+                                 stability=B.STAB_BACKTRACK)
+    assert res["outer_stages"] == ref["outer_stages"]
 
 
 @pytest.mark.parametrize("n,m", [(257, 1000), (1000, 257), (33, 4099)])

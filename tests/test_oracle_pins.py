@@ -425,6 +425,34 @@ def test_gate_restarts_momentum():
     assert rr["history"]["err"][first + 1] != rg["history"]["err"][first + 1]
 
 
+def test_backtracking_halves_mu_at_each_failure():
+    """BACKTRACK follows Algorithm 2's schedule except that a failed check ends
+    the stage at once: replaying the schedule from the recorded stability bits
+    reproduces the recorded mu of every step; runs agree with REPORT until the
+    first failure and both converge."""
+    pr = W.gmm_stored_cost_problem(6, n=50, m=50, eps=1e-2)
+    cost = O.Cost(C=pr["C"])
+    kw = dict(tol=1e-8, method=O.ACC, history=5000)
+    rb = O.solve(cost, pr["a"], pr["b"], pr["eps"], stability=O.STAB_BACKTRACK, **kw)
+    rr = O.solve(cost, pr["a"], pr["b"], pr["eps"], stability=O.STAB_REPORT, **kw)
+    assert rb["status"] == O.CONVERGED and rr["status"] == O.CONVERGED
+    assert rb["stability_failures"] > 0
+    hb = rb["history"]
+    mu, m_stage, j, stages = 0.25, 4, 0, 0
+    for e in range(1, rb["sinkhorn_steps"]):
+        assert hb["mu"][e] == mu, (e, hb["mu"][e], mu)
+        j += 1
+        if j == m_stage or hb["stab"][e] != 0:
+            mu /= 2.0
+            m_stage = int(math.floor(math.sqrt(2.0) * m_stage)) + 1
+            j = 0
+            stages += 1
+    assert rb["outer_stages"] == stages
+    first = int(np.nonzero(rr["history"]["stab"])[0][0])
+    np.testing.assert_array_equal(rr["history"]["err"][:first + 1], hb["err"][:first + 1])
+    assert rr["history"]["err"][first + 1] != hb["err"][first + 1]
+
+
 # --------------------------------------------------------------------------
 # Evaluation of given potentials and fixed-point identity.
 # --------------------------------------------------------------------------
@@ -514,3 +542,34 @@ def test_materialised_cost_reproduces_the_point_cloud_cost():
     # the scale is carried by the matrix
     cs = O.Cost(X=X, Y=Y, kind="sqeuclid", scale_to_max=True)
     np.testing.assert_array_equal(cs.materialised().matrix(), cs.matrix())
+
+
+def test_plan_and_barycentric_projection():
+    """Separable cost C_ij = r_i + s_j: the solution's plan is a b^T, so the
+    barycentric projection of any features is their b-weighted mean in every
+    row; the plan's rows sum to a (the row pass is exact) and it matches the
+    plan evaluate() sums."""
+    g = np.random.default_rng(81)
+    n, m = 7, 11
+    r = np.round(g.random(n) * 64) / 64
+    sv = np.round(g.random(m) * 64) / 64
+    C = (r[:, None] + sv[None, :]).astype(np.float32)
+    a, b = W.dirichlet1(g, n), W.dirichlet1(g, m)
+    cost = O.Cost(C=C)
+    res = O.solve(cost, a, b, 0.1, tol=1e-13, method=O.PLAIN)
+    P = O.plan(cost, 0.1, res["f"], res["g"])
+    np.testing.assert_allclose(P, np.outer(res["a"], res["b"]), rtol=1e-10, atol=1e-15)
+    np.testing.assert_allclose(P.sum(1), res["a"], rtol=1e-12)
+    Z = g.standard_normal((m, 3)).astype(np.float32)
+    bary = O.barycentric(cost, 0.1, res["f"], res["g"], Z)
+    want = (res["b"][:, None] * Z.astype(np.float64)).sum(0)
+    np.testing.assert_allclose(bary, np.tile(want, (n, 1)), rtol=1e-9, atol=1e-12)
+    # the plan of arbitrary potentials: transposition-sensitive, and its total
+    # equals evaluate()'s mass
+    f = g.standard_normal(n) * 0.1
+    gg = g.standard_normal(m) * 0.1
+    P2 = O.plan(cost, 0.3, f, gg)
+    assert P2.shape == (n, m)
+    assert abs(P2[2, 5] - np.exp((f[2] + gg[5] - float(C[2, 5])) / 0.3)) <= 1e-15
+    ev = O.evaluate(cost, 0.3, a, b, f, gg)
+    assert abs(P2.sum() - ev["mass"]) <= 1e-12 * ev["mass"]
