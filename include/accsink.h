@@ -322,6 +322,24 @@ int accsink_transport_cost(accsink_ctx *ctx, const accsink_problem *prob,
                            double eps, const double *f, const double *g,
                            double *cost_out, void *stream);
 
+/* ---- export of a solution (one-off, after a solve; FP64 per entry) ------- */
+
+/* The transport plan P_ij = exp((f_i + g_j - C_ij) / eps) (eq. P-from-dual)
+ * of device potentials f (n), g (m) in cost units (of the scaled cost under
+ * MAX_TO_ONE), any cost kind, written to the caller's device array P_out
+ * (n rows of ld_p >= m entries) as FP32 (dtype 0) or FP64 (dtype 1). Every
+ * entry is formed in FP64 as the problem defines it. */
+int accsink_plan(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                 const double *f, const double *g, void *P_out, int64_t ld_p,
+                 int32_t dtype, void *stream);
+
+/* Barycentric projection of target features through the plan (Sec. 5,
+ * colour transfer): out_i = sum_j P_ij Z_j / sum_j P_ij for device FP32
+ * features Z (m x dz, row-major) into device FP64 out (n x dz). */
+int accsink_barycentric(accsink_ctx *ctx, const accsink_problem *prob, double eps,
+                        const double *f, const double *g, const float *Z, int32_t dz,
+                        double *out, void *stream);
+
 /* ---- measurement -------------------------------------------------------- */
 
 /* Times the two streaming passes alone on `stream` with CUDA events: after

@@ -36,7 +36,8 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_server_create", "accsink_server_destroy", "accsink_server_last_error",
             "accsink_server_submit", "accsink_server_poll", "accsink_server_wait",
             "accsink_server_potentials", "accsink_server_copy_potentials",
-            "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config"]
+            "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config",
+            "accsink_plan", "accsink_barycentric"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
@@ -119,6 +120,8 @@ def lib():
                                           P(ct.c_float), P(ct.c_float)]
         L.accsink_launch_geometry.argtypes = [vp, i32, i32, i32, P(i32)]
         L.accsink_col_lse_noalloc.argtypes = [P(accsink_problem), dbl, vp, vp, vp]
+        L.accsink_plan.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, ct.c_int64, i32, vp]
+        L.accsink_barycentric.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, i32, vp, vp]
         L.accsink_solve_batch.argtypes = [vp, i32, P(accsink_problem), P(accsink_params), vp,
                                           P(vp), P(vp), P(accsink_result)]
         L.accsink_batch_set_config.argtypes = [vp, P(accsink_batch_config)]
@@ -392,6 +395,19 @@ class Context:
         self._raise(lib().accsink_transport_cost(self._h, ct.byref(prob), float(eps), _ptr(f),
                                                  _ptr(g), ct.byref(out), _stream_ptr(stream)))
         return out.value
+
+    def accsink_plan(self, prob, eps, f, g, P_out, stream=None):
+        """P_out: a CUDA float32 or float64 tensor (n x >= m, unit column stride)."""
+        import torch
+        dtype = 1 if P_out.dtype == torch.float64 else 0
+        self._raise(lib().accsink_plan(self._h, ct.byref(prob), float(eps), _ptr(f), _ptr(g),
+                                       _ptr(P_out), int(P_out.stride(0)), dtype,
+                                       _stream_ptr(stream)))
+
+    def accsink_barycentric(self, prob, eps, f, g, Z, out, stream=None):
+        self._raise(lib().accsink_barycentric(self._h, ct.byref(prob), float(eps), _ptr(f),
+                                              _ptr(g), _ptr(Z), int(Z.shape[1]), _ptr(out),
+                                              _stream_ptr(stream)))
 
     def accsink_time_passes(self, prob, eps, g, reps, stream=None):
         r, c = ct.c_float(), ct.c_float()

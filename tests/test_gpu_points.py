@@ -315,3 +315,36 @@ def test_full_size_colour_transfer_solve(ctx, colour_problem):
     np.testing.assert_allclose(r, pr["a"][rows], rtol=2e-6)
     c = O.cols_sample(cost, eps, f, g, cols)
     assert np.abs(c - pr["b"][cols]).sum() <= tol * 32 / m * 50
+
+
+# ------------------------------------------------------------ export --
+
+@pytest.mark.parametrize("kind,scale", [("dense", False), ("sqeuclid", True), ("cosine", False)])
+def test_plan_and_barycentric_match_oracle(ctx, kind, scale):
+    n, m, d, eps = 150, 97, 5, 2e-2
+    g0 = np.random.default_rng(91)
+    if kind == "dense":
+        C = g0.random((n, m)).astype(np.float32)
+        prob = B.problem_dense(to_dev(C), None, None, scale)
+        cost = O.Cost(C=C, scale_to_max=scale)
+        a, b = W.dirichlet1(g0, n), W.dirichlet1(g0, m)
+    else:
+        X, Y, a, b = points_for(kind, 92, n, m, d)
+        prob = B.problem_points(to_dev(X), to_dev(Y), kind, None, None, scale)
+        cost = O.Cost(X=X, Y=Y, kind=kind, scale_to_max=scale)
+    ref = O.solve(cost, a, b, eps, 1e-8)
+    f, g = to_dev(ref["f"]), to_dev(ref["g"])
+    P64 = torch.empty((n, m), dtype=torch.float64, device=DEV)
+    ctx.accsink_plan(prob, eps, f, g, P64)
+    P32 = torch.zeros((n, m + 3), dtype=torch.float32, device=DEV)[:, :m]
+    ctx.accsink_plan(prob, eps, f, g, P32)
+    Z = g0.standard_normal((m, 20)).astype(np.float32)
+    out = torch.empty((n, 20), dtype=torch.float64, device=DEV)
+    ctx.accsink_barycentric(prob, eps, f, g, to_dev(Z), out)
+    torch.cuda.synchronize()
+    Pref = O.plan(cost, eps, ref["f"], ref["g"])
+    np.testing.assert_allclose(P64.cpu().numpy(), Pref, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(P32.cpu().numpy(), Pref.astype(np.float32), rtol=2e-7, atol=1e-37)
+    np.testing.assert_allclose(P64.cpu().numpy().sum(1), ref["a"], rtol=1e-7)
+    np.testing.assert_allclose(out.cpu().numpy(), O.barycentric(cost, eps, ref["f"], ref["g"], Z),
+                               rtol=1e-11, atol=1e-13)
