@@ -290,7 +290,7 @@ def test_invalid_inputs_are_rejected(ctx):
         ctx.accsink_solve(B.problem_dense(to_dev(Cn), ad, bd), B.default_params(), f, g)
     assert e.value.code == B.ERR_NONFINITE
     for kw in ({"eps": 0.0}, {"eps": -1.0}, {"tol": 0.0}, {"mu0": 1.0}, {"m0": 0},
-               {"max_sinkhorn_steps": 0}, {"method": 5}, {"stability": 3}, {"carry": 4}):
+               {"max_sinkhorn_steps": 0}, {"method": 5}, {"stability": 4}, {"carry": 4}):
         with pytest.raises(B.AccsinkError) as e:
             ctx.accsink_solve(B.problem_dense(Cd, ad, bd), B.default_params(**kw), f, g)
         assert e.value.code == B.ERR_INVALID_ARG, kw
