@@ -103,6 +103,12 @@ struct Work {
     float *PXh, *PXl, *PYh, *PYl;
     int64_t ldx, ldy;         // SoA row strides (n, m rounded up to 4)
     double *rowmax;           // n: row maxima of the cost (scaling)
+    // rows split into column parts (warp-per-row pass): per part its
+    // (R, hi, lo) record and cost pair; per row an arrival counter, zero
+    // between passes
+    float4 *prec;
+    float2 *pcrec;
+    uint32_t *pcnt;
     // inputs of the single-pass entry points
     const double *b_src;      // column marginal to copy (may be NULL)
     const double *f_given;    // row potentials weighting the cost sum (may be NULL)
@@ -278,8 +284,13 @@ struct LaunchCfg {
 };
 
 cudaError_t launch_cost_stats(const CostView &cv, const Work &w, int grid, cudaStream_t s);
-cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, bool with_cost,
-                            cudaStream_t s);
+// Work split of the warp-per-row pass: `grid` CTAs; rows [0, nfull) whole,
+// the rows after them in `parts` column parts of part4 float4 slots each.
+struct RowSplit {
+    int grid = 1, nfull = 0, parts = 1, part4 = 0;
+};
+cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, const RowSplit &sp,
+                            bool with_cost, cudaStream_t s);
 cudaError_t launch_col_pass(const CostView &cv, const Work &w, int splits, cudaStream_t s);
 cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
                         const double *b_in, int normalise, cudaStream_t s);
@@ -299,11 +310,15 @@ cudaError_t launch_row_pass_tma(const CostView &cv, const Work &w, int grid, boo
                                 cudaStream_t s);
 cudaError_t setup_row_pass_tma();
 int row_pass_tma_smem_bytes();
-cudaError_t launch_row_pass_warp(const CostView &cv, const Work &w, int grid, bool with_cost,
-                                 cudaStream_t s);
+RowSplit plan_row_split(int rows, int cols, int64_t max_warps);
+// Part records a split pass needs (0 without a split).
+int64_t row_split_records(const RowSplit &r, int rows);
+cudaError_t launch_row_pass_warp(const CostView &cv, const Work &w, int grid,
+                                 const RowSplit &sp, bool with_cost, cudaStream_t s);
 int occupancy_row_pass_warp();
 cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int m,
-                                       const Work &w, int grid, cudaStream_t s);
+                                       const Work &w, int grid, const RowSplit &sp,
+                                       cudaStream_t s);
 cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaStream_t s);
 // Which kernel serves 128-bit-aligned row passes: 0 warp-per-row, 1 TMA.
 int row_kernel_choice();

@@ -54,13 +54,16 @@ struct GraphKey {
     const float *C = nullptr;
     int64_t ldc = 0;
     int n = 0, m = 0, vec = 0, row_grid = 0, splits = 0, step_grid = 0, colt_grid = 0;
+    int row_nfull = 0, row_parts = 0, colt_nfull = 0, colt_parts = 0;
     void *ws = nullptr;
     const float *ct = nullptr;
     bool operator==(const GraphKey &o) const
     {
         return C == o.C && ldc == o.ldc && n == o.n && m == o.m && vec == o.vec &&
                row_grid == o.row_grid && splits == o.splits && step_grid == o.step_grid &&
-               colt_grid == o.colt_grid && ws == o.ws && ct == o.ct;
+               colt_grid == o.colt_grid && row_nfull == o.row_nfull &&
+               row_parts == o.row_parts && colt_nfull == o.colt_nfull &&
+               colt_parts == o.colt_parts && ws == o.ws && ct == o.ct;
     }
 };
 
@@ -77,7 +80,7 @@ struct accsink_ctx {
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
-    int64_t n_cap = -1, m_cap = -1;
+    int64_t n_cap = -1, m_cap = -1, units_cap = 0;
     int splits_cap = 0, rowgrid_cap = 0, hist_cap = 0;
     Work w{};
     DevState *h_state = nullptr;      // pinned
@@ -137,25 +140,33 @@ void free_graph(accsink_ctx *ctx)
     ctx->key = GraphKey();
 }
 
+// Launch geometry of a dense solve. The warp-per-row passes may split the
+// rows of a last wave into column parts (rsplit for C, csplit for C^T);
+// `units` is the number of part records the larger split needs.
 struct Geometry {
     int stat_grid, row_grid, splits, step_grid, vec_grid, colt_grid;
+    RowSplit rsplit, csplit;
+    int64_t units;
 };
 
-// Grid of the warp-per-row kernel for `rows` rows: k rows per warp with
-// k = ceil(rows / resident warps), and just enough warps for that, so every
-// warp gets k or k - 1 rows.
-int warp_rows_grid(const accsink_ctx *ctx, int rows);
+// Warps of the warp-per-row kernel that are resident at once.
+int64_t row_warps_resident(const accsink_ctx *ctx)
+{
+    return (int64_t)ctx->num_sms * ctx->occ_row_warp * 8;
+}
 
 Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
 {
     Geometry g;
     const int S = ctx->num_sms;
     g.stat_grid = std::max(1, std::min(n, 4 * S));
+    g.rsplit = RowSplit();
     if (vec && row_kernel_choice() == 1) {
         // TMA row pass: one CTA per SM
         g.row_grid = std::max(1, std::min(S, n));
     } else if (vec) {
-        g.row_grid = warp_rows_grid(ctx, n);
+        g.rsplit = plan_row_split(n, m, row_warps_resident(ctx));
+        g.row_grid = g.rsplit.grid;
     } else {
         g.row_grid = std::max(1, std::min(S * ctx->occ_row[vec], (n + 1) / 2));
     }
@@ -167,16 +178,10 @@ Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
     // the step kernel's FP64 column work is spread over every SM
     g.step_grid = std::max(1, std::min(S, (m + 63) / 64));
     g.vec_grid = std::max(1, std::min(S, (std::max(n, m) + 63) / 64));
-    g.colt_grid = warp_rows_grid(ctx, m);
+    g.csplit = plan_row_split(m, n, row_warps_resident(ctx));
+    g.colt_grid = g.csplit.grid;
+    g.units = std::max(row_split_records(g.rsplit, n), row_split_records(g.csplit, m));
     return g;
-}
-
-int warp_rows_grid(const accsink_ctx *ctx, int rows)
-{
-    const int64_t max_warps = (int64_t)ctx->num_sms * ctx->occ_row_warp * 8;
-    const int64_t k = (rows + max_warps - 1) / max_warps;
-    const int64_t warps = (rows + k - 1) / k;
-    return (int)std::max<int64_t>(1, (warps + 7) / 8);
 }
 
 // Row stride (elements) of the transposed copy: n rounded up to 4 so every
@@ -205,16 +210,19 @@ bool ensure_ct(accsink_ctx *ctx, int n, int m)
 }
 
 // (Re)allocates the workspace for n x m with the given partial counts.
-int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, int hist)
+int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, int hist,
+                     int64_t units = 0)
 {
     if (n <= ctx->n_cap && m <= ctx->m_cap && splits <= ctx->splits_cap &&
-        row_grid <= ctx->rowgrid_cap && hist <= ctx->hist_cap && ctx->ws)
+        row_grid <= ctx->rowgrid_cap && hist <= ctx->hist_cap && units <= ctx->units_cap &&
+        ctx->ws)
         return ACCSINK_OK;
     const int64_t N = std::max<int64_t>(n, ctx->n_cap);
     const int64_t M = std::max<int64_t>(m, ctx->m_cap);
     const int SP = std::max(splits, ctx->splits_cap);
     const int RG = std::max(row_grid, ctx->rowgrid_cap);
     const int H = std::max(hist, ctx->hist_cap);
+    const int64_t U = std::max<int64_t>(std::max<int64_t>(units, ctx->units_cap), 1);
     const int64_t Mp = (M + 3) / 4 * 4;
     const int S = ctx->num_sms;
     std::vector<size_t> sizes = {
@@ -233,7 +241,8 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
         (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8,
         (size_t)std::max(H, 1) * 32, (size_t)std::max(H, 1) * 4,               // history
         (size_t)kMaxStages * kStageSlots * 8,                                  // stage table
-        sizeof(DevState)};
+        sizeof(DevState),
+        (size_t)U * 16, (size_t)U * 8, (size_t)std::max(N, M) * 4};           // prec pcrec pcnt
     size_t total = 0;
     for (size_t s : sizes) total += align_up(s, 256);
     if (ctx->budget && total > ctx->budget)
@@ -281,7 +290,11 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
     w.h_cond = (double *)take(); w.h_stab = (int32_t *)take();
     w.stage_table = (const double *)take();
     w.st = (DevState *)take();
+    w.prec = (float4 *)take();
+    w.pcrec = (float2 *)take();
+    w.pcnt = (uint32_t *)take();
     ctx->n_cap = N; ctx->m_cap = M; ctx->splits_cap = SP; ctx->rowgrid_cap = RG; ctx->hist_cap = H;
+    ctx->units_cap = U;
     return ACCSINK_OK;
 }
 
@@ -354,9 +367,11 @@ cudaError_t set_state(accsink_ctx *ctx, const DevState &hs, cudaStream_t s)
 cudaError_t launch_passes(const CostView &cv, const Work &w, const Geometry &g, const float *ct,
                           cudaStream_t s)
 {
-    cudaError_t e = launch_row_pass(cv, w, g.row_grid, false, s);
+    cudaError_t e = launch_row_pass(cv, w, g.row_grid, g.rsplit, false, s);
     if (e != cudaSuccess) return e;
-    if (ct) return launch_col_pass_transposed(ct, ct_ld(cv.n), cv.n, cv.m, w, g.colt_grid, s);
+    if (ct)
+        return launch_col_pass_transposed(ct, ct_ld(cv.n), cv.n, cv.m, w, g.colt_grid,
+                                          g.csplit, s);
     return launch_col_pass(cv, w, g.splits, s);
 }
 
@@ -369,6 +384,8 @@ int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const flo
     key.C = cv.C; key.ldc = cv.ldc; key.n = cv.n; key.m = cv.m; key.vec = cv.vec;
     key.row_grid = g.row_grid; key.splits = g.splits; key.step_grid = g.step_grid;
     key.colt_grid = g.colt_grid; key.ct = ct;
+    key.row_nfull = g.rsplit.nfull; key.row_parts = g.rsplit.parts;
+    key.colt_nfull = g.csplit.nfull; key.colt_parts = g.csplit.parts;
     key.ws = ctx->ws;
     Work w = ctx->w;
     w.ignore_done = 0;
@@ -426,7 +443,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     const CostView cv = make_view(prob);
     const int n = prob->n, m = prob->m;
     const Geometry g = geometry(ctx, n, m, cv.vec);
-    int rc = ensure_workspace(ctx, n, m, g.splits, g.row_grid, prm->history);
+    int rc = ensure_workspace(ctx, n, m, g.splits, g.row_grid, prm->history, g.units);
     if (rc != ACCSINK_OK) return rc;
     Work w = ctx->w;
     w.nstat = g.stat_grid;
@@ -509,7 +526,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     if (prm->evaluate) {
         Work we = w;
         we.ignore_done = 1;
-        CK(launch_row_pass(cv, we, g.row_grid, true, s));
+        CK(launch_row_pass(cv, we, g.row_grid, g.rsplit, true, s));
     }
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     // potentials in the units of the (possibly scaled) cost: f = eps u, g = eps x
@@ -820,7 +837,8 @@ int pass_setup(accsink_ctx *ctx, const accsink_problem *prob, double eps, cudaSt
     }
     pl.cv = make_view(prob);
     pl.geo = geometry(ctx, prob->n, prob->m, pl.cv.vec);
-    rc = ensure_workspace(ctx, prob->n, prob->m, pl.geo.splits, pl.geo.row_grid, 0);
+    rc = ensure_workspace(ctx, prob->n, prob->m, pl.geo.splits, pl.geo.row_grid, 0,
+                          pl.geo.units);
     if (rc != ACCSINK_OK) return rc;
     pl.scale = prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE;
     Work &w = pl.w;
@@ -839,7 +857,7 @@ int pass_setup(accsink_ctx *ctx, const accsink_problem *prob, double eps, cudaSt
 cudaError_t plan_row_pass(const PassPlan &pl, const Work &w, bool with_cost, cudaStream_t s)
 {
     if (pl.pts) return launch_points_pass(pl.pp.pr, w, pl.pp.prow, 0, with_cost, s);
-    return launch_row_pass(pl.cv, w, pl.geo.row_grid, with_cost, s);
+    return launch_row_pass(pl.cv, w, pl.geo.row_grid, pl.geo.rsplit, with_cost, s);
 }
 
 // Column pass in the layout the step kernel reads (partials for a dense
@@ -1182,7 +1200,7 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(prob->n), s));
     CK(launch_passes(cv, w, geo, ct, s));                 // warm-up, writes F
     CK(cudaEventRecord(ctx->ev0, s));
-    for (int r = 0; r < reps; ++r) CK(launch_row_pass(cv, w, geo.row_grid, false, s));
+    for (int r = 0; r < reps; ++r) CK(launch_row_pass(cv, w, geo.row_grid, geo.rsplit, false, s));
     CK(cudaEventRecord(ctx->ev1, s));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.0f;
@@ -1191,7 +1209,7 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     CK(cudaEventRecord(ctx->ev0, s));
     for (int r = 0; r < reps; ++r) {
         if (ct) CK(launch_col_pass_transposed(ct, ct_ld(prob->n), prob->n, prob->m, w,
-                                              geo.colt_grid, s));
+                                              geo.colt_grid, geo.csplit, s));
         else CK(launch_col_pass(cv, w, geo.splits, s));
     }
     CK(cudaEventRecord(ctx->ev1, s));

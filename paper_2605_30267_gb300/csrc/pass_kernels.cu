@@ -327,14 +327,14 @@ __global__ void __launch_bounds__(kRowNT) k_row_pass(CostView cv, Work w)
 constexpr int kRowRG = 2;
 constexpr int kRowU = 4;
 
-cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, bool with_cost,
-                            cudaStream_t s)
+cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, const RowSplit &sp,
+                            bool with_cost, cudaStream_t s)
 {
     // 128-bit-aligned costs stream through the TMA pipeline (row_tma.cu);
     // the plain kernel below serves the unaligned layouts.
     if (cv.vec) {
         if (row_kernel_choice() == 1) return launch_row_pass_tma(cv, w, grid, with_cost, s);
-        return launch_row_pass_warp(cv, w, grid, with_cost, s);
+        return launch_row_pass_warp(cv, w, grid, sp, with_cost, s);
     }
     if (cv.vec) {
         if (with_cost) k_row_pass<kRowRG, kRowU, true, true><<<grid, kRowNT, 0, s>>>(cv, w);

@@ -4,8 +4,8 @@
 //   MODE_COL: X = C^T (a transposed copy kept by the solver), operand F
 //             (rows of C): ell_j = LSE_i((f_i - C_ij) / eps).
 //
-// Every warp streams whole rows on its own: no shared memory, no CTA
-// barriers, so no warp ever waits for another. Lanes read 128-bit slots of
+// Every warp streams whole rows on its own: no CTA barrier inside the row
+// loop, so no warp ever waits for another. Lanes read 128-bit slots of
 // the row (a warp covers 512 contiguous bytes per slot); the column operand
 // (G, gamma k) is read through L1, where it stays resident because the cost
 // is read with non-allocating loads. The next chunk of the row is loaded
@@ -14,7 +14,14 @@
 //
 // Per element the arithmetic is the exact-split scheme of the plain row
 // pass. The per-row merge across lanes is done in FP32 double-float (no FP64
-// pipe in the hot loop), and lane 0 finishes the row in FP64.
+// pipe in the hot loop). The FP64 finish of a row (log, u_i, F_i) is
+// deferred: the merged sums wait in a per-warp shared-memory slot, and every
+// 32 rows the warp finishes them together, one row per lane. GB300's FP64
+// rate is 1/64 of FP32, so a finish in one lane per row held the warp (and
+// its next loads) for longer than the finish of 32 rows at once.
+#include <algorithm>
+#include <cstdint>
+
 #include "accsink_internal.cuh"
 
 namespace accsink {
@@ -46,6 +53,22 @@ __device__ __forceinline__ float term_s(float s, float G, float gk, float c, flo
     return ex2_approx(fmaf(t, kh, fmaf(t, kl, q)));
 }
 
+// term_s in two halves: q = e k_hi + gamma k (e the rounding error of
+// s = G - c) before the running reference is known, then the exponential.
+// Same operations and roundings as term_s.
+__device__ __forceinline__ float split_q(float s, float G, float gk, float c, float kh)
+{
+    const float z = s - G;
+    const float e = -c - z;
+    return fmaf(e, kh, gk);
+}
+
+__device__ __forceinline__ float term_q(float s, float q, float R, float kh, float kl)
+{
+    const float t = s - R;
+    return ex2_approx(fmaf(t, kh, fmaf(t, kl, q)));
+}
+
 // Error-free sum of two floats (Knuth 2Sum).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -58,9 +81,116 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 
 enum { MODE_ROW = 0, MODE_COL = 1 };
 
+// A finished row's warp-merged sums, parked in a shared-memory slot of its
+// warp until 32 rows (or the warp's last row) are ready: the FP64 finish
+// (log, u_i, F_i) then runs once for all of them, one row per lane, instead
+// of once per row in lane 0.
+struct Parked {
+    float R, hi, lo, chi, clo;
+    int row;
+};
+
+// Outputs of the FP64 row finish, passed by value to the out-of-line finish
+// (only a few pointers, not the whole parameter block).
+struct FinishOut {
+    double *ell;                        // column pass
+    const double *loga, *a, *f_given;   // row pass
+    double *u;
+    float2 *FF;
+    float *Fh, *Fk;
+};
+
+__device__ __forceinline__ FinishOut finish_out(const Work &w)
+{
+    return FinishOut{w.ell, w.loga, w.a, w.f_given, w.u, w.FF, w.Fh, w.Fk};
+}
+
+// FP64 finish of the parked rows, one per lane: ell_j (column pass), or u_i
+// and the column-pass operand F_i (row pass). Returns the lane's share of
+// the transport-cost sum (WITH_COST), else 0.
 template <int MODE, bool WITH_COST>
-__global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *Oh,
-                                                      const float *Ok, Work w)
+__device__ __noinline__ double finish_parked(const Parked *slots, int count, int lane,
+                                             const DevState *st, FinishOut o, float kh)
+{
+    __syncwarp();
+    if (lane >= count) return 0.0;
+    const Parked p = slots[lane];
+    const int i = p.row;
+    const double S = (double)p.hi + (double)p.lo;
+    if (MODE == MODE_COL) {
+        o.ell[i] = ((double)p.R - st->shift_f) * st->inv_eps_c + log(S);
+        return 0.0;
+    }
+    const double lse = ((double)p.R - st->shift_g) * st->inv_eps_c + log(S);
+    const double ui = o.loga[i] - lse;
+    o.u[i] = ui;
+    const double F = st->eps_c * ui + st->shift_f;
+    const float Fh = (float)F;
+    const float Fl = (float)(F - (double)Fh);
+    o.FF[i] = make_float2(Fh, Fl * kh);
+    o.Fh[i] = Fh;
+    o.Fk[i] = Fl * kh;
+    if (!WITH_COST) return 0.0;
+    const double CS = (double)p.chi + (double)p.clo;
+    const double wi = o.f_given ? exp(o.f_given[i] / st->eps_user + lse) : o.a[i];
+    return wi * (CS / S);
+}
+
+// Double-float (hi, lo) sum over the warp by a fixed xor tree (every lane
+// ends with the total).
+__device__ __forceinline__ void warp_sum_df(float &hi, float &lo)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, ohi, s, e);
+        lo = lo + olo + e;
+        two_sum(s, lo, hi, lo);
+    }
+}
+
+// Merges the column parts of one split row from their records (reference R,
+// double-float sum (hi, lo) relative to R; (chi, clo) for the cost): lane q
+// takes part q, scales it to the common reference (the product split exactly
+// by an FMA), and the warp adds the parts in a fixed order, so the result
+// does not depend on which part finished last.
+template <bool WITH_COST>
+__device__ __noinline__ void merge_parts(const float4 *prec, const float2 *pcrec, int parts,
+                                         int lane, float kh, float kl, float &R, float &hi,
+                                         float &lo, float &chi, float &clo)
+{
+    const bool have = lane < parts;
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 c = make_float2(0.f, 0.f);
+    if (have) {
+        r = __ldcg(prec + lane);
+        if (WITH_COST) c = __ldcg(pcrec + lane);
+    }
+    R = warp_max(have ? r.x : -INFINITY);
+    const float sc = have ? exp2_scaled(r.x - R, kh, kl) : 0.0f;
+    float h = r.y * sc;
+    float l = fmaf(r.y, sc, -h) + r.z * sc;
+    two_sum(h, l, hi, lo);
+    warp_sum_df(hi, lo);
+    if (WITH_COST) {
+        h = c.x * sc;
+        l = fmaf(c.x, sc, -h) + c.y * sc;
+        two_sum(h, l, chi, clo);
+        warp_sum_df(chi, clo);
+    }
+}
+
+// Work units: rows [0, nfull) whole, then every row of [nfull, n) in `parts`
+// column parts: unit nfull + q * parts + p is part p of row nfull + q and
+// covers the float4 slots [p * part4, min(m4, (p + 1) * part4)); the last
+// part of a row also takes its m % 4 ragged columns. The split rows are the
+// ones a last, part-empty wave of whole rows would leave to a few warps.
+template <int MODE, bool WITH_COST>
+__global__ void __launch_bounds__(kWarpNT, WITH_COST ? 2 : 3) k_lse_rows(CostView cv, const float *Oh,
+                                                      const float *Ok, Work w, int nfull,
+                                                      int parts, int part4)
 {
     DevState *st = w.st;
     if (!w.ignore_done && *(volatile int32_t *)&st->done) return;
@@ -68,7 +198,7 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
         st->barrier = 0u;   // for the step kernel
 
     const float kh = st->k_hi, kl = st->k_lo;
-    const int n = cv.n, m = cv.m;
+    const int m = cv.m;
     const int64_t ldc = cv.ldc;
     const int lane = threadIdx.x & 31;
     const int gwarp = (blockIdx.x * kWarpNT + threadIdx.x) >> 5;
@@ -79,20 +209,36 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
     const float4 *Gk4 = reinterpret_cast<const float4 *>(Ok);
     constexpr int kStep = 32 * kU;     // float4 slots per chunk per warp
 
-    double my_dual = 0.0, my_cost = 0.0;   // lane 0
-    for (int i = gwarp; i < n; i += nwarps) {
-        const float4 *row = reinterpret_cast<const float4 *>(cv.C + (int64_t)i * ldc);
+    __shared__ Parked park[kWarpNT / 32][32];
+    Parked *slots = park[threadIdx.x >> 5];
+    double my_cost = 0.0;
+    int parked = 0;
+    for (int unit = gwarp; unit < nfull + (cv.n - nfull) * parts; unit += nwarps) {
+        // (the row and part are recomputed after the chunk loop rather than
+        // kept live across it)
+        int v0 = 0, v1 = m4;
+        const float4 *row;
+        {
+            int i = unit;
+            if (unit >= nfull) {
+                const int q = (unit - nfull) / parts;
+                i = nfull + q;
+                v0 = (unit - nfull - q * parts) * part4;
+                v1 = min(m4, v0 + part4);
+            }
+            row = reinterpret_cast<const float4 *>(cv.C + (int64_t)i * ldc);
+        }
         Acc acc = {0.0f, 0.0f, 0.0f};
         Acc cacc = {0.0f, 0.0f, 0.0f};
         float4 cbuf[kU];
         // prefetch the first chunk
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
-            const int v = lane + 32 * u;
-            cbuf[u] = (v < m4) ? ld_stream4(reinterpret_cast<const float *>(row + v))
+            const int v = v0 + lane + 32 * u;
+            cbuf[u] = (v < v1) ? ld_stream4(reinterpret_cast<const float *>(row + v))
                                : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int vb = 0; vb < m4; vb += kStep) {
+        for (int vb = v0; vb < v1; vb += kStep) {
             float4 c[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) c[u] = cbuf[u];
@@ -101,27 +247,30 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
                 const int v = nb + lane + 32 * u;
-                if (v < m4) cbuf[u] = ld_stream4(reinterpret_cast<const float *>(row + v));
+                if (v < v1) cbuf[u] = ld_stream4(reinterpret_cast<const float *>(row + v));
             }
-            float4 g[kU], gk[kU];
-#pragma unroll
-            for (int u = 0; u < kU; ++u) {
-                const int v = vb + lane + 32 * u;
-                if (v < m4) {
-                    g[u] = __ldg(G4 + v);
-                    gk[u] = __ldg(Gk4 + v);
-                } else {
-                    g[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    gk[u] = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
-                    c[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            float4 sv[kU];
+            // per element: s = G - c (rounded) and q = e k_hi + gamma k with e
+            // the rounding error of s, so that only (s, q) stay live until
+            // the exponentials (c too for the cost sum)
+            float4 sv[kU], qv[kU];
             float cm = acc.R;
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                sv[u] = make_float4(g[u].x - c[u].x, g[u].y - c[u].y, g[u].z - c[u].z,
-                                    g[u].w - c[u].w);
+                const int v = vb + lane + 32 * u;
+                float4 g, gk;
+                if (v < v1) {
+                    g = __ldg(G4 + v);
+                    gk = __ldg(Gk4 + v);
+                } else {
+                    g = make_float4(0.f, 0.f, 0.f, 0.f);
+                    gk = make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+                    c[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                sv[u] = make_float4(g.x - c[u].x, g.y - c[u].y, g.z - c[u].z, g.w - c[u].w);
+                qv[u] = make_float4(split_q(sv[u].x, g.x, gk.x, c[u].x, kh),
+                                    split_q(sv[u].y, g.y, gk.y, c[u].y, kh),
+                                    split_q(sv[u].z, g.z, gk.z, c[u].z, kh),
+                                    split_q(sv[u].w, g.w, gk.w, c[u].w, kh));
                 cm = fmaxf(cm, fmaxf(fmaxf(sv[u].x, sv[u].y), fmaxf(sv[u].z, sv[u].w)));
             }
             if (cm > acc.R) {
@@ -135,10 +284,10 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
             float cs[kU], ccs[kU];
 #pragma unroll
             for (int u = 0; u < kU; ++u) {
-                const float p0 = term_s(sv[u].x, g[u].x, gk[u].x, c[u].x, R, kh, kl);
-                const float p1 = term_s(sv[u].y, g[u].y, gk[u].y, c[u].y, R, kh, kl);
-                const float p2 = term_s(sv[u].z, g[u].z, gk[u].z, c[u].z, R, kh, kl);
-                const float p3 = term_s(sv[u].w, g[u].w, gk[u].w, c[u].w, R, kh, kl);
+                const float p0 = term_q(sv[u].x, qv[u].x, R, kh, kl);
+                const float p1 = term_q(sv[u].y, qv[u].y, R, kh, kl);
+                const float p2 = term_q(sv[u].z, qv[u].z, R, kh, kl);
+                const float p3 = term_q(sv[u].w, qv[u].w, R, kh, kl);
                 cs[u] = (p0 + p1) + (p2 + p3);
                 if (WITH_COST)
                     ccs[u] = fmaf(c[u].x, p0, fmaf(c[u].y, p1, fmaf(c[u].z, p2, c[u].w * p3)));
@@ -147,8 +296,14 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
             kahan(acc, csum);
             if (WITH_COST) kahan(cacc, (ccs[0] + ccs[1]) + (ccs[2] + ccs[3]));
         }
-        // ragged tail (m % 4 columns)
-        if (tail0 + lane < m) {
+        int i = unit, part = 0;
+        if (unit >= nfull) {
+            const int q = (unit - nfull) / parts;
+            i = nfull + q;
+            part = unit - nfull - q * parts;
+        }
+        // ragged tail (m % 4 columns), in the row's last part
+        if ((unit < nfull || part == parts - 1) && tail0 + lane < m) {
             const int j = tail0 + lane;
             const float Gj = Oh[j], Gkj = Ok[j];
             const float c = ld_stream1(cv.C + (int64_t)i * ldc + j);
@@ -165,79 +320,123 @@ __global__ void __launch_bounds__(kWarpNT) k_lse_rows(CostView cv, const float *
             if (WITH_COST) kahan(cacc, c * p);
         }
         // merge the lanes: common reference, then a double-float tree sum
-        const float Rrow = warp_max(acc.R);
+        float Rrow = warp_max(acc.R);
         const float sc = exp2_scaled(acc.R - Rrow, kh, kl);
         float hi, lo;
         two_sum(acc.S * sc, -acc.K * sc, hi, lo);
         float chi = 0.f, clo = 0.f;
         if (WITH_COST) two_sum(cacc.S * sc, -cacc.K * sc, chi, clo);
+        warp_sum_df(hi, lo);
+        if (WITH_COST) warp_sum_df(chi, clo);
+        if (unit >= nfull) {
+            // publish this part; the last of the row's parts merges them
+            const int64_t rbase = (int64_t)(i - nfull) * parts;
+            int last = 0;
+            if (lane == 0) {
+                w.prec[rbase + part] = make_float4(Rrow, hi, lo, 0.0f);
+                if (WITH_COST) w.pcrec[rbase + part] = make_float2(chi, clo);
+                __threadfence();
+                last = atomicAdd(&w.pcnt[i - nfull], 1u) == (unsigned)(parts - 1);
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) continue;
+            __threadfence();
+            merge_parts<WITH_COST>(w.prec + rbase, w.pcrec + rbase, parts, lane, kh, kl, Rrow,
+                                   hi, lo, chi, clo);
+            if (lane == 0) w.pcnt[i - nfull] = 0u;   // ready for the next pass
+        }
+        if (lane == 0) slots[parked] = Parked{Rrow, hi, lo, chi, clo, i};
+        if (++parked == 32) {
+            my_cost += finish_parked<MODE, WITH_COST>(slots, parked, lane, st, finish_out(w), kh);
+            __syncwarp();
+            parked = 0;
+        }
+    }
+    my_cost += finish_parked<MODE, WITH_COST>(slots, parked, lane, st, finish_out(w), kh);
+    if (!WITH_COST) return;
+    // the final pass: per-warp cost sums in a fixed lane order, then per-CTA
+    // partials in a fixed order over the CTA's warps (the dual's <a, u> is
+    // summed by the step kernel from u)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-            const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
-            float s, e;
-            two_sum(hi, ohi, s, e);
-            lo = lo + olo + e;
-            two_sum(s, lo, hi, lo);
-            if (WITH_COST) {
-                const float ochi = __shfl_xor_sync(0xffffffffu, chi, o);
-                const float oclo = __shfl_xor_sync(0xffffffffu, clo, o);
-                two_sum(chi, ochi, s, e);
-                clo = clo + oclo + e;
-                two_sum(s, clo, chi, clo);
-            }
-        }
-        if (MODE == MODE_COL && lane == 0) {
-            const double S = (double)hi + (double)lo;
-            w.ell[i] = ((double)Rrow - st->shift_f) * st->inv_eps_c + log(S);
-        }
-        if (MODE == MODE_ROW && lane == 0) {
-            const double S = (double)hi + (double)lo;
-            const double lse = ((double)Rrow - st->shift_g) * st->inv_eps_c + log(S);
-            const double ui = w.loga[i] - lse;
-            w.u[i] = ui;
-            const double F = st->eps_c * ui + st->shift_f;
-            const float Fh = (float)F;
-            const float Fl = (float)(F - (double)Fh);
-            w.FF[i] = make_float2(Fh, Fl * kh);
-            w.Fh[i] = Fh;
-            w.Fk[i] = Fl * kh;
-            my_dual += w.a[i] * ui;
-            if (WITH_COST) {
-                const double CS = (double)chi + (double)clo;
-                const double wi = w.f_given ? exp(w.f_given[i] / st->eps_user + lse) : w.a[i];
-                my_cost += wi * (CS / S);
-            }
-        }
-    }
-    if (MODE == MODE_COL) return;
-    // per-CTA partials, fixed order over the CTA's warps
-    __shared__ double sh[2][kWarpNT / 32];
-    if (lane == 0) {
-        sh[0][threadIdx.x >> 5] = my_dual;
-        sh[1][threadIdx.x >> 5] = my_cost;
-    }
+    for (int o = 16; o > 0; o >>= 1) my_cost += __shfl_xor_sync(0xffffffffu, my_cost, o);
+    __shared__ double sh[kWarpNT / 32];
+    if (lane == 0) sh[threadIdx.x >> 5] = my_cost;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double d = 0.0, c = 0.0;
-        for (int q = 0; q < kWarpNT / 32; ++q) { d += sh[0][q]; c += sh[1][q]; }
-        w.rowpart[2 * blockIdx.x + 0] = d;
+        double c = 0.0;
+        for (int q = 0; q < kWarpNT / 32; ++q) c += sh[q];
+        w.rowpart[2 * blockIdx.x + 0] = 0.0;
         w.rowpart[2 * blockIdx.x + 1] = c;
     }
 }
 
-cudaError_t launch_row_pass_warp(const CostView &cv, const Work &w, int grid, bool with_cost,
-                                 cudaStream_t s)
+// Plans the units of a warp-per-row pass over `rows` rows of `cols` columns
+// with `max_warps` warps resident. Whole rows fill the full waves; when the
+// rows left for a last wave would leave at least half of the warps idle, each
+// of them is split into P = min(32, max_warps / rest, chunks / 4) parts
+// (parts of at least four chunks; P <= 32 for the merge's one lane per part),
+// and every warp is launched. Otherwise k = ceil(rows / max_warps) rows per
+// warp with just enough warps for that.
+RowSplit plan_row_split(int rows, int cols, int64_t max_warps)
 {
-    if (with_cost) k_lse_rows<MODE_ROW, true><<<grid, kWarpNT, 0, s>>>(cv, w.G, w.Gk, w);
-    else k_lse_rows<MODE_ROW, false><<<grid, kWarpNT, 0, s>>>(cv, w.G, w.Gk, w);
+    constexpr int64_t kChunk4 = 32 * kU;     // float4 slots per chunk
+    constexpr int64_t kMinPartChunks = 4;
+    constexpr int64_t kMaxParts = 32;
+    RowSplit r;
+    const int m4 = cols / 4;
+    const int64_t nch = (m4 + kChunk4 - 1) / kChunk4;
+    max_warps = std::max<int64_t>(1, max_warps);
+    r.nfull = rows;
+    r.parts = 1;
+    r.part4 = m4;
+    const int64_t full = (int64_t)rows / max_warps * max_warps;
+    const int64_t rest = rows - full;
+    if (rest > 0) {
+        const int64_t P = std::min(kMaxParts, std::min(max_warps / rest, nch / kMinPartChunks));
+        if (P >= 2) {
+            const int64_t per = (nch + P - 1) / P;   // chunks per part
+            r.nfull = (int)full;
+            r.part4 = (int)(per * kChunk4);
+            r.parts = (int)((nch + per - 1) / per);  // every part non-empty
+        }
+    }
+    int64_t warps;
+    if (r.parts > 1) {
+        warps = std::min<int64_t>(max_warps, full + rest * r.parts);
+    } else {
+        const int64_t k = std::max<int64_t>(1, (rows + max_warps - 1) / max_warps);
+        warps = (rows + k - 1) / k;
+    }
+    r.grid = (int)std::max<int64_t>(1, (warps + kWarpNT / 32 - 1) / (kWarpNT / 32));
+    return r;
+}
+
+int64_t row_split_records(const RowSplit &r, int rows)
+{
+    return r.parts > 1 ? (int64_t)(rows - r.nfull) * r.parts : 0;
+}
+
+cudaError_t launch_row_pass_warp(const CostView &cv, const Work &w, int grid,
+                                 const RowSplit &sp, bool with_cost, cudaStream_t s)
+{
+    // the final pass (with the cost sum) is never split: its per-CTA cost
+    // partials then do not depend on which warp finished a row
+    if (with_cost) {
+        k_lse_rows<MODE_ROW, true><<<grid, kWarpNT, 0, s>>>(cv, w.G, w.Gk, w, cv.n, 1, cv.m / 4);
+    } else if (sp.parts > 1) {
+        k_lse_rows<MODE_ROW, false><<<grid, kWarpNT, 0, s>>>(cv, w.G, w.Gk, w, sp.nfull, sp.parts,
+                                                              sp.part4);
+    } else {
+        k_lse_rows<MODE_ROW, false><<<grid, kWarpNT, 0, s>>>(cv, w.G, w.Gk, w, cv.n, 1, cv.m / 4);
+    }
     return cudaGetLastError();
 }
 
 // Column pass as a row pass over the transposed cost CT (m x n, row stride
 // ldct, 16-byte aligned rows): ell_j for every column j of C.
 cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int m,
-                                       const Work &w, int grid, cudaStream_t s)
+                                       const Work &w, int grid, const RowSplit &sp,
+                                       cudaStream_t s)
 {
     CostView tv;
     tv.C = CT;
@@ -245,7 +444,11 @@ cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int
     tv.n = m;
     tv.m = n;
     tv.vec = 1;
-    k_lse_rows<MODE_COL, false><<<grid, kWarpNT, 0, s>>>(tv, w.Fh, w.Fk, w);
+    if (sp.parts > 1)
+        k_lse_rows<MODE_COL, false><<<grid, kWarpNT, 0, s>>>(tv, w.Fh, w.Fk, w, sp.nfull, sp.parts,
+                                                              sp.part4);
+    else
+        k_lse_rows<MODE_COL, false><<<grid, kWarpNT, 0, s>>>(tv, w.Fh, w.Fk, w, m, 1, n / 4);
     return cudaGetLastError();
 }
 

@@ -300,7 +300,7 @@ namespace {
 
 // Record slots of a block: sums (FP64) then FP32 bounds stored as doubles.
 enum {
-    R_ERR = 0, R_RAW, R_KL, R_XB, R_C1, R_C2L,          // P1 sums
+    R_ERR = 0, R_RAW, R_KL, R_XB, R_C1, R_C2L, R_AU,    // P1 sums
     R_RAWLO, R_RAWHI, R_XLO, R_XHI, R_WLO, R_WHI,       // P1 bounds
     R_C2R, R_W1LO, R_W1HI,                              // P2
     R_NSLOTS
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     const bool wupd = is_acc && !first;
 
     // ---- P1
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l
+    double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l, <a,u>
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int col_mode = st->col_mode;
     for (int j = tid; j < m; j += nthr) {
@@ -438,11 +438,13 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         w.del[j] = del;
         if (c_out) c_out[j] = bj * exp(del);
     }
+    // <a, u> of the dual (Sec. 5), from the row pass's u in a fixed order
+    for (int i = tid; i < n; i += nthr) v[6] += w.a[i] * w.u[i];
     {
-        __shared__ double shs[6];
-        block_sum_store<6>(v, shs);
+        __shared__ double shs[7];
+        block_sum_store<7>(v, shs);
         block_minmax_f(blo, bhi);
-        if (threadIdx.x < 6) rec[R_ERR + threadIdx.x] = shs[threadIdx.x];
+        if (threadIdx.x < 7) rec[R_ERR + threadIdx.x] = shs[threadIdx.x];
         if (threadIdx.x == 0) {
             rec[R_RAWLO] = blo[0]; rec[R_RAWHI] = bhi[0];
             rec[R_XLO] = blo[1];   rec[R_XHI] = bhi[1];
@@ -452,11 +454,11 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     if (!grid_barrier(st, nb, kBarrierLimitNs)) { bail(); return; }
 
     // ---- P2
-    double t[12];
+    double t[R_WHI + 1];
     {
-        double t6[6];
-        const int ops6[6] = {0, 0, 0, 0, 0, 0};
-        grid_totals<6>(w.steppart, nb, R_ERR, ops6, t6);
+        double t6[7];
+        const int ops6[7] = {0, 0, 0, 0, 0, 0, 0};
+        grid_totals<7>(w.steppart, nb, R_ERR, ops6, t6);
         float blo2[3] = {INFINITY, INFINITY, INFINITY}, bhi2[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
             const double *r = w.steppart + (int64_t)b * kPartStride;
@@ -468,22 +470,14 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             bhi2[2] = fmaxf(bhi2[2], (float)__ldcg(&r[R_WHI]));
         }
         block_minmax_f(blo2, bhi2);
-        for (int k = 0; k < 6; ++k) t[k] = t6[k];
+        for (int k = 0; k < 7; ++k) t[k] = t6[k];
         t[R_RAWLO] = blo2[0]; t[R_RAWHI] = bhi2[0];
         t[R_XLO] = blo2[1];   t[R_XHI] = bhi2[1];
         t[R_WLO] = blo2[2];   t[R_WHI] = bhi2[2];
     }
     const double err = t[R_ERR];
     const double rbar = t[R_RAW] / (double)m;
-    double sum_au = 0.0;
-    {
-        double au[1] = {0.0};
-        const int op1[1] = {0};
-        const int rg = st->row_grid;
-        for (int b = threadIdx.x; b < rg; b += kVecNT) au[0] += __ldcg(&w.rowpart[2 * b]);
-        block_allreduce<1>(au, op1);
-        sum_au = au[0];
-    }
+    const double sum_au = t[R_AU];
     const double dual = st->eps_user * (sum_au + t[R_XB] - 1.0);
     if (mode == STEP_MAP) {
         for (int j = tid; j < m; j += nthr) s_out[j] = st->eps_user * (w.raw[j] - rbar);
