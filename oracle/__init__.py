@@ -18,9 +18,11 @@ here) -- those are "parity unpinned".
 from __future__ import annotations
 
 import ctypes as ct
+import math
 import os
 import subprocess
 import tempfile
+
 
 import numpy as np
 
@@ -103,6 +105,10 @@ def _L():
         _lib.orc_solve.restype = ct.c_int
         _lib.orc_solve.argtypes = [vp, d, ct.c_int, d, ct.c_int, ct.c_int,
                                    ct.c_int, ct.c_int, vp, vp, vp, vp]
+        _lib.orc_solve_from.restype = ct.c_int
+        _lib.orc_solve_from.argtypes = [vp, d, ct.c_int, d, ct.c_int, ct.c_int, ct.c_int,
+                                        ct.c_int, vp, vp, d, lg, lg, ct.c_int, vp, vp, vp,
+                                        vp, vp, vp, vp]
         _lib.orc_evaluate.argtypes = [vp, d, vp, vp, vp, vp, vp]
         _lib.orc_plan.argtypes = [vp, d, vp, vp, vp]
         _lib.orc_barycentric.argtypes = [vp, d, vp, vp, vp, lg, vp]
@@ -244,7 +250,7 @@ def stability_terms(b, c_k, c_k1, x_k, w_k, x_k1, w_k1, alpha):
 
 def solve(cost: Cost, a, b, eps, tol=1e-6, method=ACC, mu0=0.25, m0=4,
           max_steps=100000, stability=STAB_REPORT, history=0, keep_x=False,
-          carry_y=True):
+          carry_y=True, x0=None, w0=None, stage=None):
     """Plain Sinkhorn (method=PLAIN) or Acc-Sinkhorn with homotopy (ACC).
 
     ``carry_y`` selects how Algorithm 2 hands w to the next homotopy stage:
@@ -252,7 +258,12 @@ def solve(cost: Cost, a, b, eps, tol=1e-6, method=ACC, mu0=0.25, m0=4,
     w over unchanged as Algorithm 2 is printed.
     Marginals are normalised to unit mass first. Returns a dict with f, g
     (cost units), status, step counts and, if ``history`` > 0, per-evaluation
-    histories (err, dual, mu, stability bits and optionally the iterates)."""
+    histories (err, dual, mu, stability bits and optionally the iterates).
+
+    ``x0``, ``w0`` (m each) and ``stage`` ({mu, m_stage, j, stages}) start the
+    iteration there instead of at zero with (mu0, m0). The result's ``state``
+    holds the point the iteration would continue from: (x, w) and the stage,
+    so solve(..., x0=s["x"], w0=s["w"], stage=s) resumes it."""
     a, b = normalise(a), normalise(b)
     pr, keep = _problem(cost, eps, a, b)
     f, g = np.empty(cost.n), np.empty(cost.m)
@@ -267,19 +278,46 @@ def solve(cost: Cost, a, b, eps, tol=1e-6, method=ACC, mu0=0.25, m0=4,
         h["x"] = np.full((history, cost.m), np.nan) if keep_x else None
         hist = _History(history, _p(h["err"]), _p(h["dual"]), _p(h["mu"]),
                         _p(h["stab"]), _p(h["x"]))
-    st = _L().orc_solve(ct.byref(pr), float(tol), int(method), float(mu0), int(m0),
-                        int(max_steps), int(stability), int(bool(carry_y)),
-                        _p(f), _p(g), ct.byref(res),
-                        ct.byref(hist) if hist is not None else None)
+    x0 = None if x0 is None else _f64(x0)
+    w0 = None if w0 is None else _f64(w0)
+    stage = stage or {"mu": mu0, "m_stage": m0, "j": 0, "stages": 0}
+    xo, wo, so = np.empty(cost.m), np.empty(cost.m), np.zeros(4)
+    st = _L().orc_solve_from(ct.byref(pr), float(tol), int(method), float(mu0), int(m0),
+                             int(max_steps), int(stability), int(bool(carry_y)),
+                             _p(x0) if x0 is not None else None,
+                             _p(w0) if w0 is not None else None,
+                             float(stage["mu"]), int(stage["m_stage"]), int(stage["j"]),
+                             int(stage["stages"]), _p(f), _p(g), ct.byref(res),
+                             ct.byref(hist) if hist is not None else None,
+                             _p(xo), _p(wo), _p(so))
     if st not in (CONVERGED, MAXITER):
         raise ValueError(f"oracle rejected the arguments (status {st})")
     out = {"f": f, "g": g, "status": res.status, "sinkhorn_steps": res.sinkhorn_steps,
            "outer_stages": res.outer_stages, "stability_failures": res.stability_failures,
-           "marginal_l1": res.marginal_l1, "dual": res.dual, "a": a, "b": b}
+           "marginal_l1": res.marginal_l1, "dual": res.dual, "a": a, "b": b,
+           "state": {"x": xo, "w": wo, "mu": so[0], "m_stage": int(so[1]), "j": int(so[2]),
+                     "stages": int(so[3]), "eps": float(eps)}}
     if history > 0:
         k = min(res.sinkhorn_steps, history)
         out["history"] = {key: (v[:k] if v is not None else None) for key, v in h.items()}
     return out
+
+
+def warm_start(cost: Cost, a, b, eps, g0, mu0=0.25, m0=4, **kw):
+    """Acc or plain Sinkhorn started at the potential g0 (cost units) instead
+    of zero: x0 = g0 / eps and, for Algorithm 1, w0 = alpha0 x0 (y0 = x0)
+    with alpha0 = sqrt(2 mu0)."""
+    x0 = _f64(g0) / eps
+    return solve(cost, a, b, eps, mu0=mu0, m0=m0, x0=x0, w0=math.sqrt(2.0 * mu0) * x0, **kw)
+
+
+def resume(cost: Cost, a, b, eps, state, mu0=0.25, m0=4, **kw):
+    """Continues a solve from its returned ``state`` (x, w, stage, eps). At a
+    new eps the iterate keeps its potential g = eps x: x and w are scaled by
+    state eps / eps."""
+    mul = state["eps"] / eps
+    return solve(cost, a, b, eps, mu0=mu0, m0=m0, x0=state["x"] * mul,
+                 w0=state["w"] * mul, stage=state, **kw)
 
 
 def evaluate(cost: Cost, eps, a, b, f, g):

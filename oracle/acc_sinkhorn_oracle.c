@@ -312,19 +312,37 @@ static void record(orc_history *h, long e, long m, double err, double dual,
  * Theorem 1 follows from stage to stage.
  * a and b must be positive and sum to one. f_out (n) and g_out (m) receive
  * eps*u and eps*x at the returned iterate.
+ *
+ * orc_solve_from starts the same iteration from a given point instead of
+ * zero: x0 and w0 (m each; NULL means zero) and the homotopy position
+ * (mu_start, m_stage_start, j_start inner steps taken, stages_start stages
+ * completed). The loop is unchanged: its first S evaluation is at x0. When
+ * x_out / w_out / stage_out are given they receive the loop's state at the
+ * return, (x, w) and {mu, m_stage, j, stages}: the point the loop would
+ * continue from, so a second call started there repeats S(x) once and then
+ * takes exactly the steps an uninterrupted run would have taken.
  */
-int orc_solve(const orc_problem *p, double tol, int method, double mu0,
-              int m0, int max_steps, int stab_mode, int carry_y,
-              double *f_out, double *g_out, orc_result *res,
-              orc_history *hist)
+int orc_solve_from(const orc_problem *p, double tol, int method, double mu0,
+                   int m0, int max_steps, int stab_mode, int carry_y,
+                   const double *x0, const double *w0, double mu_start,
+                   long m_stage_start, long j_start, int stages_start,
+                   double *f_out, double *g_out, orc_result *res,
+                   orc_history *hist, double *x_out, double *w_out,
+                   double *stage_out)
 {
     const long n = p->cost->n, m = p->cost->m;
     if (n < 1 || m < 1 || !(p->eps > 0) || !(tol > 0) || max_steps < 1)
         return ORC_BADARG;
     if (method == ORC_ACC && !(mu0 > 0 && mu0 < 1 && m0 >= 1)) return ORC_BADARG;
+    if (method == ORC_ACC &&
+        !(mu_start > 0 && m_stage_start >= 1 && j_start >= 0 && j_start < m_stage_start &&
+          stages_start >= 0))
+        return ORC_BADARG;
 
     double *x = calloc((size_t)m, sizeof(double));
     double *w = calloc((size_t)m, sizeof(double));
+    if (x0) memcpy(x, x0, sizeof(double) * (size_t)m);
+    if (w0) memcpy(w, w0, sizeof(double) * (size_t)m);
     double *s = malloc(sizeof(double) * (size_t)m);
     double *c = malloc(sizeof(double) * (size_t)m);
     double *u = malloc(sizeof(double) * (size_t)n);
@@ -335,6 +353,7 @@ int orc_solve(const orc_problem *p, double tol, int method, double mu0,
     double *u1 = malloc(sizeof(double) * (size_t)n);
 
     memset(res, 0, sizeof(*res));
+    res->outer_stages = stages_start;
     int steps = 0, status = ORC_MAXITER;
     double err = orc_sinkhorn_map(p, x, u, c, s);
     steps = 1;
@@ -352,8 +371,8 @@ int orc_solve(const orc_problem *p, double tol, int method, double mu0,
             ++steps;
         }
     } else {
-        double mu = mu0;
-        long m_stage = m0, j = 0;
+        double mu = mu_start;
+        long m_stage = m_stage_start, j = j_start;
         for (;;) {
             if (err < tol) { status = ORC_CONVERGED; break; }
             if (steps >= max_steps) break;
@@ -397,7 +416,15 @@ int orc_solve(const orc_problem *p, double tol, int method, double mu0,
                 res->outer_stages++;
             }
         }
+        if (stage_out) {
+            stage_out[0] = mu;
+            stage_out[1] = (double)m_stage;
+            stage_out[2] = (double)j;
+            stage_out[3] = (double)res->outer_stages;
+        }
     }
+    if (x_out) memcpy(x_out, x, sizeof(double) * (size_t)m);
+    if (w_out) memcpy(w_out, w, sizeof(double) * (size_t)m);
 
     for (long i = 0; i < n; ++i) f_out[i] = p->eps * u[i];
     for (long q = 0; q < m; ++q) g_out[q] = p->eps * x[q];
@@ -409,6 +436,15 @@ int orc_solve(const orc_problem *p, double tol, int method, double mu0,
     free(x); free(w); free(s); free(c); free(u);
     free(x1); free(w1); free(s1); free(c1); free(u1);
     return status;
+}
+
+int orc_solve(const orc_problem *p, double tol, int method, double mu0,
+              int m0, int max_steps, int stab_mode, int carry_y,
+              double *f_out, double *g_out, orc_result *res,
+              orc_history *hist)
+{
+    return orc_solve_from(p, tol, method, mu0, m0, max_steps, stab_mode, carry_y, NULL, NULL,
+                          mu0, m0, 0, 0, f_out, g_out, res, hist, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------- */

@@ -573,3 +573,70 @@ def test_plan_and_barycentric_projection():
     assert abs(P2[2, 5] - np.exp((f[2] + gg[5] - float(C[2, 5])) / 0.3)) <= 1e-15
     ev = O.evaluate(cost, 0.3, a, b, f, gg)
     assert abs(P2.sum() - ev["mass"]) <= 1e-12 * ev["mass"]
+
+
+# --------------------------------------------------------------------------
+# Warm starts and resumed solves (Algorithm 1-2 from a given point).
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("method,carry_y,stability", [
+    (O.ACC, True, O.STAB_REPORT), (O.ACC, False, O.STAB_REPORT), (O.ACC, True, O.STAB_GATE),
+    (O.ACC, True, O.STAB_BACKTRACK), (O.PLAIN, True, O.STAB_REPORT)])
+def test_resume_matches_the_uninterrupted_run(method, carry_y, stability):
+    # A solve stopped at a loose tolerance and resumed from its state repeats
+    # S(x) once and then takes exactly the uninterrupted run's steps: the
+    # stage position, the momentum (gate and carry included) and the iterate
+    # all carry over, so the final potentials are identical to the bit.
+    pr = W.gmm_stored_cost_problem(21, n=50, m=40, eps=2e-2)
+    cost, a, b, eps = O.Cost(C=pr["C"]), pr["a"], pr["b"], pr["eps"]
+    kw = dict(method=method, carry_y=carry_y, stability=stability)
+    # (w handed over unchanged between stages stalls near 1e-9 on this problem)
+    tol = 1e-10 if carry_y else 1e-8
+    full = O.solve(cost, a, b, eps, tol=tol, history=4000, **kw)
+    part = O.solve(cost, a, b, eps, tol=1e-3, **kw)
+    res = O.resume(cost, a, b, eps, part["state"], tol=tol, history=4000, **kw)
+    assert full["status"] == O.CONVERGED
+    k = part["sinkhorn_steps"]
+    assert 1 < k < full["sinkhorn_steps"]
+    assert res["sinkhorn_steps"] == full["sinkhorn_steps"] - k + 1
+    np.testing.assert_array_equal(res["g"], full["g"])
+    np.testing.assert_array_equal(res["f"], full["f"])
+    np.testing.assert_array_equal(res["history"]["err"][1:], full["history"]["err"][k:])
+    if method == O.ACC:
+        assert res["outer_stages"] == full["outer_stages"]
+        assert part["state"]["mu"] == 0.25 * 2.0 ** -part["state"]["stages"]
+
+
+def test_warm_start_at_the_fixed_point_stops_at_once():
+    pr = W.gmm_stored_cost_problem(22, n=40, m=30, eps=1e-2)
+    cost, a, b, eps = O.Cost(C=pr["C"]), pr["a"], pr["b"], pr["eps"]
+    ref = O.solve(cost, a, b, eps, tol=1e-12)
+    for method in (O.ACC, O.PLAIN):
+        r = O.warm_start(cost, a, b, eps, ref["g"], tol=1e-9, method=method)
+        assert r["status"] == O.CONVERGED and r["sinkhorn_steps"] == 1
+
+
+def test_warm_start_from_zero_is_the_cold_start():
+    pr = W.gmm_stored_cost_problem(23, n=30, m=40, eps=2e-2)
+    cost, a, b, eps = O.Cost(C=pr["C"]), pr["a"], pr["b"], pr["eps"]
+    cold = O.solve(cost, a, b, eps, tol=1e-9)
+    warm = O.warm_start(cost, a, b, eps, np.zeros(40), tol=1e-9)
+    assert warm["sinkhorn_steps"] == cold["sinkhorn_steps"]
+    np.testing.assert_array_equal(warm["g"], cold["g"])
+
+
+def test_eps_continuation_reaches_the_unique_fixed_point():
+    # A state taken at eps1 resumed at eps2 keeps its potential g = eps x and
+    # converges to the eps2 solution (unique up to the gauge, Sec. 2).
+    pr = W.gmm_stored_cost_problem(24, n=40, m=35, eps=1e-2)
+    cost, a, b = O.Cost(C=pr["C"]), pr["a"], pr["b"]
+    e1, e2 = 5e-2, 1e-2
+    s1 = O.solve(cost, a, b, e1, tol=1e-4)
+    r = O.resume(cost, a, b, e2, s1["state"], tol=1e-11, history=2, keep_x=True)
+    np.testing.assert_allclose(e2 * r["history"]["x"][0], s1["state"]["x"] * e1, rtol=1e-15,
+                               atol=1e-300)
+    cold = O.solve(cost, a, b, e2, tol=1e-11)
+    assert r["status"] == O.CONVERGED
+    sh = r["g"].mean() - cold["g"].mean()
+    np.testing.assert_allclose(r["g"] - sh, cold["g"], atol=1e-6 * e2)
+    np.testing.assert_allclose(r["f"] + sh, cold["f"], atol=1e-6 * e2)
