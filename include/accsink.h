@@ -174,6 +174,60 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
                        double *f_out_host, double *g_out_host,
                        accsink_result *res);
 
+/* ---- warm starts and resumed solves ------------------------------------- */
+
+/* State of Algorithm 1-2 (Sec. 4) at the end of a solve: the point the
+ * iteration would continue from. x is the iterate (g = eps x in cost units),
+ * w the momentum of Algorithm 1 after that step's update (gate and stage
+ * hand-over applied), and the homotopy position of Algorithm 2. x and w are
+ * caller-owned DEVICE arrays of m doubles. The shift fields are the solver's
+ * operand offsets and the cost statistics they were derived for; a resume at
+ * the same eps on a cost with the same statistics reuses them, which makes
+ * the resumed steps identical to the bit to an uninterrupted run. */
+typedef struct accsink_state {
+    int32_t m;            /* length of x and w */
+    int32_t method;       /* ACCSINK_ACC or ACCSINK_PLAIN */
+    int32_t m_stage;      /* Algorithm 2: inner steps of the current stage */
+    int32_t j_in_stage;   /* inner steps taken in the current stage */
+    int32_t stages;       /* stages completed (mu = mu0 / 2^stages) */
+    int32_t carry;        /* carry mode of the solve (ACCSINK_CARRY_*) */
+    double eps;           /* regulariser the vectors refer to */
+    double mu0, mu;       /* homotopy: initial and current mu */
+    double shift_g, shift_f, cost_abs, cost_min, eps_c;   /* internal, see above */
+    double *x;            /* device, m doubles */
+    double *w;            /* device, m doubles */
+} accsink_state;
+
+/* Copies the state of the most recent accsink_solve / accsink_solve_from /
+ * accsink_warm_start on this context into *state (x and w on `stream`; the
+ * call returns after the copies complete). state->m, state->x and state->w
+ * must be set by the caller; m must equal that solve's m. Any other call on
+ * the context that runs kernels (single passes, another solve) replaces the
+ * state: then, or before any solve, ACCSINK_ERR_INVALID_ARG. */
+int accsink_export_state(accsink_ctx *ctx, accsink_state *state, void *stream);
+
+/* Continues the iteration from `state` (Algorithm 1-2 resumed at its
+ * homotopy position; plain Sinkhorn from x). The first S evaluation is at
+ * state->x again, so a resume repeats one evaluation of the run that made
+ * the state and then takes exactly its next steps. params->eps may differ
+ * from state->eps: x and w keep their potentials, i.e. are scaled by
+ * state->eps / params->eps (eps continuation). params->mu0 and m0 are not
+ * used (the state's are); params->method must equal state->method. res and
+ * the return value are as for accsink_solve, with res->sinkhorn_steps the
+ * evaluations of this call and res->outer_stages the stage count including
+ * the state's. */
+int accsink_solve_from(accsink_ctx *ctx, const accsink_problem *prob,
+                       const accsink_params *params, const accsink_state *state,
+                       void *stream, double *f_out, double *g_out, accsink_result *res);
+
+/* Solves from the potential g0 (device, m doubles, cost units) instead of
+ * zero: x0 = g0 / eps and, for Algorithm 1, w0 = alpha0 x0 with
+ * alpha0 = sqrt(2 mu0) (y0 = x0, the momentum a fixed point has). A g0 that
+ * already meets tol stops after one S evaluation. */
+int accsink_warm_start(accsink_ctx *ctx, const accsink_problem *prob,
+                       const accsink_params *params, const double *g0, void *stream,
+                       double *f_out, double *g_out, accsink_result *res);
+
 /* Per-step history of the last solve on this context, if params.history > 0:
  * for evaluation e (0 = x_0) err[e] = marginal L1, dual[e] = dual objective,
  * mu[e] = mu used to form that iterate (0 for x_0 and for PLAIN), stab[e] =

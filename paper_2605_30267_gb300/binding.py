@@ -37,7 +37,8 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_server_submit", "accsink_server_poll", "accsink_server_wait",
             "accsink_server_potentials", "accsink_server_copy_potentials",
             "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config",
-            "accsink_plan", "accsink_barycentric"]
+            "accsink_plan", "accsink_barycentric", "accsink_export_state",
+            "accsink_solve_from", "accsink_warm_start"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
@@ -63,6 +64,15 @@ class accsink_result(ct.Structure):
                 ("marginal_l1", ct.c_double), ("transport_cost", ct.c_double),
                 ("dual_objective", ct.c_double), ("cost_max", ct.c_double),
                 ("gpu_ms", ct.c_double), ("loop_mode", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class accsink_state(ct.Structure):
+    _fields_ = [("m", ct.c_int32), ("method", ct.c_int32), ("m_stage", ct.c_int32),
+                ("j_in_stage", ct.c_int32), ("stages", ct.c_int32), ("carry", ct.c_int32),
+                ("eps", ct.c_double), ("mu0", ct.c_double), ("mu", ct.c_double),
+                ("shift_g", ct.c_double), ("shift_f", ct.c_double), ("cost_abs", ct.c_double),
+                ("cost_min", ct.c_double), ("eps_c", ct.c_double),
+                ("x", ct.c_void_p), ("w", ct.c_void_p)]
 
 
 class accsink_batch_config(ct.Structure):
@@ -122,6 +132,11 @@ def lib():
         L.accsink_col_lse_noalloc.argtypes = [P(accsink_problem), dbl, vp, vp, vp]
         L.accsink_plan.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, ct.c_int64, i32, vp]
         L.accsink_barycentric.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, i32, vp, vp]
+        L.accsink_export_state.argtypes = [vp, P(accsink_state), vp]
+        L.accsink_solve_from.argtypes = [vp, P(accsink_problem), P(accsink_params),
+                                         P(accsink_state), vp, vp, vp, P(accsink_result)]
+        L.accsink_warm_start.argtypes = [vp, P(accsink_problem), P(accsink_params), vp, vp, vp,
+                                         vp, P(accsink_result)]
         L.accsink_solve_batch.argtypes = [vp, i32, P(accsink_problem), P(accsink_params), vp,
                                           P(vp), P(vp), P(accsink_result)]
         L.accsink_batch_set_config.argtypes = [vp, P(accsink_batch_config)]
@@ -395,6 +410,34 @@ class Context:
         self._raise(lib().accsink_transport_cost(self._h, ct.byref(prob), float(eps), _ptr(f),
                                                  _ptr(g), ct.byref(out), _stream_ptr(stream)))
         return out.value
+
+    def accsink_export_state(self, x, w, stream=None) -> accsink_state:
+        """State of the last solve on this context; x, w: device FP64 arrays of
+        length m that receive the iterate and the momentum."""
+        st = accsink_state()
+        st.m = int(x.numel())
+        st.x = _ptr(x)
+        st.w = _ptr(w)
+        self._raise(lib().accsink_export_state(self._h, ct.byref(st), _stream_ptr(stream)))
+        return st
+
+    def accsink_solve_from(self, prob, params, state: accsink_state, f_out, g_out, stream=None,
+                           allow_maxiter=True) -> accsink_result:
+        res = accsink_result()
+        rc = lib().accsink_solve_from(self._h, ct.byref(prob), ct.byref(params), ct.byref(state),
+                                      _stream_ptr(stream), _ptr(f_out), _ptr(g_out),
+                                      ct.byref(res))
+        self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+        return res
+
+    def accsink_warm_start(self, prob, params, g0, f_out, g_out, stream=None,
+                           allow_maxiter=True) -> accsink_result:
+        res = accsink_result()
+        rc = lib().accsink_warm_start(self._h, ct.byref(prob), ct.byref(params), _ptr(g0),
+                                      _stream_ptr(stream), _ptr(f_out), _ptr(g_out),
+                                      ct.byref(res))
+        self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
+        return res
 
     def accsink_plan(self, prob, eps, f, g, P_out, stream=None):
         """P_out: a CUDA float32 or float64 tensor (n x >= m, unit column stride)."""

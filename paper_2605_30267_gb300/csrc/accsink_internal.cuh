@@ -292,8 +292,22 @@ struct RowSplit {
 cudaError_t launch_row_pass(const CostView &cv, const Work &w, int grid, const RowSplit &sp,
                             bool with_cost, cudaStream_t s);
 cudaError_t launch_col_pass(const CostView &cv, const Work &w, int splits, cudaStream_t s);
+// How a solve starts (k_init): at zero, or at a given iterate.
+//   x: the iterate (multiplied by mul: a resume at a new eps), or, when
+//      div > 0, a potential g0 with x = g0 / div (a warm start);
+//   w: the momentum (times mul); NULL gives w = sqrt(2 mu) x for the Acc
+//      method (y = x) and 0 for plain Sinkhorn;
+//   keep_shifts: reuse the operand shifts below when the cost statistics
+//      and eps_c they were derived for equal this solve's.
+struct InitState {
+    const double *x = nullptr, *w = nullptr;
+    double mul = 1.0, div = 0.0;
+    int32_t keep_shifts = 0;
+    double shift_g = 0.0, shift_f = 0.0, cabs = 0.0, cmin = 0.0, eps_c = 0.0;
+};
 cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
-                        const double *b_in, int normalise, cudaStream_t s);
+                        const double *b_in, int scale_max, const InitState &is,
+                        cudaStream_t s);
 cudaError_t launch_step(const CostView &cv, const Work &w, int grid,
                         cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double *c_out,

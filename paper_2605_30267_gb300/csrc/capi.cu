@@ -81,6 +81,10 @@ struct accsink_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     int64_t n_cap = -1, m_cap = -1, units_cap = 0;
+    // the last solve's continuation state is in the workspace (x, w1)
+    bool state_ok = false;
+    int state_m = 0;
+    double state_mu0 = 0.0;
     int splits_cap = 0, rowgrid_cap = 0, hist_cap = 0;
     Work w{};
     DevState *h_state = nullptr;      // pinned
@@ -213,6 +217,8 @@ bool ensure_ct(accsink_ctx *ctx, int n, int m)
 int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, int hist,
                      int64_t units = 0)
 {
+    // every call that runs kernels on the workspace passes here first
+    ctx->state_ok = false;
     if (n <= ctx->n_cap && m <= ctx->m_cap && splits <= ctx->splits_cap &&
         row_grid <= ctx->rowgrid_cap && hist <= ctx->hist_cap && units <= ctx->units_cap &&
         ctx->ws)
@@ -436,9 +442,41 @@ int build_loop_graph(accsink_ctx *ctx, const GraphKey &key, Body body)
     return ACCSINK_OK;
 }
 
+// Where a solve starts: the k_init start and, for a resumed solve, the
+// homotopy position of Algorithm 2 (else mu0 and m0 of the params).
+struct SolveStart {
+    InitState is;
+    bool stage = false;
+    double mu = 0.0, mu0 = 0.0;
+    int m_stage = 0, j = 0, stages = 0;
+};
+
+// Homotopy fields of the host state and the stage table of a solve.
+void start_state(DevState &hs, StageTable &tab, const accsink_params *prm,
+                 const SolveStart *start)
+{
+    const bool st = start && start->stage;
+    hs.mu = st ? start->mu : prm->mu0;
+    hs.m_stage = st ? start->m_stage : prm->m0;
+    hs.j_in_stage = st ? start->j : 0;
+    hs.stages = st ? start->stages : 0;
+    fill_stage_table(tab, st ? start->mu0 : prm->mu0);
+}
+
+// Marks the workspace as holding a continuation state after a solve that
+// ended converged or at the step limit.
+void keep_state(accsink_ctx *ctx, const DevState &fs, int m, const accsink_params *prm,
+                const SolveStart *start)
+{
+    ctx->state_ok = fs.status == ACCSINK_OK || fs.status == ACCSINK_ERR_MAXITER;
+    ctx->state_m = m;
+    ctx->state_mu0 = (start && start->stage) ? start->mu0 : prm->mu0;
+}
+
 // Core solve with device pointers, run on stream s. Fills res.
 int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *prm,
-                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res)
+                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res,
+                 const SolveStart *start = nullptr)
 {
     const CostView cv = make_view(prob);
     const int n = prob->n, m = prob->m;
@@ -455,12 +493,10 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     std::memset(&hs, 0, sizeof(hs));
     hs.eps_user = prm->eps;
     hs.tol = prm->tol;
-    hs.mu = prm->mu0;
     hs.method = prm->method;
     hs.stability = prm->stability;
     hs.carry = prm->carry;
     hs.max_steps = prm->max_sinkhorn_steps;
-    hs.m_stage = prm->m0;
     hs.hist_cap = prm->history;
     hs.row_grid = g.row_grid;
     hs.col_splits = g.splits;
@@ -472,14 +508,15 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     hs.col_mode = ct ? 1 : 0;
 
     StageTable tab;
-    fill_stage_table(tab, prm->mu0);
+    start_state(hs, tab, prm, start);
 
     CK(cudaEventRecord(ctx->ev0, s));
     CK(set_state(ctx, hs, s));
     k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
     CK(cudaGetLastError());
     CK(launch_cost_stats(cv, w, g.stat_grid, s));
-    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE, s));
+    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE,
+                   start ? start->is : InitState(), s));
     if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(n), s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -556,6 +593,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     res->gpu_ms = ms;
     res->loop_mode = use_graph ? 1 : 0;
     ctx->last_hist_count = std::min(fs.steps, prm->history);
+    keep_state(ctx, fs, m, prm, start);
     if (fs.status == ACCSINK_ERR_MAXITER)
         return fail(ctx, ACCSINK_ERR_MAXITER, "not converged within max_sinkhorn_steps");
     if (fs.status != ACCSINK_OK) return fail(ctx, fs.status, "solve stopped with an error status");
@@ -670,7 +708,8 @@ cudaError_t points_prologue(const accsink_problem *prob, const PointPlan &pl, do
 // Point-cloud costs (squared Euclidean, cosine) built on the fly: the same
 // loop as solve_device with the two point passes of points.cu.
 int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *prm,
-                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res)
+                 cudaStream_t s, double *f_out, double *g_out, accsink_result *res,
+                 const SolveStart *start = nullptr)
 {
     const int n = prob->n, m = prob->m;
     PointPlan pl;
@@ -686,12 +725,10 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     std::memset(&hs, 0, sizeof(hs));
     hs.eps_user = prm->eps;
     hs.tol = prm->tol;
-    hs.mu = prm->mu0;
     hs.method = prm->method;
     hs.stability = prm->stability;
     hs.carry = prm->carry;
     hs.max_steps = prm->max_sinkhorn_steps;
-    hs.m_stage = prm->m0;
     hs.hist_cap = prm->history;
     hs.row_grid = prow;
     hs.col_splits = 1;
@@ -699,14 +736,14 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     hs.first = 1;
     hs.col_mode = 1;
     StageTable tab;
-    fill_stage_table(tab, prm->mu0);
+    start_state(hs, tab, prm, start);
 
     CK(cudaEventRecord(ctx->ev0, s));
     CK(set_state(ctx, hs, s));
     k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
     CK(cudaGetLastError());
     CK(points_prologue(prob, pl, prm->eps, s));
-    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, 0, s));
+    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, 0, start ? start->is : InitState(), s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_state->done) {
@@ -781,6 +818,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     res->gpu_ms = ms;
     res->loop_mode = use_graph ? 1 : 0;
     ctx->last_hist_count = std::min(fs.steps, prm->history);
+    keep_state(ctx, fs, m, prm, start);
     if (fs.status == ACCSINK_ERR_MAXITER)
         return fail(ctx, ACCSINK_ERR_MAXITER, "not converged within max_sinkhorn_steps");
     if (fs.status != ACCSINK_OK) return fail(ctx, fs.status, "solve stopped with an error status");
@@ -980,6 +1018,131 @@ int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob, const accsink_p
         rc = solve_points(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res);
     res->status = rc;
     return rc;
+}
+
+// Shared validation of a solve's arguments (device pointers).
+static int check_solve_args(accsink_ctx *ctx, const accsink_problem *prob,
+                            const accsink_params *params, double *f_out, double *g_out)
+{
+    int rc = validate_problem(ctx, prob, false);
+    if (rc == ACCSINK_OK) rc = validate_params(ctx, params);
+    if (rc == ACCSINK_OK && (!prob->a || !prob->b))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "a and b must be given");
+    if (rc == ACCSINK_OK && (!f_out || !g_out))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "f_out and g_out must be given");
+    return rc;
+}
+
+static int run_solve(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *params,
+                     void *stream, double *f_out, double *g_out, accsink_result *res,
+                     const SolveStart &start)
+{
+    int rc;
+    if (prob->cost_kind == ACCSINK_COST_DENSE)
+        rc = solve_device(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res, &start);
+    else
+        rc = solve_points(ctx, prob, params, (cudaStream_t)stream, f_out, g_out, res, &start);
+    res->status = rc;
+    return rc;
+}
+
+int accsink_export_state(accsink_ctx *ctx, accsink_state *state, void *stream)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!state || !state->x || !state->w)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "state, state->x and state->w must be given");
+    if (!ctx->state_ok)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG,
+                    "no solve state on this context (the last kernel-running call was not a "
+                    "completed solve)");
+    if (state->m != ctx->state_m)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "state->m differs from the last solve's m");
+    const DevState &fs = *ctx->h_state;
+    const Work &w = ctx->w;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = (size_t)state->m * sizeof(double);
+    CK(cudaMemcpyAsync(state->x, w.x, bytes, cudaMemcpyDeviceToDevice, s));
+    if (fs.method == ACCSINK_ACC) CK(cudaMemcpyAsync(state->w, w.w1, bytes, cudaMemcpyDeviceToDevice, s));
+    else CK(cudaMemsetAsync(state->w, 0, bytes, s));
+    state->method = fs.method;
+    state->m_stage = fs.m_stage;
+    state->j_in_stage = fs.j_in_stage;
+    state->stages = fs.stages;
+    state->carry = fs.carry;
+    state->eps = fs.eps_user;
+    state->mu0 = ctx->state_mu0;
+    state->mu = fs.mu;
+    state->shift_g = fs.shift_g;
+    state->shift_f = fs.shift_f;
+    state->cost_abs = fs.cabs;
+    state->cost_min = fs.cmin;
+    state->eps_c = fs.eps_c;
+    CK(cudaStreamSynchronize(s));
+    return ACCSINK_OK;
+}
+
+int accsink_solve_from(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *params,
+                       const accsink_state *state, void *stream, double *f_out, double *g_out,
+                       accsink_result *res)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
+    std::memset(res, 0, sizeof(*res));
+    res->status = ACCSINK_ERR_INVALID_ARG;
+    rc = check_solve_args(ctx, prob, params, f_out, g_out);
+    if (rc == ACCSINK_OK && (!state || !state->x || !state->w))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "state, state->x and state->w must be given");
+    if (rc == ACCSINK_OK && state->m != prob->m)
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "state->m must equal the problem's m");
+    if (rc == ACCSINK_OK && state->method != params->method)
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "params->method must equal state->method");
+    if (rc == ACCSINK_OK && !(state->eps > 0.0 && std::isfinite(state->eps)))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "state->eps must be finite and > 0");
+    if (rc == ACCSINK_OK && state->method == ACCSINK_ACC &&
+        !(state->mu0 > 0.0 && state->mu0 < 1.0 && state->mu > 0.0 && state->m_stage >= 1 &&
+          state->j_in_stage >= 0 && state->j_in_stage < state->m_stage && state->stages >= 0 &&
+          state->stages < kMaxStages))
+        rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "the state's homotopy position is not valid");
+    if (rc != ACCSINK_OK) { res->status = rc; return rc; }
+    SolveStart st;
+    st.is.x = state->x;
+    st.is.w = state->method == ACCSINK_ACC ? state->w : nullptr;
+    st.is.mul = state->eps / params->eps;
+    st.is.keep_shifts = state->eps == params->eps ? 1 : 0;
+    st.is.shift_g = state->shift_g;
+    st.is.shift_f = state->shift_f;
+    st.is.cabs = state->cost_abs;
+    st.is.cmin = state->cost_min;
+    st.is.eps_c = state->eps_c;
+    if (state->method == ACCSINK_ACC) {
+        st.stage = true;
+        st.mu = state->mu;
+        st.mu0 = state->mu0;
+        st.m_stage = state->m_stage;
+        st.j = state->j_in_stage;
+        st.stages = state->stages;
+    }
+    return run_solve(ctx, prob, params, stream, f_out, g_out, res, st);
+}
+
+int accsink_warm_start(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *params,
+                       const double *g0, void *stream, double *f_out, double *g_out,
+                       accsink_result *res)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!res) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "res is NULL");
+    std::memset(res, 0, sizeof(*res));
+    res->status = ACCSINK_ERR_INVALID_ARG;
+    rc = check_solve_args(ctx, prob, params, f_out, g_out);
+    if (rc == ACCSINK_OK && !g0) rc = fail(ctx, ACCSINK_ERR_INVALID_ARG, "g0 must be given");
+    if (rc != ACCSINK_OK) { res->status = rc; return rc; }
+    SolveStart st;
+    st.is.x = g0;
+    st.is.div = params->eps;
+    return run_solve(ctx, prob, params, stream, f_out, g_out, res, st);
 }
 
 int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,

@@ -152,13 +152,14 @@ __device__ __forceinline__ void write_G(const Work &w, int j, double gshift, flo
 }
 
 // ------------------------------------------------------------------------
-// Set-up of a solve. The host has written eps_user, tol, mu, method, ... into
-// the state (barrier = 0). Validates and normalises the marginals, derives
-// eps_c and the operand shifts, and writes x_0 = w_0 = 0 and G for x_0.
+// Set-up of a solve. The host has written eps_user, tol, mu, method, the
+// homotopy position, ... into the state (barrier = 0). Validates and
+// normalises the marginals, derives eps_c and the operand shifts, and writes
+// x_0, w_0 (zero, or the start `is` gives) and G for x_0.
 // ------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat,
                                                  const double *a_in, const double *b_in,
-                                                 int scale_max)
+                                                 int scale_max, InitState is)
 {
     DevState *st = w.st;
     const int tid = blockIdx.x * kVecNT + threadIdx.x;
@@ -206,8 +207,9 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
     const float kh = (float)k;
     const float kl = (float)(k - (double)kh);
 
-    // phase B: normalised marginals, logs, zero iterate
-    double mnla = DBL_MAX;
+    // phase B: normalised marginals, logs, the starting iterate
+    const double alpha0 = st->method == 1 ? sqrt(2.0 * st->mu) : 0.0;
+    double mnla = DBL_MAX, xlo = DBL_MAX, xhi = -DBL_MAX;
     for (int i = tid; i < n; i += nthr) {
         const double ai = a_in[i] / sa;
         w.a[i] = ai;
@@ -218,30 +220,61 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
         const double bj = b_in[j] / sb;
         w.b[j] = bj;
         w.logb[j] = log(bj);
-        w.x[j] = 0.0;
-        w.x_prev[j] = 0.0;
-        w.w[j] = 0.0;
+        double xj = 0.0, wj = 0.0;
+        if (is.x) {
+            xj = is.div > 0.0 ? is.x[j] / is.div : is.x[j] * is.mul;
+            wj = is.w ? is.w[j] * is.mul : alpha0 * xj;
+        }
+        w.x[j] = xj;
+        w.x_prev[j] = xj;
+        w.w[j] = wj;
         w.p_prev[j] = 0.0;
         w.D_prev[j] = bj;
+        xlo = fmin(xlo, xj);
+        xhi = fmax(xhi, xj);
     }
-    // block min of log a into slot 6 (slots 0..5 are still being read)
+    // block min of log a and bounds of x_0 into slots 6..8 (slots 0..5 are
+    // still being read)
     {
-        double dummy = -DBL_MAX;
-        __shared__ double shm[2];
-        block_minmax_store(mnla, dummy, shm);
-        if (threadIdx.x == 0) w.steppart[(int64_t)blockIdx.x * kPartStride + 6] = shm[0];
+        double v3[3] = {mnla, xlo, xhi};
+        const int ops3[3] = {1, 1, 2};
+        block_allreduce<3>(v3, ops3);
+        if (threadIdx.x == 0) {
+            double *r = w.steppart + (int64_t)blockIdx.x * kPartStride;
+            r[6] = v3[0];
+            r[7] = v3[1];
+            r[8] = v3[2];
+        }
     }
     if (!grid_barrier(st, 2 * nb, kBarrierLimitNs)) return;
-    double t1[1];
-    const int ops1[1] = {1};
-    grid_totals<1>(w.steppart, nb, 6, ops1, t1);
-    const double min_loga = t1[0];
+    double t3[3];
+    const int ops3[3] = {1, 1, 2};
+    grid_totals<3>(w.steppart, nb, 6, ops3, t3);
+    const double min_loga = t3[0];
     const double log_m = log((double)m);
-    // x_0 = 0: G = shift_g = max|C| makes G >= |C|; F_i >= max|C| follows from
+    // G = eps_c x + shift_g with shift_g = max|C| - eps_c min x makes
+    // G >= |C|; F_i >= max|C| follows from
     // eps_c u_i >= eps_c min log a - eps_c max x + min C - eps_c log m.
-    const double shift_g = cabs;
-    const double shift_f = cabs - (eps_c * min_loga - 0.0 + cmin - eps_c * log_m);
-    for (int j = tid; j < m; j += nthr) write_G(w, j, shift_g, kh, k);
+    // At x_0 = 0 that is shift_g = max|C|; a given x_0 has exact bounds,
+    // widened by a relative margin for the rounding of eps_c x + shift.
+    double shift_g, shift_f;
+    if (is.keep_shifts && is.cabs == cabs && is.cmin == cmin && is.eps_c == eps_c) {
+        shift_g = is.shift_g;
+        shift_f = is.shift_f;
+    } else if (is.x) {
+        const double lo = t3[1] - 1e-12 * (1.0 + fabs(t3[1]));
+        const double hi = t3[2] + 1e-12 * (1.0 + fabs(t3[2]));
+        shift_g = cabs - eps_c * lo;
+        shift_f = cabs - (eps_c * min_loga - eps_c * hi + cmin - eps_c * log_m);
+    } else {
+        shift_g = cabs;
+        shift_f = cabs - (eps_c * min_loga - 0.0 + cmin - eps_c * log_m);
+    }
+    if (is.x) {
+        for (int j = tid; j < m; j += nthr) write_G(w, j, eps_c * w.x[j] + shift_g, kh, k);
+    } else {
+        for (int j = tid; j < m; j += nthr) write_G(w, j, shift_g, kh, k);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->eps_c = eps_c;
         st->inv_eps_c = 1.0 / eps_c;
@@ -255,7 +288,8 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
         st->k_hi = kh;
         st->k_lo = kl;
         st->k2 = k;
-        st->steps = 0; st->stages = 0; st->failures = 0; st->j_in_stage = 0;
+        // (the homotopy position mu, m_stage, j_in_stage, stages is the host's)
+        st->steps = 0; st->failures = 0;
         st->first = 1; st->done = 0; st->status = 0;
         st->err = INFINITY; st->dual = 0.0; st->kl_prev = 0.0;
         st->mode = STEP_SOLVE;
@@ -263,7 +297,8 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
 }
 
 cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
-                        const double *b_in, int scale_max, cudaStream_t s)
+                        const double *b_in, int scale_max, const InitState &is,
+                        cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -274,7 +309,8 @@ cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const doubl
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_init, w, cv.n, cv.m, (int)w.nstat, a_in, b_in, scale_max);
+    return cudaLaunchKernelEx(&cfg, k_init, w, cv.n, cv.m, (int)w.nstat, a_in, b_in, scale_max,
+                              is);
 }
 
 // ------------------------------------------------------------------------
@@ -601,6 +637,13 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             w.p_prev[j] = w.del[j];
             w.D_prev[j] = w.D1[j];
             write_G(w, j, eps_c * xn + shift_g, kh, k2);
+        }
+    } else if (is_acc) {
+        // stopped at x: keep the momentum after this step's update (gate and
+        // stage hand-over applied), the w a continued iteration would use
+        for (int j = tid; j < m; j += nthr) {
+            const double w1 = wupd ? (gate ? alpha * w.x[j] : w.w1[j]) : w.w[j];
+            w.w1[j] = w1 * ratio;
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -65,6 +65,8 @@ int main(void) {
          offsetof(accsink_batch_config, row_tile_elems), offsetof(accsink_batch_config, ctas_per_sm));
   printf("%zu %zu %zu\n", sizeof(accsink_server_stats),
          offsetof(accsink_server_stats, resident_bytes), offsetof(accsink_server_stats, busy_ms));
+  printf("%zu %zu %zu %zu %zu\n", sizeof(accsink_state), offsetof(accsink_state, eps),
+         offsetof(accsink_state, eps_c), offsetof(accsink_state, x), offsetof(accsink_state, w));
   return 0;
 }
 ''')
@@ -88,6 +90,9 @@ int main(void) {
     v = [int(x) for x in lines[4].split()]
     assert v == [ct.sizeof(B.accsink_server_stats), B.accsink_server_stats.resident_bytes.offset,
                  B.accsink_server_stats.busy_ms.offset]
+    t = [int(x) for x in lines[5].split()]
+    assert t == [ct.sizeof(B.accsink_state), B.accsink_state.eps.offset,
+                 B.accsink_state.eps_c.offset, B.accsink_state.x.offset, B.accsink_state.w.offset]
 
 
 def test_host_only_calls(L):
