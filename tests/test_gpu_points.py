@@ -96,7 +96,9 @@ def potential_like(seed, k):
 
 
 @pytest.mark.parametrize("n,m", PT_SHAPES)
-@pytest.mark.parametrize("kind,d", [("sqeuclid", 3), ("sqeuclid", 9), ("cosine", 16),
+# d = 1..4 cover the exact-dimension kernels (d = 2, 3, 4) and the d < 4 bound
+@pytest.mark.parametrize("kind,d", [("sqeuclid", 1), ("sqeuclid", 2), ("sqeuclid", 3),
+                                    ("cosine", 4), ("sqeuclid", 9), ("cosine", 16),
                                     ("cosine", 64)])
 @pytest.mark.parametrize("eps", [1e-1, 1e-3])
 def test_point_row_pass_matches_oracle(ctx, n, m, kind, d, eps):
