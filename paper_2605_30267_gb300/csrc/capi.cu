@@ -402,8 +402,12 @@ int get_graph(accsink_ctx *ctx, const CostView &cv, const Geometry &g, const flo
     });
 }
 
-// WHILE(cond) { body } with the body captured from `body(stream, handle)`;
-// reuses the cached executable when `key` matches.
+// WHILE(cond) { body; body } with each body captured from
+// `body(stream, handle)`: two S evaluations per trip through the conditional
+// node, whose per-trip overhead (~4 us on this part) is then paid every other
+// evaluation. When the first body's step stops the solve, the second body's
+// kernels see `done` and return at once. Reuses the cached executable when
+// `key` matches.
 template <class Body>
 int build_loop_graph(accsink_ctx *ctx, const GraphKey &key, Body body)
 {
@@ -427,6 +431,7 @@ int build_loop_graph(accsink_ctx *ctx, const GraphKey &key, Body body)
                                       cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
     cudaError_t e1 = body(ctx->cap_stream, handle);
+    if (e1 == cudaSuccess) e1 = body(ctx->cap_stream, handle);
     cudaGraph_t out = nullptr;
     e = cudaStreamEndCapture(ctx->cap_stream, &out);
     if (e1 != cudaSuccess || e != cudaSuccess) {

@@ -12,7 +12,11 @@
 
 namespace accsink {
 
-constexpr int kVecNT = 64;   // two warps: FP64 block reductions stay short
+// Two warps per block: every FP64 instruction of a warp holds the SM's narrow
+// FP64 pipe (about 2 operations per clock on GB300) for ~16 cycles, and the
+// block reductions cost the same FP64 instructions per warp whatever the
+// column count, so more warps per block made the step slower (measured).
+constexpr int kVecNT = 64;
 constexpr uint64_t kBarrierLimitNs = 2000000000ull;   // 2 s per barrier
 
 // Sum K per-thread doubles over the block; thread k < K writes the k-th sum
@@ -411,6 +415,9 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
 
     // ---- P1
     double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l, <a,u>
+    // the first row term of <a, u>, loaded with the column loads
+    double a0 = 0.0, u0 = 0.0;
+    if (tid < n) { a0 = w.a[tid]; u0 = w.u[tid]; }
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int col_mode = st->col_mode;
     for (int j = tid; j < m; j += nthr) {
@@ -475,7 +482,8 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         if (c_out) c_out[j] = bj * exp(del);
     }
     // <a, u> of the dual (Sec. 5), from the row pass's u in a fixed order
-    for (int i = tid; i < n; i += nthr) v[6] += w.a[i] * w.u[i];
+    v[6] = a0 * u0;
+    for (int i = tid + nthr; i < n; i += nthr) v[6] += w.a[i] * w.u[i];
     {
         __shared__ double shs[7];
         block_sum_store<7>(v, shs);
@@ -492,12 +500,14 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     // ---- P2
     double t[R_WHI + 1];
     {
-        double t6[7];
+        // one read of every block's record: the P1 sums and bounds
+        double t6[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         const int ops6[7] = {0, 0, 0, 0, 0, 0, 0};
-        grid_totals<7>(w.steppart, nb, R_ERR, ops6, t6);
         float blo2[3] = {INFINITY, INFINITY, INFINITY}, bhi2[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
             const double *r = w.steppart + (int64_t)b * kPartStride;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) t6[k] += __ldcg(&r[R_ERR + k]);
             blo2[0] = fminf(blo2[0], (float)__ldcg(&r[R_RAWLO]));
             bhi2[0] = fmaxf(bhi2[0], (float)__ldcg(&r[R_RAWHI]));
             blo2[1] = fminf(blo2[1], (float)__ldcg(&r[R_XLO]));
@@ -505,6 +515,7 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
             blo2[2] = fminf(blo2[2], (float)__ldcg(&r[R_WLO]));
             bhi2[2] = fmaxf(bhi2[2], (float)__ldcg(&r[R_WHI]));
         }
+        block_allreduce<7>(t6, ops6);
         block_minmax_f(blo2, bhi2);
         for (int k = 0; k < 7; ++k) t[k] = t6[k];
         t[R_RAWLO] = blo2[0]; t[R_RAWHI] = bhi2[0];
@@ -554,15 +565,17 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     // ---- P3
     double t2[3];
     {
-        double c2[1];
+        // one read of every block's record: the P2 sum and bounds
+        double c2[1] = {0.0};
         const int op1[1] = {0};
-        grid_totals<1>(w.steppart, nb, R_C2R, op1, c2);
         float wl[3] = {INFINITY, INFINITY, INFINITY}, wh[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
             const double *r = w.steppart + (int64_t)b * kPartStride;
+            c2[0] += __ldcg(&r[R_C2R]);
             wl[0] = fminf(wl[0], (float)__ldcg(&r[R_W1LO]));
             wh[0] = fmaxf(wh[0], (float)__ldcg(&r[R_W1HI]));
         }
+        block_allreduce<1>(c2, op1);
         block_minmax_f(wl, wh);
         t2[0] = c2[0];
         t2[1] = wl[0];
