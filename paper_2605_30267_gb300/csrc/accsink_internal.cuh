@@ -132,6 +132,7 @@ struct PointView {
     const double *B64, *scal;
     int64_t ldq;
     int32_t nr, nc, d, kind;
+    int32_t prune;   // 1: points sorted along a space-filling curve; far slots skipped
 };
 
 struct CostView {
@@ -297,10 +298,13 @@ cudaError_t launch_col_pass(const CostView &cv, const Work &w, int splits, cudaS
 //      div > 0, a potential g0 with x = g0 / div (a warm start);
 //   w: the momentum (times mul); NULL gives w = sqrt(2 mu) x for the Acc
 //      method (y = x) and 0 for plain Sinkhorn;
+//   perm: the solve's columns are a permutation of the caller's (sorted
+//      point clouds);
 //   keep_shifts: reuse the operand shifts below when the cost statistics
 //      and eps_c they were derived for equal this solve's.
 struct InitState {
     const double *x = nullptr, *w = nullptr;
+    const int *perm = nullptr;   // column j of the solve reads x[perm[j]], w[perm[j]]
     double mul = 1.0, div = 0.0;
     int32_t keep_shifts = 0;
     double shift_g = 0.0, shift_f = 0.0, cabs = 0.0, cmin = 0.0, eps_c = 0.0;
@@ -340,6 +344,23 @@ int occupancy_col_pass(int vec);
 cudaError_t launch_points_pass(const PointView &pv, const Work &w, int grid, int mode,
                                bool with_cost, cudaStream_t s);
 int occupancy_points_pass();
+// Spatial sort of one point cloud: buffers in the solve's point workspace.
+// P (n x d) and a (n) receive the cloud and its marginal in Morton order;
+// perm[i] is the original index of sorted point i.
+struct PointSort {
+    uint32_t *box, *code, *code2;
+    int *idx, *perm;
+    void *temp;
+    size_t temp_bytes;
+    float *P;
+    double *a;
+};
+size_t points_sort_temp_bytes(int count);
+cudaError_t launch_points_sort(const float *P, const double *a, int n, int d, const PointSort &ps,
+                               cudaStream_t s);
+// dst[perm[i]] = scale * src[i]
+cudaError_t launch_scatter_scaled(const double *src, double scale, const int *perm, int n,
+                                  double *dst, cudaStream_t s);
 cudaError_t launch_points_rowmax(const float *X, const float *Y, int n, int m, int d, int kind,
                                  double *rowmax, int grid, cudaStream_t s);
 cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, int d, int kind,

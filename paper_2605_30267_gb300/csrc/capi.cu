@@ -84,6 +84,7 @@ struct accsink_ctx {
     // the last solve's continuation state is in the workspace (x, w1)
     bool state_ok = false;
     int state_m = 0;
+    const int *state_perm = nullptr;   // Morton order of the columns (sorted point solves)
     double state_mu0 = 0.0;
     int splits_cap = 0, rowgrid_cap = 0, hist_cap = 0;
     Work w{};
@@ -473,6 +474,7 @@ void start_state(DevState &hs, StageTable &tab, const accsink_params *prm,
 void keep_state(accsink_ctx *ctx, const DevState &fs, int m, const accsink_params *prm,
                 const SolveStart *start)
 {
+    ctx->state_perm = nullptr;
     ctx->state_ok = fs.status == ACCSINK_OK || fs.status == ACCSINK_ERR_MAXITER;
     ctx->state_m = m;
     ctx->state_mu0 = (start && start->stage) ? start->mu0 : prm->mu0;
@@ -612,7 +614,11 @@ struct PointPlan {
     CostView cv;
     Geometry g;
     Work w;
-    PointView pr, pc;
+    PointView pr{}, pc{};
+    // sorted solve: both clouds in Morton order (pruned passes); the views
+    // read the sorted copies, outputs are scattered back through the perms
+    bool sorted = false;
+    PointSort sx{}, sy{};
     int prow = 1, pcol = 1, kind = 1, nblk = 1;
     double *blockmax = nullptr, *scal = nullptr;
 };
@@ -629,9 +635,12 @@ int points_grid(const accsink_ctx *ctx, int n_rows, int d)
 
 // Allocates the solve workspace and the O((n + m) d) point workspace and
 // fills `pl`. Launches nothing.
-int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPlan &pl)
+int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPlan &pl,
+                bool sort = false)
 {
     const int n = prob->n, m = prob->m, d = prob->d;
+    // the spatial sort pays for solves in low dimension (colour-like clouds)
+    pl.sorted = sort && d <= 4;
     pl.kind = prob->cost_kind == ACCSINK_COST_SQEUCLID ? 1 : 2;
     pl.cv.C = nullptr;
     pl.cv.ldc = m;
@@ -649,6 +658,15 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
                                  (size_t)ldy * 4, (size_t)ldy * 4, (size_t)d * ldx * 4,
                                  (size_t)d * ldx * 4, (size_t)d * ldy * 4, (size_t)d * ldy * 4,
                                  (size_t)n * 8, (size_t)pl.nblk * 40, 16};
+    const size_t temp = pl.sorted ? std::max(points_sort_temp_bytes(n), points_sort_temp_bytes(m)) : 0;
+    if (pl.sorted) {
+        for (int c = 0; c < 2; ++c) {
+            const size_t cnt = c == 0 ? (size_t)n : (size_t)m;
+            for (size_t z : {(size_t)32, cnt * 4, cnt * 4, cnt * 4, cnt * 4, cnt * d * 4, cnt * 8})
+                sizes.push_back(z);
+        }
+        sizes.push_back(std::max<size_t>(temp, 16));
+    }
     size_t need = 0;
     for (size_t z : sizes) need += align_up(z, 256);
     if (need > ctx->pts_bytes) {
@@ -681,6 +699,19 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     w.rowmax = (double *)take();
     pl.blockmax = (double *)take();
     pl.scal = (double *)take();
+    if (pl.sorted) {
+        for (PointSort *ps : {&pl.sx, &pl.sy}) {
+            ps->box = (uint32_t *)take();
+            ps->code = (uint32_t *)take();
+            ps->code2 = (uint32_t *)take();
+            ps->idx = (int *)take();
+            ps->perm = (int *)take();
+            ps->P = (float *)take();
+            ps->a = (double *)take();
+        }
+        pl.sx.temp = pl.sy.temp = take();
+        pl.sx.temp_bytes = pl.sy.temp_bytes = std::max<size_t>(temp, 16);
+    }
     w.ldx = ldx;
     w.ldy = ldy;
     w.nstat = 1;
@@ -688,10 +719,12 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     w.f_given = nullptr;
     w.ignore_done = 0;
     PointView &pr = pl.pr, &pc = pl.pc;
-    pr.P = prob->X; pr.Pc = prob->Y; pr.Ah = w.G; pr.Al = w.Gk; pr.B64 = w.Bx64;
+    const float *Xv = pl.sorted ? pl.sx.P : prob->X, *Yv = pl.sorted ? pl.sy.P : prob->Y;
+    pr.prune = pc.prune = pl.sorted ? 1 : 0;
+    pr.P = Xv; pr.Pc = Yv; pr.Ah = w.G; pr.Al = w.Gk; pr.B64 = w.Bx64;
     pr.Qh = w.PYh; pr.Ql = w.PYl; pr.scal = pl.scal; pr.ldq = ldy;
     pr.nr = n; pr.nc = m; pr.d = d; pr.kind = pl.kind;
-    pc.P = prob->Y; pc.Pc = prob->X; pc.Ah = w.Fh; pc.Al = w.Fk; pc.B64 = w.By64;
+    pc.P = Yv; pc.Pc = Xv; pc.Ah = w.Fh; pc.Al = w.Fk; pc.B64 = w.By64;
     pc.Qh = w.PXh; pc.Ql = w.PXl; pc.scal = pl.scal; pc.ldq = ldx;
     pc.nr = m; pc.nc = n; pc.d = d; pc.kind = pl.kind;
     return ACCSINK_OK;
@@ -718,8 +751,18 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
 {
     const int n = prob->n, m = prob->m;
     PointPlan pl;
-    int rc = points_plan(ctx, prob, prm->history, pl);
+    int rc = points_plan(ctx, prob, prm->history, pl, true);
     if (rc != ACCSINK_OK) return rc;
+    // a sorted solve runs on the clouds (and marginals) in Morton order
+    accsink_problem ps = *prob;
+    InitState is0 = start ? start->is : InitState();
+    if (pl.sorted) {
+        ps.X = pl.sx.P;
+        ps.Y = pl.sy.P;
+        ps.a = pl.sx.a;
+        ps.b = pl.sy.a;
+        is0.perm = pl.sy.perm;
+    }
     const CostView &cv = pl.cv;
     const Geometry &g = pl.g;
     const Work &w = pl.w;
@@ -747,8 +790,12 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     CK(set_state(ctx, hs, s));
     k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
     CK(cudaGetLastError());
-    CK(points_prologue(prob, pl, prm->eps, s));
-    CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, 0, start ? start->is : InitState(), s));
+    if (pl.sorted) {
+        CK(launch_points_sort(prob->X, prob->a, n, prob->d, pl.sx, s));
+        CK(launch_points_sort(prob->Y, prob->b, m, prob->d, pl.sy, s));
+    }
+    CK(points_prologue(&ps, pl, prm->eps, s));
+    CK(launch_init(cv, w, g.vec_grid, ps.a, ps.b, 0, is0, s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_state->done) {
@@ -798,8 +845,13 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
         CK(launch_points_pass(pr, we, prow, 0, true, s));
     }
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CK(launch_scale_out(w.u, prm->eps, f_out, n, s));
-    CK(launch_scale_out(w.x, prm->eps, g_out, m, s));
+    if (pl.sorted) {
+        CK(launch_scatter_scaled(w.u, prm->eps, pl.sx.perm, n, f_out, s));
+        CK(launch_scatter_scaled(w.x, prm->eps, pl.sy.perm, m, g_out, s));
+    } else {
+        CK(launch_scale_out(w.u, prm->eps, f_out, n, s));
+        CK(launch_scale_out(w.x, prm->eps, g_out, m, s));
+    }
     CK(cudaMemcpyAsync(ctx->h_rowpart, w.rowpart, (size_t)prow * 16, cudaMemcpyDeviceToHost, s));
     CK(cudaEventRecord(ctx->ev1, s));
     CK(cudaStreamSynchronize(s));
@@ -824,6 +876,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     res->loop_mode = use_graph ? 1 : 0;
     ctx->last_hist_count = std::min(fs.steps, prm->history);
     keep_state(ctx, fs, m, prm, start);
+    ctx->state_perm = pl.sorted ? pl.sy.perm : nullptr;
     if (fs.status == ACCSINK_ERR_MAXITER)
         return fail(ctx, ACCSINK_ERR_MAXITER, "not converged within max_sinkhorn_steps");
     if (fs.status != ACCSINK_OK) return fail(ctx, fs.status, "solve stopped with an error status");
@@ -1067,9 +1120,18 @@ int accsink_export_state(accsink_ctx *ctx, accsink_state *state, void *stream)
     const Work &w = ctx->w;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = (size_t)state->m * sizeof(double);
-    CK(cudaMemcpyAsync(state->x, w.x, bytes, cudaMemcpyDeviceToDevice, s));
-    if (fs.method == ACCSINK_ACC) CK(cudaMemcpyAsync(state->w, w.w1, bytes, cudaMemcpyDeviceToDevice, s));
-    else CK(cudaMemsetAsync(state->w, 0, bytes, s));
+    if (ctx->state_perm) {
+        // the solve ran on sorted columns: back to the caller's order
+        CK(launch_scatter_scaled(w.x, 1.0, ctx->state_perm, state->m, state->x, s));
+        if (fs.method == ACCSINK_ACC)
+            CK(launch_scatter_scaled(w.w1, 1.0, ctx->state_perm, state->m, state->w, s));
+        else
+            CK(cudaMemsetAsync(state->w, 0, bytes, s));
+    } else {
+        CK(cudaMemcpyAsync(state->x, w.x, bytes, cudaMemcpyDeviceToDevice, s));
+        if (fs.method == ACCSINK_ACC) CK(cudaMemcpyAsync(state->w, w.w1, bytes, cudaMemcpyDeviceToDevice, s));
+        else CK(cudaMemsetAsync(state->w, 0, bytes, s));
+    }
     state->method = fs.method;
     state->m_stage = fs.m_stage;
     state->j_in_stage = fs.j_in_stage;

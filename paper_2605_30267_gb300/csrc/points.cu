@@ -20,6 +20,10 @@
 // same kernel with the roles of X and Y swapped.
 #include <float.h>
 
+#include <algorithm>
+
+#include <cub/device/device_radix_sort.cuh>
+
 #include "accsink_internal.cuh"
 
 namespace accsink {
@@ -107,7 +111,18 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 //   MODE 1 (column pass): A = A', rows of Y, B64 = By; finishes ell_j.
 // With h_rc = k (A-term + x.Q) the row's log-sum-exp in natural units is
 //   (R + log2 S) ln 2 - (B_r + shift) / eps_c.
-template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false>
+// PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
+// FP32 estimate of every exponent, for every row of the warp, lies more than
+// kSkipLog2 below the lane's running maximum (a lower bound of the row's) is
+// skipped. Each skipped term is below 2^-80 of its row's sum, so all of a
+// row's skipped terms together stay below 2^-49 of it for any row length
+// below 2^31: far below the FP32 accumulation. The estimate A_hi + sum_k
+// p_k Q_hi,k differs from the exact exponent by at most ~2^-21 of the terms'
+// magnitude |A| + sum_k |p_k| |Q_k| (four FP32 roundings and the dropped low
+// parts), so the threshold is lowered by 2^-20 of a bound on that magnitude.
+constexpr float kSkipLog2 = 80.0f;
+
+template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false, bool PRUNE = false>
 __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 {
     DevState *st = w.st;
@@ -143,16 +158,48 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
         }
         // whole chunks: every element valid
         for (int v = lane; v < nfull; v += 32) {
-            const float4 ah = __ldg(Ah4 + v), al = __ldg(Al4 + v);
+            const float4 ah = __ldg(Ah4 + v);
             float4 qh[PRE ? DMAX : 1], ql[PRE ? DMAX : 1];
             if (PRE) {
 #pragma unroll
-                for (int k = 0; k < DMAX; ++k) {
-                    if (k < d) {
-                        qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
-                        ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
+                for (int k = 0; k < DMAX; ++k)
+                    if (k < d) qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
+            }
+            if (PRUNE) {
+                float amax = fmaxf(fmaxf(fabsf(ah.x), fabsf(ah.y)), fmaxf(fabsf(ah.z), fabsf(ah.w)));
+                float qmax[DMAX];
+#pragma unroll
+                for (int k = 0; k < DMAX; ++k)
+                    qmax[k] = (k < d) ? fmaxf(fmaxf(fabsf(qh[k].x), fabsf(qh[k].y)),
+                                              fmaxf(fabsf(qh[k].z), fabsf(qh[k].w)))
+                                      : 0.0f;
+                bool far = true;
+#pragma unroll
+                for (int q = 0; q < RW; ++q) {
+                    float mag = amax;
+#pragma unroll
+                    for (int k = 0; k < DMAX; ++k)
+                        if (k < d) mag = fmaf(fabsf(p[q][k]), qmax[k], mag);
+                    const float lim = acc[q].R - kSkipLog2 - 1.0f - mag * 0x1p-20f;
+                    float e4[4] = {ah.x, ah.y, ah.z, ah.w};
+#pragma unroll
+                    for (int k = 0; k < DMAX; ++k) {
+                        if (k < d) {
+                            e4[0] = fmaf(p[q][k], qh[k].x, e4[0]);
+                            e4[1] = fmaf(p[q][k], qh[k].y, e4[1]);
+                            e4[2] = fmaf(p[q][k], qh[k].z, e4[2]);
+                            e4[3] = fmaf(p[q][k], qh[k].w, e4[3]);
+                        }
                     }
+                    far = far && fmaxf(fmaxf(e4[0], e4[1]), fmaxf(e4[2], e4[3])) < lim;
                 }
+                if (__all_sync(0xffffffffu, far)) continue;
+            }
+            const float4 al = __ldg(Al4 + v);
+            if (PRE) {
+#pragma unroll
+                for (int k = 0; k < DMAX; ++k)
+                    if (k < d) ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
             }
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
@@ -263,6 +310,14 @@ constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 template <int MODE, bool WC>
 static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cudaStream_t s)
 {
+    if (pv.prune && pv.d <= 4) {
+        // sorted point clouds (see the set-up): the pruned kernels
+        if (pv.d == 2) k_lse_points<MODE, 2, rows_per_warp<2>(), WC, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else if (pv.d == 3) k_lse_points<MODE, 3, rows_per_warp<3>(), WC, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else if (pv.d == 4) k_lse_points<MODE, 4, rows_per_warp<4>(), WC, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else k_lse_points<MODE, 4, rows_per_warp<4>(), WC, false, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        return cudaGetLastError();
+    }
     if (pv.d == 2) k_lse_points<MODE, 2, rows_per_warp<2>(), WC, true><<<grid, kPtNT, 0, s>>>(pv, w);
     else if (pv.d == 3) k_lse_points<MODE, 3, rows_per_warp<3>(), WC, true><<<grid, kPtNT, 0, s>>>(pv, w);
     else if (pv.d == 4) k_lse_points<MODE, 4, rows_per_warp<4>(), WC, true><<<grid, kPtNT, 0, s>>>(pv, w);
@@ -490,6 +545,134 @@ cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, in
     k_points_scale<<<1, 256, 0, s>>>(w.rowmax, n, scale_max, scal);
     k_points_setup<<<nblk, 256, 0, s>>>(X, Y, n, m, d, kind, scal, eps, w, blockmax);
     k_points_stats<<<1, 32, 0, s>>>(blockmax, nblk, d, kind, scal, w.statpart);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Spatial sort of a point cloud (set-up of a solve). The pruned passes skip
+// a warp's slot only when all of its 128 columns are far from all of its
+// rows, which happens for most slots once nearby points are adjacent: the
+// clouds are put in Morton order of their first min(d, 3) coordinates over
+// the bounding box (10 bits per coordinate). The order only changes which
+// terms share a slot and the summation order; the solve is the same problem.
+// ------------------------------------------------------------------------
+
+namespace {
+
+__device__ __forceinline__ uint32_t ord_f(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (u >> 31) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float unord_f(uint32_t e)
+{
+    return __uint_as_float((e >> 31) ? (e & 0x7fffffffu) : ~e);
+}
+
+// box[0..2] = ordered min, box[3..5] = ordered max per coordinate
+__global__ void k_bbox(const float *P, int n, int d, uint32_t *box)
+{
+    const int dd = d < 3 ? d : 3;
+    uint32_t mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, mx[3] = {0u, 0u, 0u};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int k = 0; k < dd; ++k) {
+            const uint32_t e = ord_f(P[(int64_t)i * d + k]);
+            mn[k] = min(mn[k], e);
+            mx[k] = max(mx[k], e);
+        }
+    }
+    for (int k = 0; k < dd; ++k) {
+        const uint32_t a = __reduce_min_sync(0xffffffffu, mn[k]);
+        const uint32_t b = __reduce_max_sync(0xffffffffu, mx[k]);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(box + k, a);
+            atomicMax(box + 3 + k, b);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton(const float *P, int n, int d, const uint32_t *box, uint32_t *code,
+                         int *idx)
+{
+    const int dd = d < 3 ? d : 3;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t c = 0u;
+        for (int k = 0; k < dd; ++k) {
+            const float lo = unord_f(box[k]), hi = unord_f(box[3 + k]);
+            const float t = hi > lo ? (P[(int64_t)i * d + k] - lo) / (hi - lo) : 0.0f;
+            const int q = min(1023, max(0, __float2int_rz(t * 1024.0f)));
+            c |= spread10((uint32_t)q) << k;
+        }
+        code[i] = c;
+        idx[i] = i;
+    }
+}
+
+__global__ void k_gather_points(const float *P, const double *a, int n, int d, const int *perm,
+                                float *P_out, double *a_out)
+{
+    const int64_t total = (int64_t)n * d;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / d, k = t - i * d;
+        P_out[t] = P[(int64_t)perm[i] * d + k];
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        a_out[i] = a[perm[i]];
+}
+
+__global__ void k_scatter_scaled(const double *src, double scale, const int *perm, int n,
+                                 double *dst)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        dst[perm[i]] = scale * src[i];
+}
+
+}  // namespace
+
+size_t points_sort_temp_bytes(int count)
+{
+    size_t t = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, t, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                    (const int *)nullptr, (int *)nullptr, count, 0, 30);
+    return t;
+}
+
+cudaError_t launch_points_sort(const float *P, const double *a, int n, int d, const PointSort &ps,
+                               cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(ps.box, 0xff, 3 * sizeof(uint32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ps.box + 3, 0, 3 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(1024, (n + 255) / 256));
+    k_bbox<<<grid, 256, 0, s>>>(P, n, d, ps.box);
+    k_morton<<<grid, 256, 0, s>>>(P, n, d, ps.box, ps.code, ps.idx);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    size_t t = ps.temp_bytes;
+    e = cub::DeviceRadixSort::SortPairs(ps.temp, t, ps.code, ps.code2, ps.idx, ps.perm, n, 0, 30,
+                                        s);
+    if (e != cudaSuccess) return e;
+    k_gather_points<<<grid, 256, 0, s>>>(P, a, n, d, ps.perm, ps.P, ps.a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_scaled(const double *src, double scale, const int *perm, int n,
+                                  double *dst, cudaStream_t s)
+{
+    k_scatter_scaled<<<std::max(1, std::min(1024, (n + 255) / 256)), 256, 0, s>>>(src, scale, perm,
+                                                                                 n, dst);
     return cudaGetLastError();
 }
 

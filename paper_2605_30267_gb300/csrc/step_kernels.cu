@@ -226,8 +226,9 @@ __global__ void __launch_bounds__(kVecNT) k_init(Work w, int n, int m, int nstat
         w.logb[j] = log(bj);
         double xj = 0.0, wj = 0.0;
         if (is.x) {
-            xj = is.div > 0.0 ? is.x[j] / is.div : is.x[j] * is.mul;
-            wj = is.w ? is.w[j] * is.mul : alpha0 * xj;
+            const int jj = is.perm ? is.perm[j] : j;
+            xj = is.div > 0.0 ? is.x[jj] / is.div : is.x[jj] * is.mul;
+            wj = is.w ? is.w[jj] * is.mul : alpha0 * xj;
         }
         w.x[j] = xj;
         w.x_prev[j] = xj;

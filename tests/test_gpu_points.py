@@ -350,3 +350,30 @@ def test_plan_and_barycentric_match_oracle(ctx, kind, scale):
     np.testing.assert_allclose(P64.cpu().numpy().sum(1), ref["a"], rtol=1e-7)
     np.testing.assert_allclose(out.cpu().numpy(), O.barycentric(cost, eps, ref["f"], ref["g"], Z),
                                rtol=1e-11, atol=1e-13)
+
+
+# ------------------------------------------- sorted clouds, pruned passes --
+# Solves with d <= 4 sort both clouds along a space-filling curve and skip the
+# slots whose terms are all below 2^-80 of their rows' sums. These sizes give
+# each row dozens of slots, so most of them are skipped.
+
+def test_pruned_colour_solve_matches_oracle(ctx):
+    pr = W.color_transfer_problem(seed=1, n=4096, eps=1e-3)
+    for method in (B.ACC, B.PLAIN):
+        check_points(ctx, pr["X"], pr["Y"], "sqeuclid", pr["a"], pr["b"], 1e-3, 1e-6, method,
+                     scale=True)
+
+
+def test_pruned_solve_on_offset_clouds(ctx):
+    # coordinates near 100 and an unscaled cost: the exponent terms are ~1e7
+    # log2 units, so the FP32 estimate's rounding (~1 unit) needs the
+    # magnitude-relative margin of the skip test
+    X, Y, a, b = sqeuclid_points(43, 2048, 1536, 3)
+    X += np.float32(100.0)
+    Y += np.float32(100.0)
+    check_points(ctx, X, Y, "sqeuclid", a, b, 1e-2)
+
+
+def test_pruned_cosine_solve_matches_oracle(ctx):
+    X, Y, a, b = cosine_points(44, 2048, 2304, 3)
+    check_points(ctx, X, Y, "cosine", a, b, 5e-3)
