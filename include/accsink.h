@@ -64,6 +64,7 @@ enum { ACCSINK_PLAIN = 0, ACCSINK_ACC = 1 };
 enum { ACCSINK_STAB_OFF = 0, ACCSINK_STAB_REPORT = 1, ACCSINK_STAB_GATE = 2,
        ACCSINK_STAB_BACKTRACK = 3 };
 enum { ACCSINK_CARRY_Y = 0, ACCSINK_CARRY_W = 1 };
+enum { ACCSINK_PRECISION_AUTO = 0, ACCSINK_PRECISION_FP32 = 1, ACCSINK_PRECISION_DF32 = 2 };
 
 typedef struct accsink_ctx accsink_ctx;
 
@@ -98,7 +99,16 @@ typedef struct {
  * hands w over unchanged as Algorithm 2 is printed. stability: OFF skips the
  * Theorem 4 test, REPORT counts failures, GATE also restarts the momentum
  * (w <- alpha x) after a failed step, BACKTRACK instead ends the homotopy
- * stage at once (mu <- mu / 2, so the next step uses a smaller alpha). */
+ * stage at once (mu <- mu / 2, so the next step uses a smaller alpha).
+ * precision: the arithmetic of the exponent arguments. DF32 forms every
+ * argument in FP32 double-float (exact splits; the results sit ~1e-7 from
+ * the FP64 truth, which tol = 1e-6 at eps = 1e-3 needs). FP32 drops the low
+ * parts where that is cheaper: point-cloud solves with d <= 4 then form x.y
+ * in plain FP32 (about twice as fast per pass), with argument errors of
+ * ~2^-22 of the terms' size |C| / eps, so only loose tolerances converge
+ * (e.g. 1e-5 at eps = 0.1 for costs scaled to max 1). Stored costs are read
+ * at the memory bound either way and always use DF32, as do point clouds
+ * with d > 4 and batched solves. AUTO (the default) is DF32. */
 typedef struct {
     int32_t method;
     int32_t m0;
@@ -115,7 +125,7 @@ typedef struct {
                               (another 4 n m bytes, made once per solve) so
                               the column pass streams rows too, when the
                               budget and the device allow; 0: never */
-    int32_t reserved;
+    int32_t precision;   /* ACCSINK_PRECISION_*                              */
 } accsink_params;
 
 /* Result of a solve (host struct, filled by the library). */

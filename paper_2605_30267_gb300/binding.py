@@ -21,6 +21,7 @@ SCALE_NONE, SCALE_MAX_TO_ONE = 0, 1
 PLAIN, ACC = 0, 1
 STAB_OFF, STAB_REPORT, STAB_GATE, STAB_BACKTRACK = 0, 1, 2, 3
 CARRY_Y, CARRY_W = 0, 1
+PREC_AUTO, PREC_FP32, PREC_DF32 = 0, 1, 2
 
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID_ARG", 2: "ERR_NONPOSITIVE_MARGINAL",
                 3: "ERR_NONFINITE", 4: "ERR_OOM", 5: "ERR_BUDGET", 6: "ERR_TIMEOUT",
@@ -55,7 +56,7 @@ class accsink_params(ct.Structure):
                 ("tol", ct.c_double), ("mu0", ct.c_double),
                 ("max_sinkhorn_steps", ct.c_int32), ("stability", ct.c_int32),
                 ("carry", ct.c_int32), ("evaluate", ct.c_int32), ("use_graph", ct.c_int32),
-                ("history", ct.c_int32), ("col_transpose", ct.c_int32), ("reserved", ct.c_int32)]
+                ("history", ct.c_int32), ("col_transpose", ct.c_int32), ("precision", ct.c_int32)]
 
 
 class accsink_result(ct.Structure):

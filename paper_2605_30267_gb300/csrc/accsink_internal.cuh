@@ -133,6 +133,7 @@ struct PointView {
     int64_t ldq;
     int32_t nr, nc, d, kind;
     int32_t prune;   // 1: points sorted along a space-filling curve; far slots skipped
+    int32_t fp32;    // 1: x.Q in plain FP32 (no low parts)
 };
 
 struct CostView {

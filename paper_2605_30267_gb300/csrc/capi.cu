@@ -55,6 +55,7 @@ struct GraphKey {
     int64_t ldc = 0;
     int n = 0, m = 0, vec = 0, row_grid = 0, splits = 0, step_grid = 0, colt_grid = 0;
     int row_nfull = 0, row_parts = 0, colt_nfull = 0, colt_parts = 0;
+    int prec = 0;        // kernel-argument flags that vary per solve (FP32 points)
     void *ws = nullptr;
     const float *ct = nullptr;
     bool operator==(const GraphKey &o) const
@@ -63,7 +64,7 @@ struct GraphKey {
                row_grid == o.row_grid && splits == o.splits && step_grid == o.step_grid &&
                colt_grid == o.colt_grid && row_nfull == o.row_nfull &&
                row_parts == o.row_parts && colt_nfull == o.colt_nfull &&
-               colt_parts == o.colt_parts && ws == o.ws && ct == o.ct;
+               colt_parts == o.colt_parts && prec == o.prec && ws == o.ws && ct == o.ct;
     }
 };
 
@@ -360,6 +361,8 @@ int validate_params(accsink_ctx *ctx, const accsink_params *q)
     if (q->carry != ACCSINK_CARRY_Y && q->carry != ACCSINK_CARRY_W)
         return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown carry mode");
     if (q->history < 0) return fail(ctx, ACCSINK_ERR_INVALID_ARG, "history must be >= 0");
+    if (q->precision < ACCSINK_PRECISION_AUTO || q->precision > ACCSINK_PRECISION_DF32)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "unknown precision");
     return ACCSINK_OK;
 }
 
@@ -753,6 +756,8 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     PointPlan pl;
     int rc = points_plan(ctx, prob, prm->history, pl, true);
     if (rc != ACCSINK_OK) return rc;
+    // FP32 arguments on request (header: precision)
+    pl.pr.fp32 = pl.pc.fp32 = prm->precision == ACCSINK_PRECISION_FP32 ? 1 : 0;
     // a sorted solve runs on the clouds (and marginals) in Morton order
     accsink_problem ps = *prob;
     InitState is0 = start ? start->is : InitState();
@@ -820,6 +825,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
         key.C = prob->X; key.ct = prob->Y; key.ldc = prob->d; key.n = n; key.m = m;
         key.vec = 100 + kind; key.row_grid = prow; key.colt_grid = pcol;
         key.step_grid = g.step_grid; key.ws = ctx->pts;
+        key.prec = pr.fp32 * 2 + pr.prune;
         rc = build_loop_graph(ctx, key, body);
         if (rc != ACCSINK_OK) {
             ctx->graph_broken = true;

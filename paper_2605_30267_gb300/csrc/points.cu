@@ -40,13 +40,29 @@ constexpr int kPtNT = 256;
 // set-up).
 // Small DMAX: the slot's Q columns were loaded into qh/ql once for all RW
 // rows (PRE). Larger DMAX: they are read per k from Qh/Ql (L1-resident).
+// f32: plain FP32 FMAs on the high parts only (precision FP32).
 template <int DMAX, bool PRE>
 __device__ __forceinline__ void slot_dot(const float *p, int d, const float4 &ah,
                                          const float4 &al, const float4 *qh, const float4 *ql,
                                          const float *Qh, const float *Ql, int64_t ldq, int v,
-                                         float h[4], float l[4])
+                                         float h[4], float l[4], const bool f32)
 {
     h[0] = ah.x; h[1] = ah.y; h[2] = ah.z; h[3] = ah.w;
+    if (f32) {
+        l[0] = l[1] = l[2] = l[3] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) {
+            if (k < d) {
+                const float4 a4 =
+                    PRE ? qh[k] : __ldg(reinterpret_cast<const float4 *>(Qh + k * ldq) + v);
+                h[0] = fmaf(p[k], a4.x, h[0]);
+                h[1] = fmaf(p[k], a4.y, h[1]);
+                h[2] = fmaf(p[k], a4.z, h[2]);
+                h[3] = fmaf(p[k], a4.w, h[3]);
+            }
+        }
+        return;
+    }
     l[0] = al.x; l[1] = al.y; l[2] = al.z; l[3] = al.w;
 #pragma unroll
     for (int k = 0; k < DMAX; ++k) {
@@ -122,7 +138,8 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // parts), so the threshold is lowered by 2^-20 of a bound on that magnitude.
 constexpr float kSkipLog2 = 80.0f;
 
-template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false, bool PRUNE = false>
+template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false, bool PRUNE = false,
+          bool F32 = false>
 __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 {
     DevState *st = w.st;
@@ -138,6 +155,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
     const int nfull = (nc >> 2) & ~31;         // slots in whole, unmasked 32-lane chunks
     const float cs_scale = WC ? (float)pv.scal[1] : 0.0f;
     constexpr bool PRE = DMAX <= 4;
+    constexpr bool f32 = F32;   // x.Q in plain FP32 (precision FP32)
     const float4 *Ah4 = reinterpret_cast<const float4 *>(pv.Ah);
     const float4 *Al4 = reinterpret_cast<const float4 *>(pv.Al);
 
@@ -195,16 +213,19 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                 }
                 if (__all_sync(0xffffffffu, far)) continue;
             }
-            const float4 al = __ldg(Al4 + v);
-            if (PRE) {
+            float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!f32) {
+                al = __ldg(Al4 + v);
+                if (PRE) {
 #pragma unroll
-                for (int k = 0; k < DMAX; ++k)
-                    if (k < d) ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
+                    for (int k = 0; k < DMAX; ++k)
+                        if (k < d) ql[k] = __ldg(reinterpret_cast<const float4 *>(pv.Ql + k * ldq) + v);
+                }
             }
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
                 float h[4], l[4], cst[4];
-                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l);
+                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l, f32);
                 if (WC) slot_cost<DMAX>(p[q], d, pv.kind, cs_scale, pv.Pc, 4 * v, nc, cst);
                 slot_accumulate<WC>(acc[q], cacc[q], h, l, cst);
             }
@@ -226,7 +247,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 #pragma unroll
             for (int q = 0; q < RW; ++q) {
                 float h[4], l[4], cst[4];
-                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l);
+                slot_dot<DMAX, PRE>(p[q], d, ah, al, qh, ql, pv.Qh, pv.Ql, ldq, v, h, l, f32);
                 if (WC) slot_cost<DMAX>(p[q], d, pv.kind, cs_scale, pv.Pc, c0, nc, cst);
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -310,6 +331,14 @@ constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 template <int MODE, bool WC>
 static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cudaStream_t s)
 {
+    if (pv.prune && pv.d <= 4 && pv.fp32) {
+        // sorted point clouds, FP32 arguments (precision FP32)
+        if (pv.d == 2) k_lse_points<MODE, 2, rows_per_warp<2>(), WC, true, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else if (pv.d == 3) k_lse_points<MODE, 3, rows_per_warp<3>(), WC, true, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else if (pv.d == 4) k_lse_points<MODE, 4, rows_per_warp<4>(), WC, true, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        else k_lse_points<MODE, 4, rows_per_warp<4>(), WC, false, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
+        return cudaGetLastError();
+    }
     if (pv.prune && pv.d <= 4) {
         // sorted point clouds (see the set-up): the pruned kernels
         if (pv.d == 2) k_lse_points<MODE, 2, rows_per_warp<2>(), WC, true, true><<<grid, kPtNT, 0, s>>>(pv, w);

@@ -377,3 +377,38 @@ def test_pruned_solve_on_offset_clouds(ctx):
 def test_pruned_cosine_solve_matches_oracle(ctx):
     X, Y, a, b = cosine_points(44, 2048, 2304, 3)
     check_points(ctx, X, Y, "cosine", a, b, 5e-3)
+
+
+# ------------------------------------------------------------- precision --
+# FP32 arguments (precision FP32, sorted clouds with d <= 4): the exponent
+# arguments err by ~2^-22 of the terms' size k s (|x| + |y|)^2, about 1.4e-5
+# log2 units here (eps = 0.1, points in the unit cube, cost scaled to max 1),
+# i.e. ~1e-5 relative in every P_ij: potentials within ~1e-5 eps and a
+# marginal floor of a few 1e-5.
+
+def test_fp32_point_solves_match_oracle_at_loose_tolerance(ctx):
+    pr = W.color_transfer_problem(seed=2, n=2048, eps=0.1)
+    X, Y, a, b = pr["X"], pr["Y"], pr["a"], pr["b"]
+    cost = O.Cost(X=X, Y=Y, kind="sqeuclid", scale_to_max=True)
+    ref = O.solve(cost, a, b, 0.1, tol=1e-11)
+    for method in (B.ACC, B.PLAIN):
+        f, g, res = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 0.1, 1e-5, method, True,
+                                     precision=B.PREC_FP32)
+        assert res["status"] == 0, res
+        sh = g.mean() - ref["g"].mean()
+        dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
+        assert dpot <= 1e-4 * 0.1, dpot
+        ev = O.evaluate(cost, 0.1, ref["a"], ref["b"], f, g)
+        assert ev["col_l1"] <= 5e-5 and ev["row_l1"] <= 5e-5, ev
+
+
+def test_df32_is_the_default_precision(ctx):
+    X, Y, a, b = sqeuclid_points(45, 700, 650, 3)
+    f0, g0, r0 = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True)
+    f1, g1, r1 = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True,
+                                  precision=B.PREC_DF32)
+    assert r0["sinkhorn_steps"] == r1["sinkhorn_steps"]
+    np.testing.assert_array_equal(f0, f1)
+    np.testing.assert_array_equal(g0, g1)
+    with pytest.raises(B.AccsinkError):
+        gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True, precision=3)
