@@ -360,7 +360,8 @@ int accsink_server_submit(accsink_server *S, const accsink_problem *prob_host,
         (q.method != ACCSINK_PLAIN && q.method != ACCSINK_ACC) ||
         (q.method == ACCSINK_ACC && (!(q.mu0 > 0.0 && q.mu0 < 1.0) || q.m0 < 1)) ||
         q.stability < 0 || q.stability > 3 ||
-        (q.carry != ACCSINK_CARRY_Y && q.carry != ACCSINK_CARRY_W))
+        (q.carry != ACCSINK_CARRY_Y && q.carry != ACCSINK_CARRY_W) ||
+        q.precision < ACCSINK_PRECISION_AUTO || q.precision > ACCSINK_PRECISION_DF32)
         return ACCSINK_ERR_INVALID_ARG;
     {
         std::lock_guard<std::mutex> lk(S->mu);
