@@ -207,9 +207,14 @@ def run_gpu(args):
         res = solve(B.ACC, EPS)
         evs[k][1].record(stream)
         steps.append(res.sinkhorn_steps)
-        # set-up (set_state, cost stats, init), 3 per S evaluation, final
-        # cost pass, two output scalings
-        launches += 3 + 3 * res.sinkhorn_steps + 1 + 2
+        # set-up (state, stage table, cost statistics, init, transpose), the
+        # loop's three kernels per S evaluation, launched two evaluations per
+        # trip of the graph's WHILE node (eight per host round trip in the
+        # host loop; the kernels after the stopping step return at once), the
+        # final cost pass and two output scalings
+        k = res.sinkhorn_steps
+        per = 8 if args.host_loop else 2
+        launches += 5 + 3 * per * ((k + per - 1) // per) + 1 + 2
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
