@@ -125,7 +125,7 @@ __device__ __forceinline__ float term_s(float s, float G, float gk, float c, flo
 
 }  // namespace
 
-template <class GEO, bool WITH_COST, bool ROTATE = true>
+template <class GEO, bool WITH_COST>
 __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work w)
 {
     constexpr int kRW = GEO::kRW, kNCW = GEO::kNCW, kTW = GEO::kTW, kStages = GEO::kStages;
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work 
     // Each CTA starts its sweep of a row at a different tile: with a row
     // pitch of a power of two, CTAs moving in lockstep would otherwise hit
     // the same address bits below the pitch at the same time.
-    const int rot = ROTATE ? (int)(blockIdx.x % (unsigned)ntiles_row) : 0;
+    const int rot = (int)(blockIdx.x % (unsigned)ntiles_row);
     auto tile_col = [&](int ti) {
         int tt = ti + rot;
         if (tt >= ntiles_row) tt -= ntiles_row;
@@ -333,6 +333,8 @@ __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work 
                 const float Fh = (float)F;
                 const float Fl = (float)(F - (double)Fh);
                 w.FF[i] = make_float2(Fh, Fl * kh);
+                w.Fh[i] = Fh;        // the operand of the column pass over C^T
+                w.Fk[i] = Fl * kh;
                 my_dual += w.a[i] * ui;
                 if (WITH_COST) {
                     const double wi = w.f_given ? exp(w.f_given[i] / st->eps_user + lse) : w.a[i];
@@ -356,23 +358,8 @@ __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work 
     }
 }
 
-using GeoA = RowGeo<2, 8, 512, 5>;    // 16-row groups, 9 warps
-using GeoB = RowGeo<1, 16, 512, 5>;   // 16-row groups, 17 warps
-using GeoC = RowGeo<1, 8, 512, 5>;    // 8-row groups, 9 warps, half the stage
-using GeoD = RowGeo<1, 16, 1024, 3>;  // 16-row groups, 17 warps, wide tiles
+using GeoA = RowGeo<2, 8, 512, 5>;    // 16-row groups of 2 rows per consumer warp, 9 warps
 
-template <class GEO>
-static cudaError_t launch_geo(const CostView &cv, const Work &w, int grid, bool with_cost,
-                              cudaStream_t s)
-{
-    if (with_cost)
-        k_row_pass_tma<GEO, true><<<grid, GEO::kNT, GEO::kSmemBytes, s>>>(cv, w);
-    else
-        k_row_pass_tma<GEO, false><<<grid, GEO::kNT, GEO::kSmemBytes, s>>>(cv, w);
-    return cudaGetLastError();
-}
-
-static int g_row_variant = 0;
 static int g_row_kernel = 0;
 
 int row_kernel_choice() { return g_row_kernel; }
@@ -380,48 +367,30 @@ int row_kernel_choice() { return g_row_kernel; }
 cudaError_t launch_row_pass_tma(const CostView &cv, const Work &w, int grid, bool with_cost,
                                 cudaStream_t s)
 {
-    switch (g_row_variant) {
-    case 0: return launch_geo<GeoA>(cv, w, grid, with_cost, s);
-    case 2: return launch_geo<GeoC>(cv, w, grid, with_cost, s);
-    case 1: return launch_geo<GeoB>(cv, w, grid, with_cost, s);
-    case 3: return launch_geo<GeoD>(cv, w, grid, with_cost, s);
-    case 4:
-        k_row_pass_tma<GeoA, false, false><<<grid, GeoA::kNT, GeoA::kSmemBytes, s>>>(cv, w);
-        return cudaGetLastError();
-    default: return launch_geo<GeoA>(cv, w, grid, with_cost, s);
-    }
-}
-
-template <class GEO>
-static cudaError_t setup_geo()
-{
-    cudaError_t e = cudaFuncSetAttribute(k_row_pass_tma<GEO, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)GEO::kSmemBytes);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_row_pass_tma<GEO, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GEO::kSmemBytes);
+    if (with_cost)
+        k_row_pass_tma<GeoA, true><<<grid, GeoA::kNT, GeoA::kSmemBytes, s>>>(cv, w);
+    else
+        k_row_pass_tma<GeoA, false><<<grid, GeoA::kNT, GeoA::kSmemBytes, s>>>(cv, w);
+    return cudaGetLastError();
 }
 
 // Must run once per process before the first launch (outside any capture):
-// opts the kernels in to their dynamic shared memory. ACCSINK_ROW_VARIANT
-// (0..3) selects the pipeline geometry for tuning runs.
+// opts the kernels in to their dynamic shared memory. ACCSINK_ROW_KERNEL=tma
+// selects this pipeline for the 128-bit-aligned row pass instead of the
+// warp-per-row kernel (measured slower; kept as the bulk-copy alternative).
 cudaError_t setup_row_pass_tma()
 {
     const char *k = getenv("ACCSINK_ROW_KERNEL");
     if (k && k[0] == 't') g_row_kernel = 1;
     if (k && k[0] == 'w') g_row_kernel = 0;
-    const char *v = getenv("ACCSINK_ROW_VARIANT");
-    if (v && v[0] >= '0' && v[0] <= '4') g_row_variant = v[0] - '0';
-    cudaFuncSetAttribute(k_row_pass_tma<GeoA, false, false>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GeoA::kSmemBytes);
-    cudaError_t e;
-    if ((e = setup_geo<GeoA>()) != cudaSuccess) return e;
-    if ((e = setup_geo<GeoB>()) != cudaSuccess) return e;
-    if ((e = setup_geo<GeoC>()) != cudaSuccess) return e;
-    return setup_geo<GeoD>();
+    cudaError_t e = cudaFuncSetAttribute(k_row_pass_tma<GeoA, false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)GeoA::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_row_pass_tma<GeoA, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GeoA::kSmemBytes);
 }
 
-int row_pass_tma_smem_bytes() { return (int)GeoB::kSmemBytes; }
+int row_pass_tma_smem_bytes() { return (int)GeoA::kSmemBytes; }
 
 }  // namespace accsink

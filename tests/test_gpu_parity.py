@@ -368,3 +368,40 @@ def test_full_size_solve_properties(ctx, big_problem, method):
     assert np.abs(c - pr["b"][cols]).sum() <= tol * 64 / 16384 * 50
     # transport cost from the sampled rows extrapolates consistently
     assert np.isfinite(res["transport_cost"]) and res["transport_cost"] > 0
+
+
+def test_tma_row_pass_alternative_matches_oracle():
+    """The bulk-copy (cp.async.bulk + mbarrier) row pass, selected with
+    ACCSINK_ROW_KERNEL=tma for a whole process, gives the same solve."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import numpy as np, torch
+import oracle as O
+from paper_2605_30267_gb300 import binding as B
+from paper_2605_30267_gb300 import workloads as W
+pr = W.gmm_stored_cost_problem(seed=61, n=700, m=640, eps=1e-2)
+dev = torch.device("cuda:0")
+ctx = B.Context(0)
+n, m = 700, 640
+f = torch.empty(n, dtype=torch.float64, device=dev); g = torch.empty(m, dtype=torch.float64, device=dev)
+C = torch.from_numpy(pr["C"]).to(dev)
+prob = B.problem_dense(C, torch.from_numpy(pr["a"]).to(dev), torch.from_numpy(pr["b"]).to(dev))
+res = B.result_dict(ctx.accsink_solve(prob, B.default_params(eps=1e-2, tol=1e-6), f, g))
+ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-2, tol=1e-6)
+fg, gg = f.cpu().numpy(), g.cpu().numpy()
+sh = gg.mean() - ref["g"].mean()
+d = max(np.abs(gg - sh - ref["g"]).max(), np.abs(fg + sh - ref["f"]).max())
+ev = O.evaluate(O.Cost(C=pr["C"]), 1e-2, ref["a"], ref["b"], fg, gg)
+assert res["status"] == 0, res
+assert d <= 1e-3 * 1e-2, d
+assert ev["col_l1"] <= 1.05e-6 and ev["row_l1"] <= 2e-7, ev
+print("ok", res["sinkhorn_steps"], ref["sinkhorn_steps"])
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, ACCSINK_ROW_KERNEL="tma")
+    out = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True,
+                         text=True, timeout=600)
+    assert out.returncode == 0, out.stdout[-2000:] + out.stderr[-2000:]
+    assert "ok" in out.stdout
