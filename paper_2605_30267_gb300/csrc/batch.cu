@@ -933,6 +933,22 @@ __device__ void cta_finish(BatchProb *P, BatchResult *R, bool ok)
     __syncthreads();
 }
 
+// Publishes a finished problem's result to the host-mapped copy (when the
+// launch has one): every thread's output writes are made visible first, then
+// thread 0 writes the record and, after a system-scope fence, the flag.
+__device__ void publish_early(BatchQueue *q, int p, const BatchResult *R)
+{
+    if (!q->early) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        q->early[p] = *R;
+        __threadfence_system();
+        *(volatile int32_t *)&q->early_flag[p] = 1;
+    }
+    __syncthreads();
+}
+
 // ----------------------------------------------------------------- queue --
 
 // Pops one item (thread 0). Returns false when the batch is finished or a
@@ -1249,6 +1265,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
                 }
             }
             cta_finish<true>(P, R, ok);
+            publish_early(q, p, R);
             problem_done(q);
         } else if (kind == BI_INIT) {
             const bool ok = cta_init(P);
@@ -1256,6 +1273,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
                 q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
             } else {
                 cta_finish<false>(P, R, false);
+                publish_early(q, p, R);
                 problem_done(q);
             }
         } else if (kind == BI_ROW || kind == BI_FINAL) {
@@ -1273,6 +1291,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
                     q_push(q, P->col_items, [&](int t) { return batch_item(BI_COL, p, t); });
                 } else {
                     cta_finish<false>(P, R, true);
+                    publish_early(q, p, R);
                     problem_done(q);
                 }
             }
@@ -1298,6 +1317,7 @@ __global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, 
                     q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_FINAL, p, t); });
                 } else {
                     cta_finish<false>(P, R, true);
+                    publish_early(q, p, R);
                     problem_done(q);
                 }
             }

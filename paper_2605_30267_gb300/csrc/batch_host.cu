@@ -2,10 +2,13 @@
 // layout, initial queue), launches the formation and the persistent solve,
 // and collects the results. Called by accsink_solve_batch.
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "accsink.h"
@@ -146,6 +149,22 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
 
 }  // namespace
 
+// The public result of one problem of a batched launch.
+void to_result(const BatchResult &r, float ms, accsink_result &o)
+{
+    std::memset(&o, 0, sizeof(o));
+    o.status = r.status;
+    o.sinkhorn_steps = r.steps;
+    o.outer_stages = r.stages;
+    o.stability_failures = r.failures;
+    o.marginal_l1 = r.marginal_l1;
+    o.transport_cost = r.transport_cost;
+    o.dual_objective = r.dual;
+    o.cost_max = r.cost_max;
+    o.gpu_ms = ms;
+    o.loop_mode = 2;
+}
+
 size_t batch_workspace_bytes(const BatchTuning &tn, int count, const accsink_problem *probs)
 {
     BatchPlan pl;
@@ -229,6 +248,8 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     hq.seq = dSeq;
     hq.cap = cap;
     hq.count = count;
+    hq.early = env.on_done ? env.early_dev : nullptr;
+    hq.early_flag = env.on_done ? env.flag_dev : nullptr;
     // ---- stage the host records (pinned) and launch
     const size_t hbytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchTile) * tiles.size()) +
                           up256(8 * (size_t)count) + up256(sizeof(BatchQueue)) +
@@ -280,6 +301,25 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     BK(cudaEventRecord(env.ev1, s));
     BK(cudaMemcpyAsync(hR, dR, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, s));
     BK(cudaMemcpyAsync(hQ, dQ, sizeof(BatchQueue), cudaMemcpyDeviceToHost, s));
+    if (env.on_done && env.early_host && env.flag_host) {
+        // hand back each problem as soon as the kernel has finished it
+        std::vector<char> seen(count, 0);
+        int left = count;
+        for (;;) {
+            const bool finished = cudaStreamQuery(s) != cudaErrorNotReady;
+            for (int k = 0; k < count && left > 0; ++k) {
+                if (seen[k] || *(volatile int32_t *)&env.flag_host[k] == 0) continue;
+                std::atomic_thread_fence(std::memory_order_acquire);
+                accsink_result o;
+                to_result(env.early_host[k], 0.0f, o);
+                seen[k] = 1;
+                --left;
+                env.on_done(k, o);
+            }
+            if (finished || left == 0) break;
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+    }
     BK(cudaStreamSynchronize(s));
     float ms_all = 0.0f, ms_form = 0.0f;
     cudaEventElapsedTime(&ms_all, env.ev0, env.ev1);
@@ -303,17 +343,7 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     for (int k = 0; k < count; ++k) {
         const BatchResult &r = hR[k];
         accsink_result &o = res[k];
-        std::memset(&o, 0, sizeof(o));
-        o.status = r.status;
-        o.sinkhorn_steps = r.steps;
-        o.outer_stages = r.stages;
-        o.stability_failures = r.failures;
-        o.marginal_l1 = r.marginal_l1;
-        o.transport_cost = r.transport_cost;
-        o.dual_objective = r.dual;
-        o.cost_max = r.cost_max;
-        o.gpu_ms = ms_all;
-        o.loop_mode = 2;
+        to_result(r, ms_all, o);
         if (r.status != ACCSINK_OK) {
             if (rc == ACCSINK_OK || (rc == ACCSINK_ERR_MAXITER && r.status != ACCSINK_ERR_MAXITER))
                 rc = r.status;

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
 
 #include "accsink.h"
@@ -26,11 +27,20 @@ struct BatchTuning {
     int ctas_per_sm = 0;
 };
 
+struct BatchResult;
+
 struct BatchEnv {
     int num_sms = 1;
     int occ_solve = 1;
     size_t budget_left = 0;      // 0: no cap
     cudaEvent_t ev0 = nullptr, ev_mid = nullptr, ev1 = nullptr;
+    // Early completion (optional): host-mapped arrays of at least `count`
+    // results and flags (flags zero at the call) and their device addresses.
+    // While the launch runs, batch_run polls the flags and calls on_done(k, r)
+    // once for every problem k the kernel has finished, in finishing order.
+    BatchResult *early_host = nullptr, *early_dev = nullptr;
+    int32_t *flag_host = nullptr, *flag_dev = nullptr;
+    std::function<void(int, const accsink_result &)> on_done;
 };
 
 struct BatchTiming {

@@ -71,6 +71,11 @@ struct BatchQueue {
     unsigned long long *seq;
     unsigned long long cap;      // power of two
     int32_t count;               // problems in the batch
+    // optional (a serving loop): host-mapped copies of each problem's result
+    // and a flag set once the problem's potentials are written, so the host
+    // can hand finished problems back while the launch still runs
+    BatchResult *early;
+    int32_t *early_flag;
     int32_t done_count;
     int32_t all_done;
     int32_t error;               // ACCSINK_ERR_TIMEOUT on a wait that ran out

@@ -75,6 +75,12 @@ struct accsink_server {
     accsink::BatchWorkspace ws;
     accsink::BatchTuning tuning;
     cudaMemPool_t pool = nullptr;   // server-owned pool for inputs and outputs
+    // host-mapped result records and done flags of the running batch, so a
+    // request finishes when its own problem does, not when the whole batch
+    // does (capacity in problems; grown by the worker)
+    accsink::BatchResult *early = nullptr;
+    int32_t *early_flag = nullptr;
+    int early_cap = 0;
     // accounting (under mu)
     size_t resident = 0;          // outputs held for DONE tickets
     size_t peak_in_use = 0;
@@ -206,6 +212,22 @@ void worker_loop(accsink_server *S)
         int rc = ACCSINK_ERR_CUDA;
         std::string berr = cerr;
         accsink::BatchTiming tm;
+        if (cuda_ok && k > S->early_cap) {
+            const int cap = std::max(k, 2 * S->early_cap);
+            if (S->early) cudaFreeHost(S->early);
+            if (S->early_flag) cudaFreeHost(S->early_flag);
+            S->early = nullptr;
+            S->early_flag = nullptr;
+            S->early_cap = 0;
+            if (cudaHostAlloc((void **)&S->early, sizeof(accsink::BatchResult) * cap,
+                              cudaHostAllocMapped) == cudaSuccess &&
+                cudaHostAlloc((void **)&S->early_flag, sizeof(int32_t) * cap,
+                              cudaHostAllocMapped) == cudaSuccess) {
+                S->early_cap = cap;
+            } else {
+                cudaGetLastError();   // no early completion; the batch still runs
+            }
+        }
         if (cuda_ok) {
             accsink::BatchEnv env;
             env.num_sms = S->num_sms;
@@ -214,6 +236,39 @@ void worker_loop(accsink_server *S)
             env.ev0 = S->ev0;
             env.ev_mid = S->ev_mid;
             env.ev1 = S->ev1;
+            if (S->early_cap >= k) {
+                std::memset(S->early_flag, 0, sizeof(int32_t) * k);
+                env.early_host = S->early;
+                env.flag_host = S->early_flag;
+                if (cudaHostGetDevicePointer((void **)&env.early_dev, S->early, 0) != cudaSuccess ||
+                    cudaHostGetDevicePointer((void **)&env.flag_dev, S->early_flag, 0) !=
+                        cudaSuccess) {
+                    cudaGetLastError();
+                    env.early_host = nullptr;
+                    env.flag_host = nullptr;
+                } else {
+                    // a converged (or step-limited) problem is DONE at once;
+                    // anything else is settled with the batch below
+                    env.on_done = [&](int i, const accsink_result &r) {
+                        if (r.status != ACCSINK_OK && r.status != ACCSINK_ERR_MAXITER) return;
+                        {
+                            std::lock_guard<std::mutex> lk(S->mu);
+                            auto it = S->reqs.find(group[i]);
+                            if (it == S->reqs.end()) return;
+                            Request &q = it->second;
+                            q.t_done = Clock::now();
+                            q.res = r;
+                            q.f_dev = fo[i];
+                            q.g_dev = go[i];
+                            q.out_bytes = output_bytes(q.prob);
+                            S->resident += q.out_bytes;
+                            q.state = ACCSINK_REQ_DONE;
+                            ++S->solved;
+                        }
+                        S->cv_done.notify_all();
+                    };
+                }
+            }
             rc = accsink::batch_run(env, S->ws, tuning, k, probs.data(), params.data(),
                                     fo.data(), go.data(), res.data(), S->stream, berr, &tm);
         }
@@ -231,7 +286,14 @@ void worker_loop(accsink_server *S)
                                          rc == ACCSINK_ERR_NONPOSITIVE_MARGINAL ||
                                          rc == ACCSINK_ERR_INVALID_ARG);
             for (int i = 0; i < k; ++i) {
-                Request &r = S->reqs[group[i]];
+                // a ticket handed back early may already be released
+                auto it = S->reqs.find(group[i]);
+                if (it == S->reqs.end()) continue;
+                Request &r = it->second;
+                if (r.state == ACCSINK_REQ_DONE) {
+                    r.res.gpu_ms = res[i].gpu_ms;   // handed back early; batch time only
+                    continue;
+                }
                 r.t_done = now;
                 if (ran && (res[i].status == ACCSINK_OK || res[i].status == ACCSINK_ERR_MAXITER)) {
                     r.res = res[i];
@@ -326,6 +388,8 @@ void accsink_server_destroy(accsink_server *S)
     if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->ws.dev) cudaFree(S->ws.dev);
     if (S->ws.host) cudaFreeHost(S->ws.host);
+    if (S->early) cudaFreeHost(S->early);
+    if (S->early_flag) cudaFreeHost(S->early_flag);
     if (S->stream) cudaStreamDestroy(S->stream);
     if (S->ev0) cudaEventDestroy(S->ev0);
     if (S->ev_mid) cudaEventDestroy(S->ev_mid);

@@ -170,3 +170,48 @@ def test_concurrent_clients():
         assert srv.stats()["resident_bytes"] == 0
     finally:
         srv.close()
+
+
+def test_requests_finish_with_their_own_problem():
+    """A batch hands each problem back as soon as the kernel finishes it: small
+    requests submitted with a large one complete (and may be released) while
+    the large one still runs; results and the accounting stay exact."""
+    import time
+    big = request(200, 3000, 2800, 3, 1e-3)
+    smalls = [request(201 + k, 48 + 5 * k, 40 + 3 * k, 2, 5e-2) for k in range(8)]
+    blocker = request(199, 2000, 2000, 3, 1e-3)
+    srv = B.Server(0, 4 << 30)
+    try:
+        # while the blocker runs, the large and the small requests queue up,
+        # so they share the next batch
+        t0 = submit(srv, blocker)
+        time.sleep(0.002)
+        tb = submit(srv, big)
+        ts = [submit(srv, r) for r in smalls]
+        got, before_big = {}, 0
+        for k, t in enumerate(ts):
+            rc, res, lat = srv.wait(t, 120000)
+            assert rc == B.OK, (rc, srv.last_error())
+            if srv.poll(tb) == B.REQ_RUNNING:
+                before_big += 1
+            got[k] = srv.copy_potentials(t)
+            srv.release(t)               # possibly while the batch still runs
+        rc, res, lat = srv.wait(tb, 300000)
+        assert rc == B.OK, (rc, srv.last_error())
+        fbig, gbig = srv.copy_potentials(tb)
+        srv.release(tb)
+        assert srv.wait(t0, 300000)[0] == B.OK
+        srv.release(t0)
+        time.sleep(0.05)
+        st = srv.stats()
+        assert st["solved"] == 10 and st["failed"] == 0, st
+        assert st["resident_bytes"] == 0 and st["queued"] == 0, st
+        fref, gref, _ = batch_reference(smalls + [big])
+        for k in range(8):
+            np.testing.assert_array_equal(got[k][0], fref[k])
+            np.testing.assert_array_equal(got[k][1], gref[k])
+        np.testing.assert_array_equal(fbig, fref[8])
+        np.testing.assert_array_equal(gbig, gref[8])
+        assert before_big >= 1, before_big
+    finally:
+        srv.close()
