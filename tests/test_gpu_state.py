@@ -189,3 +189,44 @@ def test_state_errors(ctx):
             c2.accsink_export_state(x, w)            # a single pass replaced the state
     finally:
         c2.close()
+
+
+# Point-cloud solves with d <= 4 run on Morton-sorted clouds: warm starts and
+# exported states go through the permutation in both directions.
+
+def points_prob(seed, n, m, d=3):
+    g0 = np.random.default_rng(seed)
+    X = g0.random((n, d)).astype(np.float32)
+    Y = g0.random((m, d)).astype(np.float32)
+    a, b = W.dirichlet1(g0, n), W.dirichlet1(g0, m)
+    prob = B.problem_points(to_dev(X), to_dev(Y), kind="sqeuclid", a=to_dev(a), b=to_dev(b),
+                            scale_to_max=True)
+    return prob, O.Cost(X=X, Y=Y, kind="sqeuclid", scale_to_max=True), a, b
+
+
+def test_points_warm_start_at_the_fixed_point_stops_at_once(ctx):
+    prob, cost, a, b = points_prob(51, 900, 1100)
+    ref = O.solve(cost, a, b, 1e-2, tol=1e-11)
+    f, g = outs(900, 1100)
+    res = B.result_dict(ctx.accsink_warm_start(prob, params(1e-2, 1e-6), to_dev(ref["g"]), f, g))
+    assert res["status"] == 0 and res["sinkhorn_steps"] == 1
+    assert gauge_close(f.cpu().numpy(), g.cpu().numpy(), ref["f"], ref["g"], 1e-5 * 1e-2)
+
+
+def test_points_eps_continuation_matches_the_oracle(ctx):
+    prob, cost, a, b = points_prob(52, 800, 700)
+    e1, e2 = 5e-2, 5e-3
+    solve(ctx, prob, 800, 700, params(e1, 1e-4))
+    st, x, w = export(ctx, 700)
+    o1 = O.solve(cost, a, b, e1, tol=1e-4)
+    # the exported iterate is in the caller's column order: it is the same
+    # potential as the oracle's to the solve's accuracy
+    assert np.abs(e1 * (x.cpu().numpy() - x.cpu().numpy().mean())
+                  - e1 * (o1["state"]["x"] - o1["state"]["x"].mean())).max() <= 1e-3 * e1
+    f, g = outs(800, 700)
+    res = B.result_dict(ctx.accsink_solve_from(prob, params(e2, 1e-6), st, f, g))
+    ores = O.resume(cost, a, b, e2, o1["state"], tol=1e-6)
+    cold = O.solve(cost, a, b, e2, tol=1e-11)
+    rs, gs = ores["sinkhorn_steps"], res["sinkhorn_steps"]
+    assert res["status"] == 0 and abs(gs - rs) <= max(1, int(0.05 * rs)), (gs, rs)
+    assert gauge_close(f.cpu().numpy(), g.cpu().numpy(), cold["f"], cold["g"], 1e-3 * e2)
