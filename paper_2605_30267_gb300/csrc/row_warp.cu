@@ -19,6 +19,12 @@
 // 32 rows the warp finishes them together, one row per lane. GB300's FP64
 // rate is 1/64 of FP32, so a finish in one lane per row held the warp (and
 // its next loads) for longer than the finish of 32 rows at once.
+//
+// Load balance: rows are dealt to warps whole, except the rows of a last,
+// part-empty wave, which are split into column parts (plan_row_split) so
+// every resident warp stays busy to the end; the last part of such a row to
+// finish merges the parts in part order (merge_parts), so the result does not
+// depend on the order in which they finished.
 #include <algorithm>
 #include <cstdint>
 
