@@ -419,6 +419,16 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
                         const double *g, int reps, void *stream, float *row_ms,
                         float *col_ms);
 
+/* Failure-path self test. Runs the solver's bounded grid barrier (the one of
+ * the step kernel) in a launch where one block never arrives, so the other
+ * blocks' waits run out after limit_s (0 < limit_s <= 2) seconds: they
+ * record ACCSINK_ERR_TIMEOUT in the solver state and return, and the context
+ * stays usable. *status_out receives the recorded status, *elapsed_s the host
+ * time the launch took. Uses (and leaves for the next solve to rewrite) the
+ * context's workspace state; returns ACCSINK_OK when the launch itself ran. */
+int accsink_selftest_timeout(accsink_ctx *ctx, double limit_s, int32_t *status_out,
+                             double *elapsed_s);
+
 /* Launch geometry the context would use for an n x m dense cost (vec = 1 for
  * the 128-bit path): out6 = {SM count, row-pass CTAs, column-pass row splits,
  * column-pass strips, step-kernel CTAs, cost-statistics CTAs}. */

@@ -39,7 +39,7 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_server_potentials", "accsink_server_copy_potentials",
             "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config",
             "accsink_plan", "accsink_barycentric", "accsink_export_state",
-            "accsink_solve_from", "accsink_warm_start"]
+            "accsink_solve_from", "accsink_warm_start", "accsink_selftest_timeout"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 
 
@@ -134,6 +134,7 @@ def lib():
         L.accsink_plan.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, ct.c_int64, i32, vp]
         L.accsink_barycentric.argtypes = [vp, P(accsink_problem), dbl, vp, vp, vp, i32, vp, vp]
         L.accsink_export_state.argtypes = [vp, P(accsink_state), vp]
+        L.accsink_selftest_timeout.argtypes = [vp, dbl, P(i32), P(dbl)]
         L.accsink_solve_from.argtypes = [vp, P(accsink_problem), P(accsink_params),
                                          P(accsink_state), vp, vp, vp, P(accsink_result)]
         L.accsink_warm_start.argtypes = [vp, P(accsink_problem), P(accsink_params), vp, vp, vp,
@@ -411,6 +412,13 @@ class Context:
         self._raise(lib().accsink_transport_cost(self._h, ct.byref(prob), float(eps), _ptr(f),
                                                  _ptr(g), ct.byref(out), _stream_ptr(stream)))
         return out.value
+
+    def accsink_selftest_timeout(self, limit_s):
+        """Runs the bounded-barrier failure path; returns (status, seconds)."""
+        st, el = ct.c_int32(), ct.c_double()
+        self._raise(lib().accsink_selftest_timeout(self._h, float(limit_s), ct.byref(st),
+                                                   ct.byref(el)))
+        return st.value, el.value
 
     def accsink_export_state(self, x, w, stream=None) -> accsink_state:
         """State of the last solve on this context; x, w: device FP64 arrays of

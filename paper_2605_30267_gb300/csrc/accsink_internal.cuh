@@ -313,6 +313,7 @@ struct InitState {
 cudaError_t launch_init(const CostView &cv, const Work &w, int grid, const double *a_in,
                         const double *b_in, int scale_max, const InitState &is,
                         cudaStream_t s);
+cudaError_t launch_barrier_selftest(DevState *st, int grid, uint64_t limit_ns, cudaStream_t s);
 cudaError_t launch_step(const CostView &cv, const Work &w, int grid,
                         cudaGraphConditionalHandle h, cudaStream_t s);
 cudaError_t launch_step_map(const CostView &cv, const Work &w, int grid, double *c_out,

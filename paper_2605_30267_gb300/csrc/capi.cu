@@ -3,6 +3,7 @@
 // [row pass -> column pass -> step] inside a conditional WHILE node, so a
 // solve needs no host round trip per iteration), a host-driven fallback loop,
 // and the single-pass entry points.
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1452,6 +1453,30 @@ int accsink_time_passes(accsink_ctx *ctx, const accsink_problem *prob, double ep
     CK(cudaEventSynchronize(ctx->ev1));
     CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (col_ms) *col_ms = ms / reps;
+    return ACCSINK_OK;
+}
+
+int accsink_selftest_timeout(accsink_ctx *ctx, double limit_s, int32_t *status_out,
+                             double *elapsed_s)
+{
+    int rc = begin(ctx);
+    if (rc != ACCSINK_OK) return rc;
+    if (!status_out || !elapsed_s || !(limit_s > 0.0) || limit_s > 2.0)
+        return fail(ctx, ACCSINK_ERR_INVALID_ARG, "status_out, elapsed_s and 0 < limit_s <= 2");
+    // the solver's own workspace and state (the next solve rewrites both)
+    rc = ensure_workspace(ctx, 64, 64, 1, 1, 0);
+    if (rc != ACCSINK_OK) return rc;
+    DevState hs;
+    std::memset(&hs, 0, sizeof(hs));
+    cudaStream_t s = nullptr;
+    CK(set_state(ctx, hs, s));
+    const int grid = std::max(2, std::min(ctx->num_sms, 8));
+    const auto t0 = std::chrono::steady_clock::now();
+    CK(launch_barrier_selftest(ctx->w.st, grid, (uint64_t)(limit_s * 1e9), s));
+    CK(cudaMemcpyAsync(ctx->h_state, ctx->w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    *elapsed_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *status_out = ctx->h_state->status;
     return ACCSINK_OK;
 }
 

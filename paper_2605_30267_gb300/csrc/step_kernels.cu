@@ -697,6 +697,30 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     }
 }
 
+// Failure-path self test of the bounded grid barrier: block 0 never
+// arrives (a flag nothing sets), so every other block's wait runs out after
+// limit_ns, records ACCSINK_ERR_TIMEOUT in the state and returns; block 0
+// returns at once. Used by a test to check the timeout path without a fault.
+__global__ void __launch_bounds__(kVecNT) k_barrier_selftest(DevState *st, uint64_t limit_ns)
+{
+    if (blockIdx.x == 0) return;
+    grid_barrier(st, gridDim.x, limit_ns);
+}
+
+cudaError_t launch_barrier_selftest(DevState *st, int grid, uint64_t limit_ns, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kVecNT);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_barrier_selftest, st, limit_ns);
+}
+
 cudaError_t launch_step(const CostView &cv, const Work &w, int grid, cudaGraphConditionalHandle h,
                         cudaStream_t s)
 {
