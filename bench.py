@@ -424,7 +424,7 @@ def measure_points(ctx, dev, stream, n, with_plain, pass_reps, sm_max_mhz, host_
     ms = max(row_ms, col_ms)
     achieved = ops * n * n / (ms * 1e-3) / 1e9
     out["pass_ms"] = {"row": round(row_ms, 4), "col": round(col_ms, 4)}
-    # The solve runs on the clouds in Morton order and skips the slots whose
+    # The solve runs on the clouds in Hilbert-curve order and skips the slots whose
     # terms are all below 2^-80 of their rows' sums; the single passes timed
     # above run every slot. Per S evaluation of the timed Acc solve:
     ms_step = out["acc_s"] * 1e3 / max(1, out["acc_steps"])

@@ -347,7 +347,7 @@ cudaError_t launch_points_pass(const PointView &pv, const Work &w, int grid, int
                                bool with_cost, cudaStream_t s);
 int occupancy_points_pass();
 // Spatial sort of one point cloud: buffers in the solve's point workspace.
-// P (n x d) and a (n) receive the cloud and its marginal in Morton order;
+// P (n x d) and a (n) receive the cloud and its marginal in Hilbert-curve order;
 // perm[i] is the original index of sorted point i.
 struct PointSort {
     uint32_t *box, *code, *code2;

@@ -86,7 +86,7 @@ struct accsink_ctx {
     // the last solve's continuation state is in the workspace (x, w1)
     bool state_ok = false;
     int state_m = 0;
-    const int *state_perm = nullptr;   // Morton order of the columns (sorted point solves)
+    const int *state_perm = nullptr;   // curve order of the columns (sorted point solves)
     double state_mu0 = 0.0;
     int splits_cap = 0, rowgrid_cap = 0, hist_cap = 0;
     Work w{};
@@ -619,7 +619,7 @@ struct PointPlan {
     Geometry g;
     Work w;
     PointView pr{}, pc{};
-    // sorted solve: both clouds in Morton order (pruned passes); the views
+    // sorted solve: both clouds in Hilbert-curve order (pruned passes); the views
     // read the sorted copies, outputs are scattered back through the perms
     bool sorted = false;
     PointSort sx{}, sy{};
@@ -759,7 +759,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     if (rc != ACCSINK_OK) return rc;
     // FP32 arguments on request (header: precision)
     pl.pr.fp32 = pl.pc.fp32 = prm->precision == ACCSINK_PRECISION_FP32 ? 1 : 0;
-    // a sorted solve runs on the clouds (and marginals) in Morton order
+    // a sorted solve runs on the clouds (and marginals) in Hilbert-curve order
     accsink_problem ps = *prob;
     InitState is0 = start ? start->is : InitState();
     if (pl.sorted) {

@@ -191,7 +191,7 @@ def test_state_errors(ctx):
         c2.close()
 
 
-# Point-cloud solves with d <= 4 run on Morton-sorted clouds: warm starts and
+# Point-cloud solves with d <= 4 run on curve-sorted clouds: warm starts and
 # exported states go through the permutation in both directions.
 
 def points_prob(seed, n, m, d=3):
