@@ -130,13 +130,14 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
 // FP32 estimate of every exponent, for every row of the warp, lies more than
 // kSkipLog2 below the lane's running maximum (a lower bound of the row's) is
-// skipped. Each skipped term is below 2^-80 of its row's sum, so all of a
-// row's skipped terms together stay below 2^-49 of it for any row length
-// below 2^31: far below the FP32 accumulation. The estimate A_hi + sum_k
+// skipped. Each skipped term is below 2^-64 of its row's sum, so all of a
+// row's skipped terms together stay below 2^-33 (~1e-10) of it for any row
+// length below 2^31: three orders of magnitude below the FP32 passes' own
+// accuracy (~1e-7 in each log-sum-exp). The estimate A_hi + sum_k
 // p_k Q_hi,k differs from the exact exponent by at most ~2^-21 of the terms'
 // magnitude |A| + sum_k |p_k| |Q_k| (four FP32 roundings and the dropped low
 // parts), so the threshold is lowered by 2^-20 of a bound on that magnitude.
-constexpr float kSkipLog2 = 80.0f;
+constexpr float kSkipLog2 = 64.0f;
 
 template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false, bool PRUNE = false,
           bool F32 = false>
