@@ -23,20 +23,6 @@ constexpr uint64_t kQueueWaitNs = 20000000000ull;  // 20 s for one queue wait
 
 // ---------------------------------------------------------------- helpers --
 
-// Order-preserving map of doubles to unsigned 64-bit integers (for atomic
-// min / max of FP64 values).
-__device__ __forceinline__ unsigned long long enc_d(double v)
-{
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
-}
-
-__device__ __forceinline__ double dec_d(unsigned long long e)
-{
-    const unsigned long long b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
-    return __longlong_as_double((long long)b);
-}
-
 // Polling load: no ordering (so it does not invalidate this SM's L1 on every
 // poll); the waiter issues one acquire fence once the value it waits for
 // is seen.
@@ -647,7 +633,8 @@ __device__ bool cta_init(BatchProb *P)
     cta_sum<5>(v);
     if (threadIdx.x == 0) {
         int status = 0;
-        if (P->nonfinite || v[4] > 0.0 || !isfinite(cmax) || !isfinite(cmin)) status = 3;
+        if (P->nonfinite & 2u) status = 6;    // ACCSINK_ERR_TIMEOUT in the formation
+        else if (P->nonfinite || v[4] > 0.0 || !isfinite(cmax) || !isfinite(cmin)) status = 3;
         else if (v[2] > 0.0 || v[3] > 0.0) status = 2;
         else if (P->scale && !(cmax > 0.0)) status = 1;
         st_s = status;

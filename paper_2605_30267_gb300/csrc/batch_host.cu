@@ -5,6 +5,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -73,10 +74,28 @@ namespace {
 struct BatchPlan {
     std::vector<BatchProb> hp;
     std::vector<ProbLayout> lay;
+    // formation tiles: CUDA-core (64 x 64), then scaling (64 x 64, scaled
+    // problems), then tensor-core (128 x 64)
     std::vector<BatchTile> tiles;
+    int nform = 0, nscale = 0, ntct = 0;
+    std::vector<int32_t> tcp;       // tensor-core problems
+    std::vector<int64_t> tcs;       // their first slice rows
+    int64_t R = 0;                  // slice rows
+    int dpad = 0;
+    size_t slice_bytes = 0, expo_bytes = 0;
     unsigned long long cap = 0;
     size_t head_bytes = 0, data_bytes = 0;
 };
+
+// Cosine costs with kBatchTcMinD <= d <= kBatchTcMaxD are formed on the
+// tensor cores unless ACCSINK_BATCH_FORM=cuda selects the CUDA-core
+// expansion for every problem.
+bool tc_form_enabled()
+{
+    const char *e = std::getenv("ACCSINK_BATCH_FORM");
+    if (e && std::strcmp(e, "cuda") == 0) return false;
+    return batch_tc_available();
+}
 
 void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
                 const accsink_params *params, BatchPlan &pl)
@@ -86,6 +105,8 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
     pl.tiles.clear();
     pl.data_bytes = 0;
     size_t outstanding = 0;
+    const bool tc_on = tc_form_enabled();
+    std::vector<BatchTile> scale_tiles, tc_tiles;
     for (int k = 0; k < count; ++k) {
         const accsink_problem &q = probs[k];
         BatchProb &P = pl.hp[k];
@@ -137,14 +158,43 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
         pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles, transposed);
         pl.data_bytes += pl.lay[k].total();
         outstanding += (size_t)std::max(P.row_tiles, P.col_items);
-        for (int r = 0; r < q.n; r += kBatchFormTile)
-            for (int c = 0; c < q.m; c += kBatchFormTile) pl.tiles.push_back({k, r, c, 0});
+        P.tc = (tc_on && q.cost_kind == ACCSINK_COST_COSINE && q.d >= kBatchTcMinD &&
+                q.d <= kBatchTcMaxD && pl.R + q.n + q.m < ((int64_t)1 << 31) - kBatchTcRows)
+                   ? 1 : 0;
+        if (P.tc) {
+            pl.tcp.push_back(k);
+            pl.tcs.push_back(pl.R);
+            P.tc_xoff = (int32_t)pl.R;
+            P.tc_yoff = (int32_t)(pl.R + q.n);
+            pl.R += (int64_t)q.n + q.m;
+            pl.dpad = std::max(pl.dpad, (q.d + kBatchTcK - 1) / kBatchTcK * kBatchTcK);
+            for (int r = 0; r < q.n; r += kBatchTcRows)
+                for (int c = 0; c < q.m; c += kBatchTcCols) tc_tiles.push_back({k, r, c, 0});
+        } else {
+            for (int r = 0; r < q.n; r += kBatchFormTile)
+                for (int c = 0; c < q.m; c += kBatchFormTile) pl.tiles.push_back({k, r, c, 0});
+        }
+        if (P.scale)
+            for (int r = 0; r < q.n; r += kBatchFormTile)
+                for (int c = 0; c < q.m; c += kBatchFormTile) scale_tiles.push_back({k, r, c, 0});
     }
+    pl.nform = (int)pl.tiles.size();
+    pl.nscale = (int)scale_tiles.size();
+    pl.ntct = (int)tc_tiles.size();
+    pl.tiles.insert(pl.tiles.end(), scale_tiles.begin(), scale_tiles.end());
+    pl.tiles.insert(pl.tiles.end(), tc_tiles.begin(), tc_tiles.end());
+    if (pl.R > 0) {
+        pl.slice_bytes = up256(batch_tc_slice_bytes(pl.R, pl.dpad));
+        pl.expo_bytes = up256((size_t)pl.R * 4);
+        pl.data_bytes += pl.slice_bytes + pl.expo_bytes;
+    }
+    const size_t ntc = pl.tcp.size();
     pl.cap = pow2_at_least(std::max<unsigned long long>(
         4096, 2 * (unsigned long long)(outstanding + count)));
     pl.head_bytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchResult) * count) +
                     up256(sizeof(BatchQueue)) + up256(pl.cap * 8) + up256(pl.cap * 8) +
-                    up256(sizeof(BatchTile) * pl.tiles.size()) + up256(8 * (size_t)count);
+                    up256(sizeof(BatchTile) * pl.tiles.size()) + up256(8 * (size_t)count) +
+                    up256(4 * ntc) + up256(8 * ntc);
 }
 
 }  // namespace
@@ -213,6 +263,9 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     unsigned long long *dSeq = (unsigned long long *)p;    p += up256(cap * 8);
     BatchTile *dT = (BatchTile *)p;        p += up256(sizeof(BatchTile) * tiles.size());
     unsigned long long *dInit = (unsigned long long *)p;   p += up256(8 * (size_t)count);
+    const size_t ntc = pl.tcp.size();
+    int32_t *dTcp = (int32_t *)p;          p += up256(4 * ntc);
+    int64_t *dTcs = (int64_t *)p;          p += up256(8 * ntc);
     for (int k = 0; k < count; ++k) {
         BatchProb &P = hp[k];
         const ProbLayout &L = lay[k];
@@ -228,6 +281,18 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         P.Gh = (float *)take(L.gh); P.Gl = (float *)take(L.gl);
         P.rowpart = (double *)take(L.rowpart);
         P.colrec = (double *)take(L.colrec);
+    }
+    BatchTcLaunch tcl{};
+    if (pl.R > 0) {
+        tcl.tiles = dT + pl.nform + pl.nscale;
+        tcl.ntiles = pl.ntct;
+        tcl.tcp = dTcp;
+        tcl.tcs = dTcs;
+        tcl.ntc = (int)ntc;
+        tcl.dpad = pl.dpad;
+        tcl.R = pl.R;
+        tcl.SL = p;                         p += pl.slice_bytes;
+        tcl.expo = (int32_t *)p;            p += pl.expo_bytes;
     }
     // initial items, largest problems first
     std::vector<int> order(count);
@@ -253,7 +318,7 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     // ---- stage the host records (pinned) and launch
     const size_t hbytes = up256(sizeof(BatchProb) * count) + up256(sizeof(BatchTile) * tiles.size()) +
                           up256(8 * (size_t)count) + up256(sizeof(BatchQueue)) +
-                          up256(sizeof(BatchResult) * count);
+                          up256(sizeof(BatchResult) * count) + up256(4 * ntc) + up256(8 * ntc);
     if (hbytes > ws.host_bytes) {
         if (ws.host) cudaFreeHost(ws.host);
         ws.host = nullptr;
@@ -270,7 +335,13 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     BatchTile *hT = (BatchTile *)h;        h += up256(sizeof(BatchTile) * tiles.size());
     unsigned long long *hI = (unsigned long long *)h;  h += up256(8 * (size_t)count);
     BatchQueue *hQ = (BatchQueue *)h;      h += up256(sizeof(BatchQueue));
-    BatchResult *hR = (BatchResult *)h;
+    BatchResult *hR = (BatchResult *)h;    h += up256(sizeof(BatchResult) * count);
+    int32_t *hTcp = (int32_t *)h;          h += up256(4 * ntc);
+    int64_t *hTcs = (int64_t *)h;
+    if (ntc) {
+        std::memcpy(hTcp, pl.tcp.data(), 4 * ntc);
+        std::memcpy(hTcs, pl.tcs.data(), 8 * ntc);
+    }
     std::memcpy(hP, hp.data(), sizeof(BatchProb) * count);
     if (!tiles.empty()) std::memcpy(hT, tiles.data(), sizeof(BatchTile) * tiles.size());
     std::memcpy(hI, init.data(), 8 * (size_t)count);
@@ -291,8 +362,13 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         BK(cudaMemcpyAsync(dT, hT, sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(dInit, hI, 8 * (size_t)count, cudaMemcpyHostToDevice, s));
     BK(cudaMemcpyAsync(dQ, hQ, sizeof(BatchQueue), cudaMemcpyHostToDevice, s));
-    BK(launch_batch_form(dP, dT, (int)tiles.size(), 0, s));
-    BK(launch_batch_scale(dP, dT, (int)tiles.size(), s));
+    if (ntc) {
+        BK(cudaMemcpyAsync(dTcp, hTcp, 4 * ntc, cudaMemcpyHostToDevice, s));
+        BK(cudaMemcpyAsync(dTcs, hTcs, 8 * ntc, cudaMemcpyHostToDevice, s));
+    }
+    BK(launch_batch_form(dP, dT, pl.nform, 0, s));
+    if (pl.R > 0) BK(launch_batch_form_tc(dP, tcl, s));
+    BK(launch_batch_scale(dP, dT + pl.nform, pl.nscale, s));
     BK(launch_queue_init(dQ, dInit, count, cap, s));
     BK(cudaEventRecord(env.ev_mid, s));
     const int per_sm = tn.ctas_per_sm > 0 ? std::min(tn.ctas_per_sm, env.occ_solve) : env.occ_solve;

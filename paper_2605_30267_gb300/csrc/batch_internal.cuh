@@ -47,10 +47,13 @@ struct BatchProb {
     int32_t row_tiles, rows_per_tile, col_tiles;
     int32_t col_items, cols_per_item;   // column-phase work items (over K^T when present)
     int32_t arrive;          // arrival counter of the phase in flight
+    int32_t tc;              // 1: cost formed on the tensor cores (batch_form_tc.cu)
+    int32_t tc_xoff, tc_yoff;   // first slice rows of X and Y (tensor-core problems)
     int32_t pad_s;
     // ---- cost statistics from the formation (ordered encodings of FP64)
     unsigned long long cmax_enc, cmin_enc, cabs_enc;
-    uint32_t nonfinite, pad_c;
+    uint32_t nonfinite;      // bit 0: a non-finite input or cost; bit 1: a formation wait ran out
+    uint32_t pad_c;
     // ---- solver state (written by the CTA that owns the current phase)
     double k2, eps_c, inv_eps, cost_div, cmax, cmin, cabs, min_loga, log_m;
     double shift_g, shift_f, mu, kl_prev, err, dual, cost;
@@ -95,6 +98,39 @@ struct BatchTile {
     int32_t prob, row0, col0, pad;
 };
 
+// Tensor-core formation of cosine costs: 128 x 64 tiles, 32 contraction
+// elements per stage, six 7-bit slices per vector; exact class sums need
+// d 2^15 < 2^24, i.e. d <= 480 (d padded to a multiple of 32).
+constexpr int kBatchTcRows = 128, kBatchTcCols = 64, kBatchTcK = 32, kBatchTcLevels = 6;
+constexpr int kBatchTcMinD = 32, kBatchTcMaxD = 480;
+
+// Arguments of the tensor-core formation (device pointers into the workspace).
+struct BatchTcLaunch {
+    const BatchTile *tiles;      // 128 x 64 tiles of the tensor-core problems
+    int ntiles;
+    const int32_t *tcp;          // the tensor-core problems
+    const int64_t *tcs;          // first slice row of each (X rows, then Y rows)
+    int ntc;
+    int dpad;                    // contraction length padded to kBatchTcK
+    int64_t R;                   // slice rows
+    void *SL;                    // FP16 slices [kBatchTcLevels][R][dpad]
+    int32_t *expo;               // exponent of each slice row
+};
+
+// Order-preserving map of doubles to unsigned 64-bit integers (for atomic
+// min / max of FP64 values).
+__device__ __forceinline__ unsigned long long enc_d(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double dec_d(unsigned long long e)
+{
+    const unsigned long long b = (e >> 63) ? (e & 0x7fffffffffffffffull) : ~e;
+    return __longlong_as_double((long long)b);
+}
+
 constexpr int kBatchThreads = 256;
 constexpr int kBatchColTile = 128;     // columns per column-pass item (32 lanes x 4)
 constexpr int kBatchFormTile = 64;     // formation tile edge
@@ -105,6 +141,9 @@ constexpr int kBatchColRec = 12 * kBatchColWarps;
 
 cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int ntiles,
                               int dmax, cudaStream_t s);
+bool batch_tc_available();
+size_t batch_tc_slice_bytes(int64_t R, int dpad);
+cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStream_t s);
 cudaError_t launch_batch_scale(BatchProb *P, const BatchTile *tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_batch_solve(BatchProb *P, BatchQueue *q, BatchResult *res, int grid,
                                cudaStream_t s);
