@@ -52,6 +52,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measured_bf16_tflops():
+    """Dense bf16 tensor peak (cuBLAS burst) from MEASURED_PEAKS.json, else the
+    fallback figure."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["bf16_tflops"])
+    except Exception:
+        return 1900.0
+
+
 def profile_traffic(kernel_file: str, profile_name: str):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on
     the current kernel source (its sha256 is recorded in the summary)."""
@@ -495,6 +506,19 @@ def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=Tr
         "cost_entry_evaluations": evals,
         "solve_entries_per_s": round(evals / (med["solve_ms"] / 1e3), 1),
     })
+    # the cosine costs are formed on the tensor cores: 21 FP16 slice-pair
+    # products per 128 x 64 tile and 16-element contraction step
+    dpad = (300 + 31) // 32 * 32
+    tiles = sum(-(-s.n // 128) * -(-s.m // 64) for s in structs)
+    macs = tiles * 128 * 64 * dpad * 21
+    form_tf = 2 * macs / (med["form_ms"] / 1e3) / 1e12
+    out["form_tensor_cores"] = {
+        "kernel": "k_batch_form_tc (tcgen05 kind::f16, FP32 accumulators in TMEM)",
+        "tiles": tiles, "slice_pair_macs": macs,
+        "achieved_tflops": round(form_tf, 1), "peak_tflops": measured_bf16_tflops(),
+        "frac": round(form_tf / measured_bf16_tflops(), 4),
+        "note": "over the whole formation phase (slicing, tiles, statistics); peak: measured "
+                "dense bf16 cuBLAS burst (FP16 runs at the same tensor rate)"}
     if one_at_a_time:
         tot = 0.0
         for k in range(count):

@@ -33,14 +33,16 @@
 // forms 1 - <x, y> and k C as (hi, lo) pairs like the CUDA-core path, and
 // folds in the cost statistics.
 //
-// One CTA forms one 128 x 64 tile (128 rows of X on the TMEM lanes, 64 rows
-// of Y on the accumulator columns). Warp 0 issues TMA loads of all six
-// slices of both operands, 32 contraction elements at a time, into a
-// three-stage ring; warp 1 owns the TMEM allocation and issues the 21 MMA
-// pairs per stage (two K = 16 steps each); warps 2-5 read the accumulators
-// back (one TMEM lane quadrant each) and write the costs. Every wait is
-// bounded: a wait that runs out marks the problem (nonfinite bit 2) and the
-// CTA drains its copies, frees its TMEM and returns.
+// A persistent CTA per SM forms 128 x 64 tiles (128 rows of X on the TMEM
+// lanes, 64 rows of Y on the accumulator columns) in turn. Warp 0 issues TMA
+// loads of all six slices of both operands, 32 contraction elements at a
+// time, into a three-stage ring that runs across tiles; warp 1 owns the TMEM
+// allocation and issues the 21 slice-pair MMAs per stage (two K = 16 steps
+// each); warps 2-9 read the accumulators back (two warps per TMEM lane
+// quadrant, 32 columns each), release them to the next tile's MMAs as soon
+// as they are read, and then write the costs. Every wait is bounded: a wait
+// that runs out marks the problem (nonfinite bit 2), and the CTA stops,
+// drains its copies, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
 #include <float.h>
@@ -59,7 +61,8 @@ constexpr int kTcK = kBatchTcK;           // contraction elements per stage: 64-
 constexpr int kTcL = kBatchTcLevels;      // slices per vector
 constexpr int kTcBeta = 7;                // bits per slice
 constexpr int kTcStages = 3;
-constexpr int kTcThreads = 192;           // TMA warp, MMA warp, four epilogue warps
+constexpr int kTcEpiWarps = 8;            // two per TMEM lane quadrant
+constexpr int kTcThreads = 64 + 32 * kTcEpiWarps;   // TMA warp, MMA warp, epilogue warps
 constexpr uint32_t kTcSliceA = kTcM * kTcK * 2;           // one slice of the X tile, bytes
 constexpr uint32_t kTcSliceB = kTcN * kTcK * 2;           // one slice of the Y tile
 constexpr uint32_t kTcABytes = kTcL * kTcSliceA;
@@ -279,18 +282,41 @@ __device__ __forceinline__ void df_min(float &mh, float &ml, float h, float l)
     if (h < mh || (h == mh && l < ml)) { mh = h; ml = l; }
 }
 
+// Arrives once on the barrier (count 1 per arriving warp).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// The 21 slice-pair MMAs of one stage, two K = 16 steps each; the first
+// MMA of each class overwrites its accumulator when `first` is set.
+__device__ __forceinline__ void stage_mmas(uint32_t tmem, uint64_t dA, uint64_t dB, uint32_t first)
+{
+#pragma unroll
+    for (int c = 0; c < kTcL; ++c) {
+#pragma unroll
+        for (int i = 0; i <= c; ++i) {
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 16; ++ks) {
+                // descriptor start fields advance by the byte offset >> 4
+                const uint64_t a = dA + (uint64_t)((i * kTcSliceA + ks * 32) >> 4);
+                const uint64_t b = dB + (uint64_t)(((c - i) * kTcSliceB + ks * 32) >> 4);
+                tc_mma(tmem + c * kTcN, a, b, kTcIdesc, (i == 0 && ks == 0) ? !first : 1u);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_batch_form_tc(BatchProb *Pall, const BatchTile *tiles, const int32_t *expo,
+    k_batch_form_tc(BatchProb *Pall, const BatchTile *tiles, int ntiles, const int32_t *expo,
                     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB)
 {
     extern __shared__ uint8_t tc_smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages], acc_bar;
+    __shared__ __align__(8) uint64_t full_bar[kTcStages], empty_bar[kTcStages];
+    __shared__ __align__(8) uint64_t accf_bar, acce_bar;
     __shared__ uint32_t tmem_base_s;
+    __shared__ volatile int abort_s;
     const uint32_t smem0 = (smem_u32(tc_smem_raw) + 1023u) & ~1023u;
-    const BatchTile tl = tiles[blockIdx.x];
-    BatchProb *P = Pall + tl.prob;
-    const int n = P->n, m = P->m;
-    const int nk = (P->d + kTcK - 1) / kTcK;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -298,7 +324,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             mbar_init(smem_u32(&full_bar[s]), 1);
             mbar_init(smem_u32(&empty_bar[s]), 1);
         }
-        mbar_init(smem_u32(&acc_bar), 1);
+        mbar_init(smem_u32(&accf_bar), 1);
+        mbar_init(smem_u32(&acce_bar), kTcEpiWarps);
+        abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -316,69 +344,92 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- TMA producer
-            const int xrow = P->tc_xoff + tl.row0, yrow = P->tc_yoff + tl.col0;
-            bool ok = true;
-            int issued = 0;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int s = kc % kTcStages;
-                if (kc >= kTcStages && !mbar_wait(smem_u32(&empty_bar[s]), ((kc / kTcStages) - 1) & 1)) {
-                    ok = false;
-                    break;
+            // ---- TMA producer: a ring of stages shared by all of this CTA's tiles
+            uint32_t it = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_s; t += gridDim.x) {
+                const BatchTile tl = tiles[t];
+                const BatchProb *P = Pall + tl.prob;
+                const int nk = (P->d + kTcK - 1) / kTcK;
+                const int xrow = P->tc_xoff + tl.row0, yrow = P->tc_yoff + tl.col0;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kTcStages;
+                    if (it >= kTcStages &&
+                        !mbar_wait(smem_u32(&empty_bar[s]), ((it / kTcStages) - 1) & 1)) {
+                        atomicOr(&Pall[tl.prob].nonfinite, 2u);
+                        abort_s = 1;
+                        break;
+                    }
+                    const uint32_t sa = smem0 + s * kTcStageBytes;
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect_tx(fb, kTcStageBytes);
+                    tma_load_3d(sa, &tmA, kc * kTcK, xrow, 0, fb);
+                    tma_load_3d(sa + kTcABytes, &tmB, kc * kTcK, yrow, 0, fb);
                 }
-                const uint32_t sa = smem0 + s * kTcStageBytes;
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                mbar_expect_tx(fb, kTcStageBytes);
-                tma_load_3d(sa, &tmA, kc * kTcK, xrow, 0, fb);
-                tma_load_3d(sa + kTcABytes, &tmB, kc * kTcK, yrow, 0, fb);
-                issued = kc + 1;
             }
             // drain: the last load of each stage has landed before the CTA exits
-            for (int kc = max(0, issued - kTcStages); kc < issued; ++kc)
-                if (!mbar_wait(smem_u32(&full_bar[kc % kTcStages]), (kc / kTcStages) & 1)) ok = false;
-            if (!ok) atomicOr(&P->nonfinite, 2u);
+            for (uint32_t j = it > (uint32_t)kTcStages ? it - kTcStages : 0u; j < it; ++j)
+                if (!mbar_wait(smem_u32(&full_bar[j % kTcStages]), (j / kTcStages) & 1)) abort_s = 1;
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issue: class c = i + j accumulates in columns [c N, c N + N)
-            bool ok = true;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int s = kc % kTcStages;
-                if (!mbar_wait(smem_u32(&full_bar[s]), (kc / kTcStages) & 1)) {
-                    ok = false;
+            uint32_t it = 0;
+            int lt = 0;
+            for (int t = blockIdx.x; t < ntiles && !abort_s; t += gridDim.x, ++lt) {
+                const BatchTile tl = tiles[t];
+                const int nk = (Pall[tl.prob].d + kTcK - 1) / kTcK;
+                // the epilogue has read the previous tile's accumulators
+                if (lt > 0 && !mbar_wait(smem_u32(&acce_bar), (lt - 1) & 1)) {
+                    atomicOr(&Pall[tl.prob].nonfinite, 2u);
+                    abort_s = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem0 + s * kTcStageBytes, sb = sa + kTcABytes;
-#pragma unroll 1
-                for (int c = 0; c < kTcL; ++c) {
-#pragma unroll 1
-                    for (int i = 0; i <= c; ++i) {
-#pragma unroll
-                        for (int ks = 0; ks < kTcK / 16; ++ks) {
-                            const uint64_t ad = sdesc_sw64(sa + i * kTcSliceA + ks * 32);
-                            const uint64_t bd = sdesc_sw64(sb + (c - i) * kTcSliceB + ks * 32);
-                            tc_mma(tmem + c * kTcN, ad, bd, kTcIdesc, (kc | i | ks) != 0);
-                        }
+                bool ok = true;
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int s = it % kTcStages;
+                    if (!mbar_wait(smem_u32(&full_bar[s]), (it / kTcStages) & 1)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    const uint32_t sa = smem0 + s * kTcStageBytes;
+                    stage_mmas(tmem, sdesc_sw64(sa), sdesc_sw64(sa + kTcABytes), kc == 0);
+                    tc_commit(smem_u32(&empty_bar[s]));
                 }
-                tc_commit(smem_u32(&empty_bar[s]));
+                tc_commit(smem_u32(&accf_bar));
+                if (!ok) {
+                    atomicOr(&Pall[tl.prob].nonfinite, 2u);
+                    abort_s = 1;
+                    ++lt;            // this tile's commit is the last one to wait for
+                    break;
+                }
             }
-            tc_commit(smem_u32(&acc_bar));
-            if (!mbar_wait(smem_u32(&acc_bar), 0)) ok = false;
-            if (!ok) atomicOr(&P->nonfinite, 2u);
+            // every MMA issued has completed before the CTA frees its TMEM
+            if (lt > 0 && !mbar_wait(smem_u32(&accf_bar), (lt - 1) & 1)) abort_s = 1;
         }
     } else {
-        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31, columns
+        // [32 h, 32 h + 32) with h = (w - 2) / 4
         const int quad = warp & 3;
-        const int r = tl.row0 + 32 * quad + lane;
-        const bool rv = r < n;
-        int ok = 0;
-        if (lane == 0) ok = mbar_wait(smem_u32(&acc_bar), 0) ? 1 : 0;
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (!ok) {
-            if (lane == 0) atomicOr(&P->nonfinite, 2u);
-        } else {
+        const int half = (warp - 2) >> 2;
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const BatchTile tl = tiles[t];
+            BatchProb *P = Pall + tl.prob;
+            const int n = P->n, m = P->m;
+            const int r = tl.row0 + 32 * quad + lane;
+            const bool rv = r < n;
+            int ok = 0;
+            if (lane == 0) ok = (!abort_s && mbar_wait(smem_u32(&accf_bar), lt & 1)) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) {
+                    atomicOr(&P->nonfinite, 2u);
+                    abort_s = 1;
+                }
+                break;
+            }
             tc_fence_after();
             const int ex = rv ? expo[P->tc_xoff + r] : 0;
             const float sx = pow2f(ex - kTcBeta);
@@ -386,47 +437,68 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const float kh = (float)kd, kl = (float)(kd - (double)kh);
             float mxh = -INFINITY, mxl = 0.0f, mnh = INFINITY, mnl = 0.0f;
             int bad = 0;
-            const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16);
-#pragma unroll 1
-            for (int cc = 0; cc < kTcN / 16; ++cc) {
-                float acc[kTcL][16];
+            const uint32_t trow = tmem + ((uint32_t)(32 * quad) << 16) + 32 * half;
+            // read this warp's 32 columns, two classes at a time, adding the
+            // exact classes into double-float sums (h, l), largest scale first
+            float h[32], l[32];
 #pragma unroll
-                for (int c = 0; c < kTcL; ++c) tmem_ld16(trow + c * kTcN + cc * 16, acc[c]);
-                tmem_wait_ld();
+            for (int j = 0; j < 2; ++j) {
 #pragma unroll
-                for (int c = 0; c < kTcL; ++c) tie16(acc[c]);
+                for (int c0 = 0; c0 < kTcL; c0 += 2) {
+                    float a0[16], a1[16];
+                    tmem_ld16(trow + c0 * kTcN + 16 * j, a0);
+                    tmem_ld16(trow + (c0 + 1) * kTcN + 16 * j, a1);
+                    tmem_wait_ld();
+                    tie16(a0);
+                    tie16(a1);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        float s2, e2;
+                        if (c0 == 0) {
+                            h[16 * j + e] = a0[e];
+                            l[16 * j + e] = 0.0f;
+                        } else {
+                            two_sum_f(h[16 * j + e], a0[e] * pow2f(-kTcBeta * c0), s2, e2);
+                            h[16 * j + e] = s2;
+                            l[16 * j + e] += e2;
+                        }
+                        two_sum_f(h[16 * j + e], a1[e] * pow2f(-kTcBeta * (c0 + 1)), s2, e2);
+                        h[16 * j + e] = s2;
+                        l[16 * j + e] += e2;
+                    }
+                }
+            }
+            // the accumulators are read: the MMA warp may start the next tile
+            // while this warp writes the costs
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acce_bar));
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int cb = tl.col0 + 32 * half + 16 * j;
                 float oh[16], ol[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
-                    const int col = tl.col0 + cc * 16 + e;
+                    const int col = cb + e;
                     const int ey = col < m ? expo[P->tc_yoff + col] : 0;
-                    // double-float sum of the exact classes, largest first
-                    float h = acc[0][e], l = 0.0f;
-#pragma unroll
-                    for (int c = 1; c < kTcL; ++c) {
-                        float s2, e2;
-                        two_sum_f(h, acc[c][e] * pow2f(-kTcBeta * c), s2, e2);
-                        h = s2;
-                        l += e2;
-                    }
                     // <x, y> = 2^(ex + ey - 2 beta) (h + l): two exact power-of-two scalings
                     const float sy = pow2f(ey - kTcBeta);
-                    h = h * sx * sy;
-                    l = l * sx * sy;
+                    const float dh = h[16 * j + e] * sx * sy;
+                    const float dl = l[16 * j + e] * sx * sy;
                     // C = 1 - <x, y>
-                    float ch, cl, t;
-                    two_sum_f(1.0f, -h, ch, t);
-                    two_sum_f(ch, t - l, ch, cl);
+                    float ch, cl, tt;
+                    two_sum_f(1.0f, -dh, ch, tt);
+                    two_sum_f(ch, tt - dl, ch, cl);
                     if (rv && col < m) {
                         if (!isfinite(ch)) bad = 1;
                         df_max(mxh, mxl, ch, cl);
                         df_min(mnh, mnl, ch, cl);
                     }
                     // k C as (hi, lo): Dekker product with FMA
-                    const float p = kh * ch;
-                    const float pe = fmaf(kh, cl, fmaf(kl, ch, fmaf(kh, ch, -p)));
+                    const float pp = kh * ch;
+                    const float pe = fmaf(kh, cl, fmaf(kl, ch, fmaf(kh, ch, -pp)));
                     float vh, vl;
-                    two_sum_f(p, pe, vh, vl);
+                    two_sum_f(pp, pe, vh, vl);
                     const bool keep = col < m;
                     oh[e] = keep ? vh : 0.0f;
                     ol[e] = keep ? vl : 0.0f;
@@ -435,7 +507,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const int64_t base = (int64_t)r * P->ldm;
 #pragma unroll
                     for (int g = 0; g < 4; ++g) {
-                        const int c4 = tl.col0 + cc * 16 + 4 * g;
+                        const int c4 = cb + 4 * g;
                         if (c4 < P->ldm) {
                             *reinterpret_cast<float4 *>(P->Kh + base + c4) =
                                 make_float4(oh[4 * g], oh[4 * g + 1], oh[4 * g + 2], oh[4 * g + 3]);
@@ -446,7 +518,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     if (P->KTh) {
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
-                            const int col = tl.col0 + cc * 16 + e;
+                            const int col = cb + e;
                             if (col < m) {
                                 P->KTh[(int64_t)col * P->ldn + r] = oh[e];
                                 P->KTl[(int64_t)col * P->ldn + r] = ol[e];
@@ -547,7 +619,15 @@ cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStrea
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_batch_form_tc<<<t.ntiles, kTcThreads, kTcSmemBytes, s>>>(P, t.tiles, t.expo, mA, mB);
+    static int grid_cap = 0;
+    if (!grid_cap) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        grid_cap = std::max(1, sms);     // one persistent CTA per SM (shared memory)
+    }
+    k_batch_form_tc<<<std::min(t.ntiles, grid_cap), kTcThreads, kTcSmemBytes, s>>>(
+        P, t.tiles, t.ntiles, t.expo, mA, mB);
     return cudaGetLastError();
 }
 
