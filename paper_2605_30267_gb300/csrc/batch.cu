@@ -1204,7 +1204,7 @@ __global__ void __launch_bounds__(256) k_batch_scale(BatchProb *Pall, const Batc
 
 // ---------------------------------------------------------- the solver --
 
-__global__ void __launch_bounds__(kBatchThreads) k_batch_solve(BatchProb *Pall, BatchQueue *q,
+__global__ void __launch_bounds__(kBatchThreads, 4) k_batch_solve(BatchProb *Pall, BatchQueue *q,
                                                                BatchResult *res)
 {
     __shared__ unsigned long long item_s;
