@@ -182,6 +182,13 @@ __device__ __forceinline__ int seg_lanes(int slots)
 
 // Row pass over rows [r0, r1) of problem P: u_i, the column operand F'_i and
 // the CTA's partials (sum a u, and with WC the transport cost in K units).
+// Scratch of the pass functions (row pass, column tiles, column pass over
+// K^T): one buffer for all of them, since a CTA runs one at a time and each
+// ends with a CTA barrier after its last read. Per-function arrays would
+// take 45 KB per CTA (one set per template instance) and cap residency.
+__shared__ __align__(16) float s_pass[3 * kBW * kBatchColTile];
+static_assert(5 * kBatchThreads <= 3 * kBW * kBatchColTile, "row-pass scratch does not fit");
+
 // Each warp takes four rows at a time (one operand load serves four rows and
 // four rows' loads are in flight); rows go in chunks of one row per thread:
 // the warps reduce each row to (R, hi, lo) in shared memory, then every
@@ -191,8 +198,8 @@ template <bool WC, bool LOCAL>
 __device__ void cta_rows(BatchProb *P, int r0, int r1, double *part2)
 {
     constexpr int RW = 4;
-    __shared__ float sR[kBatchThreads], sH[kBatchThreads], sL[kBatchThreads];
-    __shared__ float sCH[WC ? kBatchThreads : 1], sCL[WC ? kBatchThreads : 1];
+    float *sR = s_pass, *sH = s_pass + kBatchThreads, *sL = s_pass + 2 * kBatchThreads;
+    float *sCH = s_pass + 3 * kBatchThreads, *sCL = s_pass + 4 * kBatchThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int m = P->m;
     const int64_t ldm = P->ldm;
@@ -391,7 +398,10 @@ __device__ void cta_cols(BatchProb *P, int tile, const StageK &K, bool check, do
                          double (&lo3)[3], double (&hi3)[3])
 {
     const int c0 = tile * kBatchColTile;
-    __shared__ float sR[kBW][kBatchColTile], sH[kBW][kBatchColTile], sL[kBW][kBatchColTile];
+    float(*sR)[kBatchColTile] = reinterpret_cast<float(*)[kBatchColTile]>(s_pass);
+    float(*sH)[kBatchColTile] = reinterpret_cast<float(*)[kBatchColTile]>(s_pass + kBW * kBatchColTile);
+    float(*sL)[kBatchColTile] =
+        reinterpret_cast<float(*)[kBatchColTile]>(s_pass + 2 * kBW * kBatchColTile);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = P->n, m = P->m;
     const int64_t ldm = P->ldm;
@@ -479,7 +489,7 @@ __device__ void cta_cols(BatchProb *P, int tile, const StageK &K, bool check, do
 __device__ void cta_colsT(BatchProb *P, int j0, int j1, const StageK &K, bool check)
 {
     constexpr int RW = 4;
-    __shared__ float sR[kBatchThreads], sH[kBatchThreads], sL[kBatchThreads];
+    float *sR = s_pass, *sH = s_pass + kBatchThreads, *sL = s_pass + 2 * kBatchThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = P->n;
     const int64_t ldn = P->ldn;
