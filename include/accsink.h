@@ -270,8 +270,13 @@ typedef struct {
  * arrays of `count` records; the pointers inside probs are device pointers;
  * f_out and g_out are host arrays of `count` device pointers (n_k and m_k
  * doubles). Each problem's cost is formed once in the context's batch
- * workspace (8 bytes per entry, FP64-accurate), so point clouds of any
- * dimension 1 <= d <= 4096 are accepted. Returns OK when every problem
+ * workspace (8 bytes per entry, a double-float pair), so point clouds of any
+ * dimension 1 <= d <= 4096 are accepted. Cosine costs with 32 <= d <= 480 are
+ * formed on the tensor cores from exact integer slices of the vectors (dot
+ * products within d 2^-39 |x||y|; the environment variable
+ * ACCSINK_BATCH_FORM=cuda selects the CUDA-core expansion, exact to FP64
+ * rounding, for every problem); the slices take 12 bytes per vector element
+ * of workspace. Returns OK when every problem
  * converged, ACCSINK_ERR_MAXITER when some did not (their results are still
  * valid), another code for the first failed problem (see res[k].status), or
  * ACCSINK_ERR_TIMEOUT if a device-side wait of the scheduler ran out. */
