@@ -1037,28 +1037,53 @@ __device__ void problem_done(BatchQueue *q)
 
 // ------------------------------------------------------- cost formation --
 
+// Lexicographic max / min of normalised double-float pairs (numeric order).
+__device__ __forceinline__ void df_max(float &mh, float &ml, float h, float l)
+{
+    if (h > mh || (h == mh && l > ml)) { mh = h; ml = l; }
+}
+
+__device__ __forceinline__ void df_min(float &mh, float &ml, float h, float l)
+{
+    if (h < mh || (h == mh && l < ml)) { mh = h; ml = l; }
+}
+
+// (hi, lo) = k (h + l) for a double-float k = kh + kl: Dekker's product with
+// FMA, renormalised (~2^-47 relative).
+__device__ __forceinline__ void df_scale(float kh, float kl, float h, float l, float &oh, float &ol)
+{
+    const float p = kh * h;
+    const float pe = fmaf(kh, l, fmaf(kl, h, fmaf(kh, h, -p)));
+    two_sum_f(p, pe, oh, ol);
+}
+
 // One 64 x 64 tile of C_ij for one problem, unscaled, as (hi, lo): squared
 // Euclidean sum_k (x_k - y_k)^2 and cosine 1 - <x, y> accumulated exactly
 // (TwoSum on each exact product or square) and rounded once; dense costs are
 // copied. Per-problem min / max / max|C| and non-finite entries are folded
-// in with atomics. Problems without scaling get k C directly.
+// in with atomics. Problems without scaling get k C directly. The
+// per-entry arithmetic is FP32 double-float (GB300's FP64 pipe is narrow);
+// K is written with 16-byte stores and K^T through a shared-memory
+// transpose, both coalesced.
 __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const BatchTile *tiles)
 {
     constexpr int T = kBatchFormTile, KC = 32;
     __shared__ float Xs[T][KC + 1], Ys[T][KC + 1];
+    __shared__ float Th[T][T + 1], Tl[T][T + 1];
     const BatchTile tl = tiles[blockIdx.x];
     BatchProb *P = Pall + tl.prob;
     const int n = P->n, m = P->m, d = P->d, kind = P->kind;
     const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
     const int rb = tl.row0 + 4 * ty, cb = tl.col0 + 4 * tx;
-    double vals[4][4];
+    float vh[4][4], vl[4][4];
     if (kind == 0) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int r = rb + a, c = cb + b;
-                vals[a][b] = (r < n && c < m) ? (double)P->C[(int64_t)r * P->ldc + c] : 0.0;
+                vh[a][b] = (r < n && c < m) ? P->C[(int64_t)r * P->ldc + c] : 0.0f;
+                vl[a][b] = 0.0f;
             }
     } else {
         // Cosine: every partial sum of <x, y> lies within +-|x||y|, so a
@@ -1086,11 +1111,11 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                 for (int b = 0; b < 4; ++b)
                     off[a][b] = 2.0f * sN[4 * ty + a] * sN[T + 4 * tx + b] * (1.0f + 0x1p-10f);
         }
-        float s[4][4], e[4][4];
+        float sacc[4][4], e[4][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 4; ++b) { s[a][b] = (kind == 2) ? off[a][b] : 0.0f; e[a][b] = 0.0f; }
+            for (int b = 0; b < 4; ++b) { sacc[a][b] = (kind == 2) ? off[a][b] : 0.0f; e[a][b] = 0.0f; }
         for (int k0 = 0; k0 < d; k0 += KC) {
             for (int t = threadIdx.x; t < T * KC; t += 256) {
                 const int rr = t / KC, kk = t % KC;
@@ -1116,8 +1141,8 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                             const float p = dh * dh;
                             const float pe = fmaf(dh, dh, -p) + 2.0f * dh * de;  // + de^2 (negligible)
                             float t, te;
-                            two_sum_f(s[a][b], p, t, te);
-                            s[a][b] = t;
+                            two_sum_f(sacc[a][b], p, t, te);
+                            sacc[a][b] = t;
                             e[a][b] += te + pe;
                         }
                 } else {
@@ -1127,10 +1152,10 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                         for (int b = 0; b < 4; ++b) {
                             const float p = xa[a] * yb[b];
                             const float pe = fmaf(xa[a], yb[b], -p);  // exact product error
-                            const float t = s[a][b] + p;              // Fast2Sum: |s| >= |p|
-                            const float z = t - s[a][b];
+                            const float t = sacc[a][b] + p;           // Fast2Sum: |s| >= |p|
+                            const float z = t - sacc[a][b];
                             e[a][b] += (p - z) + pe;
-                            s[a][b] = t;
+                            sacc[a][b] = t;
                         }
                 }
             }
@@ -1141,73 +1166,116 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 if (kind == 1) {
-                    vals[a][b] = (double)s[a][b] + (double)e[a][b];
+                    two_sum_f(sacc[a][b], e[a][b], vh[a][b], vl[a][b]);
                 } else {
-                    const float dot_hi = s[a][b] - off[a][b];     // exact (Sterbenz)
-                    vals[a][b] = 1.0 - ((double)dot_hi + (double)e[a][b]);
+                    const float dot_hi = sacc[a][b] - off[a][b];     // exact (Sterbenz)
+                    float ch, t;
+                    two_sum_f(1.0f, -dot_hi, ch, t);
+                    two_sum_f(ch, t - e[a][b], vh[a][b], vl[a][b]);
                 }
             }
     }
-    // statistics and store
+    // statistics (double-float, FP64 once per thread), then k C
     const bool direct = !P->scale;
-    const double k = direct ? kLog2e / P->eps : 1.0;
-    double mx = -DBL_MAX, mn = DBL_MAX, ab = 0.0;
+    const double kd = direct ? kLog2e / P->eps : 1.0;
+    const float kh = (float)kd, kl = (float)(kd - (double)kh);
+    float mxh = -INFINITY, mxl = 0.0f, mnh = INFINITY, mnl = 0.0f;
     int bad = 0;
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
-        const int r = rb + a;
-        if (r >= n) continue;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const int c = cb + b;
-            if (c < m) {
-                const double v = vals[a][b];
-                if (!isfinite(v)) bad = 1;
-                mx = fmax(mx, v);
-                mn = fmin(mn, v);
-                ab = fmax(ab, fabs(v));
-                put_df(P->Kh, P->Kl, (int64_t)r * P->ldm + c, k * v);
-                if (P->KTh) put_df(P->KTh, P->KTl, (int64_t)c * P->ldn + r, k * v);
-            } else if (c < P->ldm) {
-                P->Kh[(int64_t)r * P->ldm + c] = 0.0f;
-                P->Kl[(int64_t)r * P->ldm + c] = 0.0f;
+            const bool valid = rb + a < n && cb + b < m;
+            if (valid) {
+                if (!isfinite(vh[a][b])) bad = 1;
+                df_max(mxh, mxl, vh[a][b], vl[a][b]);
+                df_min(mnh, mnl, vh[a][b], vl[a][b]);
+            }
+            float oh, ol;
+            df_scale(kh, kl, vh[a][b], vl[a][b], oh, ol);
+            vh[a][b] = valid ? oh : 0.0f;
+            vl[a][b] = valid ? ol : 0.0f;
+        }
+    }
+    // K: one 16-byte store per row and thread (columns [m, ldm) get zeros)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int r = rb + a;
+        if (r < n && cb < P->ldm) {
+            const int64_t i = (int64_t)r * P->ldm + cb;
+            *reinterpret_cast<float4 *>(P->Kh + i) = make_float4(vh[a][0], vh[a][1], vh[a][2], vh[a][3]);
+            *reinterpret_cast<float4 *>(P->Kl + i) = make_float4(vl[a][0], vl[a][1], vl[a][2], vl[a][3]);
+        }
+    }
+    if (P->KTh) {
+        // K^T through shared memory: row c of K^T, columns r (rows [n, ldn) get zeros)
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                Th[4 * tx + b][4 * ty + a] = vh[a][b];
+                Tl[4 * tx + b][4 * ty + a] = vl[a][b];
+            }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T * (T / 4); t += 256) {
+            const int cc = t / (T / 4), r4 = 4 * (t % (T / 4));
+            const int c = tl.col0 + cc, r = tl.row0 + r4;
+            if (c < m && r < P->ldn) {
+                const int64_t i = (int64_t)c * P->ldn + r;
+                *reinterpret_cast<float4 *>(P->KTh + i) =
+                    make_float4(Th[cc][r4], Th[cc][r4 + 1], Th[cc][r4 + 2], Th[cc][r4 + 3]);
+                *reinterpret_cast<float4 *>(P->KTl + i) =
+                    make_float4(Tl[cc][r4], Tl[cc][r4 + 1], Tl[cc][r4 + 2], Tl[cc][r4 + 3]);
             }
         }
     }
+    double mx = mxh == -INFINITY ? -DBL_MAX : (double)mxh + (double)mxl;
+    double mn = mnh == INFINITY ? DBL_MAX : (double)mnh + (double)mnl;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-        ab = fmax(ab, __shfl_xor_sync(0xffffffffu, ab, o));
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
     if ((threadIdx.x & 31) == 0) {
-        if (mx != -DBL_MAX) atomicMax(&P->cmax_enc, enc_d(mx));
-        if (mn != DBL_MAX) atomicMin(&P->cmin_enc, enc_d(mn));
-        atomicMax(&P->cabs_enc, enc_d(ab));
+        if (mx != -DBL_MAX) {
+            atomicMax(&P->cmax_enc, enc_d(mx));
+            atomicMin(&P->cmin_enc, enc_d(mn));
+            atomicMax(&P->cabs_enc, enc_d(fmax(fabs(mx), fabs(mn))));
+        }
         if (bad) atomicOr(&P->nonfinite, 1u);
     }
 }
 
-// k C in place for problems scaled by their maximum (k needs max C).
+// k C in place for problems scaled by their maximum (k needs max C): a
+// double-float product per entry, K and K^T each swept with coalesced
+// 16-byte accesses (padding entries hold zeros and stay zero).
 __global__ void __launch_bounds__(256) k_batch_scale(BatchProb *Pall, const BatchTile *tiles)
 {
     const BatchTile tl = tiles[blockIdx.x];
     BatchProb *P = Pall + tl.prob;
     if (!P->scale) return;
     const double k = batch_k(P);
-    const int n = P->n, m = P->m;
-    for (int t = threadIdx.x; t < kBatchFormTile * kBatchFormTile; t += 256) {
-        const int r = tl.row0 + t / kBatchFormTile, c = tl.col0 + t % kBatchFormTile;
-        if (r < n && c < m) {
-            const int64_t i = (int64_t)r * P->ldm + c;
-            const double v = (double)P->Kh[i] + (double)P->Kl[i];
-            put_df(P->Kh, P->Kl, i, k * v);
-            if (P->KTh) {
-                const int64_t it = (int64_t)c * P->ldn + r;
-                const double vt = (double)P->KTh[it] + (double)P->KTl[it];
-                put_df(P->KTh, P->KTl, it, k * vt);
-            }
+    const float kh = (float)k, kl = (float)(k - (double)kh);
+    constexpr int T = kBatchFormTile, V = kBatchFormTile / 4;
+    auto scale4 = [&](float *H, float *L, int64_t i) {
+        float4 h = *reinterpret_cast<float4 *>(H + i), l = *reinterpret_cast<float4 *>(L + i);
+        float4 oh, ol;
+        df_scale(kh, kl, h.x, l.x, oh.x, ol.x);
+        df_scale(kh, kl, h.y, l.y, oh.y, ol.y);
+        df_scale(kh, kl, h.z, l.z, oh.z, ol.z);
+        df_scale(kh, kl, h.w, l.w, oh.w, ol.w);
+        *reinterpret_cast<float4 *>(H + i) = oh;
+        *reinterpret_cast<float4 *>(L + i) = ol;
+    };
+    for (int t = threadIdx.x; t < T * V; t += 256) {
+        const int r = tl.row0 + t / V, c4 = tl.col0 + 4 * (t % V);
+        if (r < P->n && c4 < P->m) scale4(P->Kh, P->Kl, (int64_t)r * P->ldm + c4);
+    }
+    if (P->KTh) {
+        for (int t = threadIdx.x; t < T * V; t += 256) {
+            const int c = tl.col0 + t / V, r4 = tl.row0 + 4 * (t % V);
+            if (c < P->m && r4 < P->n) scale4(P->KTh, P->KTl, (int64_t)c * P->ldn + r4);
         }
     }
 }
