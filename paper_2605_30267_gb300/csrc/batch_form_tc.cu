@@ -612,21 +612,16 @@ cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStrea
     CUtensorMap mA, mB;
     if (!encode_slices(&mA, SL, t.R, t.dpad, kTcM) || !encode_slices(&mB, SL, t.R, t.dpad, kTcN))
         return cudaErrorNotSupported;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_batch_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kTcSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
-    static int grid_cap = 0;
-    if (!grid_cap) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid_cap = std::max(1, sms);     // one persistent CTA per SM (shared memory)
-    }
-    k_batch_form_tc<<<std::min(t.ntiles, grid_cap), kTcThreads, kTcSmemBytes, s>>>(
+    // per launch: the attribute and the SM count belong to the current device
+    e = cudaFuncSetAttribute(k_batch_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // one persistent CTA per SM (its shared memory allows no second)
+    k_batch_form_tc<<<std::min(t.ntiles, std::max(1, sms)), kTcThreads, kTcSmemBytes, s>>>(
         P, t.tiles, t.ntiles, t.expo, mA, mB);
     return cudaGetLastError();
 }
