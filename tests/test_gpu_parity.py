@@ -1,6 +1,7 @@
 """GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
 
-Tolerances (from the arithmetic of the kernels):
+Tolerances (from the arithmetic of the kernels: exact double-float exponent
+arguments, FP32 lane sums with Kahan compensation, FP64 row finishes):
   * one pass: |delta u| (natural-log units) <= 2e-6, i.e. f within 2e-6 eps;
   * whole solves: potentials within 1e-3 eps max-abs after centring, <C,P>
     within 1e-5 relative, step counts within 2% (or one step), FP64-truth
