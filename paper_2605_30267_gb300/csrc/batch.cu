@@ -714,26 +714,21 @@ __device__ bool cta_init(BatchProb *P)
 // One step after the row and column passes at x (see the single-problem step
 // kernel for the phases P1-P3; P1 ran in the column tiles, which left `nrec`
 // records of sums and bounds). Returns true when the solve stops.
-template <bool LOCAL>
-__device__ bool cta_step(BatchProb *P, int nrec)
-{
-    __shared__ int stop_s;
-    const int m = P->m;
-    const int method = P->method, stab = P->stability;
-    const int first = ldv<LOCAL>(&P->first);
-    const double mu = ldv<LOCAL>(&P->mu);
-    const bool is_acc = method == 1;
-    const StageK K = cta_stage_constants(is_acc, mu);
-    const double alpha = K.alpha, inv_alpha = K.inv_alpha, inv_1pa = K.inv_1pa, a2 = K.a2;
-    const double kappa1 = K.kappa1, c2f = K.c2f, ratio_next = K.ratio_next;
-    const double inv_1pa_next = K.inv_1pa_next;
-    const bool check = is_acc && !first && stab != 0;
-    const bool wupd = is_acc && !first;
+// ---- the step of Algorithm 1, in pieces: cta_step runs them all in one CTA;
+// large problems run the per-column loops (P2, the update) as work items.
 
-    // ---- P1 totals from the column records: per finishing warp in record
-    // order, then over the warps (the same order for every work split)
-    double v[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};   // err, raw, kl, <b,x>, c1, c2l
-    double lo3[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi3[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+// P1 totals from the column records (per finishing warp in record order, then
+// over the warps: the same order for every work split) and the dual.
+struct StepP1 {
+    double v[6];                 // err, raw, kl, <b,x>, c1, c2l
+    double lo3[3], hi3[3];       // bounds of raw, x, w
+    double err, rbar, dual;
+};
+
+template <bool LOCAL>
+__device__ void step_p1(BatchProb *P, int nrec, StepP1 &o)
+{
+    const int m = P->m;
     {
         __shared__ double tot_s[12];
         if (threadIdx.x < 12) {
@@ -759,55 +754,69 @@ __device__ bool cta_step(BatchProb *P, int nrec)
             tot_s[q] = a;
         }
         __syncthreads();
-        for (int q = 0; q < 6; ++q) v[q] = tot_s[q];
-        for (int q = 0; q < 3; ++q) { lo3[q] = tot_s[6 + q]; hi3[q] = tot_s[9 + q]; }
+        for (int q = 0; q < 6; ++q) o.v[q] = tot_s[q];
+        for (int q = 0; q < 3; ++q) { o.lo3[q] = tot_s[6 + q]; o.hi3[q] = tot_s[9 + q]; }
         __syncthreads();
     }
-    const double err = v[0];
-    const double rbar = v[1] / (double)m;
+    o.err = o.v[0];
+    o.rbar = o.v[1] / (double)m;
     double au[1] = {0.0};
     {
         const int rt = P->row_tiles;
         for (int t = threadIdx.x; t < rt; t += kBatchThreads) au[0] += ldv<LOCAL>(&P->rowpart[2 * t]);
         cta_sum<1>(au);
     }
-    const double dual = P->eps * (au[0] + v[3] - 1.0);
+    o.dual = P->eps * (au[0] + o.v[3] - 1.0);
+}
 
-    // ---- P2
-    double v2[1] = {0.0};
-    double wl[1] = {DBL_MAX}, wh[1] = {-DBL_MAX};
-    if (wupd) {
-        for (int j = threadIdx.x; j < m; j += kBatchThreads) {
-            const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
-            const double xj = ldv<LOCAL>(&P->x[j]);
-            const double w1 = (ldv<LOCAL>(&P->w[j]) + a2 * xj + 2.0 * s) * inv_1pa;
-            P->w1[j] = w1;
-            const double v1 = w1 * inv_alpha - xj;
-            v2[0] += v1 * v1 * ldv<LOCAL>(&P->D1[j]);
-            wl[0] = fmin(wl[0], w1);
-            wh[0] = fmax(wh[0], w1);
-        }
+// P2 over columns [j0, j1): w1 = (w + (alpha^2 - 2) x + 2 s) / (1 + alpha),
+// Theorem 4's sum_j v1_j^2 D1_j and the bounds of w1 (CTA totals).
+template <bool LOCAL>
+__device__ void step_p2(BatchProb *P, int j0, int j1, double rbar, const StageK &K, double &v2,
+                        double &wl, double &wh)
+{
+    double v2a[1] = {0.0};
+    double wla[1] = {DBL_MAX}, wha[1] = {-DBL_MAX};
+    for (int j = j0 + threadIdx.x; j < j1; j += kBatchThreads) {
+        const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
+        const double xj = ldv<LOCAL>(&P->x[j]);
+        const double w1 = (ldv<LOCAL>(&P->w[j]) + K.a2 * xj + 2.0 * s) * K.inv_1pa;
+        P->w1[j] = w1;
+        const double v1 = w1 * K.inv_alpha - xj;
+        v2a[0] += v1 * v1 * ldv<LOCAL>(&P->D1[j]);
+        wla[0] = fmin(wla[0], w1);
+        wha[0] = fmax(wha[0], w1);
     }
-    cta_sum<1>(v2);
-    cta_minmax<1>(wl, wh);
+    cta_sum<1>(v2a);
+    cta_minmax<1>(wla, wha);
+    v2 = v2a[0];
+    wl = wla[0];
+    wh = wha[0];
+}
 
-    // ---- P3: the scalar decisions by thread 0, shared with the CTA
-    struct P3 {
-        double inv_1pa_new, ratio, shift_g, shift_fn, mu_new;
-        int stab_bits, gate, stop, steps_new, ms, jst, stages, status;
-    };
+// P3: the scalar decisions (stop, gate, stage hand-over, operand shifts).
+struct P3 {
+    double inv_1pa_new, ratio, shift_g, shift_fn, mu_new;
+    int stab_bits, gate, stop, steps_new, ms, jst, stages, status;
+};
+
+template <bool LOCAL>
+__device__ P3 step_p3(BatchProb *P, const StepP1 &o, const StageK &K, double mu, bool is_acc,
+                      bool wupd, bool check, double v2, double wl, double wh)
+{
     __shared__ P3 p3s;
+    const int stab = P->stability;
     if (threadIdx.x == 0) {
         P3 r;
-        const double c1 = v[4], c2l = v[5];
-        const double c1r = kappa1 * ldv<LOCAL>(&P->kl_prev);
-        const double c2r = c2f * v2[0];
+        const double c1 = o.v[4], c2l = o.v[5];
+        const double c1r = K.kappa1 * ldv<LOCAL>(&P->kl_prev);
+        const double c2r = K.c2f * v2;
         r.stab_bits = 0;
         if (check) r.stab_bits = (c1 <= c1r ? 0 : 1) | (c2l <= c2r ? 0 : 2);
         r.gate = (stab == 2) && (r.stab_bits != 0);
         r.steps_new = ldv<LOCAL>(&P->steps) + 1;
-        const bool nonfinite = !isfinite(err);
-        const bool converged = err < P->tol;
+        const bool nonfinite = !isfinite(o.err);
+        const bool converged = o.err < P->tol;
         r.stop = converged || nonfinite || r.steps_new >= P->max_steps;
         r.status = nonfinite ? 3 : (converged ? 0 : 7);
         r.mu_new = mu;
@@ -826,15 +835,15 @@ __device__ bool cta_step(BatchProb *P, int nrec)
                 r.stages += 1;
             }
         }
-        r.inv_1pa_new = stage_end ? inv_1pa_next : inv_1pa;
-        r.ratio = (stage_end && P->carry == 0) ? ratio_next : 1.0;
-        const double slo = lo3[0] - rbar, shi = hi3[0] - rbar;
+        r.inv_1pa_new = stage_end ? K.inv_1pa_next : K.inv_1pa;
+        r.ratio = (stage_end && P->carry == 0) ? K.ratio_next : 1.0;
+        const double slo = o.lo3[0] - o.rbar, shi = o.hi3[0] - o.rbar;
         double xlo, xhi;
         if (is_acc) {
             double w1lo, w1hi;
-            if (!wupd) { w1lo = lo3[2]; w1hi = hi3[2]; }
-            else if (r.gate) { w1lo = alpha * lo3[1]; w1hi = alpha * hi3[1]; }
-            else { w1lo = wl[0]; w1hi = wh[0]; }
+            if (!wupd) { w1lo = o.lo3[2]; w1hi = o.hi3[2]; }
+            else if (r.gate) { w1lo = K.alpha * o.lo3[1]; w1hi = K.alpha * o.hi3[1]; }
+            else { w1lo = wl; w1hi = wh; }
             xlo = (w1lo * r.ratio + slo) * r.inv_1pa_new;
             xhi = (w1hi * r.ratio + shi) * r.inv_1pa_new;
         } else {
@@ -851,35 +860,47 @@ __device__ bool cta_step(BatchProb *P, int nrec)
     }
     __syncthreads();
     const P3 r = p3s;
-    const bool stop = r.stop, gate = r.gate;
-    const double inv_1pa_new = r.inv_1pa_new, ratio = r.ratio, shift_g = r.shift_g;
-    const double eps_c = P->eps_c, k2 = P->k2;
-    if (!stop) {
-        for (int j = threadIdx.x; j < m; j += kBatchThreads) {
-            const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
-            const double xj = ldv<LOCAL>(&P->x[j]);
-            double xn;
-            if (is_acc) {
-                double w1 = wupd ? (gate ? alpha * xj : P->w1[j]) : ldv<LOCAL>(&P->w[j]);
-                w1 *= ratio;
-                xn = (w1 + s) * inv_1pa_new;
-                P->w[j] = w1;
-            } else {
-                xn = s;
-            }
-            P->x_prev[j] = xj;
-            P->x[j] = xn;
-            P->p_prev[j] = ldv<LOCAL>(&P->del[j]);
-            P->D_prev[j] = ldv<LOCAL>(&P->D1[j]);
-            put_df(P->Gh, P->Gl, j, k2 * (eps_c * xn + shift_g));
-        }
-    }
     __syncthreads();
+    return r;
+}
+
+// The update over columns [j0, j1): x+, w+ (Algorithm 1), the previous
+// iterate's records for Theorem 4, and the row-pass operand G'.
+template <bool LOCAL>
+__device__ void step_update(BatchProb *P, int j0, int j1, bool is_acc, bool wupd, bool gate,
+                            double alpha, double ratio, double inv_1pa_new, double rbar,
+                            double shift_g)
+{
+    const double eps_c = P->eps_c, k2 = P->k2;
+    for (int j = j0 + threadIdx.x; j < j1; j += kBatchThreads) {
+        const double s = ldv<LOCAL>(&P->raw[j]) - rbar;
+        const double xj = ldv<LOCAL>(&P->x[j]);
+        double xn;
+        if (is_acc) {
+            double w1 = wupd ? (gate ? alpha * xj : ldv<LOCAL>(&P->w1[j])) : ldv<LOCAL>(&P->w[j]);
+            w1 *= ratio;
+            xn = (w1 + s) * inv_1pa_new;
+            P->w[j] = w1;
+        } else {
+            xn = s;
+        }
+        P->x_prev[j] = xj;
+        P->x[j] = xn;
+        P->p_prev[j] = ldv<LOCAL>(&P->del[j]);
+        P->D_prev[j] = ldv<LOCAL>(&P->D1[j]);
+        put_df(P->Gh, P->Gl, j, k2 * (eps_c * xn + shift_g));
+    }
+}
+
+// The per-problem state after a step (thread 0); returns the stop flag to the CTA.
+__device__ bool step_tail(BatchProb *P, const P3 &r, const StepP1 &o, bool wupd)
+{
+    __shared__ int stop_s;
     if (threadIdx.x == 0) {
         P->steps = r.steps_new;
-        P->err = err;
-        P->dual = dual;
-        P->kl_prev = v[2];
+        P->err = o.err;
+        P->dual = o.dual;
+        P->kl_prev = o.v[2];
         P->first = 0;
         if (r.stab_bits) P->failures += 1;
         if (wupd) {
@@ -888,16 +909,116 @@ __device__ bool cta_step(BatchProb *P, int nrec)
             P->j_in_stage = r.jst;
             P->stages = r.stages;
         }
-        if (stop) {
+        if (r.stop) {
             P->status = r.status;
         } else {
             P->shift_g = r.shift_g;
             P->shift_f = r.shift_fn;
         }
-        stop_s = stop ? 1 : 0;
+        stop_s = r.stop ? 1 : 0;
     }
     __syncthreads();
     return stop_s != 0;
+}
+
+template <bool LOCAL>
+__device__ bool cta_step(BatchProb *P, int nrec)
+{
+    const int m = P->m;
+    const int first = ldv<LOCAL>(&P->first);
+    const double mu = ldv<LOCAL>(&P->mu);
+    const bool is_acc = P->method == 1;
+    const StageK K = cta_stage_constants(is_acc, mu);
+    const bool check = is_acc && !first && P->stability != 0;
+    const bool wupd = is_acc && !first;
+    StepP1 o;
+    step_p1<LOCAL>(P, nrec, o);
+    double v2 = 0.0, wl = DBL_MAX, wh = -DBL_MAX;
+    if (wupd) step_p2<LOCAL>(P, 0, m, o.rbar, K, v2, wl, wh);
+    const P3 r = step_p3<LOCAL>(P, o, K, mu, is_acc, wupd, check, v2, wl, wh);
+    if (!r.stop)
+        step_update<LOCAL>(P, 0, m, is_acc, wupd, r.gate, K.alpha, r.ratio, r.inv_1pa_new, o.rbar,
+                           r.shift_g);
+    __syncthreads();
+    return step_tail(P, r, o, wupd);
+}
+
+// ---- a large problem's step as work items (every read of data another CTA
+// wrote goes to L2: LOCAL = false)
+
+// After the last column item: the P1 totals, kept in the problem record for
+// the CTA that finishes the P2 items. Returns true when P2 items follow.
+__device__ bool split_step_begin(BatchProb *P)
+{
+    StepP1 o;
+    step_p1<false>(P, P->col_tiles, o);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 6; ++q) P->s_v[q] = o.v[q];
+        for (int q = 0; q < 3; ++q) { P->s_lo3[q] = o.lo3[q]; P->s_hi3[q] = o.hi3[q]; }
+        P->s_err = o.err;
+        P->s_rbar = o.rbar;
+        P->s_dual = o.dual;
+    }
+    __syncthreads();
+    return P->method == 1 && !__ldcg(&P->first);
+}
+
+// One P2 item: its columns' w1 and its record (v2, min w1, max w1).
+__device__ void split_step_p2(BatchProb *P, int item)
+{
+    const double mu = __ldcg(&P->mu);
+    const StageK K = cta_stage_constants(true, mu);
+    const int j0 = item * P->step_cols, j1 = min(P->m, j0 + P->step_cols);
+    double v2, wl, wh;
+    step_p2<false>(P, j0, j1, __ldcg(&P->s_rbar), K, v2, wl, wh);
+    if (threadIdx.x == 0) {
+        P->p2rec[3 * item] = v2;
+        P->p2rec[3 * item + 1] = wl;
+        P->p2rec[3 * item + 2] = wh;
+    }
+}
+
+// After the P2 items (or at once when the step has none): the P2 totals in
+// item order, the scalar decisions and the new state; the update's scalars
+// go to the problem record for the update items. Returns the stop flag.
+__device__ bool split_step_decide(BatchProb *P, bool wupd)
+{
+    StepP1 o;
+    for (int q = 0; q < 6; ++q) o.v[q] = __ldcg(&P->s_v[q]);
+    for (int q = 0; q < 3; ++q) { o.lo3[q] = __ldcg(&P->s_lo3[q]); o.hi3[q] = __ldcg(&P->s_hi3[q]); }
+    o.err = __ldcg(&P->s_err);
+    o.rbar = __ldcg(&P->s_rbar);
+    o.dual = __ldcg(&P->s_dual);
+    const double mu = __ldcg(&P->mu);
+    const bool is_acc = P->method == 1;
+    const StageK K = cta_stage_constants(is_acc, mu);
+    const bool check = wupd && P->stability != 0;
+    double v2 = 0.0, wl = DBL_MAX, wh = -DBL_MAX;
+    if (wupd) {
+        for (int t = 0; t < P->step_items; ++t) {
+            v2 += __ldcg(&P->p2rec[3 * t]);
+            wl = fmin(wl, __ldcg(&P->p2rec[3 * t + 1]));
+            wh = fmax(wh, __ldcg(&P->p2rec[3 * t + 2]));
+        }
+    }
+    const P3 r = step_p3<false>(P, o, K, mu, is_acc, wupd, check, v2, wl, wh);
+    if (threadIdx.x == 0) {
+        P->u_alpha = K.alpha;
+        P->u_ratio = r.ratio;
+        P->u_inv1pa = r.inv_1pa_new;
+        P->u_wupd = wupd ? 1 : 0;
+        P->u_gate = r.gate;
+    }
+    return step_tail(P, r, o, wupd);
+}
+
+// One update item: x, w and G' for its columns.
+__device__ void split_step_update(BatchProb *P, int item)
+{
+    const int j0 = item * P->step_cols, j1 = min(P->m, j0 + P->step_cols);
+    step_update<false>(P, j0, j1, P->method == 1, __ldcg(&P->u_wupd) != 0, __ldcg(&P->u_gate) != 0,
+                       __ldcg(&P->u_alpha), __ldcg(&P->u_ratio), __ldcg(&P->u_inv1pa),
+                       __ldcg(&P->s_rbar), __ldcg(&P->shift_g));
 }
 
 // Outputs of a finished problem: f = eps u, g = eps x, the result record.
@@ -1282,6 +1403,23 @@ __global__ void __launch_bounds__(256) k_batch_scale(BatchProb *Pall, const Batc
 
 // ---------------------------------------------------------- the solver --
 
+// What follows a large problem's step: the next row phase (through the update
+// items when the step was split), the final evaluation pass, or the result.
+__device__ void step_continue(BatchQueue *q, BatchProb *P, BatchResult *R, int p, bool stop,
+                              bool split)
+{
+    if (!stop) {
+        if (split) q_push(q, P->step_items, [&](int t) { return batch_item(BI_UPD, p, t); });
+        else q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
+    } else if (P->evaluate) {
+        q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_FINAL, p, t); });
+    } else {
+        cta_finish<false>(P, R, true);
+        publish_early(q, p, R);
+        problem_done(q);
+    }
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_solve(BatchProb *Pall, BatchQueue *q,
                                                                BatchResult *res)
 {
@@ -1375,17 +1513,29 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_batch_solve(BatchProb *Pal
                 cta_colrec(P, tile, ws, lo3, hi3);
             }
             if (arrive_last(P, P->col_items)) {
-                const bool stop = cta_step<false>(P, P->col_tiles);
-                if (!stop) {
-                    q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
-                } else if (P->evaluate) {
-                    q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_FINAL, p, t); });
+                if (P->step_items > 0) {
+                    // large problem: P1 totals here, P2 and the update as items
+                    if (split_step_begin(P)) {
+                        q_push(q, P->step_items, [&](int t) { return batch_item(BI_P2, p, t); });
+                    } else {
+                        const bool stop = split_step_decide(P, false);
+                        step_continue(q, P, R, p, stop, true);
+                    }
                 } else {
-                    cta_finish<false>(P, R, true);
-                    publish_early(q, p, R);
-                    problem_done(q);
+                    const bool stop = cta_step<false>(P, P->col_tiles);
+                    step_continue(q, P, R, p, stop, false);
                 }
             }
+        } else if (kind == BI_P2) {
+            split_step_p2(P, tile);
+            if (arrive_last(P, P->step_items)) {
+                const bool stop = split_step_decide(P, true);
+                step_continue(q, P, R, p, stop, true);
+            }
+        } else if (kind == BI_UPD) {
+            split_step_update(P, tile);
+            if (arrive_last(P, P->step_items))
+                q_push(q, P->row_tiles, [&](int t) { return batch_item(BI_ROW, p, t); });
         }
         __syncthreads();
     }

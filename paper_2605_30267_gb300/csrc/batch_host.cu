@@ -25,15 +25,16 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Sizes of one problem's arrays, in the order they are carved.
 struct ProbLayout {
-    size_t kh, kl, kth, ktl, a, loga, u, fh, fl, mvec, gh, gl, rowpart, colrec;
+    size_t kh, kl, kth, ktl, a, loga, u, fh, fl, mvec, gh, gl, rowpart, colrec, p2rec;
     size_t total() const
     {
         return kh + kl + kth + ktl + a + loga + u + fh + fl + 12 * mvec + gh + gl + rowpart +
-               colrec;
+               colrec + p2rec;
     }
 };
 
-ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles, bool transposed)
+ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles, bool transposed,
+                  int step_items)
 {
     const int64_t ldm = (m + 3) / 4 * 4, n4 = (n + 3) / 4 * 4;
     ProbLayout L;
@@ -45,6 +46,7 @@ ProbLayout layout(int64_t n, int64_t m, int row_tiles, int col_tiles, bool trans
     L.gh = L.gl = up256((size_t)ldm * 4);
     L.rowpart = up256((size_t)row_tiles * 16);
     L.colrec = up256((size_t)col_tiles * kBatchColRec * 8);
+    L.p2rec = up256((size_t)step_items * 3 * 8);
     return L;
 }
 
@@ -90,6 +92,12 @@ struct BatchPlan {
 // Cosine costs with kBatchTcMinD <= d <= kBatchTcMaxD are formed on the
 // tensor cores unless ACCSINK_BATCH_FORM=cuda selects the CUDA-core
 // expansion for every problem.
+bool step_items_enabled()
+{
+    const char *e = std::getenv("ACCSINK_BATCH_STEP_ITEMS");
+    return !(e && std::strcmp(e, "0") == 0);
+}
+
 bool tc_form_enabled()
 {
     const char *e = std::getenv("ACCSINK_BATCH_FORM");
@@ -166,7 +174,13 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
         P.cmax_enc = 0ull;             // below every encoded value
         P.cmin_enc = ~0ull;            // above every encoded value
         P.cabs_enc = 0ull;
-        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles, transposed);
+        // the step's column loops as items for large tiled problems
+        // (ACCSINK_BATCH_STEP_ITEMS=0 keeps them in one CTA)
+        if (!P.small && q.m >= kBatchStepSplitMin && step_items_enabled()) {
+            P.step_cols = kBatchStepCols;
+            P.step_items = (q.m + kBatchStepCols - 1) / kBatchStepCols;
+        }
+        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles, transposed, P.step_items);
         pl.data_bytes += pl.lay[k].total();
         outstanding += (size_t)std::max(P.row_tiles, P.col_items);
         P.tc = (tc_on && q.cost_kind == ACCSINK_COST_COSINE && q.d >= kBatchTcMinD &&
@@ -292,6 +306,7 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         P.Gh = (float *)take(L.gh); P.Gl = (float *)take(L.gl);
         P.rowpart = (double *)take(L.rowpart);
         P.colrec = (double *)take(L.colrec);
+        P.p2rec = L.p2rec ? (double *)take(L.p2rec) : nullptr;
     }
     BatchTcLaunch tcl{};
     if (pl.R > 0) {

@@ -42,6 +42,7 @@ struct BatchProb {
     float *Gh, *Gl;          // m (padded): k (eps_c x + shift_g) as (hi, lo)
     double *rowpart;         // row tiles x 2 (sum a u, sum cost)
     double *colrec;          // column tiles x kBatchColRec (step P1 sums and bounds)
+    double *p2rec;           // step items x 3 (P2 sum, min w1, max w1), large problems
     // ---- schedule
     int32_t small;           // 1: the whole solve is one work item
     int32_t row_tiles, rows_per_tile, col_tiles;
@@ -49,6 +50,7 @@ struct BatchProb {
     int32_t arrive;          // arrival counter of the phase in flight
     int32_t tc;              // 1: cost formed on the tensor cores (batch_form_tc.cu)
     int32_t tc_xoff, tc_yoff;   // first slice rows of X and Y (tensor-core problems)
+    int32_t step_items, step_cols;   // > 0: the step's column loops as work items
     int32_t pad_s;
     // ---- cost statistics from the formation (ordered encodings of FP64)
     unsigned long long cmax_enc, cmin_enc, cabs_enc;
@@ -58,6 +60,10 @@ struct BatchProb {
     double k2, eps_c, inv_eps, cost_div, cmax, cmin, cabs, min_loga, log_m;
     double shift_g, shift_f, mu, kl_prev, err, dual, cost;
     int32_t steps, stages, m_stage, j_in_stage, failures, first, status, done;
+    // ---- a step split into work items: P1 totals, then the update's scalars
+    double s_v[6], s_lo3[3], s_hi3[3], s_err, s_rbar, s_dual;
+    double u_alpha, u_ratio, u_inv1pa;
+    int32_t u_wupd, u_gate;
 };
 
 // Result record of one problem (device, copied back to the host).
@@ -85,7 +91,16 @@ struct BatchQueue {
 };
 
 // Work item kinds.
-enum BatchItem { BI_SMALL = 0, BI_INIT = 1, BI_ROW = 2, BI_COL = 3, BI_FINAL = 4 };
+enum BatchItem {
+    BI_SMALL = 0, BI_INIT = 1, BI_ROW = 2, BI_COL = 3, BI_FINAL = 4,
+    BI_P2 = 5,    // a column range of the step's P2 sums (large problems)
+    BI_UPD = 6    // a column range of the step's update of x, w and G' (large problems)
+};
+
+// Large problems (tiled, m >= kBatchStepSplitMin) run the step's per-column
+// loops as items of kBatchStepCols columns instead of in one CTA.
+constexpr int kBatchStepSplitMin = 4096;
+constexpr int kBatchStepCols = 1024;
 
 __host__ __device__ inline unsigned long long batch_item(int kind, int prob, int tile)
 {

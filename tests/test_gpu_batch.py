@@ -286,3 +286,37 @@ def test_autotune_picks_a_candidate(ctx):
     assert len(times) == 18 and all(t > 0 for t in times)
     assert ctx.accsink_batch_get_config() == best
     ctx.accsink_batch_set_config()
+
+
+def split_step_problems():
+    # m >= 4096 and tiled: the step's P2 and update loops run as work items;
+    # the first keeps K^T (n m >= 2^20), the second sweeps column tiles of K
+    return [Prob("sqeuclid", 300, 4200, 41, 1e-2, d=3, scale=True),
+            Prob("cosine", 200, 4100, 42, 2e-2, d=24),
+            Prob("dense", 150, 4099, 43, 1e-2, method=B.PLAIN)]
+
+
+def test_split_step_matches_oracle(ctx):
+    probs = split_step_problems()
+    fs, gs, rs = run_batch(ctx, probs)
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        check_against_oracle(p, f, g, r)
+
+
+def test_split_step_equals_one_cta_step(ctx):
+    """The step's column loops as work items give the potentials of the
+    one-CTA step bit for bit (only the order of Theorem 4's P2 sum differs,
+    which feeds the stability report alone)."""
+    import os
+    probs = split_step_problems()
+    f1, g1, r1 = run_batch(ctx, probs)
+    os.environ["ACCSINK_BATCH_STEP_ITEMS"] = "0"
+    try:
+        f2, g2, r2 = run_batch(ctx, probs)
+    finally:
+        del os.environ["ACCSINK_BATCH_STEP_ITEMS"]
+    for k in range(len(probs)):
+        assert r1[k]["sinkhorn_steps"] == r2[k]["sinkhorn_steps"], k
+        np.testing.assert_array_equal(f1[k], f2[k])
+        np.testing.assert_array_equal(g1[k], g2[k])
+        assert abs(r1[k]["stability_failures"] - r2[k]["stability_failures"]) <= 1
