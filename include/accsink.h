@@ -276,7 +276,9 @@ typedef struct {
  * products within d 2^-39 |x||y|; the environment variable
  * ACCSINK_BATCH_FORM=cuda selects the CUDA-core expansion, exact to FP64
  * rounding, for every problem); the slices take 12 bytes per vector element
- * of workspace. Returns OK when every problem
+ * of workspace. Large problems (tiled, m >= 4096) run the step's per-column
+ * loops as work items over many CTAs (ACCSINK_BATCH_STEP_ITEMS=0 keeps them
+ * in one CTA; the potentials are the same bit for bit). Returns OK when every problem
  * converged, ACCSINK_ERR_MAXITER when some did not (their results are still
  * valid), another code for the first failed problem (see res[k].status), or
  * ACCSINK_ERR_TIMEOUT if a device-side wait of the scheduler ran out. */
