@@ -548,6 +548,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // after a wait that ran out, every problem with a tile on this CTA is
+    // marked (some of its costs may never have been written)
+    if (abort_s && threadIdx.x == 0)
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x)
+            atomicOr(&Pall[tiles[t].prob].nonfinite, 2u);
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
