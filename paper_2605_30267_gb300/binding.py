@@ -225,11 +225,28 @@ def problem_dense(C, a=None, b=None, scale_to_max=False) -> accsink_problem:
     return pr
 
 
+def _cost_kind(kind) -> int:
+    if kind in ("sqeuclid", COST_SQEUCLID):
+        return COST_SQEUCLID
+    if kind in ("cosine", COST_COSINE):
+        return COST_COSINE
+    raise ValueError(f"unknown point-cloud cost kind {kind!r} (sqeuclid or cosine)")
+
+
+def _method(method) -> int:
+    if method in ("acc", ACC):
+        return ACC
+    if method in ("plain", PLAIN):
+        return PLAIN
+    raise ValueError(f"unknown method {method!r} (acc or plain)")
+
+
 def problem_points(X, Y, kind="sqeuclid", a=None, b=None, scale_to_max=False) -> accsink_problem:
     """Problem struct for a point-cloud cost formed on the fly from FP32 CUDA
     point clouds X (n x d) and Y (m x d), row-major and contiguous:
     kind "sqeuclid" (||x_i - y_j||^2) or "cosine" (1 - <x_i, y_j>)."""
     import torch
+    cost_kind = _cost_kind(kind)
     _check_dev(X, torch.float32, "X")
     _check_dev(Y, torch.float32, "Y")
     if X.dim() != 2 or Y.dim() != 2 or X.shape[1] != Y.shape[1]:
@@ -240,7 +257,7 @@ def problem_points(X, Y, kind="sqeuclid", a=None, b=None, scale_to_max=False) ->
     m = Y.shape[0]
     pr = accsink_problem()
     pr.n, pr.m, pr.d = n, m, d
-    pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+    pr.cost_kind = cost_kind
     pr.X = X.data_ptr()
     pr.Y = Y.data_ptr()
     if a is not None:
@@ -306,16 +323,18 @@ class Context:
         import numpy as np
         pr = accsink_problem()
         if C is not None:
-            assert C.dtype == np.float32 and C.flags.c_contiguous
+            if C.dtype != np.float32 or not C.flags.c_contiguous or C.ndim != 2:
+                raise TypeError("C must be a contiguous 2-D float32 array")
             n, m = C.shape
             pr.n, pr.m, pr.cost_kind, pr.ldc = n, m, COST_DENSE, m
             pr.C = C.ctypes.data
         else:
-            assert X.dtype == np.float32 and X.flags.c_contiguous
-            assert Y.dtype == np.float32 and Y.flags.c_contiguous
+            for nm_, arr in (("X", X), ("Y", Y)):
+                if arr is None or arr.dtype != np.float32 or not arr.flags.c_contiguous or arr.ndim != 2:
+                    raise TypeError(f"{nm_} must be a contiguous 2-D float32 array")
             pr.n, pr.d = X.shape
             pr.m = Y.shape[0]
-            pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+            pr.cost_kind = _cost_kind(kind)
             pr.X = X.ctypes.data
             pr.Y = Y.ctypes.data
         pr.a = np.ascontiguousarray(a, np.float64).ctypes.data if a.dtype == np.float64 and a.flags.c_contiguous else None
@@ -497,7 +516,7 @@ def problem_host(a, b, C=None, X=None, Y=None, kind="sqeuclid", scale_to_max=Fal
     else:
         pr.n, pr.d = X.shape
         pr.m = Y.shape[0]
-        pr.cost_kind = COST_SQEUCLID if kind in ("sqeuclid", COST_SQEUCLID) else COST_COSINE
+        pr.cost_kind = _cost_kind(kind)
         pr.X = host(X, np.float32)
         pr.Y = host(Y, np.float32)
     pr.cost_scale = SCALE_MAX_TO_ONE if scale_to_max else SCALE_NONE
@@ -610,12 +629,12 @@ def solve_points(X, Y, a, b, eps, kind="sqeuclid", tol=1e-6, method="acc", scale
 
     Returns (f, g, result dict) with f, g FP64 CUDA tensors in cost units."""
     import torch
+    meth = _method(method)
     own = ctx is None
     ctx = ctx or Context(X.device.index or 0)
     try:
         prob = problem_points(X, Y, kind, a, b, scale_to_max)
-        p = default_params(eps=float(eps), tol=float(tol),
-                           method=ACC if method in ("acc", ACC) else PLAIN, **params)
+        p = default_params(eps=float(eps), tol=float(tol), method=meth, **params)
         f = torch.empty(X.shape[0], dtype=torch.float64, device=X.device)
         g = torch.empty(Y.shape[0], dtype=torch.float64, device=X.device)
         res = ctx.accsink_solve(prob, p, f, g, stream=stream)
@@ -631,12 +650,12 @@ def solve(C, a, b, eps, tol=1e-6, method="acc", scale_to_max=False, ctx: Context
 
     Returns (f, g, result dict) with f, g FP64 CUDA tensors in cost units."""
     import torch
+    meth = _method(method)
     own = ctx is None
     ctx = ctx or Context(C.device.index or 0)
     try:
         prob = problem_dense(C, a, b, scale_to_max)
-        p = default_params(eps=float(eps), tol=float(tol),
-                           method=ACC if method in ("acc", ACC) else PLAIN, **params)
+        p = default_params(eps=float(eps), tol=float(tol), method=meth, **params)
         f = torch.empty(C.shape[0], dtype=torch.float64, device=C.device)
         g = torch.empty(C.shape[1], dtype=torch.float64, device=C.device)
         res = ctx.accsink_solve(prob, p, f, g, stream=stream)
