@@ -203,6 +203,21 @@ def _check_dev(t, dtype, name, numel=None):
         raise ValueError(f"{name} must be contiguous")
 
 
+def _check_vec(t, n, name):
+    """A device FP64 array the library reads or writes n doubles of: a
+    contiguous CUDA float64 tensor with at least n elements (None is left to
+    the library's own null check)."""
+    if t is None:
+        return
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64:
+        raise TypeError(f"{name} must be a CUDA float64 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n > 0 and t.numel() < n:
+        raise ValueError(f"{name} must hold at least {n} elements, has {t.numel()}")
+
+
 def problem_dense(C, a=None, b=None, scale_to_max=False) -> accsink_problem:
     """Problem struct for a dense FP32 CUDA cost C (n x m, unit column stride)."""
     import torch
@@ -309,6 +324,8 @@ class Context:
     # ---- whole solves --------------------------------------------------
     def accsink_solve(self, prob: accsink_problem, params: accsink_params, f_out, g_out,
                       stream=None, allow_maxiter=True) -> accsink_result:
+        _check_vec(f_out, prob.n, "f_out")
+        _check_vec(g_out, prob.m, "g_out")
         res = accsink_result()
         rc = lib().accsink_solve(self._h, ct.byref(prob), ct.byref(params), _stream_ptr(stream),
                                  _ptr(f_out), _ptr(g_out), ct.byref(res))
@@ -355,6 +372,9 @@ class Context:
         k = len(probs)
         if not (len(params) == len(f_outs) == len(g_outs) == k):
             raise ValueError("probs, params, f_outs and g_outs must have the same length")
+        for i in range(k):
+            _check_vec(f_outs[i], probs[i].n, f"f_outs[{i}]")
+            _check_vec(g_outs[i], probs[i].m, f"g_outs[{i}]")
         pa = (accsink_problem * k)(*probs)
         qa = (accsink_params * k)(*params)
         fa = (ct.c_void_p * k)(*[_ptr(t) for t in f_outs])
@@ -412,14 +432,22 @@ class Context:
 
     # ---- single passes -------------------------------------------------
     def accsink_row_pass(self, prob, eps, g, f_out, stream=None):
+        _check_vec(g, prob.m, "g")
+        _check_vec(f_out, prob.n, "f_out")
         self._raise(lib().accsink_row_pass(self._h, ct.byref(prob), float(eps), _ptr(g),
                                            _ptr(f_out), _stream_ptr(stream)))
 
     def accsink_col_lse(self, prob, eps, f, ell_out, stream=None):
+        _check_vec(f, prob.n, "f")
+        _check_vec(ell_out, prob.m, "ell_out")
         self._raise(lib().accsink_col_lse(self._h, ct.byref(prob), float(eps), _ptr(f),
                                           _ptr(ell_out), _stream_ptr(stream)))
 
     def accsink_sinkhorn_map(self, prob, eps, g, f_out, c_out, s_out, stream=None) -> float:
+        _check_vec(g, prob.m, "g")
+        _check_vec(f_out, prob.n, "f_out")
+        _check_vec(c_out, prob.m, "c_out")
+        _check_vec(s_out, prob.m, "s_out")
         err = ct.c_double()
         self._raise(lib().accsink_sinkhorn_map(self._h, ct.byref(prob), float(eps), _ptr(g),
                                                _ptr(f_out), _ptr(c_out), _ptr(s_out),
@@ -427,6 +455,8 @@ class Context:
         return err.value
 
     def accsink_transport_cost(self, prob, eps, f, g, stream=None) -> float:
+        _check_vec(f, prob.n, "f")
+        _check_vec(g, prob.m, "g")
         out = ct.c_double()
         self._raise(lib().accsink_transport_cost(self._h, ct.byref(prob), float(eps), _ptr(f),
                                                  _ptr(g), ct.byref(out), _stream_ptr(stream)))
@@ -451,6 +481,8 @@ class Context:
 
     def accsink_solve_from(self, prob, params, state: accsink_state, f_out, g_out, stream=None,
                            allow_maxiter=True) -> accsink_result:
+        _check_vec(f_out, prob.n, "f_out")
+        _check_vec(g_out, prob.m, "g_out")
         res = accsink_result()
         rc = lib().accsink_solve_from(self._h, ct.byref(prob), ct.byref(params), ct.byref(state),
                                       _stream_ptr(stream), _ptr(f_out), _ptr(g_out),
@@ -460,6 +492,9 @@ class Context:
 
     def accsink_warm_start(self, prob, params, g0, f_out, g_out, stream=None,
                            allow_maxiter=True) -> accsink_result:
+        _check_vec(g0, prob.m, "g0")
+        _check_vec(f_out, prob.n, "f_out")
+        _check_vec(g_out, prob.m, "g_out")
         res = accsink_result()
         rc = lib().accsink_warm_start(self._h, ct.byref(prob), ct.byref(params), _ptr(g0),
                                       _stream_ptr(stream), _ptr(f_out), _ptr(g_out),

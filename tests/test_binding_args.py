@@ -45,3 +45,11 @@ def test_host_problem_struct():
     C = np.random.default_rng(2).random((3, 5)).astype(np.float32)
     pd = B.problem_host(a, b, C=C)
     assert pd.cost_kind == B.COST_DENSE and pd.ldc == 5
+
+
+def test_device_vectors_are_checked_before_the_library_sees_them():
+    B._check_vec(None, 5, "f_out")                       # left to the library's null check
+    with pytest.raises(TypeError, match="CUDA float64"):
+        B._check_vec(torch.zeros(5, dtype=torch.float64), 5, "f_out")
+    with pytest.raises(TypeError, match="CUDA float64"):
+        B._check_vec(np.zeros(5), 5, "g_out")
