@@ -505,12 +505,30 @@ class Context:
     def accsink_plan(self, prob, eps, f, g, P_out, stream=None):
         """P_out: a CUDA float32 or float64 tensor (n x >= m, unit column stride)."""
         import torch
+        _check_vec(f, prob.n, "f")
+        _check_vec(g, prob.m, "g")
+        if (not isinstance(P_out, torch.Tensor) or not P_out.is_cuda
+                or P_out.dtype not in (torch.float32, torch.float64)):
+            raise TypeError("P_out must be a CUDA float32 or float64 tensor")
+        if (P_out.dim() != 2 or P_out.shape[0] < prob.n or P_out.shape[1] < prob.m
+                or P_out.stride(1) != 1 or P_out.stride(0) < prob.m):
+            raise ValueError("P_out must be n x m (or larger) with unit column stride")
         dtype = 1 if P_out.dtype == torch.float64 else 0
         self._raise(lib().accsink_plan(self._h, ct.byref(prob), float(eps), _ptr(f), _ptr(g),
                                        _ptr(P_out), int(P_out.stride(0)), dtype,
                                        _stream_ptr(stream)))
 
     def accsink_barycentric(self, prob, eps, f, g, Z, out, stream=None):
+        """Z: CUDA float32 (m x dz, row-major); out: CUDA float64 (n x dz)."""
+        import torch
+        _check_vec(f, prob.n, "f")
+        _check_vec(g, prob.m, "g")
+        if (not isinstance(Z, torch.Tensor) or not Z.is_cuda or Z.dtype != torch.float32
+                or Z.dim() != 2 or Z.shape[0] < prob.m or not Z.is_contiguous()):
+            raise TypeError("Z must be a contiguous CUDA float32 tensor of m rows")
+        if (not isinstance(out, torch.Tensor) or not out.is_cuda or out.dtype != torch.float64
+                or not out.is_contiguous() or out.numel() < prob.n * Z.shape[1]):
+            raise TypeError("out must be a contiguous CUDA float64 tensor of n x dz elements")
         self._raise(lib().accsink_barycentric(self._h, ct.byref(prob), float(eps), _ptr(f),
                                               _ptr(g), _ptr(Z), int(Z.shape[1]), _ptr(out),
                                               _stream_ptr(stream)))
