@@ -472,6 +472,8 @@ class Context:
     def accsink_export_state(self, x, w, stream=None) -> accsink_state:
         """State of the last solve on this context; x, w: device FP64 arrays of
         length m that receive the iterate and the momentum."""
+        _check_vec(x, 0, "x")
+        _check_vec(w, int(x.numel()), "w")
         st = accsink_state()
         st.m = int(x.numel())
         st.x = _ptr(x)
