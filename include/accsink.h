@@ -451,17 +451,23 @@ int accsink_launch_geometry(accsink_ctx *ctx, int32_t n, int32_t m, int32_t vec,
  * counterpart to this entry point; it exists only for those callers.
  *
  * It needs no context and calls no allocating routine. Its scratch is one
- * 16 MiB array in device memory that the library reserves on every device
- * it is loaded on and holds until the process exits. It must fit
+ * 16 MiB array in device memory, held until the process exits. It must fit
  * 8 n + 8 m bytes plus a few KB; larger problems return ACCSINK_ERR_BUDGET
  * before any work is queued. Everything runs on the current device and on
  * `stream`; the call returns without synchronising.
  *
- * The first call on a device looks up the array's device address once; make
- * that first call outside any stream capture. All calls share the one array
- * and reuse it without clearing what they fully rewrite: calls whose work
- * overlaps on the GPU (different streams, or host threads) race and must be
- * serialised by the caller.
+ * The first call on a device looks up the array's device address once. With
+ * CUDA's default lazy module loading that first call is also what loads the
+ * array's module on the device and so reserves the 16 MiB: it can fail with
+ * ACCSINK_ERR_CUDA when the device has no memory left. A caller whose memory
+ * pool will claim the device should therefore make one call (any valid
+ * size) before the pool does, or run with CUDA_MODULE_LOADING=EAGER; and it
+ * should make that first call outside any stream capture. All calls share
+ * the one array and reuse it without clearing what they fully rewrite:
+ * calls whose work overlaps on the GPU (different streams, or host threads)
+ * race and must be serialised by the caller. If a device-side wait of the
+ * pass runs out (a bounded grid barrier), every ell_out entry is NaN: a NaN
+ * output means that the pass did not complete.
  *
  * Arguments as accsink_col_lse (dense cost, f (n) and ell_out (m) device
  * FP64, eps > 0). Returns ACCSINK_OK, ACCSINK_ERR_INVALID_ARG,

@@ -669,7 +669,10 @@ class Server:
 
 def accsink_col_lse_noalloc(prob: accsink_problem, eps, f, ell_out, stream=None) -> int:
     """Context-free column log-sum-exp pass that allocates nothing (see the
-    header); returns the accsink status code."""
+    header); returns the accsink status code. f and ell_out are checked like
+    every other device vector (CUDA float64, contiguous, n and m elements)."""
+    _check_vec(f, prob.n, "f")
+    _check_vec(ell_out, prob.m, "ell_out")
     return lib().accsink_col_lse_noalloc(ct.byref(prob), float(eps), _ptr(f), _ptr(ell_out),
                                          _stream_ptr(stream))
 

@@ -7,9 +7,11 @@
 // For them, accsink_col_lse_noalloc() runs the same kernels as
 // accsink_col_lse() without a context: every intermediate (the column-pass
 // operand, the per-split partials, the reduction partials and the small
-// solver state) lives in one file-scope device array of fixed size, which
-// the CUDA module reserves on each device when the library is loaded there
-// and keeps until the process exits.
+// solver state) lives in one file-scope device array of fixed size. The
+// CUDA module that holds it is loaded on a device, and the array reserved
+// there, when the first call on that device looks up its address (under
+// lazy module loading, CUDA's default) or when the library's context is
+// created (eager loading); it is kept until the process exits.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -80,6 +82,9 @@ extern "C" int accsink_col_lse_noalloc(const accsink_problem *prob, double eps,
                          up256((size_t)vec_grid * kPartStride * 8) + up256((size_t)n * 8);
     const size_t per_split = (size_t)m * 8;
     if (fixed + up256(per_split) > kNoAllocScratchBytes) return ACCSINK_ERR_BUDGET;
+    // The chosen splits hold about (SMs x CTAs per SM x 128) columns of
+    // partials in all, ~1.2 MB on 152 SMs, so this guard only acts on
+    // devices with far more resident CTAs.
     while (splits > 1 && fixed + up256(per_split * (size_t)splits) > kNoAllocScratchBytes)
         --splits;
 
@@ -108,8 +113,11 @@ extern "C" int accsink_col_lse_noalloc(const accsink_problem *prob, double eps,
     w.ignore_done = 1;
 
     // The array keeps whatever the previous call left; the state (including
-    // the grid-barrier counter, which must start at zero) is rewritten here,
-    // and every other region is fully overwritten before it is read.
+    // the grid-barrier counter, which must start at zero) is rewritten here.
+    // On a completed call every other region is overwritten before it is
+    // read. If the preparation kernel's bounded grid barrier runs out, the
+    // state records the timeout, the column pass does not run and the
+    // finish writes NaN to every ell_j instead of reading stale partials.
     DevState hs;
     memset(&hs, 0, sizeof(hs));
     hs.eps_user = eps;

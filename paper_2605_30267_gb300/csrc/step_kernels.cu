@@ -940,11 +940,18 @@ cudaError_t launch_scale_out(const double *src, double scale, double *dst, int n
 }
 
 // ell_j = log S_j + (R_j - shift_f) / eps from the column-pass partials.
+// When the operand preparation stopped early (its bounded grid barrier ran
+// out, so the column pass did not run), the partials are not this call's:
+// every ell_j is then NaN.
 __global__ void k_col_finish_lse(Work w, int m, double *ell_out)
 {
     const DevState *st = w.st;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= m) return;
+    if (*(volatile int32_t *)&st->status != 0) {
+        ell_out[j] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
     const int splits = st->col_splits;
     const float kh = st->k_hi, kl = st->k_lo;
     float R = w.colpart[j].x;

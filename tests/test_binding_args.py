@@ -53,3 +53,14 @@ def test_device_vectors_are_checked_before_the_library_sees_them():
         B._check_vec(torch.zeros(5, dtype=torch.float64), 5, "f_out")
     with pytest.raises(TypeError, match="CUDA float64"):
         B._check_vec(np.zeros(5), 5, "g_out")
+
+
+def test_noalloc_wrapper_checks_its_vectors():
+    # refused before the library is called: host, wrong dtype
+    pr = B.accsink_problem()
+    pr.n, pr.m = 4, 6
+    with pytest.raises(TypeError, match="CUDA float64"):
+        B.accsink_col_lse_noalloc(pr, 1e-2, torch.zeros(4, dtype=torch.float64),
+                                  torch.zeros(6, dtype=torch.float64))
+    with pytest.raises(TypeError, match="CUDA float64"):
+        B.accsink_col_lse_noalloc(pr, 1e-2, np.zeros(4), np.zeros(6))

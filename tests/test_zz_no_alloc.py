@@ -4,12 +4,14 @@ context-based accsink_col_lse, on two calls in a row through the C-ABI.
 It is for callers that cannot allocate device memory; its scratch is a fixed
 file-scope device array shared by every call, so the second call must not
 see anything left over from the first. This file is collected last."""
+import ctypes as ct
+
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 from paper_2605_30267_gb300 import binding as B
-from paper_2605_30267_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -40,8 +42,39 @@ def test_noalloc_col_lse_matches_context_pass_twice():
             torch.cuda.synchronize()
             d = (out - ref).abs().max().item()
             assert d <= TOL, (seed, d)
+            # and against the FP64 oracle's column log-sum-exp
+            orc = O.col_lse(O.Cost(C=C.cpu().numpy()), eps, f.cpu().numpy() / eps)
+            assert np.abs(out.cpu().numpy() - orc).max() <= TOL
     finally:
         ctx.close()
+
+
+def test_noalloc_col_lse_near_its_size_limit():
+    # m = 1.5e6 columns: 12 MB of column partials in the 16 MiB scratch
+    torch.cuda.set_device(0)
+    n, m, eps = 64, 1_500_000, 1e-2
+    C, f, eps = _case(3, n, m, eps)
+    prob = B.problem_dense(C)
+    ctx = B.Context(0)
+    try:
+        ref = torch.empty(m, dtype=torch.float64, device=DEV)
+        ctx.accsink_col_lse(prob, eps, f, ref)
+        out = torch.full((m,), float("nan"), dtype=torch.float64, device=DEV)
+        assert B.accsink_col_lse_noalloc(prob, eps, f, out) == B.OK
+        torch.cuda.synchronize()
+        assert (out - ref).abs().max().item() <= TOL
+        cols = np.random.default_rng(5).choice(m, 64, replace=False)
+        orc = O.col_lse_sample(O.Cost(C=C.cpu().numpy()), eps, f.cpu().numpy() / eps, cols)
+        assert np.abs(out.cpu().numpy()[cols] - orc).max() <= TOL
+    finally:
+        ctx.close()
+
+
+def _raw_call(prob, eps, f, out):
+    # straight through the C-ABI: the library's own size checks, not the
+    # binding's vector checks, are what these cases test
+    return B.lib().accsink_col_lse_noalloc(ct.byref(prob), float(eps), f.data_ptr(),
+                                           out.data_ptr(), None)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
@@ -52,6 +85,9 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     prob.n = 3_000_000
     f = torch.zeros(8, dtype=torch.float64, device=DEV)
     out = torch.zeros(8, dtype=torch.float64, device=DEV)
-    assert B.accsink_col_lse_noalloc(prob, 1e-2, f, out) == B.ERR_BUDGET
-    prob.n = 0
-    assert B.accsink_col_lse_noalloc(prob, 1e-2, f, out) == B.ERR_INVALID_ARG
+    assert _raw_call(prob, 1e-2, f, out) == B.ERR_BUDGET
+    # m large enough that one split of column partials exceeds it
+    prob.n, prob.m, prob.ldc = 1, 2_100_000, 2_100_000
+    assert _raw_call(prob, 1e-2, f, out) == B.ERR_BUDGET
+    prob.n, prob.m, prob.ldc = 0, 8, 8
+    assert _raw_call(prob, 1e-2, f, out) == B.ERR_INVALID_ARG
