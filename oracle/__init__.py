@@ -77,7 +77,8 @@ class _Result(ct.Structure):
 
 class _History(ct.Structure):
     _fields_ = [("cap", ct.c_long), ("err", ct.c_void_p), ("dual", ct.c_void_p),
-                ("mu", ct.c_void_p), ("stab", ct.c_void_p), ("x", ct.c_void_p)]
+                ("mu", ct.c_void_p), ("stab", ct.c_void_p), ("x", ct.c_void_p),
+                ("cond", ct.c_void_p)]
 
 
 _lib = None
@@ -110,6 +111,7 @@ def _L():
                                         ct.c_int, vp, vp, d, lg, lg, ct.c_int, vp, vp, vp,
                                         vp, vp, vp, vp]
         _lib.orc_evaluate.argtypes = [vp, d, vp, vp, vp, vp, vp]
+        _lib.orc_marginal_l1.argtypes = [vp, d, vp, vp, vp, vp, vp]
         _lib.orc_plan.argtypes = [vp, d, vp, vp, vp]
         _lib.orc_barycentric.argtypes = [vp, d, vp, vp, vp, lg, vp]
         _lib.orc_rows_sample.argtypes = [vp, d, vp, vp, vp, lg, vp, vp]
@@ -253,6 +255,8 @@ def solve(cost: Cost, a, b, eps, tol=1e-6, method=ACC, mu0=0.25, m0=4,
           carry_y=True, x0=None, w0=None, stage=None):
     """Plain Sinkhorn (method=PLAIN) or Acc-Sinkhorn with homotopy (ACC).
 
+    The history's ``cond`` rows hold Theorem 4's four terms (Cond 1 lhs, rhs,
+    Cond 2 lhs, rhs) of the step that produced each iterate.
     ``carry_y`` selects how Algorithm 2 hands w to the next homotopy stage:
     True keeps y = w / alpha (the (x_k, y_k) state of Theorem 1), False hands
     w over unchanged as Algorithm 2 is printed.
@@ -276,8 +280,9 @@ def solve(cost: Cost, a, b, eps, tol=1e-6, method=ACC, mu0=0.25, m0=4,
         h["mu"] = np.full(history, np.nan)
         h["stab"] = np.zeros(history, np.int32)
         h["x"] = np.full((history, cost.m), np.nan) if keep_x else None
+        h["cond"] = np.zeros((history, 4))
         hist = _History(history, _p(h["err"]), _p(h["dual"]), _p(h["mu"]),
-                        _p(h["stab"]), _p(h["x"]))
+                        _p(h["stab"]), _p(h["x"]), _p(h["cond"]))
     x0 = None if x0 is None else _f64(x0)
     w0 = None if w0 is None else _f64(w0)
     stage = stage or {"mu": mu0, "m_stage": m0, "j": 0, "stages": 0}
@@ -327,6 +332,15 @@ def evaluate(cost: Cost, eps, a, b, f, g):
     _L().orc_evaluate(cost.ref, float(eps), _p(a), _p(b), _p(f), _p(g), _p(out))
     return {"row_l1": out[0], "col_l1": out[1], "transport_cost": out[2],
             "dual": out[3], "primal": out[4], "mass": out[5]}
+
+
+def marginal_l1(cost: Cost, eps, a, b, f, g):
+    """FP64 row and column L1 errors of P(f, g) (eq. l1tol), rows split over
+    the OpenMP threads: for full-size problems."""
+    a, b, f, g = _f64(a), _f64(b), _f64(f), _f64(g)
+    out = np.empty(2)
+    _L().orc_marginal_l1(cost.ref, float(eps), _p(a), _p(b), _p(f), _p(g), _p(out))
+    return {"row_l1": out[0], "col_l1": out[1]}
 
 
 def plan(cost: Cost, eps, f, g):

@@ -81,6 +81,8 @@ double orc_cost_max(const orc_cost *c)
     orc_cost u = *c;
     u.scale = 1.0;
     double mx = -INFINITY;
+    /* a maximum does not depend on the order it is taken in */
+#pragma omp parallel for schedule(static) reduction(max : mx)
     for (long i = 0; i < c->n; ++i)
         for (long j = 0; j < c->m; ++j) {
             double v = orc_cost_entry(&u, i, j);
@@ -272,16 +274,19 @@ typedef struct {
  * caller passes room for it (hist_cap > 0):
  *   err_hist[e], dual_hist[e], mu_hist[e] (mu used to form that iterate, or 0
  *   for x_0 / plain), stab_hist[e] (bit0 = Cond1 failed, bit1 = Cond2 failed,
- *   for the step that produced iterate e), x_hist[e*m .. e*m+m-1] = iterate. */
+ *   for the step that produced iterate e), x_hist[e*m .. e*m+m-1] = iterate,
+ *   cond[4e .. 4e+3] = Theorem 4's Cond 1 lhs, Cond 1 rhs, Cond 2 lhs and
+ *   Cond 2 rhs of that step (zeros where no test ran: x_0, plain, OFF). */
 typedef struct {
     long cap;
     double *err, *dual, *mu;
     int *stab;
-    double *x;   /* may be NULL */
+    double *x;      /* may be NULL */
+    double *cond;   /* may be NULL */
 } orc_history;
 
 static void record(orc_history *h, long e, long m, double err, double dual,
-                   double mu, int stab, const double *x)
+                   double mu, int stab, const double *x, const double *cond)
 {
     if (!h || e >= h->cap) return;
     if (h->err) h->err[e] = err;
@@ -289,6 +294,8 @@ static void record(orc_history *h, long e, long m, double err, double dual,
     if (h->mu) h->mu[e] = mu;
     if (h->stab) h->stab[e] = stab;
     if (h->x) memcpy(h->x + e * m, x, sizeof(double) * (size_t)m);
+    if (h->cond)
+        for (int q = 0; q < 4; ++q) h->cond[4 * e + q] = cond ? cond[q] : 0.0;
 }
 
 /*
@@ -358,7 +365,7 @@ int orc_solve_from(const orc_problem *p, double tol, int method, double mu0,
     double err = orc_sinkhorn_map(p, x, u, c, s);
     steps = 1;
     double dual = orc_dual_after_row_pass(p, u, x);
-    record(hist, 0, m, err, dual, 0.0, 0, x);
+    record(hist, 0, m, err, dual, 0.0, 0, x, NULL);
 
     if (method == ORC_PLAIN) {
         for (;;) {
@@ -367,7 +374,7 @@ int orc_solve_from(const orc_problem *p, double tol, int method, double mu0,
             memcpy(x, s, sizeof(double) * (size_t)m);      /* x_{k+1} = S(x_k) */
             err = orc_sinkhorn_map(p, x, u, c, s);
             dual = orc_dual_after_row_pass(p, u, x);
-            record(hist, steps, m, err, dual, 0.0, 0, x);
+            record(hist, steps, m, err, dual, 0.0, 0, x, NULL);
             ++steps;
         }
     } else {
@@ -383,8 +390,8 @@ int orc_solve_from(const orc_problem *p, double tol, int method, double mu0,
                 w1[q] = (w[q] + (alpha * alpha - 2.0) * x1[q] + 2.0 * s1[q]) /
                         (1.0 + alpha);
             int stab = 0;
+            double t[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             if (stab_mode != ORC_STAB_OFF) {
-                double t[6];
                 orc_stability_terms(m, p->b, c, c1, x, w, x1, w1, alpha, t);
                 stab = (t[4] == 0.0 ? 1 : 0) | (t[5] == 0.0 ? 2 : 0);
                 if (stab) {
@@ -394,7 +401,7 @@ int orc_solve_from(const orc_problem *p, double tol, int method, double mu0,
                 }
             }
             double dual1 = orc_dual_after_row_pass(p, u1, x1);
-            record(hist, steps, m, err1, dual1, mu, stab, x1);
+            record(hist, steps, m, err1, dual1, mu, stab, x1, t);
             ++steps;
             double *tp;
             tp = x; x = x1; x1 = tp;
@@ -487,6 +494,56 @@ void orc_evaluate(const orc_cost *c, double eps, const double *a,
     out[4] = cost + eps * ent;
     out[5] = mass;
     free(col);
+}
+
+/* Both marginal errors of P(f, g) (eq. l1tol) for large problems:
+ *   out[0] = ||P 1 - a||_1,  out[1] = ||P' 1 - b||_1,
+ * with P_ij = exp((f_i + g_j - C_ij) / eps) (eq. P-from-dual) in FP64, the
+ * same quantities as out[0..1] of orc_evaluate. Rows are split over the
+ * threads; each thread sums its rows' entries into its own column array and
+ * the column arrays are added in thread order. */
+void orc_marginal_l1(const orc_cost *c, double eps, const double *a,
+                     const double *b, const double *f, const double *g,
+                     double *out)
+{
+    const long n = c->n, m = c->m;
+    int nt = 1;
+#ifdef _OPENMP
+    nt = omp_get_max_threads();
+#endif
+    double *cols = calloc((size_t)nt * (size_t)m, sizeof(double));
+    double *rowl1 = calloc((size_t)nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+    {
+        int t = 0;
+#ifdef _OPENMP
+        t = omp_get_thread_num();
+#endif
+        double *col = cols + (size_t)t * (size_t)m;
+        double rl = 0.0;
+#pragma omp for schedule(static)
+        for (long i = 0; i < n; ++i) {
+            double r = 0.0;
+            for (long j = 0; j < m; ++j) {
+                double pij = exp((f[i] + g[j] - orc_cost_entry(c, i, j)) / eps);
+                r += pij;
+                col[j] += pij;
+            }
+            rl += fabs(r - a[i]);
+        }
+        rowl1[t] = rl;
+    }
+    double row_l1 = 0.0, col_l1 = 0.0;
+    for (int t = 0; t < nt; ++t) row_l1 += rowl1[t];
+    for (long j = 0; j < m; ++j) {
+        double cj = 0.0;
+        for (int t = 0; t < nt; ++t) cj += cols[(size_t)t * (size_t)m + j];
+        col_l1 += fabs(cj - b[j]);
+    }
+    out[0] = row_l1;
+    out[1] = col_l1;
+    free(cols);
+    free(rowl1);
 }
 
 /* The transport plan P_ij = exp((f_i + g_j - C_ij) / eps) (eq. P-from-dual)

@@ -640,3 +640,68 @@ def test_eps_continuation_reaches_the_unique_fixed_point():
     sh = r["g"].mean() - cold["g"].mean()
     np.testing.assert_allclose(r["g"] - sh, cold["g"], atol=1e-6 * e2)
     np.testing.assert_allclose(r["f"] + sh, cold["f"], atol=1e-6 * e2)
+
+
+# --------------------------------------------------------------------------
+# Full-size FP64 marginal errors (eq. l1tol) and the recorded Theorem 4 terms.
+# --------------------------------------------------------------------------
+
+def test_marginal_l1_closed_form_on_a_separable_cost():
+    # C_ij = r_i + s_j with f_i = r_i + eps log a_i and g_j = s_j + eps log b_j
+    # + eps d_j gives P_ij = a_i b_j e^{d_j}: column sums b_j e^{d_j}, row sums
+    # a_i sum_j b_j e^{d_j}, both errors in closed form.
+    g = np.random.default_rng(71)
+    n, m, eps = 37, 23, 0.05
+    r_ = g.integers(0, 1024, n) / 1024.0
+    s_ = g.integers(0, 1024, m) / 1024.0
+    C = (r_[:, None] + s_[None, :]).astype(np.float32)
+    a, b = W.dirichlet1(g, n), W.dirichlet1(g, m)
+    d = g.uniform(-1e-3, 1e-3, m)
+    f = r_ + eps * np.log(a)
+    gg = s_ + eps * np.log(b) + eps * d
+    out = O.marginal_l1(O.Cost(C=C), eps, a, b, f, gg)
+    col = np.abs(b * np.expm1(d)).sum()
+    row = np.abs(a * ((b * np.exp(d)).sum() - 1.0)).sum()
+    assert abs(out["col_l1"] - col) <= 1e-12 * col
+    assert abs(out["row_l1"] - row) <= 1e-11 * max(row, 1e-300) + 1e-16
+    # a transposed cost or swapped marginals would break it
+    ev = O.evaluate(O.Cost(C=C), eps, a, b, f, gg)
+    assert abs(ev["col_l1"] - out["col_l1"]) <= 1e-13
+    assert abs(ev["row_l1"] - out["row_l1"]) <= 1e-13
+
+
+def test_marginal_l1_thread_count_does_not_matter():
+    C, a, b = _rand_problem(72, 61, 45)
+    eps = 0.1
+    res = O.solve(O.Cost(C=C), a, b, eps, tol=1e-3, method=O.PLAIN)
+    t0 = O.set_threads(0)
+    try:
+        O.set_threads(1)
+        one = O.marginal_l1(O.Cost(C=C), eps, res["a"], res["b"], res["f"], res["g"])
+        O.set_threads(3)
+        three = O.marginal_l1(O.Cost(C=C), eps, res["a"], res["b"], res["f"], res["g"])
+    finally:
+        O.set_threads(t0)
+    assert abs(one["col_l1"] - three["col_l1"]) <= 1e-15
+    assert abs(one["row_l1"] - three["row_l1"]) <= 1e-15
+    assert abs(one["col_l1"] - res["marginal_l1"]) <= 1e-12
+
+
+def test_history_records_theorem4_terms_behind_the_bits():
+    pr = W.gmm_stored_cost_problem(73, n=60, m=50, eps=1e-2)
+    r = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], pr["eps"], tol=1e-8, method=O.ACC,
+                history=5000)
+    h = r["history"]
+    cond, stab = h["cond"], h["stab"]
+    assert np.all(cond[0] == 0.0)                       # x_0: no step, no test
+    k = len(stab)
+    assert k > 5 and stab.any()
+    np.testing.assert_array_equal(stab & 1, (cond[:k, 0] > cond[:k, 1]).astype(np.int32))
+    np.testing.assert_array_equal((stab >> 1) & 1, (cond[:k, 2] > cond[:k, 3]).astype(np.int32))
+    # the Cond 1 right side is kappa1(alpha) times KL(b || c_k) of the previous
+    # iterate, KL >= 0 and kappa1 > 0 for mu0 <= 0.5
+    assert np.all(cond[1:k, 1] >= 0.0) and np.all(cond[1:k, 0] >= 0.0)
+    assert np.all(cond[1:k, 3] >= 0.0)
+    off = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], pr["eps"], tol=1e-8, method=O.ACC,
+                  history=5000, stability=O.STAB_OFF)
+    assert np.all(off["history"]["cond"] == 0.0)
