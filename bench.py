@@ -12,7 +12,8 @@ the inputs resident in HBM. The cost (1 GiB) is larger than L2 (129 MB), so
 every pass streams it from HBM; no L2 flush is needed between steps.
 
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
-on the same workload instead (bounded sample, extrapolated to a full solve).
+on the same workload instead: one full Acc solve to tol (the value) and
+single S evaluations (the steps).
 """
 from __future__ import annotations
 
@@ -36,10 +37,23 @@ SEED = 0
 METRIC = "time to marginal L1 1e-6, Acc vs plain Sinkhorn on 1 GB300; HBM GB/s; p50/p99 latency"
 WORKLOAD = ("gmm8-r3 stored sqeuclid cost n=m=16384 (1 GiB FP32, max 1), Dirichlet(1) "
             "marginals, eps=1e-3, tol=1e-6")
-# S evaluations Acc-Sinkhorn needs on this workload (measured by the GPU arm;
-# the oracle matches the GPU step count within 2% on every parity size). The
-# reference arm extrapolates its per-evaluation time with it.
-ACC_STEPS_REFERENCE = 156
+
+
+def bench_config(n):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOAD, "n": n, "m": n, "eps": EPS, "tol": TOL,
+            "method": "acc (Algorithm 1+2, mu0=0.25, m0=4, y carried across stages; the "
+                      "literal hand-over of Algorithm 2 is reported as acc_carry_w)",
+            "l2": "inputs larger than L2 (1 GiB cost vs 129 MB L2); no flush",
+            "parallelism": "none (one problem per device; replicas across ranks)"}
+
+
+# Peaks that MEASURED_PEAKS.json does not hold, measured on this GB300 (152
+# SMs, SM clock 2070 MHz) with a CUDA-event throughput probe (1216 CTAs x 256
+# threads, 8 independent dependency chains per thread, best of 5): MUFU
+# ex2.approx.ftz.f32 and FP32 FFMA lane operations per second.
+MEASURED_EX2_PER_S = 9.983e12
+MEASURED_FFMA_PER_S = 3.906e13
 
 
 def measured_peaks():
@@ -253,21 +267,26 @@ def run_gpu(args):
         traffic = profile_traffic("row_warp.cu", f"ncu_{dominant[0]}_gmm16384.txt")
 
         # ---- Acc vs plain at each eps (one solve each, after the timed region)
+        # acc: the default hand-over between homotopy stages (y = w / alpha
+        # kept, the state Theorem 1 follows); acc_carry_w: Algorithm 2 as
+        # printed, w handed over unchanged.
         versus = {}
         if not args.quick:
             for eps in (1e-1, 1e-2, 1e-3):
                 row = {}
-                for name, meth in (("acc", B.ACC), ("plain", B.PLAIN)):
+                for name, meth, kw in (("acc", B.ACC, {}), ("plain", B.PLAIN, {}),
+                                       ("acc_carry_w", B.ACC, {"carry": B.CARRY_W})):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    r = solve(meth, eps)
+                    r = solve(meth, eps, **kw)
                     e1.record(stream)
                     torch.cuda.synchronize()
                     row[name + "_s"] = round(e0.elapsed_time(e1) / 1e3, 6)
                     row[name + "_steps"] = r.sinkhorn_steps
                     row[name + "_status"] = B.STATUS_NAMES[r.status]
                 row["speedup"] = round(row["plain_s"] / row["acc_s"], 3)
+                row["speedup_carry_w"] = round(row["plain_s"] / row["acc_carry_w_s"], 3)
                 versus[f"{eps:g}"] = row
 
         # ---- end to end through the host-buffer C-ABI call
@@ -300,12 +319,8 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "f32 bulk, f64 reductions",
             "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "n": args.n, "m": args.n, "eps": EPS, "tol": TOL,
-                       "method": "acc (Algorithm 1+2, mu0=0.25, m0=4, y carried across stages)",
-                       "l2": "inputs larger than L2 (1 GiB cost vs 129 MB L2); no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "loop": "CUDA graph, conditional WHILE node" if acc_res["loop_mode"]
-                       else "host loop"},
+            "config": bench_config(args.n),
+            "loop": "CUDA graph, conditional WHILE node" if acc_res["loop_mode"] else "host loop",
             "latency_s": {"p50": round(percentile(lat, 0.5) / 1e3, 6),
                           "p99": round(percentile(lat, 0.99) / 1e3, 6)},
             "acc_steps": steps[-1],
@@ -404,9 +419,12 @@ def measure_points(ctx, dev, stream, n, with_plain, pass_reps, sm_max_mhz, host_
     g = torch.empty(n, dtype=torch.float64, device=dev)
     out = {"workload": POINTS_WORKLOAD.replace("65536", str(n)), "n": n, "m": n, "d": 3,
            "eps": EPS, "tol": TOL}
-    methods = (("acc", B.ACC), ("plain", B.PLAIN)) if with_plain else (("acc", B.ACC),)
-    for name, meth in methods:
-        p = B.default_params(eps=EPS, tol=TOL, method=meth, use_graph=0 if host_loop else 1)
+    methods = ((("acc", B.ACC, {}), ("plain", B.PLAIN, {}),
+                ("acc_carry_w", B.ACC, {"carry": B.CARRY_W}))
+               if with_plain else (("acc", B.ACC, {}),))
+    for name, meth, kw in methods:
+        p = B.default_params(eps=EPS, tol=TOL, method=meth, use_graph=0 if host_loop else 1,
+                             **kw)
         if name == "acc":
             ctx.accsink_solve(prob, p, f, g, stream=stream)          # warm-up
         e0 = torch.cuda.Event(enable_timing=True)
@@ -423,17 +441,17 @@ def measure_points(ctx, dev, stream, n, with_plain, pass_reps, sm_max_mhz, host_
             gsol = g.clone()
     if with_plain:
         out["speedup"] = round(out["plain_s"] / out["acc_s"], 3)
+        out["speedup_carry_w"] = round(out["plain_s"] / out["acc_carry_w_s"], 3)
     row_ms, col_ms = ctx.accsink_time_passes(prob, EPS, gsol, pass_reps, stream=stream)
     # FP32 work per cost entry of the exact expansion (8 per coordinate:
     # FMUL, 2 FFMA, 5 FADD) plus the exponent (2 FADD), the accumulation
     # (1 FADD), the running max and the Kahan fold (~2); ex2 runs on the XU.
     d = 3
     ops = 8 * d + 5
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    mhz = sm_max_mhz or 2070.0
-    peak = sms * 128 * mhz * 1e6 / 1e9            # FP32 lane operations, G/s
+    peak = MEASURED_FFMA_PER_S / 1e9              # FP32 lane operations, G/s
     ms = max(row_ms, col_ms)
     achieved = ops * n * n / (ms * 1e-3) / 1e9
+    entries_per_s = n * n / (ms * 1e-3)
     out["pass_ms"] = {"row": round(row_ms, 4), "col": round(col_ms, 4)}
     # The solve runs on the clouds in Hilbert-curve order and skips the slots whose
     # terms are all below 2^-80 of their rows' sums; the single passes timed
@@ -448,8 +466,17 @@ def measure_points(ctx, dev, stream, n, with_plain, pass_reps, sm_max_mhz, host_
                        "achieved": round(achieved, 1), "peak": round(peak, 1),
                        "unit": "G FP32 ops/s", "frac": round(achieved / peak, 4),
                        "ops_per_element": ops, "elements_per_launch": n * n,
-                       "peak_source": f"{sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz",
-                       "cost_entries_per_s": round(n * n / (ms * 1e-3), 1)}
+                       "ops_counted": "the exact double-float expansion the pass executes",
+                       "peak_source": "measured FFMA lane operations/s (throughput probe)",
+                       "cost_entries_per_s": round(entries_per_s, 1),
+                       # the method's own work per entry: d multiply-adds of
+                       # x.y and one exponential (no double-float expansion)
+                       "method_work": {
+                           "fma_per_element": d, "exp_per_element": 1,
+                           "fma_frac": round(d * entries_per_s / MEASURED_FFMA_PER_S, 4),
+                           "exp_frac": round(entries_per_s / MEASURED_EX2_PER_S, 4),
+                           "exp_peak_per_s": MEASURED_EX2_PER_S,
+                           "peak_source": "measured ex2.approx and FFMA rates (probe)"}}
     return out
 
 
@@ -643,7 +670,22 @@ def cpu_baseline(pr, acc_steps, evals):
                       f"of the Acc solve"}
 
 
+def _oracle_solve_time(O, cost, a, b, eps, method):
+    t0 = time.perf_counter()
+    r = O.solve(cost, a, b, eps, TOL, method=method)
+    return time.perf_counter() - t0, r
+
+
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle (plain C, OpenMP over rows and
+    columns) on this machine's host cores, on the GPU arm's workload.
+
+    value: one full Acc solve to tol at the benchmark size, measured (not
+    extrapolated). steps: `--steps` S evaluations (row pass + column pass)
+    at the benchmark size after `--warmup` untimed ones; ms_per_step is their
+    median. Beside it: the same S evaluation on one thread, full solves to
+    tol of the 256 x 256 point-cloud problem on one thread and on all cores,
+    and of the benchmark cost at eps = 1e-1 (plain and Acc)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
@@ -655,8 +697,9 @@ def run_reference(args):
     cores = O.set_threads(0)
     cost = O.Cost(C=pr["C"])
     a, b = O.normalise(pr["a"]), O.normalise(pr["b"])
+
+    # per S evaluation, all cores
     x = np.zeros(args.n)
-    acc_steps = ACC_STEPS_REFERENCE or args.ref_steps
     for _ in range(args.warmup):
         O.sinkhorn_map(cost, EPS, a, b, x)
     per = []
@@ -665,18 +708,55 @@ def run_reference(args):
         err, u, c, s = O.sinkhorn_map(cost, EPS, a, b, x)
         per.append(time.perf_counter() - t0)
         x = s
-    v = statistics.median(per) * acc_steps
-    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+    per_s = statistics.median(per)
+
+    # the full Acc solve to tol (the metric)
+    solve_s, r = _oracle_solve_time(O, cost, a, b, EPS, O.ACC)
+    acc_steps = r["sinkhorn_steps"]
+
+    extra = {"acc_steps": acc_steps, "acc_status": "converged" if r["status"] == O.CONVERGED
+             else "not converged", "acc_marginal_l1": r["marginal_l1"],
+             "per_s_evaluation_s": round(per_s, 4),
+             "extrapolated_s": round(per_s * acc_steps, 3)}
+    # one thread: one S evaluation at full size
+    O.set_threads(1)
+    t0 = time.perf_counter()
+    O.sinkhorn_map(cost, EPS, a, b, np.zeros(args.n))
+    extra["single_thread_per_s_evaluation_s"] = round(time.perf_counter() - t0, 3)
+    # the 256 x 256 point-cloud problem to tol, one thread and all cores
+    sp = W.small_pointcloud_problem(SEED)
+    scost = O.Cost(C=sp["C"])
+    small = {}
+    for label, th in (("1_thread", 1), (f"{cores}_threads", cores)):
+        O.set_threads(th)
+        for name, meth in (("acc", O.ACC), ("plain", O.PLAIN)):
+            t, rr = _oracle_solve_time(O, scost, sp["a"], sp["b"], sp["eps"], meth)
+            small[f"{name}_{label}_s"] = round(t, 4)
+            small[f"{name}_steps"] = rr["sinkhorn_steps"]
+    extra["small_pointcloud_256"] = dict(small, eps=sp["eps"], tol=TOL)
+    # the benchmark cost at eps = 1e-1, all cores
+    O.set_threads(cores)
+    big01 = {}
+    for name, meth in (("acc", O.ACC), ("plain", O.PLAIN)):
+        t, rr = _oracle_solve_time(O, cost, a, b, 1e-1, meth)
+        big01[f"{name}_s"] = round(t, 3)
+        big01[f"{name}_steps"] = rr["sinkhorn_steps"]
+    extra["eps_0.1"] = big01
+
+    sample = (f"one full FP64 oracle Acc solve to tol on {cores} threads ({acc_steps} S "
+              f"evaluations, measured); steps: single S evaluations at full size, median "
+              f"{per_s:.3f} s")
+    return {"impl": "reference", "metric": METRIC, "value": round(solve_s, 3), "unit": "s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(v * 1e3, 3), "higher_is_better": False, "scaling": "weak",
+            "ms_per_step": round(per_s * 1e3, 3), "step": "one S evaluation (row + column pass)",
+            "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)",
-            "config": {"workload": WORKLOAD, "n": args.n, "m": args.n, "eps": EPS, "tol": TOL},
-            "cpu_baseline": {"value": round(v, 3), "unit": "s", "cores": cores, "kind": "oracle",
-                             "sample": f"each step one full-size S evaluation of the FP64 oracle "
-                                       f"(median {statistics.median(per):.3f} s), extrapolated "
-                                       f"to {acc_steps} S evaluations of the Acc solve"},
-            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
+            "config": bench_config(args.n),
+            "cpu_baseline": {"value": round(solve_s, 3), "unit": "s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(solve_s, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "oracle": extra}
 
 
 def main():
@@ -687,8 +767,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--n", type=int, default=N)
     ap.add_argument("--pass-reps", type=int, default=20)
-    ap.add_argument("--cpu-evals", type=int, default=4)
-    ap.add_argument("--ref-steps", type=int, default=200)
+    ap.add_argument("--cpu-evals", type=int, default=30)
     ap.add_argument("--quick", action="store_true", help="skip the Acc-vs-plain table")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--host-loop", action="store_true",

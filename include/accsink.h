@@ -94,7 +94,15 @@ typedef struct {
  *   100000, stability REPORT, carry Y, evaluate 1, use_graph 1, history 0,
  *   col_transpose 1.
  * mu0 in (0, 1), m0 >= 1 (Algorithm 2). tol is the l1 marginal tolerance of
- * Sec. 5 eq. (l1tol). carry selects how a homotopy stage hands w to the next
+ * Sec. 5 eq. (l1tol), ||P1 - a||_1 + ||P'1 - b||_1 < tol. The solve tests it
+ * after every S evaluation on the FP64 sum of the column errors that its
+ * FP32 passes give (the row error is zero up to rounding after a row pass)
+ * and stops once that sum is below tol - 2^-22 (2^-22 = 2.4e-7): the guard
+ * covers the FP32 floor of the row marginal and the column sums' own error,
+ * so the FP64 truth of the whole sum at the returned potentials is below
+ * tol. A tol at or below 2^-22 cannot be met; such a solve runs to
+ * max_sinkhorn_steps (ACCSINK_ERR_MAXITER). res.marginal_l1 is the estimate
+ * the test used. carry selects how a homotopy stage hands w to the next
  * one: CARRY_Y keeps y = w / alpha (the state Theorem 1 follows), CARRY_W
  * hands w over unchanged as Algorithm 2 is printed. stability: OFF skips the
  * Theorem 4 test, REPORT counts failures, GATE also restarts the momentum
@@ -312,7 +320,8 @@ int accsink_batch_last_timing(const accsink_ctx *ctx, float *total_ms, float *fo
 /* A server owns a worker thread, a CUDA stream and a memory pool on one
  * device. Its calls are thread-safe (any client thread). Submitted solves
  * are admitted in FIFO order while their inputs, outputs and batch workspace
- * fit in mem_budget_bytes next to the potentials still held by clients;
+ * fit in mem_budget_bytes next to the potentials still held by clients and
+ * the group stays within its entry limit (accsink_server_set_limits);
  * each admitted group runs as one accsink_solve_batch-style persistent
  * launch. A request moves QUEUED -> RUNNING -> DONE (or FAILED); its
  * potentials stay on the device until accsink_server_release. */
@@ -356,6 +365,13 @@ int accsink_server_release(accsink_server *srv, accsink_ticket ticket);
 int accsink_server_get_stats(accsink_server *srv, accsink_server_stats *out);
 /* Work split of the server's batches (NULL: defaults). */
 int accsink_server_set_config(accsink_server *srv, const accsink_batch_config *cfg);
+/* Admission limit of one group: the sum of n m over its requests stays at or
+ * below max_group_entries (default 2^28), except that a larger request runs
+ * alone; 0 removes the limit. A batch lasts as long as its slowest problem,
+ * so under a deep queue smaller groups keep the device busier; the limit
+ * trades that against the per-launch overhead of many small groups.
+ * ACCSINK_ERR_INVALID_ARG for a negative limit. */
+int accsink_server_set_limits(accsink_server *srv, int64_t max_group_entries);
 
 /* ---- single passes (the hot path's steps, for tests and roofline timing) */
 

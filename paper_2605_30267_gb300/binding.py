@@ -38,6 +38,7 @@ EXPORTED = ["accsink_create", "accsink_destroy", "accsink_last_error", "accsink_
             "accsink_server_submit", "accsink_server_poll", "accsink_server_wait",
             "accsink_server_potentials", "accsink_server_copy_potentials",
             "accsink_server_release", "accsink_server_get_stats", "accsink_server_set_config",
+            "accsink_server_set_limits",
             "accsink_plan", "accsink_barycentric", "accsink_export_state",
             "accsink_solve_from", "accsink_warm_start", "accsink_selftest_timeout"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
@@ -159,6 +160,7 @@ def lib():
         L.accsink_server_potentials.argtypes = [vp, u64, P(vp), P(vp)]
         L.accsink_server_copy_potentials.argtypes = [vp, u64, vp, vp]
         L.accsink_server_release.argtypes = [vp, u64]
+        L.accsink_server_set_limits.argtypes = [vp, ct.c_int64]
         L.accsink_server_get_stats.argtypes = [vp, P(accsink_server_stats)]
         L.accsink_server_set_config.argtypes = [vp, P(accsink_batch_config)]
         for name in EXPORTED:
@@ -652,6 +654,12 @@ class Server:
         if rc != OK:
             raise AccsinkError(rc, "ticket cannot be released")
         self._keep.pop(ticket, None)
+
+    def set_limits(self, max_group_entries: int):
+        """Cost entries (sum of n m) one admitted group may hold (0: no limit)."""
+        rc = lib().accsink_server_set_limits(self._h, int(max_group_entries))
+        if rc != OK:
+            raise AccsinkError(rc, "bad server limit")
 
     def stats(self) -> dict:
         s = accsink_server_stats()

@@ -34,6 +34,16 @@ constexpr int kMaxStages = 160;     // homotopy stages tabulated (alpha ~ 1e-24 
 constexpr int kStageSlots = 8;      // alpha, 1/alpha, 1/(1+alpha), alpha^2-2, kappa1,
                                     // alpha^1.5, alpha_next/alpha, 1/(1+alpha_next)
 
+// Guard band of the stopping test (Sec. 5 eq. l1tol). The test runs on the
+// FP64 sum of the column errors that the FP32 passes give, which misses the
+// FP64 truth of ||P1 - a||_1 + ||P'1 - b||_1 by the row marginal's FP32 floor
+// (the row pass's u is exact only to FP32 rounding: 3e-8 to 1.2e-7 measured)
+// and the column sums' own error (up to 3e-8 measured). A solve therefore
+// stops once that estimate is below tol - 2^-22 (2.4e-7), so that the FP64
+// truth of the whole eq. l1tol sum stays below tol.
+constexpr double kStopGuard = 0x1p-22;
+inline double stop_threshold(double tol) { return tol - kStopGuard; }
+
 // Device-resident solver state. Written only by the init kernel, by block 0
 // of the step kernel (after its last grid barrier) and by the host before a
 // launch; read by every kernel.

@@ -105,6 +105,78 @@ bool tc_form_enabled()
     return batch_tc_available();
 }
 
+// The work split of one problem that depends only on its size and the
+// tuning (the BatchProb fields small, rows_per_tile, row_tiles, col_tiles,
+// ldn, cols_per_item, col_items, step_cols, step_items) and its layout.
+struct ProbShape {
+    int small = 0, rows_per_tile = 0, row_tiles = 0, col_tiles = 0, cols_per_item = 0,
+        col_items = 0, step_cols = 0, step_items = 0;
+    bool transposed = false;
+    ProbLayout lay{};
+};
+
+ProbShape prob_shape(const BatchTuning &tn, const accsink_problem &q)
+{
+    ProbShape S;
+    const int64_t nm = (int64_t)q.n * q.m;
+    // problems from kBatchTransposeMin entries are always tiled over K and
+    // K^T, whatever the split, so a problem's layout (and its last bits)
+    // depends only on its size
+    S.small = (nm <= tn.small_max_nm && nm < kBatchTransposeMin) ? 1 : 0;
+    if (S.small) {
+        S.rows_per_tile = q.n;
+        S.row_tiles = 1;
+    } else {
+        // at least one row for each of the CTA's warps, so none idles;
+        // when the problem has rows enough for 512 items of them, four
+        // rows for each (virtual) warp: the row pass gives every segment
+        // of L lanes four rows at a time, and fewer leave loads out of
+        // flight (8-row tiles of a 16384-column problem ran at 65% of
+        // HBM bandwidth; with 32 rows, 16384^2 steps took 6% less time,
+        // while 8192^2 and 4096^2 ones, then short of items for the
+        // resident CTAs, took 13-20% more)
+        const int m4 = (q.m + 3) / 4;
+        int L = 1;
+        while (L < m4 && L < 32) L <<= 1;
+        const int full = 4 * (kBatchThreads / 32) * (32 / L);
+        const int rmin = (q.n / full >= 512) ? full : kBatchThreads / 32;
+        int rpt = (int)std::max<int64_t>(rmin, tn.row_tile_elems / std::max(1, q.m));
+        rpt = std::min(rpt, q.n);
+        S.rows_per_tile = rpt;
+        S.row_tiles = (q.n + rpt - 1) / rpt;
+    }
+    S.col_tiles = (q.m + kBatchColTile - 1) / kBatchColTile;
+    S.transposed = nm >= kBatchTransposeMin;
+    if (S.transposed) {
+        // column items: K^T rows in whole warps (32), about row_tile_elems each
+        int cpi = (int)std::max<int64_t>(1, tn.row_tile_elems / std::max(1, q.n));
+        cpi = std::max(32, cpi / 32 * 32);
+        S.cols_per_item = cpi;
+        S.col_items = (q.m + cpi - 1) / cpi;
+    } else {
+        S.cols_per_item = kBatchColTile;
+        S.col_items = S.col_tiles;
+    }
+    // the step's column loops as items for large tiled problems
+    // (ACCSINK_BATCH_STEP_ITEMS=0 keeps them in one CTA)
+    if (!S.small && q.m >= kBatchStepSplitMin && step_items_enabled()) {
+        S.step_cols = kBatchStepCols;
+        S.step_items = (q.m + kBatchStepCols - 1) / kBatchStepCols;
+    }
+    S.lay = layout(q.n, q.m, S.row_tiles, S.col_tiles, S.transposed, S.step_items);
+    return S;
+}
+
+// Formation tiles of a problem: tensor-core (kBatchTcRows x kBatchTcCols)
+// or CUDA-core (kBatchFormTile square), and scaling tiles.
+int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+bool tc_eligible(bool tc_on, const accsink_problem &q, int64_t R)
+{
+    return tc_on && q.cost_kind == ACCSINK_COST_COSINE && q.d >= kBatchTcMinD &&
+           q.d <= kBatchTcMaxD && R + q.n + q.m < ((int64_t)1 << 31) - kBatchTcRows;
+}
+
 void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
                 const accsink_params *params, BatchPlan &pl)
 {
@@ -128,64 +200,26 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
             const accsink_params &pp = params[k];
             P.method = pp.method; P.stability = pp.stability; P.carry = pp.carry;
             P.max_steps = pp.max_sinkhorn_steps; P.m0 = pp.m0; P.evaluate = pp.evaluate ? 1 : 0;
-            P.eps = pp.eps; P.tol = pp.tol; P.mu0 = pp.mu0;
+            P.eps = pp.eps; P.tol = stop_threshold(pp.tol); P.mu0 = pp.mu0;
         }
         P.ldm = ((int64_t)q.m + 3) / 4 * 4;
-        const int64_t nm = (int64_t)q.n * q.m;
-        // problems from kBatchTransposeMin entries are always tiled over K and
-        // K^T, whatever the split, so a problem's layout (and its last bits)
-        // depends only on its size
-        P.small = (nm <= tn.small_max_nm && nm < kBatchTransposeMin) ? 1 : 0;
-        if (P.small) {
-            P.rows_per_tile = q.n;
-            P.row_tiles = 1;
-        } else {
-            // at least one row for each of the CTA's warps, so none idles;
-            // when the problem has rows enough for 512 items of them, four
-            // rows for each (virtual) warp: the row pass gives every segment
-            // of L lanes four rows at a time, and fewer leave loads out of
-            // flight (8-row tiles of a 16384-column problem ran at 65% of
-            // HBM bandwidth; with 32 rows, 16384^2 steps took 6% less time,
-            // while 8192^2 and 4096^2 ones, then short of items for the
-            // resident CTAs, took 13-20% more)
-            const int m4 = (q.m + 3) / 4;
-            int L = 1;
-            while (L < m4 && L < 32) L <<= 1;
-            const int full = 4 * (kBatchThreads / 32) * (32 / L);
-            const int rmin = (q.n / full >= 512) ? full : kBatchThreads / 32;
-            int rpt = (int)std::max<int64_t>(rmin, tn.row_tile_elems / std::max(1, q.m));
-            rpt = std::min(rpt, q.n);
-            P.rows_per_tile = rpt;
-            P.row_tiles = (q.n + rpt - 1) / rpt;
-        }
-        P.col_tiles = (q.m + kBatchColTile - 1) / kBatchColTile;
-        const bool transposed = nm >= kBatchTransposeMin;
+        const ProbShape S = prob_shape(tn, q);
+        P.small = S.small;
+        P.rows_per_tile = S.rows_per_tile;
+        P.row_tiles = S.row_tiles;
+        P.col_tiles = S.col_tiles;
         P.ldn = ((int64_t)q.n + 3) / 4 * 4;
-        if (transposed) {
-            // column items: K^T rows in whole warps (32), about row_tile_elems each
-            int cpi = (int)std::max<int64_t>(1, tn.row_tile_elems / std::max(1, q.n));
-            cpi = std::max(32, cpi / 32 * 32);
-            P.cols_per_item = cpi;
-            P.col_items = (q.m + cpi - 1) / cpi;
-        } else {
-            P.cols_per_item = kBatchColTile;
-            P.col_items = P.col_tiles;
-        }
+        P.cols_per_item = S.cols_per_item;
+        P.col_items = S.col_items;
         P.cmax_enc = 0ull;             // below every encoded value
         P.cmin_enc = ~0ull;            // above every encoded value
         P.cabs_enc = 0ull;
-        // the step's column loops as items for large tiled problems
-        // (ACCSINK_BATCH_STEP_ITEMS=0 keeps them in one CTA)
-        if (!P.small && q.m >= kBatchStepSplitMin && step_items_enabled()) {
-            P.step_cols = kBatchStepCols;
-            P.step_items = (q.m + kBatchStepCols - 1) / kBatchStepCols;
-        }
-        pl.lay[k] = layout(q.n, q.m, P.row_tiles, P.col_tiles, transposed, P.step_items);
+        P.step_cols = S.step_cols;
+        P.step_items = S.step_items;
+        pl.lay[k] = S.lay;
         pl.data_bytes += pl.lay[k].total();
         outstanding += (size_t)std::max(P.row_tiles, P.col_items);
-        P.tc = (tc_on && q.cost_kind == ACCSINK_COST_COSINE && q.d >= kBatchTcMinD &&
-                q.d <= kBatchTcMaxD && pl.R + q.n + q.m < ((int64_t)1 << 31) - kBatchTcRows)
-                   ? 1 : 0;
+        P.tc = tc_eligible(tc_on, q, pl.R) ? 1 : 0;
         if (P.tc) {
             pl.tcp.push_back(k);
             pl.tcs.push_back(pl.R);
@@ -241,6 +275,47 @@ void to_result(const BatchResult &r, float ms, accsink_result &o)
 }
 
 size_t batch_workspace_bytes(const BatchTuning &tn, int count, const accsink_problem *probs)
+{
+    BatchSizer sz(tn);
+    for (int k = 0; k < count; ++k) sz.add(probs[k]);
+    return sz.bytes();
+}
+
+BatchSizer::BatchSizer(const BatchTuning &tn) : tn_(tn), tc_on_(tc_form_enabled()) {}
+
+void BatchSizer::add(const accsink_problem &q)
+{
+    const ProbShape S = prob_shape(tn_, q);
+    data_ += S.lay.total();
+    outstanding_ += (size_t)std::max(S.row_tiles, S.col_items);
+    if (tc_eligible(tc_on_, q, R_)) {
+        R_ += (int64_t)q.n + q.m;
+        dpad_ = std::max(dpad_, (q.d + kBatchTcK - 1) / kBatchTcK * kBatchTcK);
+        tiles_ += ceil_div(q.n, kBatchTcRows) * ceil_div(q.m, kBatchTcCols);
+        ++ntc_;
+    } else {
+        tiles_ += ceil_div(q.n, kBatchFormTile) * ceil_div(q.m, kBatchFormTile);
+    }
+    if (q.cost_scale == ACCSINK_SCALE_MAX_TO_ONE)
+        tiles_ += ceil_div(q.n, kBatchFormTile) * ceil_div(q.m, kBatchFormTile);
+    ++count_;
+}
+
+size_t BatchSizer::bytes() const
+{
+    size_t data = data_;
+    if (R_ > 0) data += up256(batch_tc_slice_bytes(R_, dpad_)) + up256((size_t)R_ * 4);
+    const unsigned long long cap = pow2_at_least(std::max<unsigned long long>(
+        4096, 2 * (unsigned long long)(outstanding_ + count_)));
+    const size_t head = up256(sizeof(BatchProb) * count_) + up256(sizeof(BatchResult) * count_) +
+                        up256(sizeof(BatchQueue)) + up256(cap * 8) + up256(cap * 8) +
+                        up256(sizeof(BatchTile) * (size_t)tiles_) + up256(8 * (size_t)count_) +
+                        up256(4 * (size_t)ntc_) + up256(8 * (size_t)ntc_);
+    return head + data;
+}
+
+size_t batch_workspace_bytes_planned(const BatchTuning &tn, int count,
+                                     const accsink_problem *probs)
 {
     BatchPlan pl;
     plan_batch(tn, count, probs, nullptr, pl);

@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <functional>
 #include <string>
 
@@ -52,6 +53,28 @@ BatchTuning batch_default_tuning(int num_sms);
 
 // Device workspace bytes batch_run needs for these problems.
 size_t batch_workspace_bytes(const BatchTuning &tn, int count, const accsink_problem *probs);
+// The same number from the full plan (every formation tile listed); for
+// checks of the incremental sizer below.
+size_t batch_workspace_bytes_planned(const BatchTuning &tn, int count,
+                                     const accsink_problem *probs);
+
+// Workspace bytes of a batch that grows one problem at a time, in O(1) per
+// problem (the plan's sizes without its tile lists): the server's admission
+// adds queued requests one by one against its memory budget.
+class BatchSizer {
+public:
+    explicit BatchSizer(const BatchTuning &tn);
+    void add(const accsink_problem &q);
+    size_t bytes() const;
+    int count() const { return count_; }
+
+private:
+    BatchTuning tn_;
+    bool tc_on_;
+    size_t data_ = 0, outstanding_ = 0;
+    int64_t tiles_ = 0, R_ = 0;
+    int dpad_ = 0, ntc_ = 0, count_ = 0;
+};
 
 // Plans, launches and waits for one batch on stream s. Returns an ACCSINK_*
 // code; res[k] receives each problem's record; err the message on failure.

@@ -503,7 +503,7 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     hs.eps_user = prm->eps;
-    hs.tol = prm->tol;
+    hs.tol = stop_threshold(prm->tol);
     hs.method = prm->method;
     hs.stability = prm->stability;
     hs.carry = prm->carry;
@@ -778,7 +778,7 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     DevState hs;
     std::memset(&hs, 0, sizeof(hs));
     hs.eps_user = prm->eps;
-    hs.tol = prm->tol;
+    hs.tol = stop_threshold(prm->tol);
     hs.method = prm->method;
     hs.stability = prm->stability;
     hs.carry = prm->carry;

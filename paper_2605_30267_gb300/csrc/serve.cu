@@ -8,8 +8,9 @@
 // device allocations. A request moves QUEUED -> RUNNING -> DONE (or FAILED)
 // -> released. Admission is FIFO: the worker takes queued requests in order
 // while inputs, outputs and the batch workspace fit in the budget next to the
-// potentials that are still held; a request that cannot fit even alone fails
-// with ACCSINK_ERR_BUDGET.
+// potentials that are still held, and while the group's cost entries stay
+// within its limit; a request that cannot fit even alone fails with
+// ACCSINK_ERR_BUDGET.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -56,6 +57,12 @@ size_t output_bytes(const accsink_problem &p)
     return up256((size_t)p.n * 8) + up256((size_t)p.m * 8);
 }
 
+// Default admission limit of a group, in cost entries. A batch lasts as long
+// as its slowest problem, so a group admitted under a deep queue (everything
+// the budget holds) ends in a long tail with most SMs idle; bounded groups
+// keep each launch short and the device busy under sustained overload.
+constexpr int64_t kDefaultGroupEntries = int64_t(1) << 28;
+
 }  // namespace
 
 struct accsink_server {
@@ -81,6 +88,9 @@ struct accsink_server {
     accsink::BatchResult *early = nullptr;
     int32_t *early_flag = nullptr;
     int early_cap = 0;
+    // admission limit: cost entries (sum of n m) of one admitted group; a
+    // request larger than the limit still runs, alone (0: no limit)
+    int64_t max_group_entries = kDefaultGroupEntries;
     // accounting (under mu)
     size_t resident = 0;          // outputs held for DONE tickets
     size_t peak_in_use = 0;
@@ -109,22 +119,29 @@ void worker_loop(accsink_server *S)
             tuning = S->tuning;
             S->cv_work.wait(lk, [&] { return S->stopping || !S->queue.empty(); });
             if (S->stopping && S->queue.empty()) return;
-            // FIFO admission against the budget
-            std::vector<accsink_problem> trial;
+            // FIFO admission against the budget and the group limit; the
+            // group's batch workspace grows by one request at a time (O(1)
+            // per request, no re-planning of the group)
+            accsink::BatchSizer sizer(tuning);
+            int64_t entries = 0;
             while (!S->queue.empty()) {
                 const uint64_t t = S->queue.front();
                 Request &r = S->reqs[t];
-                trial.push_back(r.prob);
-                const size_t ws_need =
-                    accsink::batch_workspace_bytes(tuning, (int)trial.size(), trial.data());
+                const int64_t nm = (int64_t)r.prob.n * r.prob.m;
+                if (!group.empty() && S->max_group_entries > 0 &&
+                    entries + nm > S->max_group_entries)
+                    break;
+                accsink::BatchSizer next = sizer;
+                next.add(r.prob);
+                const size_t ws_need = next.bytes();
                 const size_t in_b = input_bytes(r.prob), out_b = output_bytes(r.prob);
                 const size_t total = S->resident + in_total + out_total + in_b + out_b + ws_need;
                 if (total > S->budget) {
-                    trial.pop_back();
                     if (group.empty()) {
                         // cannot run even alone next to the held potentials
-                        const size_t alone = in_b + out_b +
-                            accsink::batch_workspace_bytes(tuning, 1, &r.prob);
+                        accsink::BatchSizer one(tuning);
+                        one.add(r.prob);
+                        const size_t alone = in_b + out_b + one.bytes();
                         if (alone > S->budget) {
                             r.state = ACCSINK_REQ_FAILED;
                             r.res.status = ACCSINK_ERR_BUDGET;
@@ -139,6 +156,8 @@ void worker_loop(accsink_server *S)
                     }
                     break;
                 }
+                sizer = next;
+                entries += nm;
                 in_total += in_b;
                 out_total += out_b;
                 group.push_back(t);
@@ -147,9 +166,8 @@ void worker_loop(accsink_server *S)
                 r.t_start = Clock::now();
             }
             if (group.empty()) continue;
-            S->peak_in_use = std::max(S->peak_in_use, S->resident + in_total + out_total +
-                                      accsink::batch_workspace_bytes(tuning, (int)trial.size(),
-                                                                     trial.data()));
+            S->peak_in_use = std::max(S->peak_in_use,
+                                      S->resident + in_total + out_total + sizer.bytes());
         }
         // ---- stage inputs, allocate outputs (stream-ordered)
         const int k = (int)group.size();
@@ -547,6 +565,14 @@ int accsink_server_get_stats(accsink_server *S, accsink_server_stats *out)
     out->peak_bytes = (int64_t)S->peak_in_use;
     out->budget_bytes = (int64_t)S->budget;
     out->busy_ms = S->busy_ms;
+    return ACCSINK_OK;
+}
+
+int accsink_server_set_limits(accsink_server *S, int64_t max_group_entries)
+{
+    if (!S || max_group_entries < 0) return ACCSINK_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->max_group_entries = max_group_entries;
     return ACCSINK_OK;
 }
 

@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import oracle as O
-from solve_checks import check_steps, same_iterate
+from solve_checks import check_steps, check_truth, same_iterate, stop_tol
 from paper_2605_30267_gb300 import binding as B
 from paper_2605_30267_gb300 import workloads as W
 
@@ -80,7 +80,7 @@ def check_against_oracle(p, f, g, res, cost=None):
     okw = dict(method=O.ACC if p.method == B.ACC else O.PLAIN,
                carry_y=p.kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
                stability=p.kw.get("stability", B.STAB_REPORT))
-    ref = O.solve(cost, p.a, p.b, p.eps, p.tol, **okw)
+    ref = O.solve(cost, p.a, p.b, p.eps, stop_tol(p.tol), **okw)
     assert res["status"] == 0, res
     assert ref["status"] == O.CONVERGED
     rs, gs_ = ref["sinkhorn_steps"], res["sinkhorn_steps"]
@@ -90,8 +90,7 @@ def check_against_oracle(p, f, g, res, cost=None):
     dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
     assert dpot <= 1e-3 * p.eps, dpot
     ev = O.evaluate(cost, p.eps, ref["a"], ref["b"], f, g)
-    assert ev["col_l1"] <= p.tol * 1.05, ev
-    assert ev["row_l1"] <= 2e-7, ev
+    check_truth(ev, p.tol)
     evr = O.evaluate(cost, p.eps, ref["a"], ref["b"], ref["f"], ref["g"])
     assert abs(res["transport_cost"] - evr["transport_cost"]) <= \
         1e-5 * abs(evr["transport_cost"]), (res["transport_cost"], evr["transport_cost"])

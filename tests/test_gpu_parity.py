@@ -4,15 +4,17 @@ Tolerances (from the arithmetic of the kernels: exact double-float exponent
 arguments, FP32 lane sums with Kahan compensation, FP64 row finishes):
   * one pass: |delta u| (natural-log units) <= 2e-6, i.e. f within 2e-6 eps;
   * whole solves: potentials within 1e-3 eps max-abs after centring, <C,P>
-    within 1e-5 relative, step counts within 2% (or one step), FP64-truth
-    column L1 <= tol (1 + 0.05) and row L1 at the FP32 floor (<= 2e-7).
+    within 1e-5 relative, step counts within 2% (or one step) of the oracle
+    run to the library's stopping threshold, and the FP64 truth of Sec. 5
+    eq. l1tol at the returned potentials (row plus column L1) below tol, with
+    the row L1 at the FP32 floor (<= 2e-7).
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
-from solve_checks import check_steps, same_iterate
+from solve_checks import check_steps, check_truth, same_iterate, stop_tol
 from paper_2605_30267_gb300 import binding as B
 from paper_2605_30267_gb300 import workloads as W
 
@@ -153,7 +155,7 @@ def check_solve(ctx, C, a, b, eps, tol, method, scale=False, cost=None, **kw):
     okw = dict(method=O.ACC if method == B.ACC else O.PLAIN,
                carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
                stability=kw.get("stability", B.STAB_REPORT))
-    ref = O.solve(cost, a, b, eps, tol, **okw)
+    ref = O.solve(cost, a, b, eps, stop_tol(tol), **okw)
     assert res["status"] == 0, res
     assert ref["status"] == O.CONVERGED
     # steps within 2% (at least one step of slack)
@@ -166,8 +168,7 @@ def check_solve(ctx, C, a, b, eps, tol, method, scale=False, cost=None, **kw):
     assert dpot <= 1e-3 * eps, dpot
     # FP64 truth of the GPU's potentials
     ev = O.evaluate(cost, eps, ref["a"], ref["b"], f, g)
-    assert ev["col_l1"] <= tol * 1.05, ev
-    assert ev["row_l1"] <= 2e-7, ev
+    check_truth(ev, tol)
     evr = O.evaluate(cost, eps, ref["a"], ref["b"], ref["f"], ref["g"])
     assert abs(res["transport_cost"] - evr["transport_cost"]) <= 1e-5 * abs(evr["transport_cost"])
     assert abs(res["dual_objective"] - ref["dual"]) <= 1e-5 * max(1e-3, abs(ref["dual"]))
@@ -224,21 +225,56 @@ def test_column_pass_layouts_agree(ctx, n, m):
     assert np.abs((g1 - g1.mean()) - (g0 - g0.mean())).max() <= 1e-6 * 1e-2
 
 
-def test_history_tracks_oracle(ctx):
-    pr = W.gmm_stored_cost_problem(seed=12, n=200, m=180, eps=1e-2)
-    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC, history=5000)
-    h = ctx.accsink_get_history(5000)
-    ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-2, 1e-6, method=O.ACC, history=5000)
+def stability_tolerances(cond, err):
+    """Per-step tolerances of Theorem 4's four terms (Cond 1 lhs, rhs, Cond 2
+    lhs, rhs), from the arithmetic of the FP32 column sums: every term is
+    built from p = log(c / b), whose GPU value carries an absolute error of
+    ~1e-8 to 1e-7 (the column log-sum-exp's FP32 rounding), so a term made of
+    p^2- or p-weighted sums is off by about that error over the size of p,
+    i.e. over the marginal error of the step (sum_j b_j |p_j| ~ err). Relative
+    tolerance 1e-4 + 2e-7 / min(err_k, err_k+1), on the term itself; the
+    Cond 2 left side (which changes sign) takes |lhs| + |rhs| as its size.
+    Measured on GB300 the differences stay below a quarter of these."""
+    em = np.minimum(err[:-1], err[1:])[:, None]
+    rel = 1e-4 + 2e-7 / em
+    tol = rel * np.abs(cond)
+    tol[:, 2] = rel[:, 0] * (np.abs(cond[:, 2]) + np.abs(cond[:, 3]))
+    return tol
+
+
+@pytest.mark.parametrize("seed,n,m,eps", [(12, 200, 180, 1e-2), (7, 1000, 1000, 1e-3),
+                                          (5, 300, 257, 1e-1), (9, 500, 700, 1e-3)])
+def test_history_tracks_oracle(ctx, seed, n, m, eps):
+    """Per S evaluation: the mu schedule exactly, the marginal error and dual
+    objective, and Theorem 4's four terms and stability bits against the
+    oracle's (App. B)."""
+    pr = W.gmm_stored_cost_problem(seed=seed, n=n, m=m, eps=eps)
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], eps, 1e-6, B.ACC, history=20000)
+    h = ctx.accsink_get_history(20000)
+    ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], eps, stop_tol(1e-6), method=O.ACC,
+                  history=20000)
     rh = ref["history"]
     k = min(len(h["err"]), len(rh["err"]))
-    assert k == res["sinkhorn_steps"]
+    assert len(h["err"]) == res["sinkhorn_steps"]
+    assert abs(res["sinkhorn_steps"] - ref["sinkhorn_steps"]) <= 1
     np.testing.assert_array_equal(h["mu"][:k], rh["mu"][:k])
     # marginal error trajectories agree while well above the FP32 floor
     sel = rh["err"][:k] > 1e-4
     np.testing.assert_allclose(h["err"][:k][sel], rh["err"][:k][sel], rtol=1e-3)
     np.testing.assert_allclose(h["dual"][:k], rh["dual"][:k], rtol=1e-6, atol=1e-9)
-    agree = np.mean(h["stab"][:k] == rh["stab"][:k])
-    assert agree >= 0.95, agree
+    # Theorem 4's terms, step by step (evaluation 0 has no step)
+    gc, oc = h["cond"][1:k], rh["cond"][1:k]
+    tol = stability_tolerances(oc, rh["err"][:k])
+    bad = np.abs(gc - oc) > tol
+    assert not bad.any(), (np.argwhere(bad)[:5], gc[bad][:5], oc[bad][:5])
+    # the bits agree wherever the two sides differ by more than their tolerances
+    for bit, (l, r) in enumerate(((0, 1), (2, 3))):
+        decided = np.abs(oc[:, l] - oc[:, r]) > tol[:, l] + tol[:, r]
+        gb = (h["stab"][1:k] >> bit) & 1
+        ob = (rh["stab"][1:k] >> bit) & 1
+        np.testing.assert_array_equal(gb[decided], ob[decided])
+        np.testing.assert_array_equal(ob, (oc[:, l] > oc[:, r]).astype(ob.dtype))
+        assert decided.sum() >= 0.5 * len(decided)
 
 
 def test_graph_and_host_loop_are_bitwise_identical(ctx):
@@ -351,24 +387,39 @@ def test_full_size_row_and_col_pass_sampled(ctx, big_problem):
     assert np.abs(ell.cpu().numpy()[cols] - rl).max() <= PASS_TOL
 
 
-@pytest.mark.parametrize("method", [B.ACC, B.PLAIN])
-def test_full_size_solve_properties(ctx, big_problem, method):
-    """At 16384 x 16384 (eps 1e-2): converged, FP64-truth marginals on sampled
-    rows and columns, row pass exact at the returned g, transport cost."""
+@pytest.mark.parametrize("method,eps", [(B.ACC, 1e-3), (B.PLAIN, 1e-3), (B.ACC, 1e-2),
+                                        (B.ACC, 1e-1), (B.PLAIN, 1e-1)])
+def test_full_size_solve_meets_tol_in_fp64_truth(ctx, big_problem, method, eps):
+    """The benchmark's workload (16384 x 16384 stored cost, tol 1e-6; Acc at
+    eps = 1e-3 is the timed solve): converged, and the FP64 truth of Sec. 5
+    eq. l1tol at the returned potentials, every row and every column of the
+    2.7e8-entry plan summed by the oracle, is below tol."""
+    pr = big_problem
+    tol = 1e-6
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], eps, tol, method)
+    assert res["status"] == 0 and res["marginal_l1"] < stop_tol(tol), res
+    ev = O.marginal_l1(O.Cost(C=pr["C"]), eps, O.normalise(pr["a"]), O.normalise(pr["b"]), f, g)
+    check_truth(ev, tol)
+
+
+def test_full_size_acc_solve_matches_the_oracle(ctx, big_problem):
+    """16384 x 16384 at eps = 1e-2: the oracle's whole Acc solve (FP64, all
+    host cores) against the GPU's: step counts within 2%, potentials within
+    1e-3 eps after centring, the dual objective within 1e-5."""
     pr = big_problem
     eps, tol = 1e-2, 1e-6
-    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], eps, tol, method)
-    assert res["status"] == 0 and res["marginal_l1"] < tol
+    f, g, res = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], eps, tol, B.ACC)
     cost = O.Cost(C=pr["C"])
-    rows = np.random.default_rng(3).choice(16384, 64, replace=False)
-    cols = np.random.default_rng(4).choice(16384, 64, replace=False)
-    r, cs = O.rows_sample(cost, eps, f, g, rows)
-    np.testing.assert_allclose(r, pr["a"][rows], rtol=2e-6)
-    c = O.cols_sample(cost, eps, f, g, cols)
-    # sampled column errors stay within the total budget's per-column share
-    assert np.abs(c - pr["b"][cols]).sum() <= tol * 64 / 16384 * 50
-    # transport cost from the sampled rows extrapolates consistently
-    assert np.isfinite(res["transport_cost"]) and res["transport_cost"] > 0
+    okw = dict(method=O.ACC, carry_y=True, stability=O.STAB_REPORT)
+    ref = O.solve(cost, pr["a"], pr["b"], eps, stop_tol(tol), **okw)
+    assert res["status"] == 0 and ref["status"] == O.CONVERGED
+    check_steps(cost, pr["a"], pr["b"], eps, tol, okw, ref["sinkhorn_steps"],
+                res["sinkhorn_steps"])
+    ref = same_iterate(cost, pr["a"], pr["b"], eps, okw, ref, res["sinkhorn_steps"])
+    sh = g.mean() - ref["g"].mean()
+    dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
+    assert dpot <= 1e-3 * eps, dpot
+    assert abs(res["dual_objective"] - ref["dual"]) <= 1e-5 * max(1e-3, abs(ref["dual"]))
 
 
 def test_tma_row_pass_alternative_matches_oracle():
@@ -390,14 +441,14 @@ f = torch.empty(n, dtype=torch.float64, device=dev); g = torch.empty(m, dtype=to
 C = torch.from_numpy(pr["C"]).to(dev)
 prob = B.problem_dense(C, torch.from_numpy(pr["a"]).to(dev), torch.from_numpy(pr["b"]).to(dev))
 res = B.result_dict(ctx.accsink_solve(prob, B.default_params(eps=1e-2, tol=1e-6), f, g))
-ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-2, tol=1e-6)
+ref = O.solve(O.Cost(C=pr["C"]), pr["a"], pr["b"], 1e-2, tol=1e-6 - 2.0 ** -22)
 fg, gg = f.cpu().numpy(), g.cpu().numpy()
 sh = gg.mean() - ref["g"].mean()
 d = max(np.abs(gg - sh - ref["g"]).max(), np.abs(fg + sh - ref["f"]).max())
 ev = O.evaluate(O.Cost(C=pr["C"]), 1e-2, ref["a"], ref["b"], fg, gg)
 assert res["status"] == 0, res
 assert d <= 1e-3 * 1e-2, d
-assert ev["col_l1"] <= 1.05e-6 and ev["row_l1"] <= 2e-7, ev
+assert ev["col_l1"] + ev["row_l1"] < 1e-6 and ev["row_l1"] <= 2e-7, ev
 print("ok", res["sinkhorn_steps"], ref["sinkhorn_steps"])
 '''
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))

@@ -3,15 +3,16 @@ colour-transfer and word-alignment costs) against the FP64 oracle, whose cost
 is formed in FP64 from the same FP32 points.
 
 Tolerances as for stored costs: potentials within 1e-3 eps max-abs after
-centring, <C,P> within 1e-5 relative, step counts within 2% (or one step),
-FP64-truth column L1 <= tol (1 + 0.05), row L1 at the FP32 floor.
+centring, <C,P> within 1e-5 relative, step counts within 2% (or one step) of
+the oracle run to the library's stopping threshold, and the FP64 truth of
+eq. l1tol (row plus column L1) below tol with the row L1 at the FP32 floor.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle as O
-from solve_checks import check_steps, same_iterate
+from solve_checks import check_steps, check_truth, same_iterate, stop_tol
 from paper_2605_30267_gb300 import binding as B
 from paper_2605_30267_gb300 import workloads as W
 
@@ -47,7 +48,7 @@ def check_points(ctx, X, Y, kind, a, b, eps, tol=1e-6, method=B.ACC, scale=False
     okw = dict(method=O.ACC if method == B.ACC else O.PLAIN,
                carry_y=kw.get("carry", B.CARRY_Y) == B.CARRY_Y,
                stability=kw.get("stability", B.STAB_REPORT))
-    ref = O.solve(cost, a, b, eps, tol, **okw)
+    ref = O.solve(cost, a, b, eps, stop_tol(tol), **okw)
     assert res["status"] == 0, res
     assert ref["status"] == O.CONVERGED
     rs, gs = ref["sinkhorn_steps"], res["sinkhorn_steps"]
@@ -57,8 +58,7 @@ def check_points(ctx, X, Y, kind, a, b, eps, tol=1e-6, method=B.ACC, scale=False
     dpot = max(np.abs(g - sh - ref["g"]).max(), np.abs(f + sh - ref["f"]).max())
     assert dpot <= 1e-3 * eps, dpot
     ev = O.evaluate(cost, eps, ref["a"], ref["b"], f, g)
-    assert ev["col_l1"] <= tol * 1.05, ev
-    assert ev["row_l1"] <= 2e-7, ev
+    check_truth(ev, tol)
     evr = O.evaluate(cost, eps, ref["a"], ref["b"], ref["f"], ref["g"])
     assert abs(res["transport_cost"] - evr["transport_cost"]) <= \
         1e-5 * abs(evr["transport_cost"]), (res["transport_cost"], evr["transport_cost"])
@@ -301,22 +301,18 @@ def colour_problem():
 
 
 def test_full_size_colour_transfer_solve(ctx, colour_problem):
-    """n = m = 65536 RGB points, eps 1e-3, tol 1e-6 (cost scaled to max 1):
-    converged, and on sampled rows and columns the FP64 oracle's marginals of
-    the returned potentials agree with a and b."""
+    """n = m = 65536 RGB points, eps 1e-3, tol 1e-6 (cost scaled to max 1), the
+    point-cloud workload's size: converged, and the FP64 truth of eq. l1tol at
+    the returned potentials, every row and every column of the 4.3e9-entry
+    plan summed by the oracle, is below tol."""
     pr = colour_problem
     eps, tol = pr["eps"], pr["tol"]
     f, g, res = gpu_solve_points(ctx, pr["X"], pr["Y"], "sqeuclid", pr["a"], pr["b"], eps,
                                  tol, B.ACC, True)
-    assert res["status"] == 0 and res["marginal_l1"] < tol, res
+    assert res["status"] == 0 and res["marginal_l1"] < stop_tol(tol), res
     cost = O.Cost(X=pr["X"], Y=pr["Y"], kind="sqeuclid", scale_to_max=True)
-    n = m = 65536
-    rows = np.random.default_rng(5).choice(n, 32, replace=False)
-    cols = np.random.default_rng(6).choice(m, 32, replace=False)
-    r, _ = O.rows_sample(cost, eps, f, g, rows)
-    np.testing.assert_allclose(r, pr["a"][rows], rtol=2e-6)
-    c = O.cols_sample(cost, eps, f, g, cols)
-    assert np.abs(c - pr["b"][cols]).sum() <= tol * 32 / m * 50
+    ev = O.marginal_l1(cost, eps, pr["a"], pr["b"], f, g)
+    check_truth(ev, tol)
 
 
 # ------------------------------------------------------------ export --
@@ -412,3 +408,20 @@ def test_df32_is_the_default_precision(ctx):
     np.testing.assert_array_equal(g0, g1)
     with pytest.raises(B.AccsinkError):
         gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, 1e-2, 1e-6, B.ACC, True, precision=3)
+
+
+@pytest.mark.parametrize("eps", [1e-1, 1e-2, 1e-3])
+def test_pruned_solves_repeat_bit_for_bit(ctx, eps):
+    """The 333 x 200 squared-Euclidean solves (d = 3: sorted clouds, pruned
+    slots) run 20 times give bit-identical potentials and step counts: the
+    skip decision reads only the lane's own registers and a warp-wide vote
+    that every lane reaches, so nothing in it depends on scheduling."""
+    n, m, d = 333, 200, 3
+    X, Y, a, b = sqeuclid_points(n * 3 + m + d, n, m, d)
+    f0, g0, r0 = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, eps, 1e-6, B.ACC, True)
+    assert r0["status"] == 0, r0
+    for _ in range(19):
+        f1, g1, r1 = gpu_solve_points(ctx, X, Y, "sqeuclid", a, b, eps, 1e-6, B.ACC, True)
+        assert r1["sinkhorn_steps"] == r0["sinkhorn_steps"]
+        np.testing.assert_array_equal(f1, f0)
+        np.testing.assert_array_equal(g1, g0)
