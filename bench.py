@@ -349,9 +349,12 @@ def run_gpu(args):
         if not args.no_batch:
             out["batch_workload"] = measure_batch(ctx, dev, stream, args.batch_count, 3,
                                                   not args.quick, not args.quick)
+            out["batch_workload"]["large_problem"] = measure_batch_large(
+                ctx, stream, prob, args.n, steps[-1], ms_per_step)
         if not args.no_serve:
-            out["serving_workload"] = measure_serving(args.serve_rates, args.serve_window,
-                                                      args.serve_max, 64, 16)
+            out["serving_workload"] = measure_serving(
+                args.serve_rates, args.serve_window, args.serve_max, 64, 16,
+                args.serve_long_rates, args.serve_long_window, args.serve_group_cap)
     ctx.close()
     return out
 
@@ -377,7 +380,8 @@ def run_serve_only(args):
     torch.cuda.set_device(0)
     return {"metric": METRIC,
             "serving_workload": measure_serving(args.serve_rates, args.serve_window,
-                                                args.serve_max, 64, 16)}
+                                                args.serve_max, 64, 16, args.serve_long_rates,
+                                                args.serve_long_window, args.serve_group_cap)}
 
 
 def run_points_only(args):
@@ -522,6 +526,10 @@ def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=Tr
         tms.append(ctx.accsink_batch_last_timing())
     steps = [r.sinkhorn_steps for r in res]
     evals = sum(st * 2 * structs[k].n * structs[k].m for k, st in enumerate(steps))
+    # cost bytes the solve reads: every S evaluation passes over the stored
+    # double-float K (hi + lo, 8 bytes per entry) twice (row pass, column pass
+    # over K or K^T), the final evaluation pass once more
+    kbytes = sum((16 * st + 8) * structs[k].n * structs[k].m for k, st in enumerate(steps))
     med = sorted(tms, key=lambda t: t["total_ms"])[len(tms) // 2]
     out.update({
         "batch_s": round(med["total_ms"] / 1e3, 6),
@@ -533,19 +541,40 @@ def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=Tr
         "cost_entry_evaluations": evals,
         "solve_entries_per_s": round(evals / (med["solve_ms"] / 1e3), 1),
     })
+    peak, peak_kind = measured_peaks()
+    kgbs = kbytes / (med["solve_ms"] / 1e3) / 1e9
+    out["roofline"] = {
+        "bound": "hbm", "kernel": "k_batch_solve", "achieved": round(kgbs, 1), "peak": peak,
+        "unit": "GB/s", "frac": round(kgbs / peak, 4), "traffic": None,
+        "bytes_per_launch": kbytes,
+        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst)",
+        "note": "cost bytes read by the solve phase (K hi + lo, 16 B per entry per S "
+                "evaluation, 8 B for the final pass) over its time; problems with n m <= 65536 "
+                "are solved whole by one CTA and read their 512 KB or less of K mostly from "
+                "L2, so this is a read bandwidth against the HBM peak, not DRAM traffic"}
+    # the method's own contraction x.y (d multiply-adds per entry), against
+    # the slice-pair products the exact formation issues
+    method_macs = sum(s_.n * s_.m * 300 for s_ in structs)
     # the cosine costs are formed on the tensor cores: 21 FP16 slice-pair
     # products per 128 x 64 tile and 16-element contraction step
     dpad = (300 + 31) // 32 * 32
     tiles = sum(-(-s.n // 128) * -(-s.m // 64) for s in structs)
     macs = tiles * 128 * 64 * dpad * 21
     form_tf = 2 * macs / (med["form_ms"] / 1e3) / 1e12
+    method_tf = 2 * method_macs / (med["form_ms"] / 1e3) / 1e12
     out["form_tensor_cores"] = {
         "kernel": "k_batch_form_tc (tcgen05 kind::f16, FP32 accumulators in TMEM)",
         "tiles": tiles, "slice_pair_macs": macs,
         "achieved_tflops": round(form_tf, 1), "peak_tflops": measured_bf16_tflops(),
         "frac": round(form_tf / measured_bf16_tflops(), 4),
+        "method_macs": method_macs,
+        "method_tflops": round(method_tf, 2),
+        "method_frac": round(method_tf / measured_bf16_tflops(), 4),
         "note": "over the whole formation phase (slicing, tiles, statistics); peak: measured "
-                "dense bf16 cuBLAS burst (FP16 runs at the same tensor rate)"}
+                "dense bf16 cuBLAS burst (FP16 runs at the same tensor rate). method_*: the "
+                "cosine costs' own d = 300 multiply-adds per entry; the exact integer-slice "
+                "formation issues 21 slice-pair products for each (the cost of K exact to "
+                "2^-39, which FP32 or 3xTF32 products cannot give)"}
     if one_at_a_time:
         tot = 0.0
         for k in range(count):
@@ -556,17 +585,125 @@ def measure_batch(ctx, dev, stream, count, reps, one_at_a_time=True, autotune=Tr
     return out
 
 
+def measure_batch_large(ctx, stream, prob, n, steps_single, ms_single):
+    """The benchmark's own 16384 x 16384 stored-cost problem through the batched
+    engine (a batch of one): its time per S evaluation against the
+    graph-loop single solve, and the bandwidth of its cost reads (the batch
+    stores K = k C as a double-float pair: 16 bytes per entry per S
+    evaluation, against the single solve's 8)."""
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float64, device=dev)
+    p = B.default_params(eps=EPS, tol=TOL)
+    ctx.accsink_solve_batch([prob], [p], [f], [g], stream=stream)        # warm-up
+    res = ctx.accsink_solve_batch([prob], [p], [f], [g], stream=stream)
+    t = ctx.accsink_batch_last_timing()
+    st = res[0].sinkhorn_steps
+    per = t["solve_ms"] / max(1, st)
+    peak, _ = measured_peaks()
+    gbs = 16 * n * n / (per * 1e-3) / 1e9
+    return {"problem": "the benchmark workload (dense 16384 x 16384, eps=1e-3) as a batch of one",
+            "steps": st, "form_ms": round(t["form_ms"], 3), "solve_ms": round(t["solve_ms"], 3),
+            "ms_per_s_evaluation": round(per, 4),
+            "single_solve_ms_per_s_evaluation": round(ms_single / max(1, steps_single), 4),
+            "cost_read_gbs": round(gbs, 1), "frac_of_hbm_peak": round(gbs / peak, 4)}
+
+
 SERVE_WORKLOAD = ("serving: Poisson arrivals; requests are squared-Euclidean problems, points "
                   "uniform in [0,1]^d, d in {2..64}, n, m log-uniform in [64, 16384], Dirichlet(1) "
                   "marginals, eps log-uniform in [1e-3, 1e-1], tol=1e-6, cost scaled to max 1; "
                   "64 GB admission budget")
 
 
-def measure_serving(rates, window_s, max_requests, pool_size, solo_count):
+def serve_window(probs, params, rate, window_s, group_cap, seed):
+    """The request server under Poisson arrivals at `rate` for `window_s`
+    seconds (a fresh server, 64 GB budget). Requests are submitted as they
+    arrive; what the server completes inside the window counts. Reports the
+    offered and completed counts, the sustained rate (completed / window),
+    the submit-to-done latency of the completed requests, and the backlog at
+    the window's end (queued or running, with the age of the oldest); the
+    server is then closed, which drops the queued requests."""
+    import threading
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+    pool_size = len(probs)
+    arrivals = W.poisson_arrivals(seed, rate, int(rate * window_s * 1.3) + 16)
+    arrivals = arrivals[arrivals < window_s]
+    count = len(arrivals)
+    srv = B.Server(0, 64 << 30)
+    if group_cap is not None:
+        srv.set_limits(group_cap)
+    tickets = [None] * count
+    submitted = [0]
+    lats = []
+    done_t = []
+    stop = threading.Event()
+    try:
+        start = time.perf_counter()
+        end = start + window_s
+
+        def collect():
+            i = 0
+            while i < count:
+                while tickets[i] is None and not stop.is_set():
+                    time.sleep(0.0002)
+                if tickets[i] is None:
+                    return
+                left_ms = int((end - time.perf_counter()) * 1e3)
+                if left_ms <= 0:
+                    return
+                rc, res, lat = srv.wait(tickets[i], left_ms)
+                if rc == B.ERR_TIMEOUT:
+                    return
+                lats.append(lat)
+                done_t.append(time.perf_counter() - start)
+                srv.release(tickets[i])
+                i += 1
+
+        th = threading.Thread(target=collect)
+        th.start()
+        for i in range(count):
+            delay = start + arrivals[i] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            if time.perf_counter() >= end:
+                break
+            k = i % pool_size
+            tickets[i] = srv.submit(probs[k], params[k])
+            submitted[0] = i + 1
+        stop.set()
+        th.join()
+        now = time.perf_counter() - start
+        done = len(lats)
+        st = srv.stats()
+        oldest = (now - arrivals[done]) if done < submitted[0] else 0.0
+        out = {"offered_per_s": rate, "window_s": window_s, "offered": submitted[0],
+               "completed": done, "sustained_per_s": round(done / window_s, 2),
+               "latency_ms": {"p50": round(percentile(lats, 0.5), 3) if lats else None,
+                              "p99": round(percentile(lats, 0.99), 3) if lats else None},
+               "backlog_at_end": {"queued": st["queued"],
+                                  "queued_or_running": submitted[0] - done,
+                                  "oldest_age_s": round(oldest, 3)},
+               "server": {"batches": st["batches"], "peak_gb": round(st["peak_bytes"] / 1e9, 3),
+                          "busy_s": round(st["busy_ms"] / 1e3, 3),
+                          "device_busy_frac": round(st["busy_ms"] / 1e3 / window_s, 3)}}
+        if group_cap is not None:
+            out["group_entry_limit"] = group_cap
+        return out
+    finally:
+        srv.close()
+
+
+def measure_serving(rates, window_s, max_requests, pool_size, solo_count, long_rates=(),
+                    long_window_s=60.0, group_cap=None):
     """The request server at offered Poisson rates: sustained solves/s and the
     submit-to-done latency (p50/p99, queueing included), beside the same
     requests served one at a time (each submitted after the previous one
-    completed)."""
+    completed); then `long_window_s` windows at `long_rates` (serve_window)."""
     import threading
 
     import numpy as np
@@ -578,6 +715,8 @@ def measure_serving(rates, window_s, max_requests, pool_size, solo_count):
                             scale_to_max=True) for r in pool]
     params = [B.default_params(eps=r["eps"], tol=r["tol"]) for r in pool]
     srv = B.Server(0, 64 << 30)
+    if group_cap is not None:
+        srv.set_limits(group_cap)
     out = {"workload": SERVE_WORKLOAD, "pool": pool_size,
            "mean_nm": float(np.mean([r["X"].shape[0] * r["Y"].shape[0] for r in pool]))}
     try:
@@ -645,6 +784,9 @@ def measure_serving(rates, window_s, max_requests, pool_size, solo_count):
                          "busy_s": round(st["busy_ms"] / 1e3, 3)}
     finally:
         srv.close()
+    # long windows (the serving configuration: Poisson arrivals for 60 s)
+    out["windows"] = [serve_window(probs, params, r, long_window_s, group_cap, SEED + 7 * int(r))
+                      for r in long_rates]
     return out
 
 
@@ -791,6 +933,13 @@ def main():
                     help="seconds of arrivals per offered rate")
     ap.add_argument("--serve-max", type=int, default=400,
                     help="cap on requests per offered rate")
+    ap.add_argument("--serve-long-rates", type=float, nargs="*", default=[200, 2000],
+                    help="offered rates of the long serving windows")
+    ap.add_argument("--serve-long-window", type=float, default=60.0,
+                    help="seconds of Poisson arrivals per long window")
+    ap.add_argument("--serve-group-cap", type=int, default=None,
+                    help="server admission limit in cost entries per group (default: the "
+                         "library's)")
     args = ap.parse_args()
     if args.impl == "reference":
         out = run_reference(args)

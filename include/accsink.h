@@ -366,10 +366,10 @@ int accsink_server_get_stats(accsink_server *srv, accsink_server_stats *out);
 /* Work split of the server's batches (NULL: defaults). */
 int accsink_server_set_config(accsink_server *srv, const accsink_batch_config *cfg);
 /* Admission limit of one group: the sum of n m over its requests stays at or
- * below max_group_entries (default 2^28), except that a larger request runs
- * alone; 0 removes the limit. A batch lasts as long as its slowest problem,
- * so under a deep queue smaller groups keep the device busier; the limit
- * trades that against the per-launch overhead of many small groups.
+ * below max_group_entries, except that a larger request runs alone; 0 (the
+ * default) means no limit beyond the memory budget. Requests that arrive
+ * while a group runs wait for its slowest problem; a limit shortens that
+ * wait at the price of throughput (large groups keep every SM busy).
  * ACCSINK_ERR_INVALID_ARG for a negative limit. */
 int accsink_server_set_limits(accsink_server *srv, int64_t max_group_entries);
 

@@ -216,3 +216,30 @@ def test_requests_finish_with_their_own_problem():
         assert before_big >= 1, before_big
     finally:
         srv.close()
+
+
+def test_group_limit_runs_requests_alone_with_the_same_results():
+    """With a group limit of one cost entry every request runs as a batch of
+    its own; the potentials are those of the one joint batch, bit for bit
+    (a problem's arithmetic does not depend on the group it runs in)."""
+    reqs = mix()
+    srv = B.Server(0, 4 << 30)
+    try:
+        with pytest.raises(B.AccsinkError):
+            srv.set_limits(-1)
+        srv.set_limits(1)
+        tickets = [submit(srv, r) for r in reqs]
+        out = []
+        for t in tickets:
+            rc, res, lat = srv.wait(t, 120000)
+            assert rc == B.OK and res.status == 0, (rc, res.status)
+            out.append(srv.copy_potentials(t))
+            srv.release(t)
+        st = srv.stats()
+        assert st["batches"] == len(reqs) and st["solved"] == len(reqs)
+        fref, gref, _ = batch_reference(reqs)
+        for k, (f, g) in enumerate(out):
+            np.testing.assert_array_equal(f, fref[k])
+            np.testing.assert_array_equal(g, gref[k])
+    finally:
+        srv.close()
