@@ -374,6 +374,30 @@ def run_batch_only(args):
     return {"metric": METRIC, "batch_workload": out}
 
 
+def run_batch_large_only(args):
+    """Only the stored-cost workload (size --n) as a batch of one (profiling
+    the batched solver on a large problem)."""
+    import torch
+
+    from paper_2605_30267_gb300 import binding as B
+    from paper_2605_30267_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    pr = W.gmm_stored_cost_problem(seed=SEED, n=args.n, m=args.n, eps=EPS, tol=TOL)
+    C = torch.from_numpy(pr["C"]).to(dev)
+    a = torch.from_numpy(pr["a"]).to(dev)
+    b = torch.from_numpy(pr["b"]).to(dev)
+    ctx = B.Context(0)
+    stream = torch.cuda.Stream(dev)
+    prob = B.problem_dense(C, a, b)
+    f = torch.empty(args.n, dtype=torch.float64, device=dev)
+    g = torch.empty(args.n, dtype=torch.float64, device=dev)
+    r = ctx.accsink_solve(prob, B.default_params(eps=EPS, tol=TOL), f, g, stream=stream)
+    out = measure_batch_large(ctx, stream, prob, args.n, r.sinkhorn_steps, r.gpu_ms)
+    ctx.close()
+    return {"metric": METRIC, "batch_large_problem": out}
+
+
 def run_serve_only(args):
     """Only the serving workload."""
     import torch
@@ -605,7 +629,7 @@ def measure_batch_large(ctx, stream, prob, n, steps_single, ms_single):
     per = t["solve_ms"] / max(1, st)
     peak, _ = measured_peaks()
     gbs = 16 * n * n / (per * 1e-3) / 1e9
-    return {"problem": "the benchmark workload (dense 16384 x 16384, eps=1e-3) as a batch of one",
+    return {"problem": f"the stored-cost workload (dense {n} x {n}, eps=1e-3) as a batch of one",
             "steps": st, "form_ms": round(t["form_ms"], 3), "solve_ms": round(t["solve_ms"], 3),
             "ms_per_s_evaluation": round(per, 4),
             "single_solve_ms_per_s_evaluation": round(ms_single / max(1, steps_single), 4),
@@ -925,6 +949,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched workload")
     ap.add_argument("--batch-only", action="store_true",
                     help="run only the batched workload (profiling)")
+    ap.add_argument("--batch-large-only", action="store_true",
+                    help="run only the stored-cost workload of size --n as a batch of one")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving workload")
     ap.add_argument("--serve-only", action="store_true", help="run only the serving workload")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[25, 50, 100, 200, 2000],
@@ -947,6 +973,8 @@ def main():
         out = run_points_only(args)
     elif args.batch_only:
         out = run_batch_only(args)
+    elif args.batch_large_only:
+        out = run_batch_large_only(args)
     elif args.serve_only:
         out = run_serve_only(args)
     else:
