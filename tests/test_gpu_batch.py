@@ -319,3 +319,32 @@ def test_split_step_equals_one_cta_step(ctx):
         np.testing.assert_array_equal(f1[k], f2[k])
         np.testing.assert_array_equal(g1[k], g2[k])
         assert abs(r1[k]["stability_failures"] - r2[k]["stability_failures"]) <= 1
+
+
+def test_full_word_alignment_batch_meets_tol_in_fp64_truth(ctx):
+    """The batch the benchmark times (512 cosine problems, unit-norm Gaussian
+    points in R^300, n, m log-uniform in [16, 2048], eps in [0.005, 0.05]) in
+    one launch with the autotuner's usual split: every problem converges and
+    the FP64 truth of Sec. 5 eq. l1tol at its potentials (every row and column
+    of its plan, the cost formed in FP64 from the points) is below tol."""
+    batch = W.word_alignment_batch(seed=0, count=512)
+    probs = []
+    for pr in batch:
+        p = Prob.__new__(Prob)
+        p.kind, p.eps, p.tol, p.method, p.scale, p.kw = "cosine", pr["eps"], 1e-6, B.ACC, False, {}
+        p.X, p.Y, p.a, p.b = pr["X"], pr["Y"], pr["a"], pr["b"]
+        p.n, p.m = p.X.shape[0], p.Y.shape[0]
+        probs.append(p)
+    ctx.accsink_batch_set_config(row_tile_elems=16384)
+    try:
+        fs, gs, rs = run_batch(ctx, probs)
+    finally:
+        ctx.accsink_batch_set_config()
+    worst = 0.0
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        assert r["status"] == 0, r
+        cost = O.Cost(X=p.X, Y=p.Y, kind="cosine")
+        ev = O.marginal_l1(cost, p.eps, O.normalise(p.a), O.normalise(p.b), f, g)
+        check_truth(ev, p.tol)
+        worst = max(worst, ev["row_l1"] + ev["col_l1"])
+    assert worst < 1e-6
