@@ -98,7 +98,8 @@ struct Work {
     // partials
     float2 *colpart;          // splits x m : (R, S) per column per row split
     double *rowpart;          // row-grid x 2 : (sum a_i u_i, sum cost) per CTA
-    double *steppart;         // step-grid x 3 x kPartStride
+    double *steppart;         // kPartStride doubles per block of the O(n + m) kernels
+                              // (block-major; the step kernel stores them slot-major)
     double *statpart;         // cost-stats grid x 4
     // per-stage constants of Algorithm 1/2 (kStageSlots doubles per stage)
     const double *stage_table;

@@ -347,6 +347,9 @@ enum {
     R_NSLOTS
 };
 static_assert(R_NSLOTS <= kPartStride, "step-kernel record too long");
+// records a thread loads at once in the step's reductions (152 blocks of 64
+// threads: three each)
+constexpr int kRecPerThread = 4;
 
 __device__ __forceinline__ float lo_f(double v) { return __double2float_rd(v); }
 __device__ __forceinline__ float hi_f(double v) { return __double2float_ru(v); }
@@ -392,7 +395,10 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     const int tid = blockIdx.x * kVecNT + threadIdx.x;
     const int nthr = gridDim.x * kVecNT;
     const uint32_t nb = gridDim.x;
-    double *rec = w.steppart + (int64_t)blockIdx.x * kPartStride;
+    // this block's record, slot k at rec[k * nb]: the records are stored
+    // slot-major (slot k of every block contiguous), so the reads of all
+    // records by every block are coalesced
+    double *rec = w.steppart + blockIdx.x;
 
     const int method = st->method, first = st->first, stab = st->stability;
     const int mode = st->mode, splits = st->col_splits;
@@ -421,66 +427,86 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     if (tid < n) { a0 = w.a[tid]; u0 = w.u[tid]; }
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int col_mode = st->col_mode;
-    for (int j = tid; j < m; j += nthr) {
-        double ell;
-        if (col_mode == 1) {
-            ell = w.ell[j];
-        } else {
-            float R = w.colpart[j].x;
-            for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
-            double S = 0.0;
-            for (int q = 0; q < splits; ++q) {
-                const float2 pr = w.colpart[(int64_t)q * m + j];
-                S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
-            }
-            ell = log(S) + ((double)R - shift_f) * inv_eps;
-        }
-        const double xj = w.x[j];
-        const double bj = w.b[j];
-        const double wj = w.w[j];
-        const double del = xj + ell - w.logb[j];
-        const double raw = xj - del;
-        // p = log(c/b) is formed in FP64; e^p - 1, D(p)/b = (e^p - 1)/p and
-        // e^p - 1 - p are then needed to ~1e-7 relative, which FP32 gives
-        // (series for the last one at small p, where the difference cancels).
-        double xi, D1, klt;
-        const float dl = (float)del;
-        if (fabsf(dl) <= 80.0f) {
-            const float e = expm1f(dl);
-            float km;   // e^p - 1 - p
-            if (fabsf(dl) < 0.0625f) {
-                km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
-                                                     1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+    // A thread's columns two at a time: both columns' inputs are loaded
+    // before either is used (the stores in between would otherwise keep the
+    // compiler from issuing the second column's loads early); the sums take
+    // the columns in the same order as one at a time.
+    for (int j0 = tid; j0 < m; j0 += 2 * nthr) {
+        double ell[2], xj[2], bj[2], wj[2], lb[2], p0[2], xp[2], Dp[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = j0 + u * nthr;
+            if (j >= m) continue;
+            if (col_mode == 1) {
+                ell[u] = w.ell[j];
             } else {
-                km = e - dl;
+                float R = w.colpart[j].x;
+                for (int q = 1; q < splits; ++q) R = fmaxf(R, w.colpart[(int64_t)q * m + j].x);
+                double S = 0.0;
+                for (int q = 0; q < splits; ++q) {
+                    const float2 pr = w.colpart[(int64_t)q * m + j];
+                    S += (double)pr.y * (double)exp2_scaled(pr.x - R, kh, kl);
+                }
+                ell[u] = log(S) + ((double)R - shift_f) * inv_eps;
             }
-            const float dr = (dl != 0.0f) ? e / dl : 1.0f;
-            xi = bj * (double)e;
-            D1 = bj * (double)dr;
-            klt = bj * (double)km;
-        } else {
-            const double e = expm1(del);
-            xi = bj * e;
-            D1 = xi / del;
-            klt = bj * (e - del);
+            xj[u] = w.x[j];
+            bj[u] = w.b[j];
+            wj[u] = w.w[j];
+            lb[u] = w.logb[j];
+            if (check) {
+                p0[u] = w.p_prev[j];
+                xp[u] = w.x_prev[j];
+                Dp[u] = w.D_prev[j];
+            }
         }
-        v[0] += fabs(xi);
-        v[1] += raw;
-        v[2] += klt;
-        v[3] += bj * xj;
-        if (check) {
-            const double p0 = w.p_prev[j];
-            const double v0 = wj * inv_alpha - w.x_prev[j];
-            v[4] += p0 * p0 * D1;
-            v[5] += v0 * v0 * (D1 - w.D_prev[j]);
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = j0 + u * nthr;
+            if (j >= m) continue;
+            const double del = xj[u] + ell[u] - lb[u];
+            const double raw = xj[u] - del;
+            // p = log(c/b) is formed in FP64; e^p - 1, D(p)/b = (e^p - 1)/p
+            // and e^p - 1 - p are then needed to ~1e-7 relative, which FP32
+            // gives (series for the last one at small p, where the
+            // difference cancels).
+            double xi, D1, klt;
+            const float dl = (float)del;
+            if (fabsf(dl) <= 80.0f) {
+                const float e = expm1f(dl);
+                float km;   // e^p - 1 - p
+                if (fabsf(dl) < 0.0625f) {
+                    km = dl * dl * fmaf(dl, fmaf(dl, fmaf(dl, fmaf(dl, 1.0f / 720.0f, 1.0f / 120.0f),
+                                                         1.0f / 24.0f), 1.0f / 6.0f), 0.5f);
+                } else {
+                    km = e - dl;
+                }
+                const float dr = (dl != 0.0f) ? e / dl : 1.0f;
+                xi = bj[u] * (double)e;
+                D1 = bj[u] * (double)dr;
+                klt = bj[u] * (double)km;
+            } else {
+                const double e = expm1(del);
+                xi = bj[u] * e;
+                D1 = xi / del;
+                klt = bj[u] * (e - del);
+            }
+            v[0] += fabs(xi);
+            v[1] += raw;
+            v[2] += klt;
+            v[3] += bj[u] * xj[u];
+            if (check) {
+                const double v0 = wj[u] * inv_alpha - xp[u];
+                v[4] += p0[u] * p0[u] * D1;
+                v[5] += v0 * v0 * (D1 - Dp[u]);
+            }
+            blo[0] = fminf(blo[0], lo_f(raw));   bhi[0] = fmaxf(bhi[0], hi_f(raw));
+            blo[1] = fminf(blo[1], lo_f(xj[u])); bhi[1] = fmaxf(bhi[1], hi_f(xj[u]));
+            blo[2] = fminf(blo[2], lo_f(wj[u])); bhi[2] = fmaxf(bhi[2], hi_f(wj[u]));
+            w.raw[j] = raw;
+            w.D1[j] = D1;
+            w.del[j] = del;
+            if (c_out) c_out[j] = bj[u] * exp(del);
         }
-        blo[0] = fminf(blo[0], lo_f(raw)); bhi[0] = fmaxf(bhi[0], hi_f(raw));
-        blo[1] = fminf(blo[1], lo_f(xj));  bhi[1] = fmaxf(bhi[1], hi_f(xj));
-        blo[2] = fminf(blo[2], lo_f(wj));  bhi[2] = fmaxf(bhi[2], hi_f(wj));
-        w.raw[j] = raw;
-        w.D1[j] = D1;
-        w.del[j] = del;
-        if (c_out) c_out[j] = bj * exp(del);
     }
     // <a, u> of the dual (Sec. 5), from the row pass's u in a fixed order
     v[6] = a0 * u0;
@@ -489,11 +515,11 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         __shared__ double shs[7];
         block_sum_store<7>(v, shs);
         block_minmax_f(blo, bhi);
-        if (threadIdx.x < 7) rec[R_ERR + threadIdx.x] = shs[threadIdx.x];
+        if (threadIdx.x < 7) rec[(R_ERR + threadIdx.x) * nb] = shs[threadIdx.x];
         if (threadIdx.x == 0) {
-            rec[R_RAWLO] = blo[0]; rec[R_RAWHI] = bhi[0];
-            rec[R_XLO] = blo[1];   rec[R_XHI] = bhi[1];
-            rec[R_WLO] = blo[2];   rec[R_WHI] = bhi[2];
+            rec[R_RAWLO * nb] = blo[0]; rec[R_RAWHI * nb] = bhi[0];
+            rec[R_XLO * nb] = blo[1];   rec[R_XHI * nb] = bhi[1];
+            rec[R_WLO * nb] = blo[2];   rec[R_WHI * nb] = bhi[2];
         }
     }
     if (!grid_barrier(st, nb, kBarrierLimitNs)) { bail(); return; }
@@ -501,20 +527,37 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     // ---- P2
     double t[R_WHI + 1];
     {
-        // one read of every block's record: the P1 sums and bounds
+        // one read of every block's record: the P1 sums and bounds. A
+        // thread's records are all loaded before any is added (in the same
+        // order as one at a time), so their L2 round trips overlap: the
+        // records were written by blocks on every SM, half of them on the
+        // other die.
         double t6[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         const int ops6[7] = {0, 0, 0, 0, 0, 0, 0};
         float blo2[3] = {INFINITY, INFINITY, INFINITY}, bhi2[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
-            const double *r = w.steppart + (int64_t)b * kPartStride;
+        for (int b0 = threadIdx.x; b0 < (int)nb; b0 += kRecPerThread * kVecNT) {
+            double rv[kRecPerThread][R_WHI + 1];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) t6[k] += __ldcg(&r[R_ERR + k]);
-            blo2[0] = fminf(blo2[0], (float)__ldcg(&r[R_RAWLO]));
-            bhi2[0] = fmaxf(bhi2[0], (float)__ldcg(&r[R_RAWHI]));
-            blo2[1] = fminf(blo2[1], (float)__ldcg(&r[R_XLO]));
-            bhi2[1] = fmaxf(bhi2[1], (float)__ldcg(&r[R_XHI]));
-            blo2[2] = fminf(blo2[2], (float)__ldcg(&r[R_WLO]));
-            bhi2[2] = fmaxf(bhi2[2], (float)__ldcg(&r[R_WHI]));
+            for (int q = 0; q < kRecPerThread; ++q) {
+                const int b = b0 + q * kVecNT;
+                if (b < (int)nb) {
+#pragma unroll
+                    for (int k = 0; k <= R_WHI; ++k) rv[q][k] = __ldcg(&w.steppart[k * nb + b]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRecPerThread; ++q) {
+                if (b0 + q * kVecNT < (int)nb) {
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) t6[k] += rv[q][R_ERR + k];
+                    blo2[0] = fminf(blo2[0], (float)rv[q][R_RAWLO]);
+                    bhi2[0] = fmaxf(bhi2[0], (float)rv[q][R_RAWHI]);
+                    blo2[1] = fminf(blo2[1], (float)rv[q][R_XLO]);
+                    bhi2[1] = fmaxf(bhi2[1], (float)rv[q][R_XHI]);
+                    blo2[2] = fminf(blo2[2], (float)rv[q][R_WLO]);
+                    bhi2[2] = fmaxf(bhi2[2], (float)rv[q][R_WHI]);
+                }
+            }
         }
         block_allreduce<7>(t6, ops6);
         block_minmax_f(blo2, bhi2);
@@ -556,9 +599,9 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
         block_sum_store<1>(v2, shv);
         block_minmax_f(wlo, whi);
         if (threadIdx.x == 0) {
-            rec[R_C2R] = shv[0];
-            rec[R_W1LO] = wlo[0];
-            rec[R_W1HI] = whi[0];
+            rec[R_C2R * nb] = shv[0];
+            rec[R_W1LO * nb] = wlo[0];
+            rec[R_W1HI * nb] = whi[0];
         }
     }
     if (!grid_barrier(st, 2 * nb, kBarrierLimitNs)) { bail(); return; }
@@ -566,15 +609,30 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     // ---- P3
     double t2[3];
     {
-        // one read of every block's record: the P2 sum and bounds
+        // one read of every block's record: the P2 sum and bounds (loaded
+        // before use, as in P2)
         double c2[1] = {0.0};
         const int op1[1] = {0};
         float wl[3] = {INFINITY, INFINITY, INFINITY}, wh[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int b = threadIdx.x; b < (int)nb; b += kVecNT) {
-            const double *r = w.steppart + (int64_t)b * kPartStride;
-            c2[0] += __ldcg(&r[R_C2R]);
-            wl[0] = fminf(wl[0], (float)__ldcg(&r[R_W1LO]));
-            wh[0] = fmaxf(wh[0], (float)__ldcg(&r[R_W1HI]));
+        for (int b0 = threadIdx.x; b0 < (int)nb; b0 += kRecPerThread * kVecNT) {
+            double rv[kRecPerThread][3];
+#pragma unroll
+            for (int q = 0; q < kRecPerThread; ++q) {
+                const int b = b0 + q * kVecNT;
+                if (b < (int)nb) {
+                    rv[q][0] = __ldcg(&w.steppart[R_C2R * nb + b]);
+                    rv[q][1] = __ldcg(&w.steppart[R_W1LO * nb + b]);
+                    rv[q][2] = __ldcg(&w.steppart[R_W1HI * nb + b]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRecPerThread; ++q) {
+                if (b0 + q * kVecNT < (int)nb) {
+                    c2[0] += rv[q][0];
+                    wl[0] = fminf(wl[0], (float)rv[q][1]);
+                    wh[0] = fmaxf(wh[0], (float)rv[q][2]);
+                }
+            }
         }
         block_allreduce<1>(c2, op1);
         block_minmax_f(wl, wh);
@@ -634,23 +692,39 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
                                         eps_c * st->log_m);
     if (!stop) {
         const double k2 = st->k2;
-        for (int j = tid; j < m; j += nthr) {
-            const double s = w.raw[j] - rbar;
-            const double xj = w.x[j];
-            double xn;
-            if (is_acc) {
-                double w1 = wupd ? (gate ? alpha * xj : w.w1[j]) : w.w[j];
-                w1 *= ratio;
-                xn = (w1 + s) * inv_1pa_new;
-                w.w[j] = w1;
-            } else {
-                xn = s;
+        // two columns at a time, inputs loaded first (as in P1)
+        for (int j0 = tid; j0 < m; j0 += 2 * nthr) {
+            double rw[2], xj[2], wv[2], dl[2], d1[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = j0 + u * nthr;
+                if (j >= m) continue;
+                rw[u] = w.raw[j];
+                xj[u] = w.x[j];
+                wv[u] = (is_acc && !(wupd && gate)) ? (wupd ? w.w1[j] : w.w[j]) : 0.0;
+                dl[u] = w.del[j];
+                d1[u] = w.D1[j];
             }
-            w.x_prev[j] = xj;
-            w.x[j] = xn;
-            w.p_prev[j] = w.del[j];
-            w.D_prev[j] = w.D1[j];
-            write_G(w, j, eps_c * xn + shift_g, kh, k2);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int j = j0 + u * nthr;
+                if (j >= m) continue;
+                const double s = rw[u] - rbar;
+                double xn;
+                if (is_acc) {
+                    double w1 = (wupd && gate) ? alpha * xj[u] : wv[u];
+                    w1 *= ratio;
+                    xn = (w1 + s) * inv_1pa_new;
+                    w.w[j] = w1;
+                } else {
+                    xn = s;
+                }
+                w.x_prev[j] = xj[u];
+                w.x[j] = xn;
+                w.p_prev[j] = dl[u];
+                w.D_prev[j] = d1[u];
+                write_G(w, j, eps_c * xn + shift_g, kh, k2);
+            }
         }
     } else if (is_acc) {
         // stopped at x: keep the momentum after this step's update (gate and
