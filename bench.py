@@ -233,12 +233,12 @@ def run_gpu(args):
         evs[k][1].record(stream)
         steps.append(res.sinkhorn_steps)
         # set-up (state, stage table, cost statistics, init, transpose), the
-        # loop's three kernels per S evaluation, launched two evaluations per
+        # loop's three kernels per S evaluation, launched four evaluations per
         # trip of the graph's WHILE node (eight per host round trip in the
         # host loop; the kernels after the stopping step return at once), the
         # final cost pass and two output scalings
         k = res.sinkhorn_steps
-        per = 8 if args.host_loop else 2
+        per = 8 if args.host_loop else 4
         launches += 5 + 3 * per * ((k + per - 1) // per) + 1 + 2
     ev1.record(stream)
     torch.cuda.synchronize()

@@ -422,9 +422,10 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
 
     // ---- P1
     double v[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};  // err, raw, kl, <b,x>, c1, c2l, <a,u>
-    // the first row term of <a, u>, loaded with the column loads
-    double a0 = 0.0, u0 = 0.0;
+    // the first two row terms of <a, u>, loaded with the column loads
+    double a0 = 0.0, u0 = 0.0, a1 = 0.0, u1 = 0.0;
     if (tid < n) { a0 = w.a[tid]; u0 = w.u[tid]; }
+    if (tid + nthr < n) { a1 = w.a[tid + nthr]; u1 = w.u[tid + nthr]; }
     float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
     const int col_mode = st->col_mode;
     // A thread's columns two at a time: both columns' inputs are loaded
@@ -510,7 +511,8 @@ __global__ void __launch_bounds__(kVecNT) k_step(Work w, int n, int m,
     }
     // <a, u> of the dual (Sec. 5), from the row pass's u in a fixed order
     v[6] = a0 * u0;
-    for (int i = tid + nthr; i < n; i += nthr) v[6] += w.a[i] * w.u[i];
+    if (tid + nthr < n) v[6] += a1 * u1;
+    for (int i = tid + 2 * nthr; i < n; i += nthr) v[6] += w.a[i] * w.u[i];
     {
         __shared__ double shs[7];
         block_sum_store<7>(v, shs);
