@@ -264,7 +264,9 @@ def run_gpu(args):
         col_gbs = col_bytes / (col_ms * 1e-3) / 1e9
         dominant = ("row_pass", row_ms, row_bytes, row_gbs) if row_ms >= col_ms else \
             ("col_pass", col_ms, col_bytes, col_gbs)
-        traffic = profile_traffic("row_warp.cu", f"ncu_{dominant[0]}_gmm16384.txt")
+        # the committed DRAM counters are for the 16384^2 workload only
+        traffic = (profile_traffic("row_warp.cu", f"ncu_{dominant[0]}_gmm16384.txt")
+                   if args.n == N else None)
 
         # ---- Acc vs plain at each eps (one solve each, after the timed region)
         # acc: the default hand-over between homotopy stages (y = w / alpha
