@@ -19,6 +19,11 @@
 // O(10) for every term that matters, so each term's exponent is accurate to
 // ~1e-7. Sums use short FP32 chunks folded into Kahan-compensated partials;
 // cross-thread merges and every per-row / per-column finish are FP64.
+// A product whose rounded value enters an error-free transformation (its
+// error recovered by an FMA, a TwoSum or a Kahan update) is written
+// __fmul_rn, which the compiler never fuses into a neighbouring add: a fused
+// multiply-add there would silently break the exactness (the register
+// allocation of a build decides where nvcc contracts a plain a * b + c).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -145,6 +150,9 @@ struct PointView {
     int32_t nr, nc, d, kind;
     int32_t prune;   // 1: points sorted along a space-filling curve; far slots skipped
     int32_t fp32;    // 1: x.Q in plain FP32 (no low parts)
+    // pruned passes: per group of four rows, the slot of the column nearest to
+    // the group's first row (-1: none); may be NULL
+    const int32_t *hint;
 };
 
 struct CostView {
@@ -237,9 +245,9 @@ __device__ __forceinline__ void slot_accumulate(Lse2 &acc, Lse2 &cacc, const flo
     const float m4 = fmaxf(fmaxf(h[0], h[1]), fmaxf(h[2], h[3]));
     if (m4 > acc.R) {
         const float f = ex2_approx(acc.R - m4);
-        acc.S *= f;
-        acc.K *= f;
-        if (WC) { cacc.S *= f; cacc.K *= f; }
+        acc.S = __fmul_rn(acc.S, f);
+        acc.K = __fmul_rn(acc.K, f);
+        if (WC) { cacc.S = __fmul_rn(cacc.S, f); cacc.K = __fmul_rn(cacc.K, f); }
         acc.R = m4;
     }
     float s = 0.0f, cs = 0.0f;
@@ -369,6 +377,9 @@ struct PointSort {
     double *a;
 };
 size_t points_sort_temp_bytes(int count);
+// Slot hints of the pruned passes over rows of P against columns of Q (d <= 4).
+cudaError_t launch_points_hint(const float *P, int nr, const float *Q, int nc, int d, int kind,
+                               int32_t *hint, int grid, cudaStream_t s);
 cudaError_t launch_points_sort(const float *P, const double *a, int n, int d, const PointSort &ps,
                                cudaStream_t s);
 // dst[perm[i]] = scale * src[i]

@@ -141,7 +141,7 @@ __device__ __forceinline__ void seg_merge(const Lse2 &a, int L, float &Rw, float
     Rw = a.R;
     for (int o = L >> 1; o > 0; o >>= 1) Rw = fmaxf(Rw, __shfl_xor_sync(0xffffffffu, Rw, o));
     const float sc = (a.R == -INFINITY) ? 0.0f : ex2_approx(a.R - Rw);
-    two_sum_f(a.S * sc, -a.K * sc, hi, lo);
+    two_sum_f(__fmul_rn(a.S, sc), -__fmul_rn(a.K, sc), hi, lo);
     for (int o = L >> 1; o > 0; o >>= 1) {
         const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
         const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -158,7 +158,7 @@ __device__ __forceinline__ void seg_merge_same_r(const Lse2 &a, float Ra, float 
                                                  float &hi, float &lo)
 {
     const float sc = (Ra == -INFINITY) ? 0.0f : ex2_approx(Ra - Rw);
-    two_sum_f(a.S * sc, -a.K * sc, hi, lo);
+    two_sum_f(__fmul_rn(a.S, sc), -__fmul_rn(a.K, sc), hi, lo);
     for (int o = L >> 1; o > 0; o >>= 1) {
         const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
         const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
@@ -1173,7 +1173,7 @@ __device__ __forceinline__ void df_min(float &mh, float &ml, float h, float l)
 // FMA, renormalised (~2^-47 relative).
 __device__ __forceinline__ void df_scale(float kh, float kl, float h, float l, float &oh, float &ol)
 {
-    const float p = kh * h;
+    const float p = __fmul_rn(kh, h);   // never fused: pe is its error
     const float pe = fmaf(kh, l, fmaf(kl, h, fmaf(kh, h, -p)));
     two_sum_f(p, pe, oh, ol);
 }
@@ -1259,7 +1259,7 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                         for (int b = 0; b < 4; ++b) {
                             float dh, de;
                             two_sum_f(xa[a], -yb[b], dh, de);       // exact difference
-                            const float p = dh * dh;
+                            const float p = __fmul_rn(dh, dh);
                             const float pe = fmaf(dh, dh, -p) + 2.0f * dh * de;  // + de^2 (negligible)
                             float t, te;
                             two_sum_f(sacc[a][b], p, t, te);
@@ -1271,7 +1271,7 @@ __global__ void __launch_bounds__(256) k_batch_form(BatchProb *Pall, const Batch
                     for (int a = 0; a < 4; ++a)
 #pragma unroll
                         for (int b = 0; b < 4; ++b) {
-                            const float p = xa[a] * yb[b];
+                            const float p = __fmul_rn(xa[a], yb[b]);
                             const float pe = fmaf(xa[a], yb[b], -p);  // exact product error
                             const float t = sacc[a][b] + p;           // Fast2Sum: |s| >= |p|
                             const float z = t - sacc[a][b];

@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         df_min(mnh, mnl, ch, cl);
                     }
                     // k C as (hi, lo): Dekker product with FMA
-                    const float pp = kh * ch;
+                    const float pp = __fmul_rn(kh, ch);
                     const float pe = fmaf(kh, cl, fmaf(kl, ch, fmaf(kh, ch, -pp)));
                     float vh, vl;
                     two_sum_f(pp, pe, vh, vl);

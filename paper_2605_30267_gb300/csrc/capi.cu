@@ -626,6 +626,7 @@ struct PointPlan {
     PointSort sx{}, sy{};
     int prow = 1, pcol = 1, kind = 1, nblk = 1;
     double *blockmax = nullptr, *scal = nullptr;
+    int32_t *hint_r = nullptr, *hint_c = nullptr;   // slot hints (sorted solves)
 };
 
 int points_grid(const accsink_ctx *ctx, int n_rows, int d)
@@ -671,6 +672,9 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
                 sizes.push_back(z);
         }
         sizes.push_back(std::max<size_t>(temp, 16));
+        // slot hints of the pruned passes, one per group of rows of a warp
+        sizes.push_back((size_t)((n + 3) / 4) * 4);
+        sizes.push_back((size_t)((m + 3) / 4) * 4);
     }
     size_t need = 0;
     for (size_t z : sizes) need += align_up(z, 256);
@@ -716,6 +720,8 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
         }
         pl.sx.temp = pl.sy.temp = take();
         pl.sx.temp_bytes = pl.sy.temp_bytes = std::max<size_t>(temp, 16);
+        pl.hint_r = (int32_t *)take();
+        pl.hint_c = (int32_t *)take();
     }
     w.ldx = ldx;
     w.ldy = ldy;
@@ -732,6 +738,9 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     pc.P = Yv; pc.Pc = Xv; pc.Ah = w.Fh; pc.Al = w.Fk; pc.B64 = w.By64;
     pc.Qh = w.PXh; pc.Ql = w.PXl; pc.scal = pl.scal; pc.ldq = ldx;
     pc.nr = m; pc.nc = n; pc.d = d; pc.kind = pl.kind;
+    // the pruned kernels group rows by four (d <= 4)
+    pr.hint = (pl.sorted && points_rows_per_warp(d) == 4) ? pl.hint_r : nullptr;
+    pc.hint = (pl.sorted && points_rows_per_warp(d) == 4) ? pl.hint_c : nullptr;
     return ACCSINK_OK;
 }
 
@@ -802,6 +811,11 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
         CK(launch_points_sort(prob->Y, prob->b, m, prob->d, pl.sy, s));
     }
     CK(points_prologue(&ps, pl, prm->eps, s));
+    if (pl.sorted) {
+        // slot hints of the pruned passes, from the sorted points alone
+        CK(launch_points_hint(pl.sx.P, n, pl.sy.P, m, prob->d, kind, pl.hint_r, prow, s));
+        CK(launch_points_hint(pl.sy.P, m, pl.sx.P, n, prob->d, kind, pl.hint_c, pcol, s));
+    }
     CK(launch_init(cv, w, g.vec_grid, ps.a, ps.b, 0, is0, s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));

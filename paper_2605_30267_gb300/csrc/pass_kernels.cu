@@ -86,8 +86,8 @@ struct Acc {
 __device__ __forceinline__ void acc_rescale(Acc &a, float newR, float kh, float kl)
 {
     const float f = exp2_scaled(a.R - newR, kh, kl);
-    a.S *= f;
-    a.K *= f;
+    a.S = __fmul_rn(a.S, f);
+    a.K = __fmul_rn(a.K, f);
     a.R = newR;
 }
 
@@ -212,8 +212,8 @@ __global__ void __launch_bounds__(kRowNT) k_row_pass(CostView cv, Work w)
                 if (cm > acc[r].R) {
                     if (WITH_COST) {
                         const float f = exp2_scaled(acc[r].R - cm, kh, kl);
-                        cacc[r].S *= f;
-                        cacc[r].K *= f;
+                        cacc[r].S = __fmul_rn(cacc[r].S, f);
+                        cacc[r].K = __fmul_rn(cacc[r].K, f);
                     }
                     acc_rescale(acc[r], cm, kh, kl);
                 }
@@ -246,8 +246,8 @@ __global__ void __launch_bounds__(kRowNT) k_row_pass(CostView cv, Work w)
                 if (s > acc[r].R) {
                     if (WITH_COST) {
                         const float f = exp2_scaled(acc[r].R - s, kh, kl);
-                        cacc[r].S *= f;
-                        cacc[r].K *= f;
+                        cacc[r].S = __fmul_rn(cacc[r].S, f);
+                        cacc[r].K = __fmul_rn(cacc[r].K, f);
                     }
                     acc_rescale(acc[r], s, kh, kl);
                 }

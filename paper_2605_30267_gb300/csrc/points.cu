@@ -79,7 +79,7 @@ __device__ __forceinline__ void slot_dot(const float *p, int d, const float4 &ah
             const float qlv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-                const float pr = p[k] * qv[e];
+                const float pr = __fmul_rn(p[k], qv[e]);   // never fused: pe is its error
                 float pe = fmaf(p[k], qv[e], -pr);     // exact product error
                 pe = fmaf(p[k], qlv[e], pe);
                 const float hn = h[e] + pr;             // Fast2Sum
@@ -130,7 +130,14 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
 // FP32 estimate of every exponent, for every row of the warp, lies more than
 // kSkipLog2 below the lane's running maximum (a lower bound of the row's) is
-// skipped. Each skipped term is below 2^-64 of its row's sum, so all of a
+// skipped. Each row's running maximum starts just below its largest term in
+// the slot that holds the column nearest to the group's first row (pv.hint,
+// found once per solve from the points alone): the FP32 estimate of that term
+// less the estimate's error bound, which is below an actual term of the row
+// and so still a lower bound of its maximum; far slots are then skipped from
+// the start of the row rather than only once the loop has reached the row's
+// best columns. The hints depend only on the points, so repeated and resumed
+// solves take the same steps bit for bit. Each skipped term is below 2^-64 of its row's sum, so all of a
 // row's skipped terms together stay below 2^-33 (~1e-10) of it for any row
 // length below 2^31: three orders of magnitude below the FP32 passes' own
 // accuracy (~1e-7 in each log-sum-exp). The estimate A_hi + sum_k
@@ -138,6 +145,42 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // magnitude |A| + sum_k |p_k| |Q_k| (four FP32 roundings and the dropped low
 // parts), so the threshold is lowered by 2^-20 of a bound on that magnitude.
 constexpr float kSkipLog2 = 64.0f;
+
+// Running maxima at the start of a row group: every lane evaluates the FP32
+// estimate of the hinted slot hv (the same loads for all lanes) and takes, per
+// row, its largest term less the estimate's error bound, which stays below
+// that actual term (the margin of the skip test). The slot's terms themselves
+// are added in the pass's loop. Out of line: it runs once per row group and
+// keeps its registers out of the loop's.
+template <int DMAX, int RW>
+__device__ __noinline__ void hinted_start(const PointView &pv, const float (&p)[RW][DMAX], int d,
+                                          int hv, float (&R0)[RW])
+{
+    const float4 ah = __ldg(reinterpret_cast<const float4 *>(pv.Ah) + hv);
+    float4 qh[DMAX];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+        if (k < d) qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * pv.ldq) + hv);
+    const float amax = fmaxf(fmaxf(fabsf(ah.x), fabsf(ah.y)), fmaxf(fabsf(ah.z), fabsf(ah.w)));
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+        float mag = amax;
+        float e4[4] = {ah.x, ah.y, ah.z, ah.w};
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) {
+            if (k < d) {
+                const float qm = fmaxf(fmaxf(fabsf(qh[k].x), fabsf(qh[k].y)),
+                                       fmaxf(fabsf(qh[k].z), fabsf(qh[k].w)));
+                mag = fmaf(fabsf(p[q][k]), qm, mag);
+                e4[0] = fmaf(p[q][k], qh[k].x, e4[0]);
+                e4[1] = fmaf(p[q][k], qh[k].y, e4[1]);
+                e4[2] = fmaf(p[q][k], qh[k].z, e4[2]);
+                e4[3] = fmaf(p[q][k], qh[k].w, e4[3]);
+            }
+        }
+        R0[q] = fmaxf(fmaxf(e4[0], e4[1]), fmaxf(e4[2], e4[3])) - 1.0f - mag * 0x1p-20f;
+    }
+}
 
 template <int MODE, int DMAX, int RW, bool WC, bool EXACT = false, bool PRUNE = false,
           bool F32 = false>
@@ -174,6 +217,15 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
         for (int q = 0; q < RW; ++q) {
             acc[q] = {-INFINITY, 0.0f, 0.0f};
             cacc[q] = {0.0f, 0.0f, 0.0f};
+        }
+        if (PRUNE && pv.hint) {
+            const int hv = pv.hint[r0 / RW];
+            if (hv >= 0 && hv < nfull) {
+                float R0[RW];
+                hinted_start<DMAX, RW>(pv, p, d, hv, R0);
+#pragma unroll
+                for (int q = 0; q < RW; ++q) acc[q].R = R0[q];
+            }
         }
         // whole chunks: every element valid
         for (int v = lane; v < nfull; v += 32) {
@@ -264,8 +316,8 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
             const float Rrow = warp_max(acc[q].R);
             const float sc = ex2_approx(acc[q].R - Rrow);
             float hi, lo, chi = 0.f, clo = 0.f;
-            two_sum_f(acc[q].S * sc, -acc[q].K * sc, hi, lo);
-            if (WC) two_sum_f(cacc[q].S * sc, -cacc[q].K * sc, chi, clo);
+            two_sum_f(__fmul_rn(acc[q].S, sc), -__fmul_rn(acc[q].K, sc), hi, lo);
+            if (WC) two_sum_f(__fmul_rn(cacc[q].S, sc), -__fmul_rn(cacc[q].K, sc), chi, clo);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -406,10 +458,10 @@ __global__ void __launch_bounds__(kPtNT) k_points_rowmax(const float *X, const f
                     if (kind == 1) {
                         float dh, de;
                         two_sum_f(x[k], -y, dh, de);          // exact difference
-                        term = dh * dh;                      // (dh + de)^2 to double-float
+                        term = __fmul_rn(dh, dh);            // (dh + de)^2 to double-float
                         te = fmaf(dh, dh, -term) + 2.0f * dh * de;
                     } else {
-                        term = x[k] * y;
+                        term = __fmul_rn(x[k], y);
                         te = fmaf(x[k], y, -term);
                     }
                     float s2, e2;
@@ -700,6 +752,57 @@ size_t points_sort_temp_bytes(int count)
     cub::DeviceRadixSort::SortPairs(nullptr, t, (const uint32_t *)nullptr, (uint32_t *)nullptr,
                                     (const int *)nullptr, (int *)nullptr, count, 0, 30);
     return t;
+}
+
+// Slot hints of the pruned passes (d <= 4, sorted clouds): for each group of
+// four rows of P (nr x d), the float4 slot of Q (nc x d) holding the column of
+// smallest cost to the group's first row (squared distance, or 1 - <p, q>),
+// by brute force with one warp per group and ties to the lower column; -1 when
+// that slot lies in the ragged tail (the passes never skip tail slots).
+template <int DMAX>
+__global__ void __launch_bounds__(kPtNT) k_points_hint(const float *P, int nr, const float *Q,
+                                                       int nc, int d, int kind, int32_t *hint)
+{
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * kPtNT + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * kPtNT) >> 5;
+    const int groups = (nr + 3) / 4;
+    const int nfull = (nc >> 2) & ~31;
+    for (int g = gwarp; g < groups; g += nwarps) {
+        float p[DMAX];
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) p[k] = (k < d) ? P[(int64_t)(4 * g) * d + k] : 0.0f;
+        float best = INFINITY;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < nc; j += 32) {
+            float c = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DMAX; ++k) {
+                if (k < d) {
+                    const float q = Q[(int64_t)j * d + k];
+                    if (kind == 1) { const float t = p[k] - q; c = fmaf(t, t, c); }
+                    else c = fmaf(-p[k], q, c);
+                }
+            }
+            if (c < best) { best = c; bj = j; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ob < best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        if (lane == 0) hint[g] = (bj != 0x7fffffff && bj / 4 < nfull) ? bj / 4 : -1;
+    }
+}
+
+cudaError_t launch_points_hint(const float *P, int nr, const float *Q, int nc, int d, int kind,
+                               int32_t *hint, int grid, cudaStream_t s)
+{
+    if (d == 2) k_points_hint<2><<<grid, kPtNT, 0, s>>>(P, nr, Q, nc, d, kind, hint);
+    else if (d == 3) k_points_hint<3><<<grid, kPtNT, 0, s>>>(P, nr, Q, nc, d, kind, hint);
+    else k_points_hint<4><<<grid, kPtNT, 0, s>>>(P, nr, Q, nc, d, kind, hint);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_points_sort(const float *P, const double *a, int n, int d, const PointSort &ps,

@@ -284,9 +284,9 @@ __global__ void __launch_bounds__(GEO::kNT, 1) k_row_pass_tma(CostView cv, Work 
                 }
                 if (cm > acc[r].R) {
                     const float f = exp2_scaled(acc[r].R - cm, kh, kl);
-                    acc[r].S *= f;
-                    acc[r].K *= f;
-                    if (WITH_COST) { cacc[r].S *= f; cacc[r].K *= f; }
+                    acc[r].S = __fmul_rn(acc[r].S, f);
+                    acc[r].K = __fmul_rn(acc[r].K, f);
+                    if (WITH_COST) { cacc[r].S = __fmul_rn(cacc[r].S, f); cacc[r].K = __fmul_rn(cacc[r].K, f); }
                     acc[r].R = cm;
                 }
                 const float R = acc[r].R;

@@ -176,12 +176,12 @@ __device__ __noinline__ void merge_parts(const float4 *prec, const float2 *pcrec
     }
     R = warp_max(have ? r.x : -INFINITY);
     const float sc = have ? exp2_scaled(r.x - R, kh, kl) : 0.0f;
-    float h = r.y * sc;
+    float h = __fmul_rn(r.y, sc);
     float l = fmaf(r.y, sc, -h) + r.z * sc;
     two_sum(h, l, hi, lo);
     warp_sum_df(hi, lo);
     if (WITH_COST) {
-        h = c.x * sc;
+        h = __fmul_rn(c.x, sc);
         l = fmaf(c.x, sc, -h) + c.y * sc;
         two_sum(h, l, chi, clo);
         warp_sum_df(chi, clo);
@@ -281,9 +281,9 @@ __global__ void __launch_bounds__(kWarpNT, WITH_COST ? 2 : 3) k_lse_rows(CostVie
             }
             if (cm > acc.R) {
                 const float f = exp2_scaled(acc.R - cm, kh, kl);
-                acc.S *= f;
-                acc.K *= f;
-                if (WITH_COST) { cacc.S *= f; cacc.K *= f; }
+                acc.S = __fmul_rn(acc.S, f);
+                acc.K = __fmul_rn(acc.K, f);
+                if (WITH_COST) { cacc.S = __fmul_rn(cacc.S, f); cacc.K = __fmul_rn(cacc.K, f); }
                 acc.R = cm;
             }
             const float R = acc.R;
@@ -316,9 +316,9 @@ __global__ void __launch_bounds__(kWarpNT, WITH_COST ? 2 : 3) k_lse_rows(CostVie
             const float s = Gj - c;
             if (s > acc.R) {
                 const float f = exp2_scaled(acc.R - s, kh, kl);
-                acc.S *= f;
-                acc.K *= f;
-                if (WITH_COST) { cacc.S *= f; cacc.K *= f; }
+                acc.S = __fmul_rn(acc.S, f);
+                acc.K = __fmul_rn(acc.K, f);
+                if (WITH_COST) { cacc.S = __fmul_rn(cacc.S, f); cacc.K = __fmul_rn(cacc.K, f); }
                 acc.R = s;
             }
             const float p = term_s(s, Gj, Gkj, c, acc.R, kh, kl);
@@ -329,9 +329,9 @@ __global__ void __launch_bounds__(kWarpNT, WITH_COST ? 2 : 3) k_lse_rows(CostVie
         float Rrow = warp_max(acc.R);
         const float sc = exp2_scaled(acc.R - Rrow, kh, kl);
         float hi, lo;
-        two_sum(acc.S * sc, -acc.K * sc, hi, lo);
+        two_sum(__fmul_rn(acc.S, sc), -__fmul_rn(acc.K, sc), hi, lo);
         float chi = 0.f, clo = 0.f;
-        if (WITH_COST) two_sum(cacc.S * sc, -cacc.K * sc, chi, clo);
+        if (WITH_COST) two_sum(__fmul_rn(cacc.S, sc), -__fmul_rn(cacc.K, sc), chi, clo);
         warp_sum_df(hi, lo);
         if (WITH_COST) warp_sum_df(chi, clo);
         if (unit >= nfull) {
