@@ -263,12 +263,20 @@ int accsink_get_history(accsink_ctx *ctx, int32_t capacity, double *err,
  *                  CTA (default 65536);
  *   row_tile_elems cost entries per row-pass work item of larger problems
  *                  (default 65536; column items are 128 columns);
- *   ctas_per_sm    persistent CTAs per SM (0: as many as fit). */
+ *   ctas_per_sm    persistent CTAs per SM (0: as many as fit);
+ *   dense_solo_min_nm
+ *                  dense problems (ACCSINK_COST_DENSE) with n*m at least this,
+ *                  and a batch's only problem when it is dense, are solved one
+ *                  at a time after the batched launch, exactly as
+ *                  accsink_solve solves them with use_graph = 1 (res[k].loop_mode
+ *                  is then 1): that path reads the stored FP32 cost (4 bytes
+ *                  per entry per pass) where the batched launch reads its
+ *                  double-float K (8 bytes). Default 2^24; negative: never. */
 typedef struct {
     int32_t small_max_nm;
     int32_t row_tile_elems;
     int32_t ctas_per_sm;
-    int32_t reserved;
+    int32_t dense_solo_min_nm;
 } accsink_batch_config;
 
 /* Solves `count` independent problems (Sec. 1, eq. EOT, each with its own
@@ -286,7 +294,9 @@ typedef struct {
  * rounding, for every problem); the slices take 12 bytes per vector element
  * of workspace. Large problems (tiled, m >= 4096) run the step's per-column
  * loops as work items over many CTAs (ACCSINK_BATCH_STEP_ITEMS=0 keeps them
- * in one CTA; the potentials are the same bit for bit). Returns OK when every problem
+ * in one CTA; the potentials are the same bit for bit). Large dense problems
+ * are solved one at a time by the single-solve path (see dense_solo_min_nm
+ * above; history is not kept for them). Returns OK when every problem
  * converged, ACCSINK_ERR_MAXITER when some did not (their results are still
  * valid), another code for the first failed problem (see res[k].status), or
  * ACCSINK_ERR_TIMEOUT if a device-side wait of the scheduler ran out. */
@@ -301,9 +311,10 @@ int accsink_batch_get_config(const accsink_ctx *ctx, accsink_batch_config *cfg);
 
 /* Autotuner: solves the batch once with each candidate work split, keeps the
  * fastest in the context and writes it to *best. times_ms (host, capacity
- * cap, may be NULL) receives each candidate's time and *tried their number.
- * Arguments otherwise as accsink_solve_batch (the outputs hold the last
- * candidate's solve). */
+ * cap, may be NULL) receives each candidate's time of the batched launch and
+ * *tried their number; the dense problems solved one at a time are solved
+ * once, with the first candidate. Arguments otherwise as accsink_solve_batch
+ * (the outputs hold the last candidate's solve). */
 int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_problem *probs,
                            const accsink_params *params, void *stream,
                            double *const *f_out, double *const *g_out,
@@ -311,7 +322,8 @@ int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_proble
                            float *times_ms, int32_t cap, int32_t *tried);
 
 /* Device times of the last batch on this context: total, cost formation and
- * persistent solve, in milliseconds (host pointers, any may be NULL). */
+ * persistent solve, in milliseconds (host pointers, any may be NULL); total
+ * and solve include the dense problems solved one at a time. */
 int accsink_batch_last_timing(const accsink_ctx *ctx, float *total_ms, float *form_ms,
                               float *solve_ms);
 
@@ -363,7 +375,8 @@ int accsink_server_copy_potentials(accsink_server *srv, accsink_ticket ticket,
 /* Frees a DONE or FAILED ticket and its potentials. */
 int accsink_server_release(accsink_server *srv, accsink_ticket ticket);
 int accsink_server_get_stats(accsink_server *srv, accsink_server_stats *out);
-/* Work split of the server's batches (NULL: defaults). */
+/* Work split of the server's batches (NULL: defaults). dense_solo_min_nm is
+ * not used: every admitted request runs in its group's batched launch. */
 int accsink_server_set_config(accsink_server *srv, const accsink_batch_config *cfg);
 /* Admission limit of one group: the sum of n m over its requests stays at or
  * below max_group_entries, except that a larger request runs alone; 0 (the

@@ -79,7 +79,7 @@ class accsink_state(ct.Structure):
 
 class accsink_batch_config(ct.Structure):
     _fields_ = [("small_max_nm", ct.c_int32), ("row_tile_elems", ct.c_int32),
-                ("ctas_per_sm", ct.c_int32), ("reserved", ct.c_int32)]
+                ("ctas_per_sm", ct.c_int32), ("dense_solo_min_nm", ct.c_int32)]
 
 
 class accsink_server_stats(ct.Structure):
@@ -393,15 +393,16 @@ class Context:
         self._raise(rc, (OK, ERR_MAXITER) if allow_maxiter else (OK,))
         return [ra[i] for i in range(k)]
 
-    def accsink_batch_set_config(self, small_max_nm=0, row_tile_elems=0, ctas_per_sm=0):
-        c = accsink_batch_config(small_max_nm, row_tile_elems, ctas_per_sm, 0)
+    def accsink_batch_set_config(self, small_max_nm=0, row_tile_elems=0, ctas_per_sm=0,
+                                 dense_solo_min_nm=0):
+        c = accsink_batch_config(small_max_nm, row_tile_elems, ctas_per_sm, dense_solo_min_nm)
         self._raise(lib().accsink_batch_set_config(self._h, ct.byref(c)))
 
     def accsink_batch_get_config(self) -> dict:
         c = accsink_batch_config()
         self._raise(lib().accsink_batch_get_config(self._h, ct.byref(c)))
         return {"small_max_nm": c.small_max_nm, "row_tile_elems": c.row_tile_elems,
-                "ctas_per_sm": c.ctas_per_sm}
+                "ctas_per_sm": c.ctas_per_sm, "dense_solo_min_nm": c.dense_solo_min_nm}
 
     def accsink_batch_autotune(self, probs, params, f_outs, g_outs, stream=None):
         k, pa, qa, fa, ga, ra = self._batch_arrays(probs, params, f_outs, g_outs)
@@ -412,7 +413,8 @@ class Context:
                                           ct.byref(best), times, 64, ct.byref(tried))
         self._raise(rc)
         return ({"small_max_nm": best.small_max_nm, "row_tile_elems": best.row_tile_elems,
-                 "ctas_per_sm": best.ctas_per_sm}, list(times)[:tried.value])
+                 "ctas_per_sm": best.ctas_per_sm, "dense_solo_min_nm": best.dense_solo_min_nm},
+                list(times)[:tried.value])
 
     def accsink_batch_last_timing(self):
         t, f, s = ct.c_float(), ct.c_float(), ct.c_float()

@@ -65,6 +65,7 @@ BatchTuning batch_default_tuning(int num_sms)
     t.small_max_nm = 1 << 16;
     t.row_tile_elems = 1 << 16;
     t.ctas_per_sm = 0;          // occupancy
+    t.dense_solo_min_nm = 1 << 24;
     (void)num_sms;
     return t;
 }

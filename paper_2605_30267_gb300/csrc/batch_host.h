@@ -21,11 +21,16 @@ struct BatchWorkspace {
 
 // Work split of a batch. small_max_nm: problems with n m at most this are
 // solved whole by one CTA; row_tile_elems: cost entries per row-pass item of
-// the larger ones; ctas_per_sm: persistent CTAs per SM (0: occupancy).
+// the larger ones; ctas_per_sm: persistent CTAs per SM (0: occupancy);
+// dense_solo_min_nm: dense problems with n m at least this (and a batch's
+// only problem, when it is dense) are solved one at a time by the
+// single-solve path instead of the batched launch (negative: never). The
+// batched launch itself (batch_run) takes every problem it is given.
 struct BatchTuning {
     int small_max_nm = 1 << 16;
     int row_tile_elems = 1 << 16;
     int ctas_per_sm = 0;
+    int dense_solo_min_nm = 1 << 24;
 };
 
 struct BatchResult;
@@ -46,6 +51,7 @@ struct BatchEnv {
 
 struct BatchTiming {
     float total_ms = 0, form_ms = 0, solve_ms = 0;
+    float solo_ms = 0;      // the dense problems solved one at a time (in total and solve)
     int grid = 0;
 };
 

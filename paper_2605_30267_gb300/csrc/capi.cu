@@ -1548,22 +1548,92 @@ int validate_batch(accsink_ctx *ctx, int32_t count, const accsink_problem *probs
     return ACCSINK_OK;
 }
 
+// A dense problem that the single-solve path (graph loop over the stored
+// cost, 4 bytes per entry per pass) serves better than the batched launch
+// (8 bytes of K per entry per pass, items shared with the other problems):
+// a batch's only dense problem at any size (about 3x faster alone at every
+// size measured, 256^2 to 8192^2), and from tn.dense_solo_min_nm entries on
+// (there a dense problem costs the batched launch more device time than it
+// takes alone).
+bool dense_solo(const BatchTuning &tn, int32_t count, const accsink_problem &p)
+{
+    if (p.cost_kind != ACCSINK_COST_DENSE || tn.dense_solo_min_nm < 0) return false;
+    return count == 1 || (int64_t)p.n * p.m >= (int64_t)tn.dense_solo_min_nm;
+}
+
+// The batch's return code from the parts' codes: OK, MAXITER when some
+// problems did not converge, else the first other error.
+int merge_status(int rc, int part)
+{
+    if (part == ACCSINK_OK) return rc;
+    if (rc == ACCSINK_OK || (rc == ACCSINK_ERR_MAXITER && part != ACCSINK_ERR_MAXITER)) return part;
+    return rc;
+}
+
+// Solves a batch: the dense problems that dense_solo picks one at a time by
+// the single-solve path (after the batched launch, with use_graph set and no
+// history), the others in one batched launch. with_solo = false leaves the
+// solo problems' outputs and results untouched (the autotuner solves them
+// once).
 int run_batch(accsink_ctx *ctx, const BatchTuning &tn, int32_t count, const accsink_problem *probs,
               const accsink_params *params, void *stream, double *const *f_out,
-              double *const *g_out, accsink_result *res)
+              double *const *g_out, accsink_result *res, bool with_solo = true)
 {
+    ctx->batch_timing = BatchTiming{};
     if (count == 0) return ACCSINK_OK;
-    BatchEnv env;
-    env.num_sms = ctx->num_sms;
-    env.occ_solve = ctx->occ_batch;
-    const size_t used = ctx->ws_bytes + ctx->stage_bytes + ctx->ct_bytes + ctx->pts_bytes;
-    env.budget_left = ctx->budget ? (ctx->budget > used ? ctx->budget - used : 1) : 0;
-    env.ev0 = ctx->ev0;
-    env.ev_mid = ctx->ev_mid;
-    env.ev1 = ctx->ev1;
+    std::vector<int> solo, rest;
+    for (int k = 0; k < count; ++k) (dense_solo(tn, count, probs[k]) ? solo : rest).push_back(k);
+    int rc = ACCSINK_OK;
     std::string err;
-    const int rc = batch_run(env, ctx->batch, tn, count, probs, params, f_out, g_out, res,
-                             (cudaStream_t)stream, err, &ctx->batch_timing);
+    if (!rest.empty()) {
+        const int nr = (int)rest.size();
+        std::vector<accsink_problem> rp(nr);
+        std::vector<accsink_params> rq(nr);
+        std::vector<double *> rf(nr), rg(nr);
+        std::vector<accsink_result> rr(nr);
+        for (int i = 0; i < nr; ++i) {
+            rp[i] = probs[rest[i]];
+            rq[i] = params[rest[i]];
+            rf[i] = f_out[rest[i]];
+            rg[i] = g_out[rest[i]];
+        }
+        BatchEnv env;
+        env.num_sms = ctx->num_sms;
+        env.occ_solve = ctx->occ_batch;
+        const size_t used = ctx->ws_bytes + ctx->stage_bytes + ctx->ct_bytes + ctx->pts_bytes;
+        env.budget_left = ctx->budget ? (ctx->budget > used ? ctx->budget - used : 1) : 0;
+        env.ev0 = ctx->ev0;
+        env.ev_mid = ctx->ev_mid;
+        env.ev1 = ctx->ev1;
+        rc = batch_run(env, ctx->batch, tn, nr, rp.data(), rq.data(), rf.data(), rg.data(),
+                       rr.data(), (cudaStream_t)stream, err, &ctx->batch_timing);
+        for (int i = 0; i < nr; ++i) res[rest[i]] = rr[i];
+        if (rc != ACCSINK_OK && rc != ACCSINK_ERR_MAXITER) return fail(ctx, rc, err);
+    }
+    if (!with_solo) {
+        if (rc != ACCSINK_OK) return fail(ctx, rc, err);
+        return ACCSINK_OK;
+    }
+    float solo_ms = 0.0f;
+    for (int k : solo) {
+        accsink_params q = params[k];
+        q.use_graph = 1;
+        q.history = 0;
+        std::memset(&res[k], 0, sizeof(res[k]));
+        const int r = solve_device(ctx, &probs[k], &q, (cudaStream_t)stream, f_out[k], g_out[k],
+                                   &res[k]);
+        res[k].status = r;
+        if (r != ACCSINK_OK && r != ACCSINK_ERR_MAXITER && err.empty())
+            err = "problem " + std::to_string(k) + ": " + ctx->err;
+        solo_ms += (float)res[k].gpu_ms;
+        rc = merge_status(rc, r);
+    }
+    ctx->batch_timing.solo_ms = solo_ms;
+    ctx->batch_timing.total_ms += solo_ms;
+    ctx->batch_timing.solve_ms += solo_ms;
+    if (rc == ACCSINK_ERR_MAXITER) err = "some problems did not converge within max_sinkhorn_steps";
+    else if (rc != ACCSINK_OK && err.empty())
+        err = "some problems stopped with an error status (see res[k].status)";
     if (rc != ACCSINK_OK) return fail(ctx, rc, err);
     return ACCSINK_OK;
 }
@@ -1590,10 +1660,12 @@ int accsink_batch_set_config(accsink_ctx *ctx, const accsink_batch_config *cfg)
     BatchTuning t = batch_default_tuning(ctx->num_sms);
     if (cfg) {
         if (cfg->small_max_nm < 0 || cfg->row_tile_elems < 0 || cfg->ctas_per_sm < 0)
-            return fail(ctx, ACCSINK_ERR_INVALID_ARG, "batch config fields must be >= 0");
+            return fail(ctx, ACCSINK_ERR_INVALID_ARG,
+                        "small_max_nm, row_tile_elems and ctas_per_sm must be >= 0");
         if (cfg->small_max_nm) t.small_max_nm = cfg->small_max_nm;
         if (cfg->row_tile_elems) t.row_tile_elems = cfg->row_tile_elems;
         t.ctas_per_sm = cfg->ctas_per_sm;
+        if (cfg->dense_solo_min_nm) t.dense_solo_min_nm = cfg->dense_solo_min_nm < 0 ? -1 : cfg->dense_solo_min_nm;
     }
     ctx->batch_tuning = t;
     return ACCSINK_OK;
@@ -1606,6 +1678,7 @@ int accsink_batch_get_config(const accsink_ctx *ctx, accsink_batch_config *cfg)
     cfg->small_max_nm = ctx->batch_tuning.small_max_nm;
     cfg->row_tile_elems = ctx->batch_tuning.row_tile_elems;
     cfg->ctas_per_sm = ctx->batch_tuning.ctas_per_sm;
+    cfg->dense_solo_min_nm = ctx->batch_tuning.dense_solo_min_nm;
     return ACCSINK_OK;
 }
 
@@ -1623,19 +1696,22 @@ int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_proble
     const int smalls[] = {1 << 14, 1 << 16, 1 << 18};
     const int tiles[] = {1 << 14, 1 << 16, 1 << 18};
     const int per_sm[] = {0, 1};
+    // The dense problems solved one at a time are solved with the first
+    // candidate only; the candidates are compared on the batched launch.
     BatchTuning bt = ctx->batch_tuning;
     float best_ms = INFINITY;
     int k = 0;
     for (int sm : smalls)
         for (int tl : tiles)
             for (int ps : per_sm) {
-                BatchTuning t;
+                BatchTuning t = ctx->batch_tuning;
                 t.small_max_nm = sm;
                 t.row_tile_elems = tl;
                 t.ctas_per_sm = ps;
-                const int r = run_batch(ctx, t, count, probs, params, stream, f_out, g_out, res);
+                const int r = run_batch(ctx, t, count, probs, params, stream, f_out, g_out, res,
+                                        k == 0);
                 if (r != ACCSINK_OK && r != ACCSINK_ERR_MAXITER) return r;
-                const float ms = ctx->batch_timing.total_ms;
+                const float ms = ctx->batch_timing.total_ms - ctx->batch_timing.solo_ms;
                 if (times_ms && k < cap) times_ms[k] = ms;
                 ++k;
                 if (ms < best_ms) { best_ms = ms; bt = t; }
@@ -1647,6 +1723,7 @@ int accsink_batch_autotune(accsink_ctx *ctx, int32_t count, const accsink_proble
         best->small_max_nm = bt.small_max_nm;
         best->row_tile_elems = bt.row_tile_elems;
         best->ctas_per_sm = bt.ctas_per_sm;
+        best->dense_solo_min_nm = bt.dense_solo_min_nm;
     }
     return ACCSINK_OK;
 }

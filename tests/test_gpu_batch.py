@@ -3,9 +3,11 @@ against the FP64 oracle, problem by problem.
 
 Each problem of a batch must meet the single-solve tolerances: potentials
 within 1e-3 eps max-abs after centring (at the same iterate), <C,P> within
-1e-5 relative, steps within 2% (or one step), FP64-truth column L1 <= tol
-(1 + 0.05) and row L1 at the FP32 floor. The work split (whole-problem items
-or row / column tiles) must not change any potential.
+1e-5 relative, steps within 2% (or one step), and the FP64 truth of Sec. 5
+eq. l1tol (row plus column L1) below tol. The work split (whole-problem items
+or row / column tiles) must not change any potential. Large dense problems
+(and a batch's only problem when it is dense) are solved one at a time by the
+single-solve path: their potentials are those of accsink_solve bit for bit.
 """
 import numpy as np
 import pytest
@@ -348,3 +350,75 @@ def test_full_word_alignment_batch_meets_tol_in_fp64_truth(ctx):
         check_truth(ev, p.tol)
         worst = max(worst, ev["row_l1"] + ev["col_l1"])
     assert worst < 1e-6
+
+
+def single_solve(ctx, p):
+    f = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    g = torch.empty(p.m, dtype=torch.float64, device=DEV)
+    q = p.params()
+    q.use_graph = 1
+    r = ctx.accsink_solve(p.struct(), q, f, g)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), g.cpu().numpy(), B.result_dict(r)
+
+
+def test_large_dense_problems_take_the_single_solve_path(ctx):
+    """Dense problems from dense_solo_min_nm entries on run one at a time by
+    the single-solve path (loop_mode 1, potentials of accsink_solve bit for
+    bit, parity with the oracle); the rest of the batch stays in the batched
+    launch (loop_mode 2) with its usual results."""
+    big = [Prob("dense", 300, 400, 51, 1e-2, scale=True),
+           Prob("dense", 257, 513, 52, 5e-3, method=B.PLAIN)]
+    rest = mixed_problems()[3:8]
+    probs = rest[:2] + [big[0]] + rest[2:] + [big[1]]
+    ctx.accsink_batch_set_config(dense_solo_min_nm=100000)
+    try:
+        assert ctx.accsink_batch_get_config()["dense_solo_min_nm"] == 100000
+        fs, gs, rs = run_batch(ctx, probs)
+        t = ctx.accsink_batch_last_timing()
+    finally:
+        ctx.accsink_batch_set_config()
+    assert ctx.accsink_batch_get_config()["dense_solo_min_nm"] == 1 << 24
+    solo_ms = 0.0
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        check_against_oracle(p, f, g, r)
+        if p in big:
+            assert r["loop_mode"] == 1, r
+            f1, g1, r1 = single_solve(ctx, p)
+            np.testing.assert_array_equal(f, f1)
+            np.testing.assert_array_equal(g, g1)
+            assert r["sinkhorn_steps"] == r1["sinkhorn_steps"]
+            solo_ms += r["gpu_ms"]
+        else:
+            assert r["loop_mode"] == 2, r
+    assert t["total_ms"] >= solo_ms > 0.0
+    # the batched members' results do not depend on the routed ones
+    f2, g2, r2 = run_batch(ctx, rest)
+    for k, p in enumerate(rest):
+        j = probs.index(p)
+        np.testing.assert_array_equal(fs[j], f2[k])
+        np.testing.assert_array_equal(gs[j], g2[k])
+
+
+def test_lone_dense_problem_takes_the_single_solve_path(ctx):
+    """A batch of one dense problem is solved by the single-solve path at any
+    size; with dense_solo_min_nm < 0 it stays in the batched launch, and both
+    meet the oracle."""
+    p = Prob("dense", 150, 120, 9, 1e-2, scale=True, spread=3.5)
+    f, g, r = run_batch(ctx, [p])
+    assert r[0]["loop_mode"] == 1
+    f1, g1, _ = single_solve(ctx, p)
+    np.testing.assert_array_equal(f[0], f1)
+    np.testing.assert_array_equal(g[0], g1)
+    check_against_oracle(p, f[0], g[0], r[0])
+    ctx.accsink_batch_set_config(dense_solo_min_nm=-1)
+    try:
+        f2, g2, r2 = run_batch(ctx, [p])
+    finally:
+        ctx.accsink_batch_set_config()
+    assert r2[0]["loop_mode"] == 2
+    check_against_oracle(p, f2[0], g2[0], r2[0])
+    # a lone point-cloud problem stays in the batched launch
+    q = mixed_problems()[4]
+    _, _, r3 = run_batch(ctx, [q])
+    assert r3[0]["loop_mode"] == 2
