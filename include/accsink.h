@@ -294,7 +294,10 @@ typedef struct {
  * rounding, for every problem); the slices take 12 bytes per vector element
  * of workspace. Large problems (tiled, m >= 4096) run the step's per-column
  * loops as work items over many CTAs (ACCSINK_BATCH_STEP_ITEMS=0 keeps them
- * in one CTA; the potentials are the same bit for bit). Large dense problems
+ * in one CTA; the potentials are the same bit for bit). The launch sequence
+ * (record upload, cost formation, the persistent solve, result download) is
+ * captured into a CUDA graph and replayed on `stream` as one launch
+ * (ACCSINK_BATCH_GRAPH=0 issues it directly). Large dense problems
  * are solved one at a time by the single-solve path (see dense_solo_min_nm
  * above; history is not kept for them). Returns OK when every problem
  * converged, ACCSINK_ERR_MAXITER when some did not (their results are still

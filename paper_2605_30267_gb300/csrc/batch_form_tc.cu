@@ -605,6 +605,18 @@ bool batch_tc_available() { return encode_fn() != nullptr; }
 
 size_t batch_tc_slice_bytes(int64_t R, int dpad) { return (size_t)kTcL * R * dpad * 2; }
 
+cudaError_t prepare_batch_form_tc(int *sms)
+{
+    // per batch: the attribute and the SM count belong to the current device
+    cudaError_t e = cudaFuncSetAttribute(k_batch_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev);
+    return e;
+}
+
 cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStream_t s)
 {
     if (t.ntiles <= 0 || t.R <= 0) return cudaSuccess;
@@ -617,16 +629,8 @@ cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStrea
     CUtensorMap mA, mB;
     if (!encode_slices(&mA, SL, t.R, t.dpad, kTcM) || !encode_slices(&mB, SL, t.R, t.dpad, kTcN))
         return cudaErrorNotSupported;
-    // per launch: the attribute and the SM count belong to the current device
-    e = cudaFuncSetAttribute(k_batch_form_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kTcSmemBytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
     // one persistent CTA per SM (its shared memory allows no second)
-    k_batch_form_tc<<<std::min(t.ntiles, std::max(1, sms)), kTcThreads, kTcSmemBytes, s>>>(
+    k_batch_form_tc<<<std::min(t.ntiles, std::max(1, t.sms)), kTcThreads, kTcSmemBytes, s>>>(
         P, t.tiles, t.ntiles, t.expo, mA, mB);
     return cudaGetLastError();
 }

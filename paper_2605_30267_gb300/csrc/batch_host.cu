@@ -59,6 +59,15 @@ unsigned long long pow2_at_least(unsigned long long v)
 
 }  // namespace
 
+void batch_workspace_free(BatchWorkspace &ws)
+{
+    if (ws.exec) cudaGraphExecDestroy(ws.exec);
+    if (ws.cap) cudaStreamDestroy(ws.cap);
+    if (ws.dev) cudaFree(ws.dev);
+    if (ws.host) cudaFreeHost(ws.host);
+    ws = BatchWorkspace{};
+}
+
 BatchTuning batch_default_tuning(int num_sms)
 {
     BatchTuning t;
@@ -90,15 +99,24 @@ struct BatchPlan {
     size_t head_bytes = 0, data_bytes = 0;
 };
 
-// Cosine costs with kBatchTcMinD <= d <= kBatchTcMaxD are formed on the
-// tensor cores unless ACCSINK_BATCH_FORM=cuda selects the CUDA-core
-// expansion for every problem.
+// ACCSINK_BATCH_STEP_ITEMS=0 keeps a large problem's step in one CTA.
 bool step_items_enabled()
 {
     const char *e = std::getenv("ACCSINK_BATCH_STEP_ITEMS");
     return !(e && std::strcmp(e, "0") == 0);
 }
 
+// ACCSINK_BATCH_GRAPH=0 issues a batch's launch sequence directly instead of
+// replaying it as a CUDA graph.
+bool batch_graph_enabled()
+{
+    const char *e = std::getenv("ACCSINK_BATCH_GRAPH");
+    return !(e && e[0] == '0');
+}
+
+// Cosine costs with kBatchTcMinD <= d <= kBatchTcMaxD are formed on the
+// tensor cores unless ACCSINK_BATCH_FORM=cuda selects the CUDA-core
+// expansion for every problem.
 bool tc_form_enabled()
 {
     const char *e = std::getenv("ACCSINK_BATCH_FORM");
@@ -458,27 +476,90 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
         }                                                               \
     } while (0)
 
-    BK(cudaEventRecord(env.ev0, s));
-    BK(cudaMemcpyAsync(dP, hP, sizeof(BatchProb) * count, cudaMemcpyHostToDevice, s));
-    if (!tiles.empty())
-        BK(cudaMemcpyAsync(dT, hT, sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, s));
-    BK(cudaMemcpyAsync(dInit, hI, 8 * (size_t)count, cudaMemcpyHostToDevice, s));
-    BK(cudaMemcpyAsync(dQ, hQ, sizeof(BatchQueue), cudaMemcpyHostToDevice, s));
-    if (ntc) {
-        BK(cudaMemcpyAsync(dTcp, hTcp, 4 * ntc, cudaMemcpyHostToDevice, s));
-        BK(cudaMemcpyAsync(dTcs, hTcs, 8 * ntc, cudaMemcpyHostToDevice, s));
-    }
-    BK(launch_batch_form(dP, dT, pl.nform, 0, s));
-    if (pl.R > 0) BK(launch_batch_form_tc(dP, tcl, s));
-    BK(launch_batch_scale(dP, dT + pl.nform, pl.nscale, s));
-    BK(launch_queue_init(dQ, dInit, count, cap, s));
-    BK(cudaEventRecord(env.ev_mid, s));
+    if (pl.R > 0) BK(prepare_batch_form_tc(&tcl.sms));
     const int per_sm = tn.ctas_per_sm > 0 ? std::min(tn.ctas_per_sm, env.occ_solve) : env.occ_solve;
     const int grid = std::max(1, env.num_sms * per_sm);
-    BK(launch_batch_solve(dP, dQ, dR, grid, s));
-    BK(cudaEventRecord(env.ev1, s));
-    BK(cudaMemcpyAsync(hR, dR, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, s));
-    BK(cudaMemcpyAsync(hQ, dQ, sizeof(BatchQueue), cudaMemcpyDeviceToHost, s));
+    // The launch sequence of the batch: record upload, cost formation, queue
+    // set-up, the persistent solve and the result download. It is captured
+    // into a CUDA graph on the workspace's own stream and replayed on s as one
+    // launch (the previous batch's executable graph is updated in place when
+    // the sequence has the same shape); ACCSINK_BATCH_GRAPH=0 issues it
+    // directly on s.
+    const bool graph = batch_graph_enabled();
+    if (graph && !ws.cap) BK(cudaStreamCreateWithFlags(&ws.cap, cudaStreamNonBlocking));
+    cudaStream_t cs = graph ? ws.cap : s;
+    const char *failed = nullptr;
+    auto sequence = [&]() -> cudaError_t {
+        cudaError_t e;
+#define SQ(call)                                   \
+    do {                                           \
+        e = (call);                                \
+        if (e != cudaSuccess) { failed = #call; return e; } \
+    } while (0)
+        auto rec = [&](cudaEvent_t ev) {
+            return graph ? cudaEventRecordWithFlags(ev, cs, cudaEventRecordExternal)
+                         : cudaEventRecord(ev, cs);
+        };
+        SQ(rec(env.ev0));
+        SQ(cudaMemcpyAsync(dP, hP, sizeof(BatchProb) * count, cudaMemcpyHostToDevice, cs));
+        if (!tiles.empty())
+            SQ(cudaMemcpyAsync(dT, hT, sizeof(BatchTile) * tiles.size(), cudaMemcpyHostToDevice, cs));
+        SQ(cudaMemcpyAsync(dInit, hI, 8 * (size_t)count, cudaMemcpyHostToDevice, cs));
+        SQ(cudaMemcpyAsync(dQ, hQ, sizeof(BatchQueue), cudaMemcpyHostToDevice, cs));
+        if (ntc) {
+            SQ(cudaMemcpyAsync(dTcp, hTcp, 4 * ntc, cudaMemcpyHostToDevice, cs));
+            SQ(cudaMemcpyAsync(dTcs, hTcs, 8 * ntc, cudaMemcpyHostToDevice, cs));
+        }
+        SQ(launch_batch_form(dP, dT, pl.nform, 0, cs));
+        if (pl.R > 0) SQ(launch_batch_form_tc(dP, tcl, cs));
+        SQ(launch_batch_scale(dP, dT + pl.nform, pl.nscale, cs));
+        SQ(launch_queue_init(dQ, dInit, count, cap, cs));
+        SQ(rec(env.ev_mid));
+        SQ(launch_batch_solve(dP, dQ, dR, grid, cs));
+        SQ(rec(env.ev1));
+        SQ(cudaMemcpyAsync(hR, dR, sizeof(BatchResult) * count, cudaMemcpyDeviceToHost, cs));
+        SQ(cudaMemcpyAsync(hQ, dQ, sizeof(BatchQueue), cudaMemcpyDeviceToHost, cs));
+#undef SQ
+        return cudaSuccess;
+    };
+    if (!graph) {
+        const cudaError_t e = sequence();
+        if (e != cudaSuccess) {
+            err = std::string(failed) + ": " + cudaGetErrorString(e);
+            return ACCSINK_ERR_CUDA;
+        }
+    } else {
+        BK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        const cudaError_t e = sequence();
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            err = e != cudaSuccess ? std::string(failed) + " (captured): " + cudaGetErrorString(e)
+                                   : std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ec);
+            return ACCSINK_ERR_CUDA;
+        }
+        bool updated = false;
+        if (ws.exec) {
+            cudaGraphExecUpdateResultInfo info;
+            updated = cudaGraphExecUpdate(ws.exec, g, &info) == cudaSuccess;
+            if (!updated) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(ws.exec);
+                ws.exec = nullptr;
+            }
+        }
+        cudaError_t ei = cudaSuccess;
+        if (!updated) ei = cudaGraphInstantiate(&ws.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ws.exec = nullptr;
+            err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ei);
+            return ACCSINK_ERR_CUDA;
+        }
+        BK(cudaGraphLaunch(ws.exec, s));
+    }
     if (env.on_done && env.early_host && env.flag_host) {
         // hand back each problem as soon as the kernel has finished it
         std::vector<char> seen(count, 0);

@@ -12,12 +12,19 @@
 namespace accsink {
 
 // Device workspace of a context's batches (grow-only) and its pinned staging.
+// Device and pinned host workspace of batched launches, and the CUDA graph
+// their launch sequence is replayed from (captured on `cap`).
 struct BatchWorkspace {
     void *dev = nullptr;
     size_t bytes = 0;
     void *host = nullptr;
     size_t host_bytes = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
 };
+
+// Frees everything a BatchWorkspace holds.
+void batch_workspace_free(BatchWorkspace &ws);
 
 // Work split of a batch. small_max_nm: problems with n m at most this are
 // solved whole by one CTA; row_tile_elems: cost entries per row-pass item of

@@ -130,6 +130,7 @@ struct BatchTcLaunch {
     int64_t R;                   // slice rows
     void *SL;                    // FP16 slices [kBatchTcLevels][R][dpad]
     int32_t *expo;               // exponent of each slice row
+    int sms;                     // persistent CTAs (one per SM), from prepare_batch_form_tc
 };
 
 // Order-preserving map of doubles to unsigned 64-bit integers (for atomic
@@ -158,6 +159,9 @@ cudaError_t launch_batch_form(const BatchProb *P, const BatchTile *tiles, int nt
                               int dmax, cudaStream_t s);
 bool batch_tc_available();
 size_t batch_tc_slice_bytes(int64_t R, int dpad);
+// Sets the formation kernel's shared-memory attribute and returns the current
+// device's SM count in *sms (host calls only, made before a graph capture).
+cudaError_t prepare_batch_form_tc(int *sms);
 cudaError_t launch_batch_form_tc(BatchProb *P, const BatchTcLaunch &t, cudaStream_t s);
 cudaError_t launch_batch_scale(BatchProb *P, const BatchTile *tiles, int ntiles, cudaStream_t s);
 cudaError_t launch_batch_solve(BatchProb *P, BatchQueue *q, BatchResult *res, int grid,

@@ -1061,8 +1061,7 @@ void accsink_destroy(accsink_ctx *ctx)
     if (ctx->stage) cudaFree(ctx->stage);
     if (ctx->ct) cudaFree(ctx->ct);
     if (ctx->pts) cudaFree(ctx->pts);
-    if (ctx->batch.dev) cudaFree(ctx->batch.dev);
-    if (ctx->batch.host) cudaFreeHost(ctx->batch.host);
+    batch_workspace_free(ctx->batch);
     if (ctx->ev_mid) cudaEventDestroy(ctx->ev_mid);
     if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);

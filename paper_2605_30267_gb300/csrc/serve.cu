@@ -406,8 +406,7 @@ void accsink_server_destroy(accsink_server *S)
     }
     cudaStreamSynchronize(S->stream);
     if (S->pool) cudaMemPoolDestroy(S->pool);
-    if (S->ws.dev) cudaFree(S->ws.dev);
-    if (S->ws.host) cudaFreeHost(S->ws.host);
+    accsink::batch_workspace_free(S->ws);
     if (S->early) cudaFreeHost(S->early);
     if (S->early_flag) cudaFreeHost(S->early_flag);
     if (S->stream) cudaStreamDestroy(S->stream);

@@ -304,6 +304,30 @@ def test_split_step_matches_oracle(ctx):
         check_against_oracle(p, f, g, r)
 
 
+def test_graph_replay_equals_direct_launches(ctx):
+    """The batch's launch sequence replayed as a CUDA graph (the default; the
+    second run updates the executable graph in place, a batch of another
+    shape re-instantiates it) gives the potentials of the same sequence
+    issued directly, bit for bit."""
+    import os
+    probs = mixed_problems() + large_problems()[:2]
+    f1, g1, r1 = run_batch(ctx, probs)
+    run_batch(ctx, probs[:5])
+    f2, g2, r2 = run_batch(ctx, probs)
+    os.environ["ACCSINK_BATCH_GRAPH"] = "0"
+    try:
+        f3, g3, r3 = run_batch(ctx, probs)
+    finally:
+        del os.environ["ACCSINK_BATCH_GRAPH"]
+    for k in range(len(probs)):
+        for f, g, r in ((f2, g2, r2), (f3, g3, r3)):
+            assert r[k]["sinkhorn_steps"] == r1[k]["sinkhorn_steps"], k
+            np.testing.assert_array_equal(f[k], f1[k])
+            np.testing.assert_array_equal(g[k], g1[k])
+    t = ctx.accsink_batch_last_timing()
+    assert t["total_ms"] >= t["form_ms"] > 0.0
+
+
 def test_split_step_equals_one_cta_step(ctx):
     """The step's column loops as work items give the potentials of the
     one-CTA step bit for bit (only the order of Theorem 4's P2 sum differs,
