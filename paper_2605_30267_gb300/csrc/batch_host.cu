@@ -124,9 +124,10 @@ bool tc_form_enabled()
     return batch_tc_available();
 }
 
-// The work split of one problem that depends only on its size and the
-// tuning (the BatchProb fields small, rows_per_tile, row_tiles, col_tiles,
-// ldn, cols_per_item, col_items, step_cols, step_items) and its layout.
+// The work split of one problem that depends only on its size, the tuning
+// and whether the batch is wide (the BatchProb fields small, rows_per_tile,
+// row_tiles, col_tiles, ldn, cols_per_item, col_items, step_cols,
+// step_items) and its layout.
 struct ProbShape {
     int small = 0, rows_per_tile = 0, row_tiles = 0, col_tiles = 0, cols_per_item = 0,
         col_items = 0, step_cols = 0, step_items = 0;
@@ -134,31 +135,50 @@ struct ProbShape {
     ProbLayout lay{};
 };
 
-ProbShape prob_shape(const BatchTuning &tn, const accsink_problem &q)
+// Problems from kBatchTransposeMin entries are always tiled over K and K^T,
+// whatever the split, so a problem's layout (and its last bits) depends only
+// on its size.
+bool is_small(const BatchTuning &tn, const accsink_problem &q)
+{
+    const int64_t nm = (int64_t)q.n * q.m;
+    return nm <= tn.small_max_nm && nm < kBatchTransposeMin;
+}
+
+// Rows of a row item that give every (virtual) warp of the CTA four rows:
+// the row pass works on four rows at a time per segment of L lanes (L the
+// lanes a row of m columns takes, at most 32).
+int full_rows(int m)
+{
+    const int m4 = (m + 3) / 4;
+    int L = 1;
+    while (L < m4 && L < 32) L <<= 1;
+    return 4 * (kBatchThreads / 32) * (32 / L);
+}
+
+// wide: the batch has row items of full_rows rows enough for the resident
+// CTAs (see plan_batch). The rows of an item do not change any potential
+// (each row is reduced by one warp segment whatever the item), only the
+// order of the per-item dual and cost partials.
+ProbShape prob_shape(const BatchTuning &tn, const accsink_problem &q, bool wide = false)
 {
     ProbShape S;
     const int64_t nm = (int64_t)q.n * q.m;
-    // problems from kBatchTransposeMin entries are always tiled over K and
-    // K^T, whatever the split, so a problem's layout (and its last bits)
-    // depends only on its size
-    S.small = (nm <= tn.small_max_nm && nm < kBatchTransposeMin) ? 1 : 0;
+    S.small = is_small(tn, q) ? 1 : 0;
     if (S.small) {
         S.rows_per_tile = q.n;
         S.row_tiles = 1;
     } else {
         // at least one row for each of the CTA's warps, so none idles;
-        // when the problem has rows enough for 512 items of them, four
-        // rows for each (virtual) warp: the row pass gives every segment
-        // of L lanes four rows at a time, and fewer leave loads out of
-        // flight (8-row tiles of a 16384-column problem ran at 65% of
-        // HBM bandwidth; with 32 rows, 16384^2 steps took 6% less time,
-        // while 8192^2 and 4096^2 ones, then short of items for the
-        // resident CTAs, took 13-20% more)
-        const int m4 = (q.m + 3) / 4;
-        int L = 1;
-        while (L < m4 && L < 32) L <<= 1;
-        const int full = 4 * (kBatchThreads / 32) * (32 / L);
-        const int rmin = (q.n / full >= 512) ? full : kBatchThreads / 32;
+        // when the batch is wide or the problem has rows enough for 512
+        // items of them, four rows for each (virtual) warp: fewer leave
+        // loads out of flight (8-row tiles of a 16384-column problem ran at
+        // 65% of HBM bandwidth; with 32 rows, 16384^2 steps took 6% less
+        // time, while 8192^2 and 4096^2 ones alone, then short of items
+        // for the resident CTAs, took 13-20% more; in a batch of 256
+        // serving requests the solve took 11% less time, in the 512-problem
+        // word-alignment batch 5% less)
+        const int full = full_rows(q.m);
+        const int rmin = (wide || q.n / full >= 512) ? full : kBatchThreads / 32;
         int rpt = (int)std::max<int64_t>(rmin, tn.row_tile_elems / std::max(1, q.m));
         rpt = std::min(rpt, q.n);
         S.rows_per_tile = rpt;
@@ -196,9 +216,18 @@ bool tc_eligible(bool tc_on, const accsink_problem &q, int64_t R)
            q.d <= kBatchTcMaxD && R + q.n + q.m < ((int64_t)1 << 31) - kBatchTcRows;
 }
 
+// resident: the persistent CTAs of the launch (0: size the plan for any
+// launch, as the workspace sizers do). A batch is wide when its tiled
+// problems' row items of full_rows rows number at least twice the resident
+// CTAs; its rows per item then never fall below full_rows. A wide plan has
+// no more row items, hence no more bytes, than the same plan not wide.
 void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
-                const accsink_params *params, BatchPlan &pl)
+                const accsink_params *params, BatchPlan &pl, int resident = 0)
 {
+    int64_t full_items = 0;
+    for (int k = 0; k < count; ++k)
+        if (!is_small(tn, probs[k])) full_items += ceil_div(probs[k].n, full_rows(probs[k].m));
+    const bool wide = resident > 0 && full_items >= 2 * (int64_t)resident;
     pl.hp.assign(count, BatchProb{});
     pl.lay.resize(count);
     pl.tiles.clear();
@@ -222,7 +251,7 @@ void plan_batch(const BatchTuning &tn, int count, const accsink_problem *probs,
             P.eps = pp.eps; P.tol = stop_threshold(pp.tol); P.mu0 = pp.mu0;
         }
         P.ldm = ((int64_t)q.m + 3) / 4 * 4;
-        const ProbShape S = prob_shape(tn, q);
+        const ProbShape S = prob_shape(tn, q, wide);
         P.small = S.small;
         P.rows_per_tile = S.rows_per_tile;
         P.row_tiles = S.row_tiles;
@@ -347,8 +376,10 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
               BatchTiming *timing)
 {
     // ---- plan
+    const int per_sm = tn.ctas_per_sm > 0 ? std::min(tn.ctas_per_sm, env.occ_solve) : env.occ_solve;
+    const int grid = std::max(1, env.num_sms * per_sm);
     BatchPlan pl;
-    plan_batch(tn, count, probs, params, pl);
+    plan_batch(tn, count, probs, params, pl, grid);
     std::vector<BatchProb> &hp = pl.hp;
     const std::vector<ProbLayout> &lay = pl.lay;
     const std::vector<BatchTile> &tiles = pl.tiles;
@@ -477,8 +508,6 @@ int batch_run(const BatchEnv &env, BatchWorkspace &ws, const BatchTuning &tn, in
     } while (0)
 
     if (pl.R > 0) BK(prepare_batch_form_tc(&tcl.sms));
-    const int per_sm = tn.ctas_per_sm > 0 ? std::min(tn.ctas_per_sm, env.occ_solve) : env.occ_solve;
-    const int grid = std::max(1, env.num_sms * per_sm);
     // The launch sequence of the batch: record upload, cost formation, queue
     // set-up, the persistent solve and the result download. It is captured
     // into a CUDA graph on the workspace's own stream and replayed on s as one

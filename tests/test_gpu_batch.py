@@ -328,6 +328,24 @@ def test_graph_replay_equals_direct_launches(ctx):
     assert t["total_ms"] >= t["form_ms"] > 0.0
 
 
+def test_wide_batch_keeps_each_problems_potentials(ctx):
+    """A batch whose tiled problems have row items enough for the resident
+    CTAs gives every row item four rows per warp (40 problems of 1000 rows:
+    1280 items of 32 rows against 608 CTAs); a problem's potentials are
+    those it gets in a small batch (8-row items), bit for bit, and match the
+    oracle."""
+    probs = [Prob("sqeuclid", 1000, 100 + 3 * k, 60 + k, 1e-2, d=3, scale=True)
+             for k in range(40)]
+    f1, g1, r1 = run_batch(ctx, probs)
+    for k in (0, 17, 39):
+        f2, g2, r2 = run_batch(ctx, [probs[k], probs[(k + 1) % 40]])
+        assert r2[0]["sinkhorn_steps"] == r1[k]["sinkhorn_steps"]
+        np.testing.assert_array_equal(f2[0], f1[k])
+        np.testing.assert_array_equal(g2[0], g1[k])
+    for k in (0, 39):
+        check_against_oracle(probs[k], f1[k], g1[k], r1[k])
+
+
 def test_split_step_equals_one_cta_step(ctx):
     """The step's column loops as work items give the potentials of the
     one-CTA step bit for bit (only the order of Theorem 4's P2 sum differs,
