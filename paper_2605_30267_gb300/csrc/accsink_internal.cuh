@@ -153,6 +153,16 @@ struct PointView {
     // pruned passes: per group of four rows, the slot of the column nearest to
     // the group's first row (-1: none); may be NULL
     const int32_t *hint;
+    // pruned passes: log2 of the ratio below a row's largest term under which
+    // a term is skipped (see points.cu)
+    float skip;
+    // pruned passes, per block of 128 columns (32 float4 slots) of the whole
+    // chunks: qbox[2 b], qbox[2 b + 1] = the minimum and maximum of each of
+    // the block's Q coordinates (d <= 4), fixed for the solve; abox[b] = the
+    // maximum of the block's A and of |A| (high parts), set before every
+    // pass by launch_points_pass. NULL: no block test.
+    const float4 *qbox;
+    float2 *abox;
 };
 
 struct CostView {
@@ -391,6 +401,21 @@ cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, in
                                 int scale_max, double eps, const Work &w, double *scal,
                                 double *blockmax, int nblk, cudaStream_t s);
 int points_rows_per_warp(int d);
+// Blocks of 128 columns in the whole 32-slot chunks of nc columns.
+inline int points_blocks(int nc) { return nc >> 7; }
+// The per-block coordinate boxes of Q (nc x d SoA with leading dimension
+// ldq, d <= 4) for the block test of the pruned passes.
+cudaError_t launch_points_qbox(const float *Qh, int64_t ldq, int nc, int d, float4 *qbox,
+                               cudaStream_t s);
+// log2 threshold of the pruned passes for rows of nc terms: every skipped
+// term is below 2^-(skip + 1) of its row's largest, so all of a row's
+// skipped terms together stay below 2^-35 of its sum.
+inline float points_skip_log2(int nc)
+{
+    int l = 0;
+    while ((1ll << l) < (long long)nc) ++l;
+    return (float)(34 + l);
+}
 void setup_col_pass();
 
 }  // namespace accsink

@@ -627,6 +627,8 @@ struct PointPlan {
     int prow = 1, pcol = 1, kind = 1, nblk = 1;
     double *blockmax = nullptr, *scal = nullptr;
     int32_t *hint_r = nullptr, *hint_c = nullptr;   // slot hints (sorted solves)
+    float4 *qbox_r = nullptr, *qbox_c = nullptr;     // block boxes (sorted solves)
+    float2 *abox_r = nullptr, *abox_c = nullptr;
 };
 
 int points_grid(const accsink_ctx *ctx, int n_rows, int d)
@@ -675,6 +677,12 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
         // slot hints of the pruned passes, one per group of rows of a warp
         sizes.push_back((size_t)((n + 3) / 4) * 4);
         sizes.push_back((size_t)((m + 3) / 4) * 4);
+        // block boxes of the pruned passes (columns of the row pass: Y; of
+        // the column pass: X)
+        sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(m) * 32));
+        sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(n) * 32));
+        sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(m) * 8));
+        sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(n) * 8));
     }
     size_t need = 0;
     for (size_t z : sizes) need += align_up(z, 256);
@@ -722,6 +730,10 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
         pl.sx.temp_bytes = pl.sy.temp_bytes = std::max<size_t>(temp, 16);
         pl.hint_r = (int32_t *)take();
         pl.hint_c = (int32_t *)take();
+        pl.qbox_r = (float4 *)take();
+        pl.qbox_c = (float4 *)take();
+        pl.abox_r = (float2 *)take();
+        pl.abox_c = (float2 *)take();
     }
     w.ldx = ldx;
     w.ldy = ldy;
@@ -741,6 +753,12 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     // the pruned kernels group rows by four (d <= 4)
     pr.hint = (pl.sorted && points_rows_per_warp(d) == 4) ? pl.hint_r : nullptr;
     pc.hint = (pl.sorted && points_rows_per_warp(d) == 4) ? pl.hint_c : nullptr;
+    pr.skip = points_skip_log2(m);
+    pc.skip = points_skip_log2(n);
+    pr.qbox = pl.sorted ? pl.qbox_r : nullptr;
+    pc.qbox = pl.sorted ? pl.qbox_c : nullptr;
+    pr.abox = pl.sorted ? pl.abox_r : nullptr;
+    pc.abox = pl.sorted ? pl.abox_c : nullptr;
     return ACCSINK_OK;
 }
 
@@ -815,6 +833,9 @@ int solve_points(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
         // slot hints of the pruned passes, from the sorted points alone
         CK(launch_points_hint(pl.sx.P, n, pl.sy.P, m, prob->d, kind, pl.hint_r, prow, s));
         CK(launch_points_hint(pl.sy.P, m, pl.sx.P, n, prob->d, kind, pl.hint_c, pcol, s));
+        // coordinate boxes of the column blocks, from the scaled copies
+        CK(launch_points_qbox(w.PYh, w.ldy, m, prob->d, pl.qbox_r, s));
+        CK(launch_points_qbox(w.PXh, w.ldx, n, prob->d, pl.qbox_c, s));
     }
     CK(launch_init(cv, w, g.vec_grid, ps.a, ps.b, 0, is0, s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));

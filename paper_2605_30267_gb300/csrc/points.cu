@@ -129,22 +129,28 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 //   (R + log2 S) ln 2 - (B_r + shift) / eps_c.
 // PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
 // FP32 estimate of every exponent, for every row of the warp, lies more than
-// kSkipLog2 below the lane's running maximum (a lower bound of the row's) is
-// skipped. Each row's running maximum starts just below its largest term in
+// pv.skip below the lane's running maximum (a lower bound of the row's) is
+// skipped. Before that, whole blocks of 128 columns are tested without
+// loading them (pv.qbox): an upper bound of the block's exponents for a row
+// p is max A + sum_k max(p_k Qmin_k, p_k Qmax_k) over the block's coordinate
+// box, and a block whose bound lies more than pv.skip below the warp's
+// running maximum for every row of the group is passed over; each lane
+// tests one of 32 blocks at a time and the warp works through the others. Each row's running maximum starts just below its largest term in
 // the slot that holds the column nearest to the group's first row (pv.hint,
 // found once per solve from the points alone): the FP32 estimate of that term
 // less the estimate's error bound, which is below an actual term of the row
 // and so still a lower bound of its maximum; far slots are then skipped from
 // the start of the row rather than only once the loop has reached the row's
 // best columns. The hints depend only on the points, so repeated and resumed
-// solves take the same steps bit for bit. Each skipped term is below 2^-64 of its row's sum, so all of a
-// row's skipped terms together stay below 2^-33 (~1e-10) of it for any row
-// length below 2^31: three orders of magnitude below the FP32 passes' own
-// accuracy (~1e-7 in each log-sum-exp). The estimate A_hi + sum_k
-// p_k Q_hi,k differs from the exact exponent by at most ~2^-21 of the terms'
-// magnitude |A| + sum_k |p_k| |Q_k| (four FP32 roundings and the dropped low
-// parts), so the threshold is lowered by 2^-20 of a bound on that magnitude.
-constexpr float kSkipLog2 = 64.0f;
+// solves take the same steps bit for bit. Each skipped term is below
+// 2^-(skip + 1) of its row's largest, and skip = 34 + ceil(log2 nc), so all
+// of a row's skipped terms together stay below 2^-35 (~3e-11) of its sum:
+// three orders of magnitude below the FP32 passes' own accuracy (~1e-7 in
+// each log-sum-exp). The estimate A_hi + sum_k p_k Q_hi,k (and the block
+// bound, with at most nine FP32 roundings for d <= 4) differs from the exact
+// exponent by at most 2^-20 of the terms' magnitude |A| + sum_k |p_k| |Q_k|
+// (the roundings and the dropped low parts, each below 2^-24 of it), so the
+// threshold is lowered by 2^-20 of a bound on that magnitude.
 
 // Running maxima at the start of a row group: every lane evaluates the FP32
 // estimate of the hinted slot hv (the same loads for all lanes) and takes, per
@@ -227,8 +233,8 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                 for (int q = 0; q < RW; ++q) acc[q].R = R0[q];
             }
         }
-        // whole chunks: every element valid
-        for (int v = lane; v < nfull; v += 32) {
+        // whole chunks: every element valid; chunk(v) works on slot v
+        auto chunk = [&](int v) {
             const float4 ah = __ldg(Ah4 + v);
             float4 qh[PRE ? DMAX : 1], ql[PRE ? DMAX : 1];
             if (PRE) {
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 #pragma unroll
                     for (int k = 0; k < DMAX; ++k)
                         if (k < d) mag = fmaf(fabsf(p[q][k]), qmax[k], mag);
-                    const float lim = acc[q].R - kSkipLog2 - 1.0f - mag * 0x1p-20f;
+                    const float lim = acc[q].R - pv.skip - 1.0f - mag * 0x1p-20f;
                     float e4[4] = {ah.x, ah.y, ah.z, ah.w};
 #pragma unroll
                     for (int k = 0; k < DMAX; ++k) {
@@ -264,7 +270,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                     }
                     far = far && fmaxf(fmaxf(e4[0], e4[1]), fmaxf(e4[2], e4[3])) < lim;
                 }
-                if (__all_sync(0xffffffffu, far)) continue;
+                if (__all_sync(0xffffffffu, far)) return;
             }
             float4 al = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!f32) {
@@ -282,6 +288,43 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                 if (WC) slot_cost<DMAX>(p[q], d, pv.kind, cs_scale, pv.Pc, 4 * v, nc, cst);
                 slot_accumulate<WC>(acc[q], cacc[q], h, l, cst);
             }
+        };
+        if (PRUNE && pv.qbox) {
+            const int nb = nfull >> 5;
+            for (int b0 = 0; b0 < nb; b0 += 32) {
+                bool near = false;
+                const int b = b0 + lane;
+                // the warp's running maxima: lower bounds of the rows' largest terms
+                float Rw[RW];
+#pragma unroll
+                for (int q = 0; q < RW; ++q) Rw[q] = warp_max(acc[q].R);
+                if (b < nb) {
+                    const float2 ab = pv.abox[b];
+                    const float4 qlo = pv.qbox[2 * b], qhi = pv.qbox[2 * b + 1];
+                    const float qmn[4] = {qlo.x, qlo.y, qlo.z, qlo.w};
+                    const float qmx[4] = {qhi.x, qhi.y, qhi.z, qhi.w};
+#pragma unroll
+                    for (int q = 0; q < RW; ++q) {
+                        float ub = ab.x, mag = ab.y;
+#pragma unroll
+                        for (int k = 0; k < DMAX; ++k) {
+                            if (k < d) {
+                                ub += fmaxf(p[q][k] * qmn[k], p[q][k] * qmx[k]);
+                                mag = fmaf(fabsf(p[q][k]), fmaxf(fabsf(qmn[k]), fabsf(qmx[k])), mag);
+                            }
+                        }
+                        near = near || !(ub < Rw[q] - pv.skip - 1.0f - mag * 0x1p-20f);
+                    }
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, near);
+                while (mask) {
+                    const int bb = b0 + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    chunk(32 * bb + lane);
+                }
+            }
+        } else {
+            for (int v = lane; v < nfull; v += 32) chunk(v);
         }
         // ragged tail: at most one slot per lane, masked per element
         for (int v = nfull + lane; v < nc4; v += 32) {
@@ -381,9 +424,71 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 template <int DMAX>
 constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 
+// abox[b] = (max, max |.|) of the high parts of A over block b (128 columns,
+// one warp per block). The A of a pass is written by the step kernel (row
+// pass) or by the row pass (column pass), so this runs before every pass.
+__global__ void __launch_bounds__(kPtNT) k_points_abox(const float *Ah, int nb, float2 *abox)
+{
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
+    for (int b = wg; b < nb; b += nw) {
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(Ah) + 32 * b + lane);
+        float mx = fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w));
+        float mg = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+        mx = warp_max(mx);
+        mg = warp_max(mg);
+        if (lane == 0) abox[b] = make_float2(mx, mg);
+    }
+}
+
+// qbox[2 b] / qbox[2 b + 1] = per-coordinate minimum / maximum of block b's
+// Q (coordinates k >= d are 0), one warp per block.
+__global__ void __launch_bounds__(kPtNT) k_points_qbox(const float *Qh, int64_t ldq, int nb,
+                                                       int d, float4 *qbox)
+{
+    const int lane = threadIdx.x & 31;
+    const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
+    for (int b = wg; b < nb; b += nw) {
+        float mn[4] = {0.f, 0.f, 0.f, 0.f}, mx[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < d && k < 4; ++k) {
+            const float4 q = __ldg(reinterpret_cast<const float4 *>(Qh + k * ldq) + 32 * b + lane);
+            float lo = fminf(fminf(q.x, q.y), fminf(q.z, q.w));
+            float hi = fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+                hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+            }
+            mn[k] = lo;
+            mx[k] = hi;
+        }
+        if (lane == 0) {
+            qbox[2 * b] = make_float4(mn[0], mn[1], mn[2], mn[3]);
+            qbox[2 * b + 1] = make_float4(mx[0], mx[1], mx[2], mx[3]);
+        }
+    }
+}
+
+cudaError_t launch_points_qbox(const float *Qh, int64_t ldq, int nc, int d, float4 *qbox,
+                               cudaStream_t s)
+{
+    const int nb = points_blocks(nc);
+    if (nb <= 0) return cudaSuccess;
+    k_points_qbox<<<(nb + 7) / 8, kPtNT, 0, s>>>(Qh, ldq, nb, d, qbox);
+    return cudaGetLastError();
+}
+
 template <int MODE, bool WC>
 static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cudaStream_t s)
 {
+    if (pv.prune && pv.d <= 4 && pv.qbox) {
+        const int nb = points_blocks(pv.nc);
+        if (nb > 0) {
+            k_points_abox<<<(nb + 7) / 8, kPtNT, 0, s>>>(pv.Ah, nb, pv.abox);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
     if (pv.prune && pv.d <= 4 && pv.fp32) {
         // sorted point clouds, FP32 arguments (precision FP32)
         if (pv.d == 2) k_lse_points<MODE, 2, rows_per_warp<2>(), WC, true, true, true><<<grid, kPtNT, 0, s>>>(pv, w);
