@@ -152,6 +152,14 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // (the roundings and the dropped low parts, each below 2^-24 of it), so the
 // threshold is lowered by 2^-20 of a bound on that magnitude.
 
+// The constant c of the squared-Euclidean block bound (see k_points_abox);
+// any c > 0 gives a valid bound, c = 4 k s (Q = 2 k s y) the tightest. The
+// block-record kernel and the passes compute it with the same expression.
+__device__ __forceinline__ float box_cq(const DevState *st, const PointView &pv)
+{
+    return 4.0f * (float)(st->k2 * pv.scal[1]);
+}
+
 // Running maxima at the start of a row group: every lane evaluates the FP32
 // estimate of the hinted slot hv (the same loads for all lanes) and takes, per
 // row, its largest term less the estimate's error bound, which stays below
@@ -291,6 +299,9 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
         };
         if (PRUNE && pv.qbox) {
             const int nb = nfull >> 5;
+            // squared Euclidean: the bound through the box's distance to the rows
+            const float cq = pv.kind == 1 ? box_cq(st, pv) : 1.0f;
+            const bool geo = pv.kind == 1 && cq > 0.0f && cq < FLT_MAX;
             for (int b0 = 0; b0 < nb; b0 += 32) {
                 bool near = false;
                 const int b = b0 + lane;
@@ -305,15 +316,38 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                     const float qmx[4] = {qhi.x, qhi.y, qhi.z, qhi.w};
 #pragma unroll
                     for (int q = 0; q < RW; ++q) {
-                        float ub = ab.x, mag = ab.y;
+                        float ub, mag;
+                        if (geo) {
+                            // max g - |Q - z|^2 / c over the box + |z|^2 / c, z = (c / 2) p;
+                            // the margin covers ~20 roundings of terms below mag
+                            float zz = 0.f, dd = 0.f, qq = 0.f;
 #pragma unroll
-                        for (int k = 0; k < DMAX; ++k) {
-                            if (k < d) {
-                                ub += fmaxf(p[q][k] * qmn[k], p[q][k] * qmx[k]);
-                                mag = fmaf(fabsf(p[q][k]), fmaxf(fabsf(qmn[k]), fabsf(qmx[k])), mag);
+                            for (int k = 0; k < DMAX; ++k) {
+                                if (k < d) {
+                                    const float z = 0.5f * cq * p[q][k];
+                                    const float dq = fmaxf(0.0f, fmaxf(qmn[k] - z, z - qmx[k]));
+                                    const float qa = fmaxf(fabsf(qmn[k]), fabsf(qmx[k]));
+                                    zz = fmaf(z, z, zz);
+                                    dd = fmaf(dq, dq, dd);
+                                    qq = fmaf(qa, qa, qq);
+                                }
                             }
+                            ub = ab.x + (zz - dd) / cq;
+                            mag = ab.y + 2.0f * (zz + qq) / cq;
+                            mag *= 0x1p-18f;
+                        } else {
+                            ub = ab.x;
+                            mag = ab.y;
+#pragma unroll
+                            for (int k = 0; k < DMAX; ++k) {
+                                if (k < d) {
+                                    ub += fmaxf(p[q][k] * qmn[k], p[q][k] * qmx[k]);
+                                    mag = fmaf(fabsf(p[q][k]), fmaxf(fabsf(qmn[k]), fabsf(qmx[k])), mag);
+                                }
+                            }
+                            mag *= 0x1p-20f;
                         }
-                        near = near || !(ub < Rw[q] - pv.skip - 1.0f - mag * 0x1p-20f);
+                        near = near || !(ub < Rw[q] - pv.skip - 1.0f - mag);
                     }
                 }
                 unsigned mask = __ballot_sync(0xffffffffu, near);
@@ -424,20 +458,44 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 template <int DMAX>
 constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 
-// abox[b] = (max, max |.|) of the high parts of A over block b (128 columns,
-// one warp per block). The A of a pass is written by the step kernel (row
-// pass) or by the row pass (column pass), so this runs before every pass.
-__global__ void __launch_bounds__(kPtNT) k_points_abox(const float *Ah, int nb, float2 *abox)
+// abox[b] = (max, max |.|) over block b (128 columns, one warp per block) of
+// the high parts of A, or for squared-Euclidean costs of g_j = A_j +
+// |Q_j|^2 / c and |A_j| + |Q_j|^2 / c: with z = (c / 2) p the exponent of a
+// row p is A_j + p.Q_j = g_j - |Q_j - z|^2 / c + |z|^2 / c for any c > 0, so
+// max g less the box's distance term bounds the block (k G_j less the
+// squared distance, when c = 4 k s). The A of a pass is written by the step
+// kernel (row pass) or by the row pass (column pass), so this runs before
+// every pass.
+__global__ void __launch_bounds__(kPtNT) k_points_abox(PointView pv, const DevState *st, int nb)
 {
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
+    const float cq = pv.kind == 1 ? box_cq(st, pv) : 1.0f;
+    const bool geo = pv.kind == 1 && cq > 0.0f && cq < FLT_MAX;
     for (int b = wg; b < nb; b += nw) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(Ah) + 32 * b + lane);
-        float mx = fmaxf(fmaxf(a.x, a.y), fmaxf(a.z, a.w));
-        float mg = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
+        const int v = 32 * b + lane;
+        const float4 a = __ldg(reinterpret_cast<const float4 *>(pv.Ah) + v);
+        float g[4] = {a.x, a.y, a.z, a.w};
+        float m4[4] = {fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)};
+        if (geo) {
+            float qq[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < pv.d && k < 4; ++k) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * pv.ldq) + v);
+                qq[0] = fmaf(q.x, q.x, qq[0]); qq[1] = fmaf(q.y, q.y, qq[1]);
+                qq[2] = fmaf(q.z, q.z, qq[2]); qq[3] = fmaf(q.w, q.w, qq[3]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float t = qq[e] / cq;
+                g[e] += t;
+                m4[e] += t;
+            }
+        }
+        float mx = fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
+        float mg = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
         mx = warp_max(mx);
         mg = warp_max(mg);
-        if (lane == 0) abox[b] = make_float2(mx, mg);
+        if (lane == 0) pv.abox[b] = make_float2(mx, mg);
     }
 }
 
@@ -484,7 +542,7 @@ static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cuda
     if (pv.prune && pv.d <= 4 && pv.qbox) {
         const int nb = points_blocks(pv.nc);
         if (nb > 0) {
-            k_points_abox<<<(nb + 7) / 8, kPtNT, 0, s>>>(pv.Ah, nb, pv.abox);
+            k_points_abox<<<(nb + 7) / 8, kPtNT, 0, s>>>(pv, w.st, nb);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
