@@ -130,12 +130,14 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
 // FP32 estimate of every exponent, for every row of the warp, lies more than
 // pv.skip below the lane's running maximum (a lower bound of the row's) is
-// skipped. Before that, whole blocks of 128 columns are tested without
-// loading them (pv.qbox): an upper bound of the block's exponents for a row
-// p is max A + sum_k max(p_k Qmin_k, p_k Qmax_k) over the block's coordinate
-// box, and a block whose bound lies more than pv.skip below the warp's
-// running maximum for every row of the group is passed over; each lane
-// tests one of 32 blocks at a time and the warp works through the others. Each row's running maximum starts just below its largest term in
+// skipped. With block records (pv.qbox, sorted solves) whole blocks of 128
+// columns are tested instead, without loading them: an upper bound of the
+// block's exponents for a row p is max A + sum_k max(p_k Qmin_k, p_k Qmax_k)
+// over the block's coordinate box (for squared-Euclidean costs the tighter
+// bound through the box's distance to the row, see k_points_abox), and a
+// block whose bound lies more than pv.skip below the warp's running maximum
+// for every row of the group is passed over; each lane tests one of 32
+// blocks at a time and the warp works through the others. Each row's running maximum starts just below its largest term in
 // the slot that holds the column nearest to the group's first row (pv.hint,
 // found once per solve from the points alone): the FP32 estimate of that term
 // less the estimate's error bound, which is below an actual term of the row
@@ -250,7 +252,10 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                 for (int k = 0; k < DMAX; ++k)
                     if (k < d) qh[k] = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * ldq) + v);
             }
-            if (PRUNE) {
+            if (PRUNE && !pv.qbox) {
+                // the slot test (when no block records: the block test
+                // already passed over the far blocks, and repeating it per
+                // slot cost 6% of the colour solve)
                 float amax = fmaxf(fmaxf(fabsf(ah.x), fabsf(ah.y)), fmaxf(fabsf(ah.z), fabsf(ah.w)));
                 float qmax[DMAX];
 #pragma unroll
