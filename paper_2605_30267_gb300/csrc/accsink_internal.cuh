@@ -156,8 +156,8 @@ struct PointView {
     // pruned passes: log2 of the ratio below a row's largest term under which
     // a term is skipped (see points.cu)
     float skip;
-    // pruned passes, per block of 128 columns (32 float4 slots) of the whole
-    // chunks: qbox[2 b], qbox[2 b + 1] = the minimum and maximum of each of
+    // pruned passes, per block of 64 columns (kBoxSlots float4 slots) of the
+    // whole chunks: qbox[2 b], qbox[2 b + 1] = the minimum and maximum of each of
     // the block's Q coordinates (d <= 4), fixed for the solve; abox[b] = the
     // maximum of the block's A and of |A| (high parts), set before every
     // pass by launch_points_pass. NULL: no block test.
@@ -401,8 +401,11 @@ cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, in
                                 int scale_max, double eps, const Work &w, double *scal,
                                 double *blockmax, int nblk, cudaStream_t s);
 int points_rows_per_warp(int d);
-// Blocks of 128 columns in the whole 32-slot chunks of nc columns.
-inline int points_blocks(int nc) { return nc >> 7; }
+// Block records of the pruned passes cover kBoxSlots float4 slots (64
+// columns) each; the whole 32-slot chunks of nc columns hold
+// points_blocks(nc) of them.
+constexpr int kBoxSlots = 16;
+inline int points_blocks(int nc) { return ((nc >> 2) & ~31) / kBoxSlots; }
 // The per-block coordinate boxes of Q (nc x d SoA with leading dimension
 // ldq, d <= 4) for the block test of the pruned passes.
 cudaError_t launch_points_qbox(const float *Qh, int64_t ldq, int nc, int d, float4 *qbox,

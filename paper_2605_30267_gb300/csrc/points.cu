@@ -130,14 +130,18 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // PRUNE (d <= 4, points sorted along a space-filling curve): a slot whose
 // FP32 estimate of every exponent, for every row of the warp, lies more than
 // pv.skip below the lane's running maximum (a lower bound of the row's) is
-// skipped. With block records (pv.qbox, sorted solves) whole blocks of 128
-// columns are tested instead, without loading them: an upper bound of the
-// block's exponents for a row p is max A + sum_k max(p_k Qmin_k, p_k Qmax_k)
-// over the block's coordinate box (for squared-Euclidean costs the tighter
-// bound through the box's distance to the row, see k_points_abox), and a
-// block whose bound lies more than pv.skip below the warp's running maximum
-// for every row of the group is passed over; each lane tests one of 32
-// blocks at a time and the warp works through the others. Each row's running maximum starts just below its largest term in
+// skipped. With block records (pv.qbox, sorted solves) blocks of 64 columns
+// (kBoxSlots slots) are tested instead, without loading them: an upper bound
+// of the block's exponents for a row p is max A + sum_k max(p_k Qmin_k,
+// p_k Qmax_k) over the block's coordinate box (for squared-Euclidean costs
+// the tighter bound through the box's distance to the row, see
+// k_points_abox), and a block whose bound lies more than pv.skip below the
+// warp's running maximum for every row of the group is passed over; each
+// lane tests one of 32 blocks at a time and the warp then works on the near
+// ones two at a time (half a warp per block, a slot per lane). Blocks of 64
+// columns were faster than blocks of 32 or 128 (colour solve 0.489 s against
+// 0.537 and 0.504 s): smaller boxes prune more but cost more tests.
+// Each row's running maximum starts just below its largest term in
 // the slot that holds the column nearest to the group's first row (pv.hint,
 // found once per solve from the points alone): the FP32 estimate of that term
 // less the estimate's error bound, which is below an actual term of the row
@@ -303,7 +307,8 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
             }
         };
         if (PRUNE && pv.qbox) {
-            const int nb = nfull >> 5;
+            constexpr int S = kBoxSlots, G = 32 / S;   // slots per block, blocks per warp pass
+            const int nb = nfull / S;
             // squared Euclidean: the bound through the box's distance to the rows
             const float cq = pv.kind == 1 ? box_cq(st, pv) : 1.0f;
             const bool geo = pv.kind == 1 && cq > 0.0f && cq < FLT_MAX;
@@ -355,11 +360,15 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                         near = near || !(ub < Rw[q] - pv.skip - 1.0f - mag);
                     }
                 }
+                // the near blocks, G at a time: lane group lane / S takes the
+                // (lane / S)-th remaining one, a slot of it per lane
                 unsigned mask = __ballot_sync(0xffffffffu, near);
                 while (mask) {
-                    const int bb = b0 + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    chunk(32 * bb + lane);
+                    unsigned mine = mask;
+                    for (int i = 0; i < lane / S; ++i) mine &= mine - 1;
+#pragma unroll
+                    for (int i = 0; i < G; ++i) mask &= mask - 1;
+                    if (mine) chunk(S * (b0 + __ffs(mine) - 1) + (lane % S));
                 }
             }
         } else {
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
 template <int DMAX>
 constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 
-// abox[b] = (max, max |.|) over block b (128 columns, one warp per block) of
+// abox[b] = (max, max |.|) over block b (kBoxSlots slots, a lane per slot) of
 // the high parts of A, or for squared-Euclidean costs of g_j = A_j +
 // |Q_j|^2 / c and |A_j| + |Q_j|^2 / c: with z = (c / 2) p the exponent of a
 // row p is A_j + p.Q_j = g_j - |Q_j - z|^2 / c + |z|^2 / c for any c > 0, so
@@ -477,14 +486,18 @@ __global__ void __launch_bounds__(kPtNT) k_points_abox(PointView pv, const DevSt
     const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
     const float cq = pv.kind == 1 ? box_cq(st, pv) : 1.0f;
     const bool geo = pv.kind == 1 && cq > 0.0f && cq < FLT_MAX;
-    for (int b = wg; b < nb; b += nw) {
-        const int v = 32 * b + lane;
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(pv.Ah) + v);
+    constexpr int S = kBoxSlots;
+    for (int b0 = wg * (32 / S); b0 < nb; b0 += nw * (32 / S)) {
+        const int b = b0 + lane / S;
+        const int v = S * b + lane % S;
+        const bool have = b < nb;
+        const float4 a = have ? __ldg(reinterpret_cast<const float4 *>(pv.Ah) + v)
+                              : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
         float g[4] = {a.x, a.y, a.z, a.w};
         float m4[4] = {fabsf(a.x), fabsf(a.y), fabsf(a.z), fabsf(a.w)};
         if (geo) {
             float qq[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int k = 0; k < pv.d && k < 4; ++k) {
+            for (int k = 0; k < pv.d && k < 4 && have; ++k) {
                 const float4 q = __ldg(reinterpret_cast<const float4 *>(pv.Qh + k * pv.ldq) + v);
                 qq[0] = fmaf(q.x, q.x, qq[0]); qq[1] = fmaf(q.y, q.y, qq[1]);
                 qq[2] = fmaf(q.z, q.z, qq[2]); qq[3] = fmaf(q.w, q.w, qq[3]);
@@ -497,35 +510,45 @@ __global__ void __launch_bounds__(kPtNT) k_points_abox(PointView pv, const DevSt
             }
         }
         float mx = fmaxf(fmaxf(g[0], g[1]), fmaxf(g[2], g[3]));
-        float mg = fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3]));
-        mx = warp_max(mx);
-        mg = warp_max(mg);
-        if (lane == 0) pv.abox[b] = make_float2(mx, mg);
+        float mg = have ? fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])) : 0.0f;
+#pragma unroll
+        for (int o = S / 2; o > 0; o >>= 1) {
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            mg = fmaxf(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+        }
+        if (have && lane % S == 0) pv.abox[b] = make_float2(mx, mg);
     }
 }
 
 // qbox[2 b] / qbox[2 b + 1] = per-coordinate minimum / maximum of block b's
-// Q (coordinates k >= d are 0), one warp per block.
+// Q (coordinates k >= d are 0), a lane per slot.
 __global__ void __launch_bounds__(kPtNT) k_points_qbox(const float *Qh, int64_t ldq, int nb,
                                                        int d, float4 *qbox)
 {
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
-    for (int b = wg; b < nb; b += nw) {
+    constexpr int S = kBoxSlots;
+    for (int b0 = wg * (32 / S); b0 < nb; b0 += nw * (32 / S)) {
+        const int b = b0 + lane / S;
+        const bool have = b < nb;
         float mn[4] = {0.f, 0.f, 0.f, 0.f}, mx[4] = {0.f, 0.f, 0.f, 0.f};
         for (int k = 0; k < d && k < 4; ++k) {
-            const float4 q = __ldg(reinterpret_cast<const float4 *>(Qh + k * ldq) + 32 * b + lane);
-            float lo = fminf(fminf(q.x, q.y), fminf(q.z, q.w));
-            float hi = fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w));
+            float lo = INFINITY, hi = -INFINITY;
+            if (have) {
+                const float4 q =
+                    __ldg(reinterpret_cast<const float4 *>(Qh + k * ldq) + S * b + lane % S);
+                lo = fminf(fminf(q.x, q.y), fminf(q.z, q.w));
+                hi = fmaxf(fmaxf(q.x, q.y), fmaxf(q.z, q.w));
+            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+            for (int o = S / 2; o > 0; o >>= 1) {
                 lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
                 hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
             }
             mn[k] = lo;
             mx[k] = hi;
         }
-        if (lane == 0) {
+        if (have && lane % S == 0) {
             qbox[2 * b] = make_float4(mn[0], mn[1], mn[2], mn[3]);
             qbox[2 * b + 1] = make_float4(mx[0], mx[1], mx[2], mx[3]);
         }
@@ -537,7 +560,8 @@ cudaError_t launch_points_qbox(const float *Qh, int64_t ldq, int nc, int d, floa
 {
     const int nb = points_blocks(nc);
     if (nb <= 0) return cudaSuccess;
-    k_points_qbox<<<(nb + 7) / 8, kPtNT, 0, s>>>(Qh, ldq, nb, d, qbox);
+    const int per_cta = (kPtNT / 32) * (32 / kBoxSlots);
+    k_points_qbox<<<(nb + per_cta - 1) / per_cta, kPtNT, 0, s>>>(Qh, ldq, nb, d, qbox);
     return cudaGetLastError();
 }
 
@@ -547,7 +571,8 @@ static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cuda
     if (pv.prune && pv.d <= 4 && pv.qbox) {
         const int nb = points_blocks(pv.nc);
         if (nb > 0) {
-            k_points_abox<<<(nb + 7) / 8, kPtNT, 0, s>>>(pv, w.st, nb);
+            const int per_cta = (kPtNT / 32) * (32 / kBoxSlots);
+            k_points_abox<<<(nb + per_cta - 1) / per_cta, kPtNT, 0, s>>>(pv, w.st, nb);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }
@@ -800,8 +825,8 @@ cudaError_t launch_points_setup(const float *X, const float *Y, int n, int m, in
 
 // ------------------------------------------------------------------------
 // Spatial sort of a point cloud (set-up of a solve). The pruned passes skip
-// a warp's slot only when all of its 128 columns are far from all of its
-// rows, which happens for most slots once nearby points are adjacent: the
+// a block of columns only when all of its columns are far from all of a
+// warp's rows, which happens for most blocks once nearby points are adjacent: the
 // clouds are put in Hilbert-curve order of their first min(d, 3) coordinates
 // over the bounding box (10 bits per coordinate). A Hilbert curve has no
 // long jumps between consecutive cells, so fewer slots straddle near and far
