@@ -369,6 +369,10 @@ cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int
                                        const Work &w, int grid, const RowSplit &sp,
                                        cudaStream_t s);
 cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaStream_t s);
+// The transposed copy and the cost statistics of k_cost_stats in one read of
+// C (cv.vec only): `grid` CTAs, each writing its partial to w.statpart.
+cudaError_t launch_transpose_stats(const CostView &cv, float *CT, int64_t ldct, const Work &w,
+                                   int grid, cudaStream_t s);
 // Which kernel serves 128-bit-aligned row passes: 0 warp-per-row, 1 TMA.
 int row_kernel_choice();
 int occupancy_col_pass(int vec);

@@ -526,10 +526,14 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     CK(set_state(ctx, hs, s));
     k_set_table<<<1, 128, 0, s>>>(tab, const_cast<double *>(w.stage_table));
     CK(cudaGetLastError());
-    CK(launch_cost_stats(cv, w, g.stat_grid, s));
+    // the cost statistics the init kernel needs, and C^T, in one read of C
+    // when C is 16-byte aligned
+    const bool fused = ct && cv.vec;
+    if (fused) CK(launch_transpose_stats(cv, ctx->ct, ct_ld(n), w, g.stat_grid, s));
+    else CK(launch_cost_stats(cv, w, g.stat_grid, s));
     CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE,
                    start ? start->is : InitState(), s));
-    if (ct) CK(launch_transpose(cv, ctx->ct, ct_ld(n), s));
+    if (ct && !fused) CK(launch_transpose(cv, ctx->ct, ct_ld(n), s));
     CK(cudaMemcpyAsync(ctx->h_state, w.st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (ctx->h_state->done) {

@@ -26,6 +26,7 @@
 // finish merges the parts in part order (merge_parts), so the result does not
 // depend on the order in which they finished.
 #include <algorithm>
+#include <cfloat>
 #include <cstdint>
 
 #include "accsink_internal.cuh"
@@ -484,6 +485,104 @@ __global__ void k_transpose(const float *__restrict__ C, int64_t ldc, int n, int
         const int j = j0 + ty + k, i = i0 + tx;
         if (i < n && j < m) CT[(int64_t)j * ldct + i] = tile[tx][ty + k];
     }
+}
+
+// C^T and the cost statistics (max C, min C, max |C|, count of non-finite
+// entries over the finite ones, as k_cost_stats) in one read of C, for a
+// 16-byte-aligned C with ldc % 4 == 0. Each CTA walks 64 x 64 tiles (row-major
+// tile order, grid-stride): 128-bit loads of the tile into shared memory
+// (4 per thread), then 128-bit stores of its transpose, each gathered from a
+// shared-memory column; the CTA's statistics go to statpart[4 blockIdx.x ..].
+// Entries of a stored float4 past n (the padding of a C^T row) are zero; a
+// row's columns past m (ldc > m) are loaded but neither counted nor stored.
+__global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict__ C, int64_t ldc,
+                                                         int n, int m,
+                                                         float *__restrict__ CT, int64_t ldct,
+                                                         double *statpart)
+{
+    constexpr int T = 64;
+    __shared__ float tile[T][T + 1];
+    const int tid = threadIdx.x;
+    const int tr = tid >> 4, tc = tid & 15;       // 16 threads per 64-float row segment
+    const int tiles_j = (m + T - 1) / T;
+    const int64_t ntiles = (int64_t)((n + T - 1) / T) * tiles_j;
+    float mx = -FLT_MAX, mn = FLT_MAX, ab = 0.0f;
+    int bad = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+        float4 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + tr + 16 * r, j = j0 + 4 * tc;
+            v[r] = (i < n && j < m) ? ld_stream4(C + (int64_t)i * ldc + j)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n && j < m) {
+                const float e[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j + q >= m) continue;        // the row's padding (ldc > m)
+                    if (!isfinite(e[q])) { ++bad; continue; }
+                    mx = fmaxf(mx, e[q]);
+                    mn = fminf(mn, e[q]);
+                    ab = fmaxf(ab, fabsf(e[q]));
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float *row = tile[tr + 16 * r];
+            row[4 * tc + 0] = v[r].x;
+            row[4 * tc + 1] = v[r].y;
+            row[4 * tc + 2] = v[r].z;
+            row[4 * tc + 3] = v[r].w;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int jl = tr + 16 * r, il = 4 * tc;
+            const int j = j0 + jl, i = i0 + il;
+            if (j < m && i < n) {
+                float4 o;
+                o.x = tile[il + 0][jl];
+                o.y = (i + 1 < n) ? tile[il + 1][jl] : 0.0f;
+                o.z = (i + 2 < n) ? tile[il + 2][jl] : 0.0f;
+                o.w = (i + 3 < n) ? tile[il + 3][jl] : 0.0f;
+                *reinterpret_cast<float4 *>(CT + (int64_t)j * ldct + i) = o;
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ float s_mx[8], s_mn[8], s_ab[8];
+    __shared__ int s_bad[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        ab = fmaxf(ab, __shfl_xor_sync(0xffffffffu, ab, o));
+        bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) { s_mx[wid] = mx; s_mn[wid] = mn; s_ab[wid] = ab; s_bad[wid] = bad; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int q = 1; q < 8; ++q) {
+            mx = fmaxf(mx, s_mx[q]); mn = fminf(mn, s_mn[q]);
+            ab = fmaxf(ab, s_ab[q]); bad += s_bad[q];
+        }
+        statpart[4 * blockIdx.x + 0] = mx;
+        statpart[4 * blockIdx.x + 1] = mn;
+        statpart[4 * blockIdx.x + 2] = ab;
+        statpart[4 * blockIdx.x + 3] = bad;
+    }
+}
+
+cudaError_t launch_transpose_stats(const CostView &cv, float *CT, int64_t ldct, const Work &w,
+                                   int grid, cudaStream_t s)
+{
+    if (!cv.vec) return cudaErrorInvalidValue;
+    k_transpose_stats<<<std::max(1, grid), 256, 0, s>>>(cv.C, cv.ldc, cv.n, cv.m, CT, ldct,
+                                                        w.statpart);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaStream_t s)

@@ -313,6 +313,42 @@ def test_solve_host_matches_device_solve(ctx):
 
 # ------------------------------------------------------------- errors ----
 
+def test_fused_transpose_statistics_ignore_row_padding(ctx):
+    """A 16-byte-aligned C whose rows are padded (ldc = m + 3, m % 4 == 1) goes
+    through the one-read transpose and statistics. The padding is not part of
+    the problem: with NaN, +1e9 or -1e9 in it the solve succeeds, reports
+    max C of the problem, and gives the same potentials bit for bit. A NaN
+    inside the problem is still found."""
+    n, m = 257, 1001
+    C, a, b = rand_dense(41, n, m)
+    ad, bd = to_dev(a), to_dev(b)
+    p = B.default_params(eps=1e-2, tol=1e-6)
+    out = []
+    for pad in (float("nan"), 1e9, -1e9):
+        big = torch.full((n, m + 3), pad, dtype=torch.float32, device=DEV)
+        big[:, :m] = to_dev(C)
+        Cpad = big[:, :m]
+        assert Cpad.stride(0) == m + 3 and Cpad.data_ptr() % 16 == 0
+        f = torch.empty(n, dtype=torch.float64, device=DEV)
+        g = torch.empty(m, dtype=torch.float64, device=DEV)
+        r = ctx.accsink_solve(B.problem_dense(Cpad, ad, bd), p, f, g)
+        torch.cuda.synchronize()
+        assert r.status == 0 and r.cost_max == float(C.max()), (pad, r.status, r.cost_max)
+        out.append((f.cpu().numpy(), g.cpu().numpy(), r.sinkhorn_steps))
+    for f, g, st in out[1:]:
+        assert st == out[0][2]
+        np.testing.assert_array_equal(f, out[0][0])
+        np.testing.assert_array_equal(g, out[0][1])
+    Cn = C[:, :1000].copy()
+    Cn[7, 999] = np.nan
+    bn = W.dirichlet1(np.random.default_rng(3), 1000)
+    with pytest.raises(B.AccsinkError) as e:
+        ctx.accsink_solve(B.problem_dense(to_dev(Cn), ad, to_dev(bn)), p,
+                          torch.empty(n, dtype=torch.float64, device=DEV),
+                          torch.empty(1000, dtype=torch.float64, device=DEV))
+    assert e.value.code == B.ERR_NONFINITE
+
+
 def test_invalid_inputs_are_rejected(ctx):
     C, a, b = rand_dense(1, 20, 30)
     Cd, ad, bd = to_dev(C), to_dev(a), to_dev(b)
