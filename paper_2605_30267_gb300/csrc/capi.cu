@@ -166,7 +166,9 @@ Geometry geometry(const accsink_ctx *ctx, int n, int m, int vec)
 {
     Geometry g;
     const int S = ctx->num_sms;
-    g.stat_grid = std::max(1, std::min(n, 4 * S));
+    // eight CTAs per SM for the statistics (with the transposed copy: one read
+    // of C); the workspace's statpart holds one 32-byte partial per CTA of 8 S
+    g.stat_grid = std::max(1, std::min(n, 8 * S));
     g.rsplit = RowSplit();
     if (vec && row_kernel_choice() == 1) {
         // TMA row pass: one CTA per SM
@@ -246,7 +248,7 @@ int ensure_workspace(accsink_ctx *ctx, int n, int m, int splits, int row_grid, i
         (size_t)SP * (size_t)M * 8,                                            // colpart
         (size_t)RG * 16,                                                       // rowpart
         (size_t)std::max(S, 1) * kPartStride * 8,                              // steppart
-        (size_t)4 * S * 32,                                                    // statpart
+        (size_t)8 * S * 32,                                                    // statpart
         (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8, (size_t)std::max(H, 1) * 8,
         (size_t)std::max(H, 1) * 32, (size_t)std::max(H, 1) * 4,               // history
         (size_t)kMaxStages * kStageSlots * 8,                                  // stage table

@@ -508,14 +508,22 @@ __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict
     const int64_t ntiles = (int64_t)((n + T - 1) / T) * tiles_j;
     float mx = -FLT_MAX, mn = FLT_MAX, ab = 0.0f;
     int bad = 0;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // tile t's four float4 of this thread (zeros outside C), and the
+    // statistics of the ones inside
+    auto load = [&](int64_t t, float4 (&v)[4]) {
         const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
-        float4 v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = i0 + tr + 16 * r, j = j0 + 4 * tc;
             v[r] = (i < n && j < m) ? ld_stream4(C + (int64_t)i * ldc + j)
                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto visit = [&](int64_t t, const float4 (&v)[4]) {
+        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = i0 + tr + 16 * r, j = j0 + 4 * tc;
             if (i < n && j < m) {
                 const float e[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
 #pragma unroll
@@ -528,6 +536,13 @@ __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict
                 }
             }
         }
+    };
+    float4 v[4];
+    int64_t t = blockIdx.x;
+    if (t < ntiles) load(t, v);
+    for (; t < ntiles; t += gridDim.x) {
+        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+        visit(t, v);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             float *row = tile[tr + 16 * r];
@@ -537,6 +552,8 @@ __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict
             row[4 * tc + 3] = v[r].w;
         }
         __syncthreads();
+        // the next tile's loads go out before this tile's stores
+        if (t + gridDim.x < ntiles) load(t + gridDim.x, v);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int jl = tr + 16 * r, il = 4 * tc;
