@@ -163,6 +163,11 @@ struct PointView {
     // pass by launch_points_pass. NULL: no block test.
     const float4 *qbox;
     float2 *abox;
+    // pruned passes without the cost sum: row groups are taken from this
+    // counter (zeroed by the block-record kernel before every pass) instead of
+    // dealt round-robin, so warps whose rows prune well take more of them.
+    // NULL: round-robin.
+    unsigned int *next_group;
 };
 
 struct CostView {

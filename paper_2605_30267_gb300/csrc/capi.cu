@@ -635,6 +635,7 @@ struct PointPlan {
     int32_t *hint_r = nullptr, *hint_c = nullptr;   // slot hints (sorted solves)
     float4 *qbox_r = nullptr, *qbox_c = nullptr;     // block boxes (sorted solves)
     float2 *abox_r = nullptr, *abox_c = nullptr;
+    unsigned int *next_group = nullptr;              // row-group counters (sorted solves)
 };
 
 int points_grid(const accsink_ctx *ctx, int n_rows, int d)
@@ -689,6 +690,7 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
         sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(n) * 32));
         sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(m) * 8));
         sizes.push_back(std::max<size_t>(16, (size_t)points_blocks(n) * 8));
+        sizes.push_back(16);   // row-group counters of the two pruned passes
     }
     size_t need = 0;
     for (size_t z : sizes) need += align_up(z, 256);
@@ -740,6 +742,7 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
         pl.qbox_c = (float4 *)take();
         pl.abox_r = (float2 *)take();
         pl.abox_c = (float2 *)take();
+        pl.next_group = (unsigned int *)take();
     }
     w.ldx = ldx;
     w.ldy = ldy;
@@ -765,6 +768,8 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     pc.qbox = pl.sorted ? pl.qbox_c : nullptr;
     pr.abox = pl.sorted ? pl.abox_r : nullptr;
     pc.abox = pl.sorted ? pl.abox_c : nullptr;
+    pr.next_group = pl.sorted ? pl.next_group : nullptr;
+    pc.next_group = pl.sorted ? pl.next_group + 1 : nullptr;
     return ACCSINK_OK;
 }
 

@@ -224,7 +224,21 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
     const float4 *Al4 = reinterpret_cast<const float4 *>(pv.Al);
 
     double my_dual = 0.0, my_cost = 0.0;
-    for (int r0 = gwarp * RW; r0 < nr; r0 += nwarps * RW) {
+    // row groups dealt round-robin, or taken from the counter (the next
+    // group's number is fetched while this one is worked on); each group's
+    // rows are reduced the same way whichever warp takes them, and the
+    // with-cost pass, whose per-warp sums must not depend on the order,
+    // stays round-robin
+    const bool dyn = PRUNE && !WC && pv.next_group != nullptr;
+    int r0 = gwarp * RW;
+    if (dyn) {
+        unsigned g0 = 0;
+        if (lane == 0) g0 = atomicAdd(pv.next_group, 1u);
+        r0 = (int)__shfl_sync(0xffffffffu, g0, 0) * RW;
+    }
+    while (r0 < nr) {
+        unsigned gnext = 0;
+        if (dyn && lane == 0) gnext = atomicAdd(pv.next_group, 1u);
         float p[RW][DMAX];
 #pragma unroll
         for (int q = 0; q < RW; ++q) {
@@ -451,6 +465,8 @@ __global__ void __launch_bounds__(kPtNT) k_lse_points(PointView pv, Work w)
                 }
             }
         }
+        if (dyn) r0 = (int)__shfl_sync(0xffffffffu, gnext, 0) * RW;
+        else r0 += nwarps * RW;
     }
     if (MODE == 1) return;
     __shared__ double sh[2][kPtNT / 32];
@@ -482,6 +498,7 @@ constexpr int rows_per_warp() { return DMAX <= 8 ? 4 : (DMAX <= 16 ? 2 : 1); }
 // every pass.
 __global__ void __launch_bounds__(kPtNT) k_points_abox(PointView pv, const DevState *st, int nb)
 {
+    if (pv.next_group && blockIdx.x == 0 && threadIdx.x == 0) *pv.next_group = 0u;
     const int lane = threadIdx.x & 31;
     const int wg = (blockIdx.x * kPtNT + threadIdx.x) >> 5, nw = (gridDim.x * kPtNT) >> 5;
     const float cq = pv.kind == 1 ? box_cq(st, pv) : 1.0f;
@@ -569,13 +586,12 @@ template <int MODE, bool WC>
 static cudaError_t launch_pts(const PointView &pv, const Work &w, int grid, cudaStream_t s)
 {
     if (pv.prune && pv.d <= 4 && pv.qbox) {
+        // block records and the row-group counter, before every pruned pass
         const int nb = points_blocks(pv.nc);
-        if (nb > 0) {
-            const int per_cta = (kPtNT / 32) * (32 / kBoxSlots);
-            k_points_abox<<<(nb + per_cta - 1) / per_cta, kPtNT, 0, s>>>(pv, w.st, nb);
-            const cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        }
+        const int per_cta = (kPtNT / 32) * (32 / kBoxSlots);
+        k_points_abox<<<std::max(1, (nb + per_cta - 1) / per_cta), kPtNT, 0, s>>>(pv, w.st, nb);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
     }
     if (pv.prune && pv.d <= 4 && pv.fp32) {
         // sorted point clouds, FP32 arguments (precision FP32)
