@@ -384,6 +384,8 @@ int occupancy_col_pass(int vec);
 cudaError_t launch_points_pass(const PointView &pv, const Work &w, int grid, int mode,
                                bool with_cost, cudaStream_t s);
 int occupancy_points_pass();
+// CTAs per SM of the pruned pass kernel for dimension d <= 4.
+int occupancy_points_pruned(int d);
 // Spatial sort of one point cloud: buffers in the solve's point workspace.
 // P (n x d) and a (n) receive the cloud and its marginal in Hilbert-curve order;
 // perm[i] is the original index of sorted point i.

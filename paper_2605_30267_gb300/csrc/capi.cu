@@ -665,6 +665,17 @@ int points_plan(accsink_ctx *ctx, const accsink_problem *prob, int hist, PointPl
     pl.g = geometry(ctx, n, m, 1);
     pl.prow = points_grid(ctx, n, d);
     pl.pcol = points_grid(ctx, m, d);
+    if (pl.sorted) {
+        // the pruned passes take row groups from a counter, so every
+        // resident CTA is launched (at least one group of four rows per warp)
+        const int64_t full = (int64_t)ctx->num_sms * occupancy_points_pruned(d);
+        auto dyn_grid = [&](int rows) {
+            const int64_t groups = (rows + 3) / 4;
+            return (int)std::max<int64_t>(1, std::min(full, (groups + 7) / 8));
+        };
+        pl.prow = dyn_grid(n);
+        pl.pcol = dyn_grid(m);
+    }
     int rc = ensure_workspace(ctx, n, m, 1, pl.prow, hist);
     if (rc != ACCSINK_OK) return rc;
     const int64_t ldx = (n + 3) / 4 * 4, ldy = (m + 3) / 4 * 4;

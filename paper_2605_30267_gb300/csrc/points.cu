@@ -634,6 +634,15 @@ int occupancy_points_pass()
     return b > 0 ? b : 1;
 }
 
+int occupancy_points_pruned(int d)
+{
+    int b = 0;
+    if (d == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lse_points<0, 2, 4, false, true, true>, kPtNT, 0);
+    else if (d == 3) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lse_points<0, 3, 4, false, true, true>, kPtNT, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_lse_points<0, 4, 4, false, true, true>, kPtNT, 0);
+    return b > 0 ? b : 1;
+}
+
 int points_rows_per_warp(int d)
 {
     return d <= 8 ? rows_per_warp<4>() : (d <= 16 ? rows_per_warp<16>() : rows_per_warp<64>());
