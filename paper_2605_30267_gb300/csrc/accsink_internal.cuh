@@ -423,12 +423,12 @@ cudaError_t launch_points_qbox(const float *Qh, int64_t ldq, int nc, int d, floa
                                cudaStream_t s);
 // log2 threshold of the pruned passes for rows of nc terms: every skipped
 // term is below 2^-(skip + 1) of its row's largest, so all of a row's
-// skipped terms together stay below 2^-35 of its sum.
+// skipped terms together stay below 2^-30 of its sum.
 inline float points_skip_log2(int nc)
 {
     int l = 0;
     while ((1ll << l) < (long long)nc) ++l;
-    return (float)(34 + l);
+    return (float)(29 + l);
 }
 void setup_col_pass();
 

@@ -149,9 +149,9 @@ __device__ __forceinline__ void slot_cost(const float *p, int d, int kind, float
 // the start of the row rather than only once the loop has reached the row's
 // best columns. The hints depend only on the points, so repeated and resumed
 // solves take the same steps bit for bit. Each skipped term is below
-// 2^-(skip + 1) of its row's largest, and skip = 34 + ceil(log2 nc), so all
-// of a row's skipped terms together stay below 2^-35 (~3e-11) of its sum:
-// three orders of magnitude below the FP32 passes' own accuracy (~1e-7 in
+// 2^-(skip + 1) of its row's largest, and skip = 29 + ceil(log2 nc), so all
+// of a row's skipped terms together stay below 2^-30 (~1e-9) of its sum:
+// two orders of magnitude below the FP32 passes' own accuracy (~1e-7 in
 // each log-sum-exp). The estimate A_hi + sum_k p_k Q_hi,k (and the block
 // bound, with at most nine FP32 roundings for d <= 4) differs from the exact
 // exponent by at most 2^-20 of the terms' magnitude |A| + sum_k |p_k| |Q_k|
