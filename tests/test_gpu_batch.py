@@ -304,6 +304,19 @@ def test_split_step_matches_oracle(ctx):
         check_against_oracle(p, f, g, r)
 
 
+def test_large_dimension_points_match_oracle(ctx):
+    """Point clouds above the tensor-core range and at the dimension limit
+    (d = 481 and 4096) form their costs with the CUDA-core expansion; each
+    problem meets the oracle."""
+    probs = [Prob("cosine", 40, 37, 71, 1e-2, d=481),
+             Prob("sqeuclid", 20, 30, 72, 1e-2, d=4096, scale=True),
+             Prob("cosine", 25, 50, 73, 2e-2, d=4096)]
+    fs, gs, rs = run_batch(ctx, probs)
+    for p, f, g, r in zip(probs, fs, gs, rs):
+        assert r["loop_mode"] == 2
+        check_against_oracle(p, f, g, r)
+
+
 def test_graph_replay_equals_direct_launches(ctx):
     """The batch's launch sequence replayed as a CUDA graph (the default; the
     second run updates the executable graph in place, a batch of another
@@ -464,3 +477,13 @@ def test_lone_dense_problem_takes_the_single_solve_path(ctx):
     q = mixed_problems()[4]
     _, _, r3 = run_batch(ctx, [q])
     assert r3[0]["loop_mode"] == 2
+    # the autotuner on a batch whose only problem leaves the batched launch:
+    # solved once, nothing left to time, the outputs still the single solve's
+    fa = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    ga = torch.empty(p.m, dtype=torch.float64, device=DEV)
+    best, times = ctx.accsink_batch_autotune([p.struct()], [p.params()], [fa], [ga])
+    torch.cuda.synchronize()
+    assert len(times) == 18 and all(t == 0.0 for t in times)
+    np.testing.assert_array_equal(fa.cpu().numpy(), f1)
+    np.testing.assert_array_equal(ga.cpu().numpy(), g1)
+    ctx.accsink_batch_set_config()
