@@ -375,9 +375,12 @@ cudaError_t launch_col_pass_transposed(const float *CT, int64_t ldct, int n, int
                                        cudaStream_t s);
 cudaError_t launch_transpose(const CostView &cv, float *CT, int64_t ldct, cudaStream_t s);
 // The transposed copy and the cost statistics of k_cost_stats in one read of
-// C (cv.vec only): `grid` CTAs, each writing its partial to w.statpart.
+// C (cv.vec only): `grid` CTAs, each writing its partial to
+// w.statpart[part0 + blockIdx.x]; only rows [r0, r1) of C (r0 a multiple of
+// 64, r1 a multiple of 64 or n; r1 = -1: n).
 cudaError_t launch_transpose_stats(const CostView &cv, float *CT, int64_t ldct, const Work &w,
-                                   int grid, cudaStream_t s);
+                                   int grid, cudaStream_t s, int r0 = 0, int r1 = -1,
+                                   int part0 = 0);
 // Which kernel serves 128-bit-aligned row passes: 0 warp-per-row, 1 TMA.
 int row_kernel_choice();
 int occupancy_col_pass(int vec);

@@ -73,6 +73,9 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+// Row chunks of the overlapped host upload (accsink_solve_host).
+constexpr int kUploadChunks = 8;
+
 struct accsink_ctx {
     int device = 0;
     size_t budget = 0;
@@ -100,6 +103,9 @@ struct accsink_ctx {
     cudaGraphExec_t exec = nullptr;
     GraphKey key;
     cudaStream_t cap_stream = nullptr;
+    // overlapped upload of accsink_solve_host: copy stream and chunk events
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t up_ev[kUploadChunks + 1] = {};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int last_hist_count = 0;
     bool graph_broken = false;
@@ -488,9 +494,11 @@ void keep_state(accsink_ctx *ctx, const DevState &fs, int m, const accsink_param
 }
 
 // Core solve with device pointers, run on stream s. Fills res.
+// prepared_nstat > 0: C^T and the cost statistics (that many partials) were
+// already written on s (accsink_solve_host's overlapped upload).
 int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_params *prm,
                  cudaStream_t s, double *f_out, double *g_out, accsink_result *res,
-                 const SolveStart *start = nullptr)
+                 const SolveStart *start = nullptr, int prepared_nstat = 0)
 {
     const CostView cv = make_view(prob);
     const int n = prob->n, m = prob->m;
@@ -531,7 +539,8 @@ int solve_device(accsink_ctx *ctx, const accsink_problem *prob, const accsink_pa
     // the cost statistics the init kernel needs, and C^T, in one read of C
     // when C is 16-byte aligned
     const bool fused = ct && cv.vec;
-    if (fused) CK(launch_transpose_stats(cv, ctx->ct, ct_ld(n), w, g.stat_grid, s));
+    if (prepared_nstat > 0 && fused) w.nstat = prepared_nstat;   // written by the caller
+    else if (fused) CK(launch_transpose_stats(cv, ctx->ct, ct_ld(n), w, g.stat_grid, s));
     else CK(launch_cost_stats(cv, w, g.stat_grid, s));
     CK(launch_init(cv, w, g.vec_grid, prob->a, prob->b, prob->cost_scale == ACCSINK_SCALE_MAX_TO_ONE,
                    start ? start->is : InitState(), s));
@@ -1109,6 +1118,9 @@ void accsink_destroy(accsink_ctx *ctx)
     if (ctx->h_rowpart) cudaFreeHost(ctx->h_rowpart);
     if (ctx->h_state) cudaFreeHost(ctx->h_state);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->up_ev)
+        if (e) cudaEventDestroy(e);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
@@ -1276,6 +1288,56 @@ int accsink_warm_start(accsink_ctx *ctx, const accsink_problem *prob, const accs
     return run_solve(ctx, prob, params, stream, f_out, g_out, res, st);
 }
 
+namespace {
+
+// Uploads a dense host cost into pd->C (the device staging buffer, row
+// stride pd->ldc) in row chunks on a copy stream, and writes C^T and the
+// cost statistics of each chunk on s as soon as it has landed, so the one
+// read of C they need overlaps with the rest of the upload. Only where the
+// solve would take that fused path (a transposed copy, 16-byte rows);
+// returns the number of statistics partials written, 0 when it did nothing
+// (the caller uploads C whole), or -1 on a CUDA error.
+int upload_dense_overlapped(accsink_ctx *ctx, const accsink_problem *pd, const float *C_host,
+                            const accsink_params *prm, cudaStream_t s)
+{
+    const CostView cv = make_view(pd);
+    const int n = pd->n, m = pd->m;
+    if (!cv.vec || !prm->col_transpose || n < 2 * 64) return 0;
+    const Geometry g = geometry(ctx, n, m, cv.vec);
+    if (ensure_workspace(ctx, n, m, g.splits, g.row_grid, prm->history, g.units) != ACCSINK_OK)
+        return 0;
+    if (!ensure_ct(ctx, n, m)) return 0;
+    if (!ctx->copy_stream &&
+        cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return -1;
+    for (cudaEvent_t &e : ctx->up_ev)
+        if (!e && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return -1;
+    const int grid = std::max(1, g.stat_grid / kUploadChunks);
+    const int rows = (int)(((n + kUploadChunks - 1) / kUploadChunks + 63) / 64 * 64);
+    const int64_t ldc = cv.ldc;
+    // the staging buffer may still be read by earlier work on s
+    if (cudaEventRecord(ctx->up_ev[kUploadChunks], s) != cudaSuccess ||
+        cudaStreamWaitEvent(ctx->copy_stream, ctx->up_ev[kUploadChunks], 0) != cudaSuccess)
+        return -1;
+    const Work w = ctx->w;
+    int parts = 0;
+    for (int c = 0, r0 = 0; r0 < n; ++c, r0 += rows) {
+        const int r1 = std::min(n, r0 + rows);
+        const size_t off = (size_t)r0 * (size_t)ldc;
+        const size_t cnt = (size_t)(r1 - 1 - r0) * (size_t)ldc + (size_t)m;
+        if (cudaMemcpyAsync(const_cast<float *>(pd->C) + off, C_host + off, cnt * sizeof(float),
+                            cudaMemcpyHostToDevice, ctx->copy_stream) != cudaSuccess ||
+            cudaEventRecord(ctx->up_ev[c], ctx->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s, ctx->up_ev[c], 0) != cudaSuccess ||
+            launch_transpose_stats(cv, ctx->ct, ct_ld(n), w, grid, s, r0, r1, parts) != cudaSuccess)
+            return -1;
+        parts += grid;
+    }
+    return parts;
+}
+
+}  // namespace
+
 int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
                        const accsink_params *params, void *stream, double *f_out_host,
                        double *g_out_host, accsink_result *res)
@@ -1322,10 +1384,16 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
     double *dg = (double *)p;
     cudaStream_t s = (cudaStream_t)stream;
     accsink_problem pd = *prob_host;
+    int prepared = 0;
     if (dense) {
-        CK(cudaMemcpyAsync(dC, prob_host->C, cbytes, cudaMemcpyHostToDevice, s));
         pd.C = dC;
         pd.ldc = ldc;
+        prepared = upload_dense_overlapped(ctx, &pd, prob_host->C, params, s);
+        if (prepared < 0) {
+            res->status = ACCSINK_ERR_CUDA;
+            return fail(ctx, ACCSINK_ERR_CUDA, "overlapped upload of C failed");
+        }
+        if (prepared == 0) CK(cudaMemcpyAsync(dC, prob_host->C, cbytes, cudaMemcpyHostToDevice, s));
     } else {
         float *dY = (float *)((char *)dC + align_up(xbytes, 256));
         CK(cudaMemcpyAsync(dC, prob_host->X, xbytes, cudaMemcpyHostToDevice, s));
@@ -1337,7 +1405,7 @@ int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
     CK(cudaMemcpyAsync(db, prob_host->b, (size_t)m * 8, cudaMemcpyHostToDevice, s));
     pd.a = da;
     pd.b = db;
-    rc = dense ? solve_device(ctx, &pd, params, s, df, dg, res)
+    rc = dense ? solve_device(ctx, &pd, params, s, df, dg, res, nullptr, prepared)
                : solve_points(ctx, &pd, params, s, df, dg, res);
     if (rc != ACCSINK_OK && rc != ACCSINK_ERR_MAXITER) { res->status = rc; return rc; }
     CK(cudaMemcpyAsync(f_out_host, df, (size_t)n * 8, cudaMemcpyDeviceToHost, s));

@@ -493,38 +493,47 @@ __global__ void k_transpose(const float *__restrict__ C, int64_t ldc, int n, int
 // tile order, grid-stride): 128-bit loads of the tile into shared memory
 // (4 per thread), then 128-bit stores of its transpose, each gathered from a
 // shared-memory column; the CTA's statistics go to statpart[4 blockIdx.x ..].
-// Entries of a stored float4 past n (the padding of a C^T row) are zero; a
-// row's columns past m (ldc > m) are loaded but neither counted nor stored.
+// Entries of a stored float4 past n (the padding of a C^T row) are zero; no
+// column past m is read.
 __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict__ C, int64_t ldc,
                                                          int n, int m,
                                                          float *__restrict__ CT, int64_t ldct,
-                                                         double *statpart)
+                                                         double *statpart, int r0, int r1)
 {
     constexpr int T = 64;
     __shared__ float tile[T][T + 1];
     const int tid = threadIdx.x;
     const int tr = tid >> 4, tc = tid & 15;       // 16 threads per 64-float row segment
     const int tiles_j = (m + T - 1) / T;
-    const int64_t ntiles = (int64_t)((n + T - 1) / T) * tiles_j;
+    const int64_t ntiles = (int64_t)((r1 - r0 + T - 1) / T) * tiles_j;
     float mx = -FLT_MAX, mn = FLT_MAX, ab = 0.0f;
     int bad = 0;
     // tile t's four float4 of this thread (zeros outside C), and the
     // statistics of the ones inside
     auto load = [&](int64_t t, float4 (&v)[4]) {
-        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+        const int i0 = r0 + (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = i0 + tr + 16 * r, j = j0 + 4 * tc;
-            v[r] = (i < n && j < m) ? ld_stream4(C + (int64_t)i * ldc + j)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float *src = C + (int64_t)i * ldc + j;
+            if (i < r1 && j + 3 < m) {
+                v[r] = ld_stream4(src);
+            } else if (i < r1 && j < m) {
+                // a row's last m % 4 columns: no read past column m - 1 (the
+                // last row of C may end there)
+                v[r] = make_float4(ld_stream1(src), j + 1 < m ? ld_stream1(src + 1) : 0.f,
+                                   j + 2 < m ? ld_stream1(src + 2) : 0.f, 0.f);
+            } else {
+                v[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
     };
     auto visit = [&](int64_t t, const float4 (&v)[4]) {
-        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+        const int i0 = r0 + (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int i = i0 + tr + 16 * r, j = j0 + 4 * tc;
-            if (i < n && j < m) {
+            if (i < r1 && j < m) {
                 const float e[4] = {v[r].x, v[r].y, v[r].z, v[r].w};
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
@@ -541,7 +550,7 @@ __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict
     int64_t t = blockIdx.x;
     if (t < ntiles) load(t, v);
     for (; t < ntiles; t += gridDim.x) {
-        const int i0 = (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
+        const int i0 = r0 + (int)(t / tiles_j) * T, j0 = (int)(t % tiles_j) * T;
         visit(t, v);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -594,11 +603,14 @@ __global__ void __launch_bounds__(256) k_transpose_stats(const float *__restrict
 }
 
 cudaError_t launch_transpose_stats(const CostView &cv, float *CT, int64_t ldct, const Work &w,
-                                   int grid, cudaStream_t s)
+                                   int grid, cudaStream_t s, int r0, int r1, int part0)
 {
     if (!cv.vec) return cudaErrorInvalidValue;
+    if (r1 < 0) r1 = cv.n;
+    if (r0 % 64 != 0 || r1 < r0 || r1 > cv.n || (r1 % 64 != 0 && r1 != cv.n))
+        return cudaErrorInvalidValue;
     k_transpose_stats<<<std::max(1, grid), 256, 0, s>>>(cv.C, cv.ldc, cv.n, cv.m, CT, ldct,
-                                                        w.statpart);
+                                                        w.statpart + 4 * (int64_t)part0, r0, r1);
     return cudaGetLastError();
 }
 

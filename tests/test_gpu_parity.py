@@ -311,6 +311,23 @@ def test_solve_host_matches_device_solve(ctx):
     np.testing.assert_array_equal(g1, g2)
 
 
+@pytest.mark.parametrize("n,m", [(1000, 1004), (130, 64), (129, 8)])
+def test_overlapped_host_upload_matches_device_solve(ctx, n, m):
+    """A cost with 16-byte rows from host memory is uploaded in row chunks
+    while the transposed copy and the statistics of the chunks already landed
+    are written (the last chunk ragged); the solve equals the device solve bit
+    for bit."""
+    pr = W.gmm_stored_cost_problem(seed=16, n=n, m=m, eps=1e-2)
+    f1, g1, r1 = gpu_solve(ctx, pr["C"], pr["a"], pr["b"], 1e-2, 1e-6, B.ACC)
+    f2 = np.empty(n)
+    g2 = np.empty(m)
+    r2 = ctx.accsink_solve_host(pr["C"], pr["a"], pr["b"], B.default_params(eps=1e-2), f2, g2)
+    assert r2.status == 0 and r2.sinkhorn_steps == r1["sinkhorn_steps"]
+    assert r2.cost_max == r1["cost_max"]
+    np.testing.assert_array_equal(f1, f2)
+    np.testing.assert_array_equal(g1, g2)
+
+
 # ------------------------------------------------------------- errors ----
 
 def test_fused_transpose_statistics_ignore_row_padding(ctx):
