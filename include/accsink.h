@@ -185,8 +185,12 @@ int accsink_solve(accsink_ctx *ctx, const accsink_problem *prob,
 /* Same solve (any cost kind) with every problem pointer and f_out/g_out in
  * HOST memory:
  * the library copies the inputs to its workspace, solves, and copies the
- * potentials back, all on `stream`. Host buffers may be pageable or pinned
- * (pinned copies are faster). */
+ * potentials back, ordered on `stream`. A dense C with rows of a multiple of
+ * 4 floats is copied in row chunks on a stream of the context, each chunk
+ * transposed as soon as it has landed (the results are those of
+ * accsink_solve bit for bit). Host buffers may be pageable or pinned (pinned
+ * copies are faster and overlap with the device work). The call returns when
+ * the potentials are in f_out/g_out. */
 int accsink_solve_host(accsink_ctx *ctx, const accsink_problem *prob_host,
                        const accsink_params *params, void *stream,
                        double *f_out_host, double *g_out_host,
