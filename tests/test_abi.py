@@ -61,8 +61,9 @@ int main(void) {
          offsetof(accsink_params, max_sinkhorn_steps), offsetof(accsink_params, history));
   printf("%zu %zu %zu\n", sizeof(accsink_result), offsetof(accsink_result, marginal_l1),
          offsetof(accsink_result, gpu_ms));
-  printf("%zu %zu %zu\n", sizeof(accsink_batch_config),
-         offsetof(accsink_batch_config, row_tile_elems), offsetof(accsink_batch_config, ctas_per_sm));
+  printf("%zu %zu %zu %zu\n", sizeof(accsink_batch_config),
+         offsetof(accsink_batch_config, row_tile_elems), offsetof(accsink_batch_config, ctas_per_sm),
+         offsetof(accsink_batch_config, dense_solo_min_nm));
   printf("%zu %zu %zu\n", sizeof(accsink_server_stats),
          offsetof(accsink_server_stats, resident_bytes), offsetof(accsink_server_stats, busy_ms));
   printf("%zu %zu %zu %zu %zu\n", sizeof(accsink_state), offsetof(accsink_state, eps),
@@ -86,7 +87,8 @@ int main(void) {
                  B.accsink_result.gpu_ms.offset]
     c = [int(v) for v in lines[3].split()]
     assert c == [ct.sizeof(B.accsink_batch_config), B.accsink_batch_config.row_tile_elems.offset,
-                 B.accsink_batch_config.ctas_per_sm.offset]
+                 B.accsink_batch_config.ctas_per_sm.offset,
+                 B.accsink_batch_config.dense_solo_min_nm.offset]
     v = [int(x) for x in lines[4].split()]
     assert v == [ct.sizeof(B.accsink_server_stats), B.accsink_server_stats.resident_bytes.offset,
                  B.accsink_server_stats.busy_ms.offset]
